@@ -1,0 +1,1077 @@
+// pmg_oracle.cpp -- TEST INFRASTRUCTURE ONLY.
+//
+// A plain, slow, FP64 CPU restatement of the implicit P-multigrid flux
+// reconstruction solver of Wang & Yu (arXiv 1908.03972) for the 2D Euler
+// equations with Weiss-Smith/Turkel local preconditioning.  It exists only to
+// check the CUDA library: tests, the smoke check and the CPU-baseline leg of
+// the benchmark may load it; the product path never does.  It shares no code,
+// header, table or constant generator with the CUDA library.
+//
+// Every function cites the part of the paper it follows.  Where the paper is
+// silent the reading taken is stated next to the code.  The residual is a
+// template over the scalar type so that the block Jacobians can be taken by
+// complex-step differentiation (exact to rounding, neighbours frozen).
+//
+// Layout conventions (shared with the library only through the C interface):
+//   solution point (i, j) of a degree-P element has index j*(P+1)+i, i along xi;
+//   a state array is variable-major: q[(v*E + e)*N + pt], v in (p, u, v, T);
+//   an element block row/column index is v*N + pt;
+//   faces: 0 eta=-1, 1 xi=+1, 2 eta=+1, 3 xi=-1; face points are ordered by the
+//   tangential reference coordinate increasing.
+//   nbr[(e*4+f)*3 + {0,1,2}] = (neighbour element, neighbour face, reversed?).
+//   Element geometry: (Ng+1)^2 Lagrange nodes at equispaced reference
+//   positions, index b*(Ng+1)+a, a along xi; nodes[(e*(Ng+1)^2 + node)*2 + {x,y}].
+#include <complex>
+#include <vector>
+#include <cmath>
+#include <cstring>
+#include <cstdio>
+
+typedef std::complex<double> cplx;
+
+// ---------------------------------------------------------------------------
+// Scalar helpers that keep the residual analytic for the complex step.
+// ---------------------------------------------------------------------------
+static inline double re(double x) { return x; }
+static inline double re(const cplx& x) { return x.real(); }
+template <class S> static inline S cs_abs(const S& x) { return re(x) < 0 ? -x : x; }
+template <class S> static inline S cs_min(const S& a, const S& b) { return re(a) <= re(b) ? a : b; }
+template <class S> static inline S cs_max(const S& a, const S& b) { return re(a) >= re(b) ? a : b; }
+static inline double cs_sqrt(double x) { return std::sqrt(x); }
+static inline cplx cs_sqrt(const cplx& x) { return std::sqrt(x); }
+
+// ---------------------------------------------------------------------------
+// 1D reference element: Gauss-Legendre points, Lagrange basis, the DG
+// (Radau) correction functions.  Section 2.3: tensor products of 1D
+// correction polynomials on quadrilaterals.  Reading: solution points are the
+// Gauss-Legendre points and g is the Radau polynomial that recovers nodal DG.
+// ---------------------------------------------------------------------------
+static void legendre(int n, double x, double* L, double* dL) {
+  // Three-term recurrence (k+1) L_{k+1} = (2k+1) x L_k - k L_{k-1};
+  // derivative from (1-x^2) L_n' = n (L_{n-1} - x L_n), with the endpoint value
+  // L_n'(+-1) = (+-1)^{n-1} n(n+1)/2.
+  double l0 = 1.0, l1 = x;
+  if (n == 0) { *L = 1.0; *dL = 0.0; return; }
+  for (int k = 1; k < n; ++k) {
+    double l2 = ((2.0 * k + 1.0) * x * l1 - k * l0) / (k + 1.0);
+    l0 = l1; l1 = l2;
+  }
+  *L = l1;
+  if (std::fabs(std::fabs(x) - 1.0) < 1e-15) {
+    double s = (x > 0) ? 1.0 : ((n - 1) % 2 == 0 ? 1.0 : -1.0);
+    *dL = s * n * (n + 1) / 2.0;
+  } else {
+    *dL = n * (l0 - x * l1) / (1.0 - x * x);
+  }
+}
+
+struct Basis1D {
+  int P;
+  std::vector<double> x, w;        // P+1 Gauss-Legendre points, weights
+  std::vector<double> D;           // D[i*(P+1)+k] = l_k'(x_i)
+  std::vector<double> lm, lp;      // l_k(-1), l_k(+1)
+  std::vector<double> gL, gR;      // g_L'(x_i), g_R'(x_i)
+};
+
+static double lagrange(const std::vector<double>& x, int k, double t) {
+  double v = 1.0;
+  for (size_t m = 0; m < x.size(); ++m)
+    if ((int)m != k) v *= (t - x[m]) / (x[k] - x[m]);
+  return v;
+}
+
+static double lagrange_deriv(const std::vector<double>& x, int k, double t) {
+  // d/dt of prod_{m!=k} (t-x_m)/(x_k-x_m), by the product rule.
+  double s = 0.0;
+  for (size_t j = 0; j < x.size(); ++j) {
+    if ((int)j == k) continue;
+    double term = 1.0 / (x[k] - x[j]);
+    for (size_t m = 0; m < x.size(); ++m)
+      if ((int)m != k && m != j) term *= (t - x[m]) / (x[k] - x[m]);
+    s += term;
+  }
+  return s;
+}
+
+static Basis1D make_basis(int P) {
+  Basis1D b;
+  b.P = P;
+  int n = P + 1;
+  b.x.resize(n); b.w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    // Newton on L_n from the Chebyshev-like initial guess, ascending order.
+    double t = -std::cos(M_PI * (4.0 * i + 3.0) / (4.0 * n + 2.0));
+    for (int it = 0; it < 100; ++it) {
+      double L, dL;
+      legendre(n, t, &L, &dL);
+      double dt = L / dL;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    double L, dL;
+    legendre(n, t, &L, &dL);
+    b.x[i] = t;
+    b.w[i] = 2.0 / ((1.0 - t * t) * dL * dL);
+  }
+  b.D.resize(n * n);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) b.D[i * n + k] = lagrange_deriv(b.x, k, b.x[i]);
+  b.lm.resize(n); b.lp.resize(n);
+  for (int k = 0; k < n; ++k) { b.lm[k] = lagrange(b.x, k, -1.0); b.lp[k] = lagrange(b.x, k, 1.0); }
+  // g_L = (-1)^P/2 (L_P - L_{P+1}), g_R = 1/2 (L_P + L_{P+1}): degree P+1,
+  // g_L(-1)=1, g_L(1)=0, g_R mirrored, both orthogonal to degree P-1.
+  b.gL.resize(n); b.gR.resize(n);
+  double sgn = (P % 2 == 0) ? 1.0 : -1.0;
+  for (int i = 0; i < n; ++i) {
+    double L0, dL0, L1, dL1;
+    legendre(P, b.x[i], &L0, &dL0);
+    legendre(P + 1, b.x[i], &L1, &dL1);
+    b.gL[i] = 0.5 * sgn * (dL0 - dL1);
+    b.gR[i] = 0.5 * (dL0 + dL1);
+  }
+  return b;
+}
+
+// Dense real Gaussian elimination with partial pivoting (used for the small
+// mass-matrix solves and for the block LU of Section 2.4).
+static bool lu_factor(int n, double* A, int* piv) {
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    double best = std::fabs(A[k * n + k]);
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(A[i * n + k]) > best) { best = std::fabs(A[i * n + k]); p = i; }
+    piv[k] = p;
+    if (best == 0.0) return false;
+    if (p != k)
+      for (int j = 0; j < n; ++j) std::swap(A[k * n + j], A[p * n + j]);
+    for (int i = k + 1; i < n; ++i) {
+      double l = A[i * n + k] / A[k * n + k];
+      A[i * n + k] = l;
+      for (int j = k + 1; j < n; ++j) A[i * n + j] -= l * A[k * n + j];
+    }
+  }
+  return true;
+}
+
+static void lu_solve(int n, const double* LU, const int* piv, double* b) {
+  for (int k = 0; k < n; ++k) std::swap(b[k], b[piv[k]]);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j) b[i] -= LU[i * n + j] * b[j];
+  for (int i = n - 1; i >= 0; --i) {
+    for (int j = i + 1; j < n; ++j) b[i] -= LU[i * n + j] * b[j];
+    b[i] /= LU[i * n + i];
+  }
+}
+
+// Restriction = L2 projection onto degree Pc in reference coordinates (the
+// projection operator of Section 3), built from the mass matrix with the fine
+// Gauss quadrature, which integrates degree Pc+Pf exactly.
+static std::vector<double> make_restriction(const Basis1D& f, const Basis1D& c) {
+  int nf = f.P + 1, nc = c.P + 1;
+  std::vector<double> Mc(nc * nc, 0.0), B(nc * nf, 0.0);
+  for (int i = 0; i < nc; ++i)
+    for (int j = 0; j < nc; ++j)
+      for (int q = 0; q < nf; ++q)
+        Mc[i * nc + j] += f.w[q] * lagrange(c.x, i, f.x[q]) * lagrange(c.x, j, f.x[q]);
+  for (int i = 0; i < nc; ++i)
+    for (int q = 0; q < nf; ++q) B[i * nf + q] = f.w[q] * lagrange(c.x, i, f.x[q]);
+  std::vector<int> piv(nc);
+  lu_factor(nc, Mc.data(), piv.data());
+  std::vector<double> R(nc * nf);
+  std::vector<double> col(nc);
+  for (int q = 0; q < nf; ++q) {
+    for (int i = 0; i < nc; ++i) col[i] = B[i * nf + q];
+    lu_solve(nc, Mc.data(), piv.data(), col.data());
+    for (int i = 0; i < nc; ++i) R[i * nf + q] = col[i];
+  }
+  return R;
+}
+
+// Prolongation = evaluation of the coarse Lagrange polynomial at the fine points.
+static std::vector<double> make_prolongation(const Basis1D& f, const Basis1D& c) {
+  int nf = f.P + 1, nc = c.P + 1;
+  std::vector<double> I(nf * nc);
+  for (int i = 0; i < nf; ++i)
+    for (int k = 0; k < nc; ++k) I[i * nc + k] = lagrange(c.x, k, f.x[i]);
+  return I;
+}
+
+// ---------------------------------------------------------------------------
+// Thermodynamics and preconditioning, Sections 2.1-2.2.  Nondimensional ideal
+// gas with R = 1: rho = p/T, E = T/(gamma-1) + |v|^2/2, H = E + p/rho,
+// c^2 = gamma T, Cp = gamma/(gamma-1).  Working variables q_p = (p, u, v, T).
+// ---------------------------------------------------------------------------
+struct Phys {
+  double gamma, Ma_inf, kappa;
+  int cutoff;  // 1: eps = min(1, max(kappa Ma_inf, Ma)); 0: eps = min(1, Ma)
+};
+
+template <class S> static void cons_from_prim(const S q[4], const Phys& ph, S qc[4]) {
+  S rho = q[0] / q[3];
+  S E = q[3] / (ph.gamma - 1.0) + 0.5 * (q[1] * q[1] + q[2] * q[2]);
+  qc[0] = rho; qc[1] = rho * q[1]; qc[2] = rho * q[2]; qc[3] = rho * E;
+}
+
+static void prim_from_cons(const double qc[4], const Phys& ph, double q[4]) {
+  double rho = qc[0], u = qc[1] / rho, v = qc[2] / rho;
+  double p = (ph.gamma - 1.0) * (qc[3] - 0.5 * rho * (u * u + v * v));
+  q[0] = p; q[1] = u; q[2] = v; q[3] = p / rho;
+}
+
+// M = dq_c/dq_p written out (Section 2.2).
+template <class S> static void M_matrix(const S q[4], const Phys& ph, S M[4][4]) {
+  S p = q[0], u = q[1], v = q[2], T = q[3];
+  S rho = p / T, rp = 1.0 / T, rT = -rho / T;
+  double Cp = ph.gamma / (ph.gamma - 1.0);
+  S H = Cp * T + 0.5 * (u * u + v * v);
+  M[0][0] = rp;           M[0][1] = 0.0;     M[0][2] = 0.0;     M[0][3] = rT;
+  M[1][0] = rp * u;       M[1][1] = rho;     M[1][2] = 0.0;     M[1][3] = rT * u;
+  M[2][0] = rp * v;       M[2][1] = 0.0;     M[2][2] = rho;     M[2][3] = rT * v;
+  M[3][0] = rp * H - 1.0; M[3][1] = rho * u; M[3][2] = rho * v; M[3][3] = rT * H + rho * Cp;
+}
+
+// eps of eq. eps_nonmove; with the cut-off off, eps is the local Mach number
+// (Section 4.1).  Reading: no lower floor.
+template <class S> static S precond_eps(const S q[4], const Phys& ph) {
+  S Ma = cs_sqrt((q[1] * q[1] + q[2] * q[2]) / (ph.gamma * q[3]));
+  S e = ph.cutoff ? cs_max(S(ph.kappa * ph.Ma_inf), Ma) : Ma;
+  return cs_min(S(1.0), e);
+}
+
+// Gamma of eq. preconditioning (2D rows), Theta of eq. theta, U_r = eps c.
+template <class S> static void Gamma_matrix(const S q[4], const S& eps, const Phys& ph, S G[4][4]) {
+  S p = q[0], u = q[1], v = q[2], T = q[3];
+  S rho = p / T, rT = -rho / T;
+  double Cp = ph.gamma / (ph.gamma - 1.0);
+  S H = Cp * T + 0.5 * (u * u + v * v);
+  S c2 = ph.gamma * T;
+  S Ur2 = eps * eps * c2;
+  S Th = 1.0 / Ur2 - rT / (rho * Cp);
+  G[0][0] = Th;           G[0][1] = 0.0;     G[0][2] = 0.0;     G[0][3] = rT;
+  G[1][0] = Th * u;       G[1][1] = rho;     G[1][2] = 0.0;     G[1][3] = rT * u;
+  G[2][0] = Th * v;       G[2][1] = 0.0;     G[2][2] = rho;     G[2][3] = rT * v;
+  G[3][0] = Th * H - 1.0; G[3][1] = rho * u; G[3][2] = rho * v; G[3][3] = rT * H + rho * Cp;
+}
+
+// Inviscid flux through a (possibly unnormalised) direction (nx, ny):
+// (rho u_n, rho u_n u + p nx, rho u_n v + p ny, rho u_n H), Section 2.1.
+template <class S> static void euler_flux_n(const S q[4], double nx, double ny, const Phys& ph, S f[4]) {
+  S p = q[0], u = q[1], v = q[2], T = q[3];
+  S rho = p / T;
+  double Cp = ph.gamma / (ph.gamma - 1.0);
+  S H = Cp * T + 0.5 * (u * u + v * v);
+  S un = u * nx + v * ny;
+  f[0] = rho * un;
+  f[1] = rho * un * u + p * nx;
+  f[2] = rho * un * v + p * ny;
+  f[3] = rho * un * H;
+}
+
+// A_n = d f_n / d q_p, differentiated by hand from euler_flux_n.
+template <class S> static void flux_jacobian_n(const S q[4], double nx, double ny, const Phys& ph, S A[4][4]) {
+  S p = q[0], u = q[1], v = q[2], T = q[3];
+  S rho = p / T, rp = 1.0 / T, rT = -rho / T;
+  double Cp = ph.gamma / (ph.gamma - 1.0);
+  S H = Cp * T + 0.5 * (u * u + v * v);
+  S un = u * nx + v * ny;
+  A[0][0] = rp * un;          A[0][1] = rho * nx;                A[0][2] = rho * ny;                A[0][3] = rT * un;
+  A[1][0] = rp * un * u + nx; A[1][1] = rho * un + rho * u * nx; A[1][2] = rho * u * ny;            A[1][3] = rT * un * u;
+  A[2][0] = rp * un * v + ny; A[2][1] = rho * v * nx;            A[2][2] = rho * un + rho * v * ny; A[2][3] = rT * un * v;
+  A[3][0] = rp * un * H;      A[3][1] = rho * nx * H + rho * un * u;
+  A[3][2] = rho * ny * H + rho * un * v;                         A[3][3] = rT * un * H + rho * un * Cp;
+}
+
+// Solve G X = A for the 4x4 X by elimination with partial pivoting on the real part.
+template <class S> static void solve4(S G[4][4], S A[4][4], S X[4][4]) {
+  S a[4][8];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) { a[i][j] = G[i][j]; a[i][4 + j] = A[i][j]; }
+  for (int k = 0; k < 4; ++k) {
+    int p = k;
+    for (int i = k + 1; i < 4; ++i)
+      if (std::fabs(re(a[i][k])) > std::fabs(re(a[p][k]))) p = i;
+    if (p != k) for (int j = 0; j < 8; ++j) std::swap(a[k][j], a[p][j]);
+    for (int i = k + 1; i < 4; ++i) {
+      S l = a[i][k] / a[k][k];
+      for (int j = k; j < 8; ++j) a[i][j] -= l * a[k][j];
+    }
+  }
+  for (int c = 0; c < 4; ++c)
+    for (int i = 3; i >= 0; --i) {
+      S s = a[i][4 + c];
+      for (int j = i + 1; j < 4; ++j) s -= a[i][j] * X[j][c];
+      X[i][c] = s / a[i][i];
+    }
+}
+
+// Preconditioned Roe flux, eq. invis_com: the central average minus
+// Gamma R|Lambda|R^-1 (q_p^+ - q_p^-)/2, with every matrix evaluated at the
+// arithmetic mean of the two primitive states (reading of "averaged values";
+// no entropy fix).  |Gamma^-1 A_n| is formed with Sylvester's formula from the
+// three distinct eigenvalues u_n, u_n' +- c' of eq. eigenvalues_para, which
+// needs no eigenvectors.  (Sx, Sy) is the area-scaled normal from - to +; the
+// result is the flux through that area.
+template <class S>
+static void roe_flux(const S qm[4], const S qp[4], double Sx, double Sy, const Phys& ph, S out[4]) {
+  double dS = std::sqrt(Sx * Sx + Sy * Sy);
+  double nx = Sx / dS, ny = Sy / dS;
+  S qa[4];
+  for (int k = 0; k < 4; ++k) qa[k] = 0.5 * (qm[k] + qp[k]);
+  S eps = precond_eps(qa, ph);
+  S G[4][4], A[4][4], Mt[4][4];
+  Gamma_matrix(qa, eps, ph, G);
+  flux_jacobian_n(qa, nx, ny, ph, A);
+  solve4(G, A, Mt);
+  // eigenvalues, eq. eigenvalues_para
+  S p = qa[0], T = qa[3];
+  S rho = p / T, rp = 1.0 / T, rT = -rho / T;
+  double Cp = ph.gamma / (ph.gamma - 1.0);
+  S c = cs_sqrt(ph.gamma * T);
+  S Ur = eps * c;
+  S un = qa[1] * nx + qa[2] * ny;
+  S beta = rp + rT / (rho * Cp);
+  S alpha = 0.5 * (1.0 - beta * Ur * Ur);
+  S cpr = cs_sqrt(alpha * alpha * un * un + Ur * Ur);
+  S unp = un * (1.0 - alpha);
+  S lam[3] = {un, unp + cpr, unp - cpr};
+  S absM[4][4];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) absM[i][j] = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    S Pk[4][4];
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) Pk[i][j] = (i == j) ? S(1.0) : S(0.0);
+    for (int jj = 0; jj < 3; ++jj) {
+      if (jj == k) continue;
+      S fac[4][4], tmp[4][4];
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j)
+          fac[i][j] = (Mt[i][j] - (i == j ? lam[jj] : S(0.0))) / (lam[k] - lam[jj]);
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+          S s = 0.0;
+          for (int m = 0; m < 4; ++m) s += Pk[i][m] * fac[m][j];
+          tmp[i][j] = s;
+        }
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) Pk[i][j] = tmp[i][j];
+    }
+    S al = cs_abs(lam[k]);
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) absM[i][j] += al * Pk[i][j];
+  }
+  S dq[4], t1[4], diss[4];
+  for (int k = 0; k < 4; ++k) dq[k] = qp[k] - qm[k];
+  for (int i = 0; i < 4; ++i) {
+    S s = 0.0;
+    for (int j = 0; j < 4; ++j) s += absM[i][j] * dq[j];
+    t1[i] = s;
+  }
+  for (int i = 0; i < 4; ++i) {
+    S s = 0.0;
+    for (int j = 0; j < 4; ++j) s += G[i][j] * t1[j];
+    diss[i] = s;
+  }
+  S fm[4], fp[4];
+  euler_flux_n(qm, nx, ny, ph, fm);
+  euler_flux_n(qp, nx, ny, ph, fp);
+  for (int k = 0; k < 4; ++k) out[k] = (0.5 * (fm[k] + fp[k]) - 0.5 * diss[k]) * dS;
+}
+
+// ---------------------------------------------------------------------------
+// Geometry: Lagrange mapping of order Ng on equispaced reference nodes.
+// Reading: every P-level evaluates the exact mapping at its own points.
+// ---------------------------------------------------------------------------
+struct LevelGeom {
+  int P, N;
+  Basis1D b;
+  std::vector<double> met;   // per (e, pt): x_xi, x_eta, y_xi, y_eta, |J|
+  std::vector<double> fS;    // per (e, face, k): outward area-scaled normal (Sx, Sy)
+};
+
+static void map_derivs(int Ng, const double* xn, double xi, double eta,
+                       double* x_xi, double* x_eta, double* y_xi, double* y_eta) {
+  std::vector<double> r(Ng + 1);
+  for (int a = 0; a <= Ng; ++a) r[a] = -1.0 + 2.0 * a / (Ng > 0 ? Ng : 1);
+  *x_xi = *x_eta = *y_xi = *y_eta = 0.0;
+  for (int b = 0; b <= Ng; ++b)
+    for (int a = 0; a <= Ng; ++a) {
+      double la = lagrange(r, a, xi), lb = lagrange(r, b, eta);
+      double da = lagrange_deriv(r, a, xi), db = lagrange_deriv(r, b, eta);
+      const double* X = xn + (b * (Ng + 1) + a) * 2;
+      *x_xi += da * lb * X[0]; *x_eta += la * db * X[0];
+      *y_xi += da * lb * X[1]; *y_eta += la * db * X[1];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Solver context
+// ---------------------------------------------------------------------------
+struct OrcConfig {
+  int n_levels;
+  int P[8];
+  int n_smooth[8];
+  double gamma, Ma_inf, kappa;
+  int cutoff;
+  int esdirk_stages;      // 4 = ESDIRK3 (the scheme implemented)
+  double dtau_init, dtau_max, tol;
+  int refresh_every, max_pseudo;
+};
+
+struct Level {
+  LevelGeom g;
+  std::vector<double> q, qb, S, F;        // state, restricted state, forcing, residual
+  std::vector<double> lu;                 // per element n*n LU factors
+  std::vector<int> piv;
+};
+
+struct Oracle {
+  OrcConfig cfg;
+  Phys ph;
+  int E, Ng;
+  std::vector<double> nodes;
+  std::vector<int> nbr;
+  std::vector<Level> lev;
+  std::vector<std::vector<double>> Rm, Pm;   // restriction / prolongation 1D, level l -> l+1
+  // stage data (finest level)
+  std::vector<double> src;                   // (q_c^n + dt sum a_ij R^j)/(omega dt)
+  double omega_dt;
+  double dtau;
+  // ESDIRK3 tableau
+  double A[6][6], b[6], c[6];
+  int s;
+};
+
+static void build_level_geom(Oracle* o, int P, LevelGeom* g) {
+  g->P = P; g->N = (P + 1) * (P + 1);
+  g->b = make_basis(P);
+  int n1 = P + 1, E = o->E, Ng = o->Ng, nn = (Ng + 1) * (Ng + 1);
+  g->met.assign((size_t)E * g->N * 5, 0.0);
+  g->fS.assign((size_t)E * 4 * n1 * 2, 0.0);
+  for (int e = 0; e < E; ++e) {
+    const double* xn = &o->nodes[(size_t)e * nn * 2];
+    for (int j = 0; j < n1; ++j)
+      for (int i = 0; i < n1; ++i) {
+        double a, bb, c, d;
+        map_derivs(Ng, xn, g->b.x[i], g->b.x[j], &a, &bb, &c, &d);
+        double* m = &g->met[((size_t)e * g->N + j * n1 + i) * 5];
+        m[0] = a; m[1] = bb; m[2] = c; m[3] = d; m[4] = a * d - bb * c;
+      }
+    for (int f = 0; f < 4; ++f)
+      for (int k = 0; k < n1; ++k) {
+        double xi, eta;
+        if (f == 0) { xi = g->b.x[k]; eta = -1.0; }
+        else if (f == 1) { xi = 1.0; eta = g->b.x[k]; }
+        else if (f == 2) { xi = g->b.x[k]; eta = 1.0; }
+        else { xi = -1.0; eta = g->b.x[k]; }
+        double x_xi, x_eta, y_xi, y_eta;
+        map_derivs(Ng, xn, xi, eta, &x_xi, &x_eta, &y_xi, &y_eta);
+        double Sx, Sy;
+        if (f == 0) { Sx = y_xi; Sy = -x_xi; }          // -(grad eta)|J|
+        else if (f == 1) { Sx = y_eta; Sy = -x_eta; }   // +(grad xi)|J|
+        else if (f == 2) { Sx = -y_xi; Sy = x_xi; }     // +(grad eta)|J|
+        else { Sx = -y_eta; Sy = x_eta; }               // -(grad xi)|J|
+        double* s = &g->fS[(((size_t)e * 4 + f) * n1 + k) * 2];
+        s[0] = Sx; s[1] = Sy;
+      }
+  }
+}
+
+// Point index along the line normal to face f through face point k, at
+// position m along the normal direction.
+static inline int line_pt(int P, int f, int k, int m) {
+  int n1 = P + 1;
+  if (f == 0 || f == 2) return m * n1 + k;   // i = k, j = m
+  return k * n1 + m;                          // j = k, i = m
+}
+
+// Trace of a state (one element, variable-major with stride N) at face point
+// (f, k): extrapolation of the solution polynomial along the normal line.
+template <class S>
+static void trace_state(const Basis1D& b, const S* qe, int N, int f, int k, S out[4]) {
+  int n1 = b.P + 1;
+  const std::vector<double>& l = (f == 1 || f == 2) ? b.lp : b.lm;
+  for (int v = 0; v < 4; ++v) {
+    S s = 0.0;
+    for (int m = 0; m < n1; ++m) s += l[m] * qe[v * N + line_pt(b.P, f, k, m)];
+    out[v] = s;
+  }
+}
+
+// Neighbour traces for every element face point from a real state array.
+static void neighbour_traces(const Oracle* o, const Level& L, const double* q, std::vector<double>& tr) {
+  int P = L.g.P, n1 = P + 1, N = L.g.N, E = o->E;
+  tr.assign((size_t)E * 4 * n1 * 4, 0.0);
+  std::vector<double> qe(4 * N);
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 4; ++f) {
+      int en = o->nbr[(e * 4 + f) * 3 + 0], fn = o->nbr[(e * 4 + f) * 3 + 1];
+      int rev = o->nbr[(e * 4 + f) * 3 + 2];
+      for (int v = 0; v < 4; ++v)
+        for (int p = 0; p < N; ++p) qe[v * N + p] = q[((size_t)v * E + en) * N + p];
+      for (int k = 0; k < n1; ++k) {
+        int kn = rev ? P - k : k;
+        double t[4];
+        trace_state(L.g.b, qe.data(), N, fn, kn, t);
+        for (int v = 0; v < 4; ++v) tr[(((size_t)e * 4 + f) * n1 + k) * 4 + v] = t[v];
+      }
+    }
+}
+
+// FR/CPR residual R = -div f of one element (Section 2.3, eq. eqn:FR_diff):
+// contravariant fluxes at solution points, Lagrange derivative, and the DG
+// correction of the jumps between the common and the local (extrapolated flux
+// polynomial) normal fluxes at the flux points.  Neighbour traces are frozen.
+template <class S>
+static void element_residual(const Oracle* o, const Level& L, int e, const S* qe,
+                             const double* ntr, S* Re) {
+  const Basis1D& b = L.g.b;
+  int P = b.P, n1 = P + 1, N = L.g.N;
+  const Phys& ph = o->ph;
+  std::vector<S> Ft(4 * N), Gt(4 * N);
+  for (int pt = 0; pt < N; ++pt) {
+    const double* m = &L.g.met[((size_t)e * N + pt) * 5];
+    S q[4] = {qe[0 * N + pt], qe[1 * N + pt], qe[2 * N + pt], qe[3 * N + pt]};
+    S fx[4], fy[4];
+    euler_flux_n(q, 1.0, 0.0, ph, fx);
+    euler_flux_n(q, 0.0, 1.0, ph, fy);
+    for (int v = 0; v < 4; ++v) {
+      Ft[v * N + pt] = m[3] * fx[v] - m[1] * fy[v];    //  y_eta f - x_eta g
+      Gt[v * N + pt] = -m[2] * fx[v] + m[0] * fy[v];   // -y_xi f + x_xi g
+    }
+  }
+  std::vector<S> acc(4 * N, S(0.0));
+  for (int v = 0; v < 4; ++v)
+    for (int j = 0; j < n1; ++j)
+      for (int i = 0; i < n1; ++i) {
+        S s = 0.0;
+        for (int m = 0; m < n1; ++m) s += b.D[i * n1 + m] * Ft[v * N + j * n1 + m];
+        for (int m = 0; m < n1; ++m) s += b.D[j * n1 + m] * Gt[v * N + m * n1 + i];
+        acc[v * N + j * n1 + i] = s;
+      }
+  for (int f = 0; f < 4; ++f)
+    for (int k = 0; k < n1; ++k) {
+      S qm[4], qp[4], fo[4];
+      trace_state(b, qe, N, f, k, qm);
+      for (int v = 0; v < 4; ++v) qp[v] = ntr[(((size_t)e * 4 + f) * n1 + k) * 4 + v];
+      const double* Sv = &L.g.fS[(((size_t)e * 4 + f) * n1 + k) * 2];
+      roe_flux(qm, qp, Sv[0], Sv[1], ph, fo);
+      double sg = (f == 1 || f == 2) ? 1.0 : -1.0;        // outward -> reference-direction
+      const std::vector<double>& l = (f == 1 || f == 2) ? b.lp : b.lm;
+      const std::vector<double>& gp = (f == 1 || f == 2) ? b.gR : b.gL;
+      for (int v = 0; v < 4; ++v) {
+        const std::vector<S>& Fl = (f == 1 || f == 3) ? Ft : Gt;
+        S loc = 0.0;
+        for (int m = 0; m < n1; ++m) loc += l[m] * Fl[v * N + line_pt(P, f, k, m)];
+        S jump = sg * fo[v] - loc;
+        for (int m = 0; m < n1; ++m) acc[v * N + line_pt(P, f, k, m)] += gp[m] * jump;
+      }
+    }
+  for (int v = 0; v < 4; ++v)
+    for (int pt = 0; pt < N; ++pt) {
+      double J = L.g.met[((size_t)e * N + pt) * 5 + 4];
+      Re[v * N + pt] = -acc[v * N + pt] / J;
+    }
+}
+
+static void full_residual(const Oracle* o, const Level& L, const double* q, double* R) {
+  int N = L.g.N, E = o->E;
+  std::vector<double> tr;
+  neighbour_traces(o, L, q, tr);
+  std::vector<double> qe(4 * N), Re(4 * N);
+  for (int e = 0; e < E; ++e) {
+    for (int v = 0; v < 4; ++v)
+      for (int p = 0; p < N; ++p) qe[v * N + p] = q[((size_t)v * E + e) * N + p];
+    element_residual<double>(o, L, e, qe.data(), tr.data(), Re.data());
+    for (int v = 0; v < 4; ++v)
+      for (int p = 0; p < N; ++p) R[((size_t)v * E + e) * N + p] = Re[v * N + p];
+  }
+}
+
+// Level system residual F_l(q) - S_l.  F follows eq. ESDIRK_primitive:
+// F = -q_c(q)/(omega dt) + R(q) + src.  On the finest level src is the stage
+// source; on coarser levels the state-independent source is dropped (reading:
+// it cancels exactly between F_l(q) and S_l = F_l(q^b) + P d).
+static void level_F(const Oracle* o, int l, const double* q, bool with_src, bool minus_S, double* F) {
+  const Level& L = o->lev[l];
+  int N = L.g.N, E = o->E;
+  size_t tot = (size_t)4 * E * N;
+  full_residual(o, L, q, F);
+  for (int e = 0; e < E; ++e)
+    for (int p = 0; p < N; ++p) {
+      double qq[4], qc[4];
+      for (int v = 0; v < 4; ++v) qq[v] = q[((size_t)v * E + e) * N + p];
+      cons_from_prim(qq, o->ph, qc);
+      for (int v = 0; v < 4; ++v) {
+        size_t id = ((size_t)v * E + e) * N + p;
+        F[id] += -qc[v] / o->omega_dt;
+        if (with_src) F[id] += o->src[id];
+      }
+    }
+  if (minus_S)
+    for (size_t i = 0; i < tot; ++i) F[i] -= L.S[i];
+}
+
+// Element block D_e = Gamma/dtau + M/(omega dt) - dR_e/dq_e
+// (eq. linearized_pseudo_transient_final, block diagonal of eq.
+// smoothing_element_jacobi).  dR_e/dq_e by complex step with neighbours frozen.
+static void element_block(const Oracle* o, const Level& L, int e, const double* q,
+                          const double* ntr, double dtau, double* Dm) {
+  int N = L.g.N, n = 4 * N, E = o->E;
+  const double h = 1e-30;
+  std::vector<cplx> qe(n), Re(n);
+  for (int col = 0; col < n; ++col) {
+    for (int v = 0; v < 4; ++v)
+      for (int p = 0; p < N; ++p) qe[v * N + p] = cplx(q[((size_t)v * E + e) * N + p], 0.0);
+    qe[col] += cplx(0.0, h);
+    element_residual<cplx>(o, L, e, qe.data(), ntr, Re.data());
+    for (int row = 0; row < n; ++row) Dm[row * n + col] = -Re[row].imag() / h;
+  }
+  for (int p = 0; p < N; ++p) {
+    double qq[4];
+    for (int v = 0; v < 4; ++v) qq[v] = q[((size_t)v * E + e) * N + p];
+    double eps = precond_eps(qq, o->ph);
+    double G[4][4], M[4][4];
+    Gamma_matrix(qq, eps, o->ph, G);
+    M_matrix(qq, o->ph, M);
+    for (int a = 0; a < 4; ++a)
+      for (int c = 0; c < 4; ++c)
+        Dm[(a * N + p) * n + (c * N + p)] += G[a][c] / dtau + M[a][c] / o->omega_dt;
+  }
+}
+
+static int refresh_level(Oracle* o, int l) {
+  Level& L = o->lev[l];
+  int N = L.g.N, n = 4 * N, E = o->E;
+  std::vector<double> tr;
+  neighbour_traces(o, L, L.q.data(), tr);
+  L.lu.assign((size_t)E * n * n, 0.0);
+  L.piv.assign((size_t)E * n, 0);
+  for (int e = 0; e < E; ++e) {
+    double* Dm = &L.lu[(size_t)e * n * n];
+    element_block(o, L, e, L.q.data(), tr.data(), o->dtau, Dm);
+    if (!lu_factor(n, Dm, &L.piv[(size_t)e * n])) return -4;
+  }
+  return 0;
+}
+
+// Element-Jacobi sweep, eq. smoothing_element_jacobi with alpha_r = 1.
+static void smooth(Oracle* o, int l, int nsweep) {
+  Level& L = o->lev[l];
+  int N = L.g.N, n = 4 * N, E = o->E;
+  std::vector<double> x(n);
+  L.F.resize((size_t)4 * E * N);
+  for (int s = 0; s < nsweep; ++s) {
+    level_F(o, l, L.q.data(), l == 0, l > 0, L.F.data());
+    for (int e = 0; e < E; ++e) {
+      for (int v = 0; v < 4; ++v)
+        for (int p = 0; p < N; ++p) x[v * N + p] = L.F[((size_t)v * E + e) * N + p];
+      lu_solve(n, &L.lu[(size_t)e * n * n], &L.piv[(size_t)e * n], x.data());
+      for (int v = 0; v < 4; ++v)
+        for (int p = 0; p < N; ++p) L.q[((size_t)v * E + e) * N + p] += x[v * N + p];
+    }
+  }
+}
+
+static void apply_tensor(const std::vector<double>& op, int nout, int nin, int E,
+                         const double* in, double* out) {
+  // out[v][e][(j,i)] = sum_{a,b} op[i][a] op[j][b] in[v][e][(b,a)]
+  int Nin = nin * nin, Nout = nout * nout;
+  for (int v = 0; v < 4; ++v)
+    for (int e = 0; e < E; ++e)
+      for (int j = 0; j < nout; ++j)
+        for (int i = 0; i < nout; ++i) {
+          double s = 0.0;
+          for (int bb = 0; bb < nin; ++bb)
+            for (int a = 0; a < nin; ++a)
+              s += op[i * nin + a] * op[j * nin + bb] * in[((size_t)v * E + e) * Nin + bb * nin + a];
+          out[((size_t)v * E + e) * Nout + j * nout + i] = s;
+        }
+}
+
+// One FAS V-cycle from level l down (Section 3): pre-smooth, defect,
+// restrict state and defect, coarse forcing, recurse, prolong the
+// correction, post-smooth.  The coarsest level smooths once.
+static int vcycle_level(Oracle* o, int l, bool refresh) {
+  Level& L = o->lev[l];
+  int E = o->E;
+  if (refresh) { int st = refresh_level(o, l); if (st) return st; }
+  smooth(o, l, o->cfg.n_smooth[l]);
+  if (l == o->cfg.n_levels - 1) return 0;
+  Level& C = o->lev[l + 1];
+  int Nf = L.g.N, Nc = C.g.N;
+  std::vector<double> d((size_t)4 * E * Nf);
+  level_F(o, l, L.q.data(), l == 0, l > 0, d.data());
+  for (auto& x : d) x = -x;                                   // d = S - F(q^a)
+  C.q.resize((size_t)4 * E * Nc);
+  apply_tensor(o->Rm[l], C.g.P + 1, L.g.P + 1, E, L.q.data(), C.q.data());
+  C.qb = C.q;
+  std::vector<double> Pd((size_t)4 * E * Nc), Fc((size_t)4 * E * Nc);
+  apply_tensor(o->Rm[l], C.g.P + 1, L.g.P + 1, E, d.data(), Pd.data());
+  level_F(o, l + 1, C.q.data(), false, false, Fc.data());
+  C.S.resize((size_t)4 * E * Nc);
+  for (size_t i = 0; i < C.S.size(); ++i) C.S[i] = Fc[i] + Pd[i];
+  int st = vcycle_level(o, l + 1, refresh);
+  if (st) return st;
+  std::vector<double> corr((size_t)4 * E * Nc), pc((size_t)4 * E * Nf);
+  for (size_t i = 0; i < corr.size(); ++i) corr[i] = C.q[i] - C.qb[i];
+  apply_tensor(o->Pm[l], L.g.P + 1, C.g.P + 1, E, corr.data(), pc.data());
+  for (size_t i = 0; i < pc.size(); ++i) L.q[i] += pc[i];
+  smooth(o, l, o->cfg.n_smooth[l]);
+  return 0;
+}
+
+static double l2norm(const std::vector<double>& x) {
+  double s = 0.0;
+  for (double v : x) s += v * v;
+  return std::sqrt(s);
+}
+
+// ESDIRK3 tableau (Section 2.4 cites Bijl et al. 2002, which prints nothing):
+// reading = the stiffly accurate, L-stable 4-stage third-order ESDIRK with
+// c = (0, 2g, 3/5, 1), a_ii = g, last row = b, derived here from the order
+// conditions.  g is the root in (0.4, 0.5) of g^3 - 3g^2 + 3g/2 - 1/6 = 0.
+static void esdirk3_tableau(double A[6][6], double b[6], double c[6]) {
+  double lo = 0.4, hi = 0.5;
+  auto fpoly = [](double g) { return g * g * g - 3 * g * g + 1.5 * g - 1.0 / 6.0; };
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if ((fpoly(lo) < 0) == (fpoly(mid) < 0)) lo = mid; else hi = mid;
+  }
+  double g = 0.5 * (lo + hi);
+  for (int i = 0; i < 6; ++i) { b[i] = c[i] = 0.0; for (int j = 0; j < 6; ++j) A[i][j] = 0.0; }
+  c[0] = 0.0; c[1] = 2 * g; c[2] = 0.6; c[3] = 1.0;
+  // b1..b3 from sum b = 1, sum b c = 1/2, sum b c^2 = 1/3 with b4 = g, c4 = 1.
+  double M3[9] = {1, 1, 1, c[0], c[1], c[2], c[0] * c[0], c[1] * c[1], c[2] * c[2]};
+  double r3[3] = {1 - g, 0.5 - g, 1.0 / 3.0 - g};
+  int piv[3];
+  lu_factor(3, M3, piv);
+  lu_solve(3, M3, piv, r3);
+  b[0] = r3[0]; b[1] = r3[1]; b[2] = r3[2]; b[3] = g;
+  A[1][0] = g; A[1][1] = g;
+  // sum_i b_i (A c)_i = 1/6 fixes a32:  b2 (2g^2) + b3 (2 g a32 + 0.6 g) + b4 (1/2) = 1/6
+  double a32 = (1.0 / 6.0 - b[1] * 2 * g * g - b[2] * 0.6 * g - b[3] * 0.5) / (b[2] * 2 * g);
+  A[2][1] = a32; A[2][2] = g; A[2][0] = c[2] - g - a32;
+  for (int j = 0; j < 4; ++j) A[3][j] = b[j];
+}
+
+extern "C" {
+
+int orc_basis(int P, double* x, double* w, double* D, double* lm, double* lp, double* gL, double* gR) {
+  Basis1D b = make_basis(P);
+  int n = P + 1;
+  for (int i = 0; i < n; ++i) {
+    x[i] = b.x[i]; w[i] = b.w[i]; lm[i] = b.lm[i]; lp[i] = b.lp[i]; gL[i] = b.gL[i]; gR[i] = b.gR[i];
+  }
+  for (int i = 0; i < n * n; ++i) D[i] = b.D[i];
+  return 0;
+}
+
+int orc_transfer(int Pf, int Pc, double* Rop, double* Pop) {
+  Basis1D f = make_basis(Pf), c = make_basis(Pc);
+  std::vector<double> R = make_restriction(f, c), I = make_prolongation(f, c);
+  memcpy(Rop, R.data(), sizeof(double) * R.size());
+  memcpy(Pop, I.data(), sizeof(double) * I.size());
+  return 0;
+}
+
+int orc_esdirk3(double* A, double* b, double* c) {
+  double AA[6][6], bb[6], cc[6];
+  esdirk3_tableau(AA, bb, cc);
+  for (int i = 0; i < 4; ++i) {
+    b[i] = bb[i]; c[i] = cc[i];
+    for (int j = 0; j < 4; ++j) A[i * 4 + j] = AA[i][j];
+  }
+  return 0;
+}
+
+// Pointwise physics, exposed for the pins.
+int orc_point_matrices(const double* q, double gamma, double Ma_inf, double kappa, int cutoff,
+                       double* M, double* G, double* eps_out) {
+  Phys ph = {gamma, Ma_inf, kappa, cutoff};
+  double MM[4][4], GG[4][4];
+  double e = precond_eps(q, ph);
+  M_matrix(q, ph, MM);
+  Gamma_matrix(q, e, ph, GG);
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) { M[i * 4 + j] = MM[i][j]; G[i * 4 + j] = GG[i][j]; }
+  *eps_out = e;
+  return 0;
+}
+
+int orc_flux(const double* q, double nx, double ny, double gamma, double* f, double* A) {
+  Phys ph = {gamma, 0.0, 1.0, 0};
+  euler_flux_n(q, nx, ny, ph, f);
+  double AA[4][4];
+  flux_jacobian_n(q, nx, ny, ph, AA);
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) A[i * 4 + j] = AA[i][j];
+  return 0;
+}
+
+// Complex-step derivative of the flux, to pin the hand-written Jacobian.
+int orc_flux_cs(const double* q, double nx, double ny, double gamma, double* A) {
+  Phys ph = {gamma, 0.0, 1.0, 0};
+  for (int c = 0; c < 4; ++c) {
+    cplx qq[4], f[4];
+    for (int v = 0; v < 4; ++v) qq[v] = cplx(q[v], v == c ? 1e-30 : 0.0);
+    euler_flux_n(qq, nx, ny, ph, f);
+    for (int v = 0; v < 4; ++v) A[v * 4 + c] = f[v].imag() / 1e-30;
+  }
+  return 0;
+}
+
+int orc_roe(const double* qm, const double* qp, double Sx, double Sy, double gamma, double Ma_inf,
+            double kappa, int cutoff, double* out) {
+  Phys ph = {gamma, Ma_inf, kappa, cutoff};
+  roe_flux(qm, qp, Sx, Sy, ph, out);
+  return 0;
+}
+
+int orc_cons_from_prim(const double* q, double gamma, double* qc) {
+  Phys ph = {gamma, 0.0, 1.0, 0};
+  cons_from_prim(q, ph, qc);
+  return 0;
+}
+
+int orc_prim_from_cons(const double* qc, double gamma, double* q) {
+  Phys ph = {gamma, 0.0, 1.0, 0};
+  prim_from_cons(qc, ph, q);
+  return 0;
+}
+
+void* orc_create(const OrcConfig* cfg, int E, int Ng, const double* nodes, const int* nbr) {
+  Oracle* o = new Oracle();
+  o->cfg = *cfg;
+  o->ph = {cfg->gamma, cfg->Ma_inf, cfg->kappa, cfg->cutoff};
+  o->E = E; o->Ng = Ng;
+  int nn = (Ng + 1) * (Ng + 1);
+  o->nodes.assign(nodes, nodes + (size_t)E * nn * 2);
+  o->nbr.assign(nbr, nbr + (size_t)E * 12);
+  o->lev.resize(cfg->n_levels);
+  for (int l = 0; l < cfg->n_levels; ++l) {
+    build_level_geom(o, cfg->P[l], &o->lev[l].g);
+    size_t tot = (size_t)4 * E * o->lev[l].g.N;
+    o->lev[l].q.assign(tot, 0.0);
+    o->lev[l].S.assign(tot, 0.0);
+  }
+  for (int l = 0; l + 1 < cfg->n_levels; ++l) {
+    o->Rm.push_back(make_restriction(o->lev[l].g.b, o->lev[l + 1].g.b));
+    o->Pm.push_back(make_prolongation(o->lev[l].g.b, o->lev[l + 1].g.b));
+  }
+  esdirk3_tableau(o->A, o->b, o->c);
+  o->s = 4;
+  o->omega_dt = 1.0;
+  o->dtau = cfg->dtau_init;
+  o->src.assign((size_t)4 * E * o->lev[0].g.N, 0.0);
+  return o;
+}
+
+void orc_destroy(void* h) { delete (Oracle*)h; }
+
+int orc_metrics(void* h, int level, double* met, double* fS) {
+  Oracle* o = (Oracle*)h;
+  const Level& L = o->lev[level];
+  memcpy(met, L.g.met.data(), sizeof(double) * L.g.met.size());
+  memcpy(fS, L.g.fS.data(), sizeof(double) * L.g.fS.size());
+  return 0;
+}
+
+// Physical coordinates of the solution points of a level, (E, N, 2).
+int orc_coords(void* h, int level, double* xy) {
+  Oracle* o = (Oracle*)h;
+  const Level& L = o->lev[level];
+  int P = L.g.P, n1 = P + 1, N = L.g.N, Ng = o->Ng, nn = (Ng + 1) * (Ng + 1);
+  std::vector<double> r(Ng + 1);
+  for (int a = 0; a <= Ng; ++a) r[a] = -1.0 + 2.0 * a / Ng;
+  for (int e = 0; e < o->E; ++e)
+    for (int j = 0; j < n1; ++j)
+      for (int i = 0; i < n1; ++i) {
+        double x = 0.0, y = 0.0;
+        for (int b = 0; b <= Ng; ++b)
+          for (int a = 0; a <= Ng; ++a) {
+            double phi = lagrange(r, a, L.g.b.x[i]) * lagrange(r, b, L.g.b.x[j]);
+            x += phi * o->nodes[((size_t)e * nn + b * (Ng + 1) + a) * 2 + 0];
+            y += phi * o->nodes[((size_t)e * nn + b * (Ng + 1) + a) * 2 + 1];
+          }
+        xy[((size_t)e * N + j * n1 + i) * 2 + 0] = x;
+        xy[((size_t)e * N + j * n1 + i) * 2 + 1] = y;
+      }
+  return 0;
+}
+
+int orc_residual(void* h, int level, const double* q, double* R) {
+  Oracle* o = (Oracle*)h;
+  full_residual(o, o->lev[level], q, R);
+  return 0;
+}
+
+// Sets the stage data used by the level-0 system: src and omega*dt.
+int orc_set_stage(void* h, const double* src, double omega_dt) {
+  Oracle* o = (Oracle*)h;
+  o->omega_dt = omega_dt;
+  memcpy(o->src.data(), src, sizeof(double) * o->src.size());
+  return 0;
+}
+
+// F_l(q) (with the stage source on level 0, without S).
+int orc_stage_F(void* h, int level, const double* q, double* F) {
+  Oracle* o = (Oracle*)h;
+  level_F(o, level, q, level == 0, false, F);
+  return 0;
+}
+
+// Full element blocks D_e (row-major n*n per element) of a level at state q.
+int orc_blocks(void* h, int level, const double* q, double dtau, double* D) {
+  Oracle* o = (Oracle*)h;
+  const Level& L = o->lev[level];
+  int n = 4 * L.g.N;
+  std::vector<double> tr;
+  neighbour_traces(o, L, q, tr);
+  for (int e = 0; e < o->E; ++e) element_block(o, L, e, q, tr.data(), dtau, D + (size_t)e * n * n);
+  return 0;
+}
+
+int orc_lu_solve(int n, const double* A, const double* rhs, double* x) {
+  std::vector<double> a(A, A + (size_t)n * n);
+  std::vector<int> piv(n);
+  if (!lu_factor(n, a.data(), piv.data())) return -4;
+  for (int i = 0; i < n; ++i) x[i] = rhs[i];
+  lu_solve(n, a.data(), piv.data(), x);
+  return 0;
+}
+
+int orc_restrict(void* h, int lf, const double* qf, double* qc) {
+  Oracle* o = (Oracle*)h;
+  apply_tensor(o->Rm[lf], o->lev[lf + 1].g.P + 1, o->lev[lf].g.P + 1, o->E, qf, qc);
+  return 0;
+}
+
+int orc_prolong(void* h, int lf, const double* qc, double* qf) {
+  Oracle* o = (Oracle*)h;
+  apply_tensor(o->Pm[lf], o->lev[lf].g.P + 1, o->lev[lf + 1].g.P + 1, o->E, qc, qf);
+  return 0;
+}
+
+// One V-cycle on the finest-level state q (in/out) with the current stage data.
+int orc_vcycle(void* h, double* q, double dtau, int refresh) {
+  Oracle* o = (Oracle*)h;
+  Level& L = o->lev[0];
+  memcpy(L.q.data(), q, sizeof(double) * L.q.size());
+  std::fill(L.S.begin(), L.S.end(), 0.0);
+  o->dtau = dtau;
+  int st = vcycle_level(o, 0, refresh != 0);
+  memcpy(q, L.q.data(), sizeof(double) * L.q.size());
+  return st;
+}
+
+// Pseudo-transient continuation of one implicit stage (Section 2.4): a
+// V-cycle per pseudo-iteration, SER growth of dtau (eq. ser, exponent 1.5),
+// smoother refresh at m = 0 and every refresh_every iterations while
+// dtau < dtau_max, stop at ||F^m|| <= tol ||F^0|| (unweighted 2-norm over all
+// finest points and equations, evaluated at the start of each V-cycle).
+// SER growth of eq. ser with the pseudo time step in place of the CFL
+// number (dtau set directly, Section 4.1): fixed exponent 1.5, no lower clamp.
+static double ser_next(double dtau, double prev_norm, double norm, double dtau_max) {
+  return std::min(dtau * std::pow(prev_norm / norm, 1.5), dtau_max);
+}
+
+// Smoother refresh rule (Sections 4.1, 4.4): at the first pseudo-iteration
+// of a stage, then every k-th one until the smoother has been built with
+// dtau = dtau_max; after that it is no longer updated.  Reading: "if
+// dtau = dtau_max the smoother is not updated anymore" refers to a smoother
+// already built at dtau_max (taken literally, a dtau that reaches dtau_max
+// within the first k iterations would freeze the smoother at dtau_init).
+static bool refresh_due(int m, int k, double dtau_last_refresh, double dtau_max) {
+  return m == 0 || (m % k == 0 && dtau_last_refresh < dtau_max);
+}
+
+// Pseudo-transient continuation of one implicit stage (Section 2.4): a
+// V-cycle per pseudo-iteration, SER growth of dtau, smoother refresh per
+// refresh_due, stop at ||F^m|| <= tol ||F^0|| (unweighted 2-norm over all
+// finest points and equations, evaluated at the start of each V-cycle).
+static int stage_solve(Oracle* o, double* q, int* iters, double* drop, double* norms_out, int max_norms) {
+  Level& L = o->lev[0];
+  size_t tot = L.q.size();
+  std::vector<double> F(tot);
+  double dtau = o->cfg.dtau_init, n0 = 0.0, prev = 0.0, dtau_built = 0.0;
+  for (int m = 0;; ++m) {
+    level_F(o, 0, q, true, false, F.data());
+    double nm = l2norm(F);
+    if (norms_out && m < max_norms) norms_out[m] = nm;
+    if (m == 0) n0 = nm;
+    if (nm <= o->cfg.tol * n0 || n0 == 0.0) { *iters = m; *drop = n0 > 0 ? nm / n0 : 0.0; return 0; }
+    if (!std::isfinite(nm)) { *iters = m; *drop = nm; return -5; }
+    if (m >= o->cfg.max_pseudo) { *iters = m; *drop = nm / n0; return -6; }
+    if (m > 0) dtau = ser_next(dtau, prev, nm, o->cfg.dtau_max);
+    bool refresh = refresh_due(m, o->cfg.refresh_every, dtau_built, o->cfg.dtau_max);
+    if (refresh) dtau_built = dtau;
+    int st = orc_vcycle(o, q, dtau, refresh);
+    if (st) return st;
+    prev = nm;
+  }
+}
+
+// The dtau / refresh schedule stage_solve follows for a given norm sequence.
+int orc_ser_schedule(const double* norms, int n, double dtau_init, double dtau_max, int k,
+                     double* dtau_out, int* refresh_out) {
+  double dtau = dtau_init, built = 0.0;
+  for (int m = 0; m < n; ++m) {
+    if (m > 0) dtau = ser_next(dtau, norms[m - 1], norms[m], dtau_max);
+    dtau_out[m] = dtau;
+    refresh_out[m] = refresh_due(m, k, built, dtau_max) ? 1 : 0;
+    if (refresh_out[m]) built = dtau;
+  }
+  return 0;
+}
+
+int orc_stage_solve(void* h, double* q, int* iters, double* drop, double* norms, int max_norms) {
+  return stage_solve((Oracle*)h, q, iters, drop, norms, max_norms);
+}
+
+// One ESDIRK3 physical step (eq. ESDIRK_ns with the stage systems of eq.
+// ESDIRK_primitive); stage initial guess q^{i,0} = q^{i-1} (reading).
+int orc_esdirk_step(void* h, double* q, double dt, int* iters, double* drops) {
+  Oracle* o = (Oracle*)h;
+  Level& L = o->lev[0];
+  int E = o->E, N = L.g.N;
+  size_t tot = (size_t)4 * E * N;
+  int s = o->s;
+  std::vector<double> qcn(tot), qi(q, q + tot);
+  std::vector<std::vector<double>> Rs(s, std::vector<double>(tot));
+  for (int e = 0; e < E; ++e)
+    for (int p = 0; p < N; ++p) {
+      double qq[4], qc[4];
+      for (int v = 0; v < 4; ++v) qq[v] = q[((size_t)v * E + e) * N + p];
+      cons_from_prim(qq, o->ph, qc);
+      for (int v = 0; v < 4; ++v) qcn[((size_t)v * E + e) * N + p] = qc[v];
+    }
+  full_residual(o, L, qi.data(), Rs[0].data());
+  double omega = o->A[1][1];
+  o->omega_dt = omega * dt;
+  for (int i = 1; i < s; ++i) {
+    for (size_t k = 0; k < tot; ++k) {
+      double acc = qcn[k];
+      for (int j = 0; j < i; ++j) acc += dt * o->A[i][j] * Rs[j][k];
+      o->src[k] = acc / o->omega_dt;
+    }
+    int st = stage_solve(o, qi.data(), &iters[i - 1], &drops[i - 1], nullptr, 0);
+    if (st) return st;
+    full_residual(o, L, qi.data(), Rs[i].data());
+  }
+  for (int e = 0; e < E; ++e)
+    for (int p = 0; p < N; ++p) {
+      double qc[4], qq[4];
+      for (int v = 0; v < 4; ++v) {
+        size_t k = ((size_t)v * E + e) * N + p;
+        double acc = qcn[k];
+        for (int i = 0; i < s; ++i) acc += dt * o->b[i] * Rs[i][k];
+        qc[v] = acc;
+      }
+      prim_from_cons(qc, o->ph, qq);
+      for (int v = 0; v < 4; ++v) q[((size_t)v * E + e) * N + p] = qq[v];
+    }
+  return 0;
+}
+
+}  // extern "C"

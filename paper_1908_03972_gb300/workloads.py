@@ -1,0 +1,161 @@
+"""Seeded synthetic inputs: meshes and initial states.
+
+This module holds no arithmetic of the solver.  It builds the geometry and
+connectivity arrays that the library (and the test oracle) take as input, and
+evaluates analytic flow fields at point coordinates supplied by the caller.
+
+Mesh conventions (the library's C interface documents the same layout):
+
+* ``nodes``: float64 ``(E, (Ng+1)**2, 2)``: Lagrange geometry nodes of each
+  element at equispaced reference positions, node index ``b*(Ng+1)+a`` with
+  ``a`` along the first reference direction xi.
+* ``nbr``: int32 ``(E, 4, 3)``: for each local face (0: eta=-1, 1: xi=+1,
+  2: eta=+1, 3: xi=-1) the neighbour element, its local face and a flag that
+  is 1 when the two faces number their points in opposite order.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+GAMMA = 1.4
+
+
+def periodic_box(nx: int, ny: int, x0: float = 0.0, x1: float = 10.0,
+                 y0: float = 0.0, y1: float = 10.0, Ng: int = 1,
+                 perturb: float = 0.0, seed: int = 1234):
+    """Doubly periodic ``nx`` x ``ny`` quadrilateral mesh of a rectangle.
+
+    With ``perturb > 0`` every node is moved by a smooth periodic displacement
+    made of a few seeded Fourier modes, so that ``Ng >= 2`` elements are
+    genuinely curved while periodic faces still match.  Element ``e = jy*nx+ix``.
+    """
+    Lx, Ly = x1 - x0, y1 - y0
+    rng = np.random.default_rng(seed)
+    modes = []
+    if perturb > 0.0:
+        for _ in range(3):
+            kx, ky = rng.integers(1, 3, size=2)
+            ax, ay = rng.uniform(-1.0, 1.0, size=2)
+            ph = rng.uniform(0.0, 2 * math.pi, size=2)
+            modes.append((kx, ky, ax, ay, ph))
+    hx, hy = Lx / nx, Ly / ny
+
+    def disp(X, Y):
+        dx = np.zeros_like(X)
+        dy = np.zeros_like(Y)
+        for kx, ky, ax, ay, ph in modes:
+            arg = 2 * math.pi * (kx * (X - x0) / Lx + ky * (Y - y0) / Ly)
+            dx += ax * np.sin(arg + ph[0])
+            dy += ay * np.sin(arg + ph[1])
+        scale = perturb * min(hx, hy) / max(1, len(modes))
+        return dx * scale, dy * scale
+
+    r = np.linspace(0.0, 1.0, Ng + 1)
+    E = nx * ny
+    nodes = np.zeros((E, (Ng + 1) ** 2, 2))
+    for jy in range(ny):
+        for ix in range(nx):
+            e = jy * nx + ix
+            A, B = np.meshgrid(r, r, indexing="xy")   # A along xi (columns)
+            X = x0 + (ix + A) * hx
+            Y = y0 + (jy + B) * hy
+            dX, dY = disp(X, Y)
+            nodes[e, :, 0] = (X + dX).reshape(-1)
+            nodes[e, :, 1] = (Y + dY).reshape(-1)
+    nbr = np.zeros((E, 4, 3), dtype=np.int32)
+    for jy in range(ny):
+        for ix in range(nx):
+            e = jy * nx + ix
+            nbr[e, 0] = (((jy - 1) % ny) * nx + ix, 2, 0)
+            nbr[e, 1] = (jy * nx + (ix + 1) % nx, 3, 0)
+            nbr[e, 2] = (((jy + 1) % ny) * nx + ix, 0, 0)
+            nbr[e, 3] = (jy * nx + (ix - 1) % nx, 1, 0)
+    return nodes, nbr
+
+
+def flip_elements(nodes: np.ndarray, nbr: np.ndarray, which, Ng: int):
+    """Rotate the local numbering of the listed elements by 180 degrees.
+
+    The mesh is unchanged geometrically, but the rotated elements meet their
+    neighbours with reversed face-point order, which exercises the
+    orientation flag of the connectivity table.
+    """
+    nodes = nodes.copy()
+    nbr = nbr.copy()
+    n1 = Ng + 1
+    which = set(int(e) for e in which)
+    for e in which:
+        nodes[e] = nodes[e].reshape(n1, n1, 2)[::-1, ::-1].reshape(-1, 2)
+    # local face f of a rotated element is old face (f+2)%4
+    old = nbr.copy()
+    for e in range(nbr.shape[0]):
+        for f in range(4):
+            of = (f + 2) % 4 if e in which else f
+            en, fn, _ = old[e, of]
+            fn_new = (fn + 2) % 4 if en in which else fn
+            # both elements sharing the face agree on orientation unless exactly one is rotated
+            rev = 1 if ((e in which) != (int(en) in which)) else 0
+            nbr[e, f] = (en, fn_new, rev)
+    return nodes, nbr
+
+
+def freestream_T(Ma_inf: float, speed: float = math.sqrt(2.0), gamma: float = GAMMA) -> float:
+    """Free-stream temperature for a Mach number defined with |v_inf| (R = 1)."""
+    c = speed / Ma_inf
+    return c * c / gamma
+
+
+def isentropic_vortex(xy: np.ndarray, t: float = 0.0, Ma_inf: float = 0.005,
+                      strength: float = 5.0, phi: float = 0.5,
+                      center=(5.0, 5.0), period=(10.0, 10.0),
+                      gamma: float = GAMMA) -> np.ndarray:
+    """Isentropic vortex of eq. VP_Solution advected by (u, v) = (1, 1).
+
+    ``xy`` has shape ``(..., 2)``.  Returns primitive variables (p, u, v, T)
+    in an array of shape ``(4,) + xy.shape[:-1]``.  r is the Euclidean
+    distance to the (periodically nearest) vortex centre; the free stream is
+    rho = u = v = 1 with Ma_inf = |v_inf| / c_inf and R = 1.
+    """
+    Tinf = freestream_T(Ma_inf, gamma=gamma)
+    xc = center[0] + t
+    yc = center[1] + t
+    dx = xy[..., 0] - xc
+    dy = xy[..., 1] - yc
+    if period is not None:
+        dx = dx - period[0] * np.round(dx / period[0])
+        dy = dy - period[1] * np.round(dy / period[1])
+    r2 = dx * dx + dy * dy
+    ex = np.exp(phi * (1.0 - r2))
+    du = -strength / (2 * math.pi) * dy * ex
+    dv = strength / (2 * math.pi) * dx * ex
+    dT = -strength ** 2 * (gamma - 1.0) / (16.0 * phi * gamma * math.pi ** 2) * ex * ex
+    T = Tinf + dT
+    rho = (T / Tinf) ** (1.0 / (gamma - 1.0))
+    p = rho * T
+    return np.stack([p, 1.0 + du, 1.0 + dv, T])
+
+
+def to_soa(field: np.ndarray) -> np.ndarray:
+    """(4, E, N) field -> contiguous float64 state array, variable-major."""
+    return np.ascontiguousarray(field, dtype=np.float64)
+
+
+def uniform_state(E: int, N: int, p: float, u: float, v: float, T: float) -> np.ndarray:
+    q = np.empty((4, E, N))
+    q[0], q[1], q[2], q[3] = p, u, v, T
+    return q
+
+
+def random_perturbed_state(E: int, N: int, Ma_inf: float = 0.005, amp: float = 0.05,
+                           seed: int = 7) -> np.ndarray:
+    """Free stream (rho = u = v = 1) plus seeded noise, for parity tests."""
+    rng = np.random.default_rng(seed)
+    Tinf = freestream_T(Ma_inf)
+    q = uniform_state(E, N, Tinf, 1.0, 1.0, Tinf)
+    q[0] += amp * rng.standard_normal((E, N))
+    q[1] += amp * rng.standard_normal((E, N))
+    q[2] += amp * rng.standard_normal((E, N))
+    q[3] += 1e-3 * amp * rng.standard_normal((E, N))
+    return q
