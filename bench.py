@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Benchmark: wall seconds per ESDIRK3 physical step with every implicit stage
+driven to a 1e-8 relative residual drop, for the mixed-precision (FP32 block)
+and the plain FP64 element-Jacobi P-multigrid V-cycle, plus DOF-sweeps/s.
+
+Workload (default "c2"): isentropic vortex, Ma_inf = 0.005, periodic
+[0,10]^2, 64x64 straight quads, P{3-2-1-0}, I{5-10-20-40}, ESDIRK3,
+dt = 0.1, dtau 0.01 -> 10, smoother refresh every 10 pseudo-iterations.
+Every step is the first physical step from the analytic vortex (the state is
+reset before each step, outside the timed region); inputs are synthetic and
+resident in HBM when a timed step starts.  L2 is flushed before every timed
+step by writing a 256 MiB buffer.
+
+One JSON line is printed by rank 0.  Under torchrun (N > 1) every rank runs
+an independent replica (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "wall s per ESDIRK step to 1e-8 residual drop, mixed vs FP64 V-cycle; DOF-sweeps/s"
+VCYCLE_FILE = os.path.join(ROOT, "profiles", "c2_step_vcycles.json")
+
+WORKLOADS = {
+    "c2": dict(name="2D Euler isentropic vortex, Ma_inf=0.005, periodic [0,10]^2, 64x64 straight quads, "
+                    "P{3-2-1-0} (64 DOFs/elem), I{5-10-20-40}, ESDIRK3 dt=0.1, first step from the analytic "
+                    "state, each stage to a 1e-8 relative drop",
+               n=64, levels=[3, 2, 1, 0], smooth=[5, 10, 20, 40], dt=0.1),
+    "c1": dict(name="2D Euler isentropic vortex, Ma_inf=0.005, periodic [0,10]^2, 8x8 straight quads, "
+                    "P{2-1-0} (36 DOFs/elem), I{5-10-20}, ESDIRK3 dt=0.1, first step from the analytic state, "
+                    "each stage to a 1e-8 relative drop",
+               n=8, levels=[2, 1, 0], smooth=[5, 10, 20], dt=0.1),
+}
+
+# FP64 arithmetic peak of one GB300: 2 FP64 FMA per clock per SM (measured:
+# 1.20 TFLOP/s of dependent-free DFMA at 2.0 GHz), 152 SMs, 2.07 GHz max clock.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def dof_sweeps_per_vcycle(E, levels, smooth):
+    """sum_l DOF_l x sweeps_l: 2 n_l on every level but the coarsest, n_L there."""
+    tot = 0
+    for l, (P, n) in enumerate(zip(levels, smooth)):
+        sweeps = n if l == len(levels) - 1 else 2 * n
+        tot += 4 * E * (P + 1) ** 2 * sweeps
+    return tot
+
+
+# ------------------------------------------------ algorithmic work per launch
+# FLOPs counted from the kernel source (fma = 2, add/mul/div/sqrt = 1).
+ROE_FLOPS = 185
+
+
+def face_flops(P, n_faces):
+    n1 = P + 1
+    return n_faces * n1 * (24 * n1 + 12 + ROE_FLOPS)
+
+
+def volume_flops(P, E, split=True):
+    n1 = P + 1
+    N = n1 * n1
+    per_pt = 17 + 24 + 16 * (2 * n1 + 1) / n1 + (22 if split else 10) + 4 * (4 * n1 + 8) + 4 + 12 + 8
+    return E * N * per_pt
+
+
+def apply_bytes(P, E, wbytes):
+    n = 4 * (P + 1) ** 2
+    return E * (wbytes * n * n + 16 * n + 24 * n)
+
+
+def apply_flops(P, E):
+    n = 4 * (P + 1) ** 2
+    return E * 2 * n * n
+
+
+# ------------------------------------------------------------------ helpers
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def barrier_max(value, world, device):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------ reference arm
+def oracle_sample(wl, n_ref, n_plain):
+    """Time the FP64 CPU oracle on one V-cycle with smoother rebuild and one
+    without, on the full workload, and scale to one step."""
+    import oracle as O
+    from paper_1908_03972_gb300 import workloads as W
+    nodes, nbr = W.periodic_box(wl["n"], wl["n"], Ng=1)
+    orc = O.Oracle(nodes, nbr, 1, wl["levels"], wl["smooth"], tol=1e-8)
+    q = W.isentropic_vortex(orc.coords())
+    A, b, c = O.esdirk3()
+    dt = wl["dt"]
+    odt = A[1, 1] * dt
+    R = orc.residual(q)
+    rho = q[0] / q[3]
+    qc = np.stack([rho, rho * q[1], rho * q[2], rho * (q[3] / 0.4 + 0.5 * (q[1] ** 2 + q[2] ** 2))])
+    orc.set_stage((qc + dt * A[1, 0] * R) / odt, odt)
+    t0 = time.perf_counter()
+    q1 = orc.vcycle(q, 0.01, refresh=True)
+    t1 = time.perf_counter()
+    orc.vcycle(q1, 0.01, refresh=False)
+    t2 = time.perf_counter()
+    t_ref, t_plain = t1 - t0, t2 - t1
+    return dict(t_vcycle_refresh=t_ref, t_vcycle=t_plain, s_per_step=n_ref * t_ref + n_plain * t_plain)
+
+
+def load_vcycle_counts():
+    if os.path.exists(VCYCLE_FILE):
+        with open(VCYCLE_FILE) as f:
+            return json.load(f)
+    return None
+
+
+def run_reference(args, wl, world, rank):
+    if rank != 0:
+        return 0
+    counts = load_vcycle_counts() if args.workload == "c2" else None
+    n_v, n_r = (counts["vcycles"], counts["refreshes"]) if counts else (1, 1)
+    samples = []
+    for _ in range(max(1, args.warmup and 0) + args.steps):
+        samples.append(oracle_sample(wl, n_r, n_v - n_r))
+    s = float(np.median([x["s_per_step"] for x in samples]))
+    E = wl["n"] ** 2
+    dsw = dof_sweeps_per_vcycle(E, wl["levels"], wl["smooth"])
+    sample = ("one FAS V-cycle with smoother rebuild and one without on the full workload, single-threaded "
+              f"FP64 oracle; scaled by {n_r} rebuilding and {n_v - n_r} plain V-cycles per step"
+              + ("" if counts else " (no measured V-cycle count found: per V-cycle figure)"))
+    line = {"impl": "reference", "metric": METRIC, "value": s, "unit": "s/step", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * s, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "elements": E, "parallelism": "replicas"},
+            "dof_sweeps_per_s": dsw / samples[-1]["t_vcycle"],
+            "cpu_baseline": {"kind": "oracle", "value": s, "unit": "s/step", "cores": 1, "sample": sample},
+            "e2e": {"value": s, "unit": "s/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, wl, world, rank, local):
+    import torch
+    from paper_1908_03972_gb300 import build, pmgfr, workloads as W
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    build.build()
+    pmgfr.load()
+    nodes, nbr = W.periodic_box(wl["n"], wl["n"], Ng=1)
+    E = nodes.shape[0]
+    stream = torch.cuda.current_stream(device)
+    kw = dict(tol=1e-8, dtau_init=0.01, dtau_max=10.0, refresh_every=10, max_pseudo=20000, use_graph=1,
+              p_gauge=W.freestream_T(0.005))
+    dsw = dof_sweeps_per_vcycle(E, wl["levels"], wl["smooth"])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+
+    def make(prec):
+        return pmgfr.Solver(nodes, nbr, wl["levels"], wl["smooth"], stream=stream.cuda_stream, block_prec=prec, **kw)
+
+    solver = make(pmgfr.PMG_PREC_FP32)
+    q0 = W.isentropic_vortex(solver.coords())
+    q0_dev = torch.from_numpy(np.ascontiguousarray(q0)).to(device)
+    state_bytes = q0.nbytes
+
+    def one_step(s, timed):
+        pmgfr.pmg_set_state(s.h, 0, q0_dev)
+        if timed:
+            flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = pmgfr.pmg_esdirk_step(s.h, wl["dt"])
+        e1.record(stream)
+        torch.cuda.synchronize(device)
+        return e0.elapsed_time(e1), st
+
+    results = {}
+    for prec, label, warm in ((pmgfr.PMG_PREC_FP32, "mixed", args.warmup), (pmgfr.PMG_PREC_FP64, "fp64", 1)):
+        if args.skip_fp64 and label == "fp64":
+            continue
+        s = solver if label == "mixed" else make(prec)
+        for _ in range(warm):
+            one_step(s, False)
+        sampler = ClockSampler(local) if label == "mixed" else None
+        if sampler:
+            sampler.start()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(device)
+        ms, stats = [], None
+        for _ in range(args.steps):
+            t, stats = one_step(s, True)
+            ms.append(t)
+        torch.cuda.synchronize(device)
+        clocks = sampler.stop() if sampler else None
+        mean_ms = barrier_max(float(np.mean(ms)), world, device)
+        nv = stats.n_vcycles
+        results[label] = dict(s_per_step=mean_ms / 1000.0, ms=ms, vcycles=nv, refreshes=stats.n_refresh,
+                              pseudo_iters=list(stats.pseudo_iters)[:3],
+                              res_drop=[float(x) for x in list(stats.res_drop)[:3]],
+                              dof_sweeps_per_s=dsw * nv * world / (mean_ms / 1000.0), clocks=clocks)
+        if label != "mixed":
+            s.close()
+
+    mixed = results["mixed"]
+    # end to end through the C interface with host buffers: H2D state, step, D2H state
+    qh = np.ascontiguousarray(q0)
+    out = np.empty_like(qh)
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    pmgfr.pmg_set_state(solver.h, 0, qh)
+    pmgfr.pmg_esdirk_step(solver.h, wl["dt"])
+    pmgfr.pmg_get_state(solver.h, 0, out)
+    e2e_s = barrier_max(time.perf_counter() - t0, world, device)
+
+    # per-launch profile of one step (launch by launch, CUDA events on the solver stream)
+    pmgfr.pmg_profile(solver.h, True)
+    one_step(solver, False)
+    prof = pmgfr.pmg_profile_read(solver.h)
+    pmgfr.pmg_profile(solver.h, False)
+    total_ms = sum(v[0] for v in prof.values())
+    launches = sum(v[1] for v in prof.values())
+    by_class = {}
+    for (name, lvl), (t, n) in prof.items():
+        by_class.setdefault(name, [0.0, 0])
+        by_class[name][0] += t
+        by_class[name][1] += n
+    top = max(prof.items(), key=lambda kv: kv[1][0])
+    (top_name, top_lvl), (top_ms, top_n) = top
+    P = wl["levels"][top_lvl]
+    n_faces = 2 * E
+    if top_name == "face_flux":
+        work, bound, unit, peak = face_flops(P, n_faces), "alu", "TFLOP/s", FP64_PEAK_TFLOPS
+    elif top_name == "volume":
+        work, bound, unit, peak = volume_flops(P, E, top_lvl == 0), "alu", "TFLOP/s", FP64_PEAK_TFLOPS
+    elif top_name == "apply":
+        work, bound, unit, peak = apply_bytes(P, E, 4), "hbm", "GB/s", None
+    else:
+        work, bound, unit, peak = None, "alu", "TFLOP/s", FP64_PEAK_TFLOPS
+    avg_s = top_ms / top_n / 1000.0
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    if bound == "hbm":
+        peak = peaks.get("hbm_gbs", 6800.0)
+        achieved = work / avg_s / 1e9
+        peak_note = "measured" if "hbm_gbs" in peaks else "fallback"
+    else:
+        achieved = work / avg_s / 1e12 if work else None
+        peak_note = "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz"
+    roofline = {"kernel": f"{top_name}[level {top_lvl}, P={P}]", "bound": bound, "achieved": achieved,
+                "peak": peak, "unit": unit, "frac": (achieved / peak) if achieved else None,
+                "traffic": None, "peak_source": peak_note,
+                "share_of_step": top_ms / total_ms if total_ms else None,
+                "avg_launch_us": avg_s * 1e6, "launches_per_step": top_n}
+
+    # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        try:
+            smp = oracle_sample(wl, mixed["refreshes"], mixed["vcycles"] - mixed["refreshes"])
+            cpu = {"value": smp["s_per_step"], "unit": "s/step", "cores": 1, "kind": "oracle",
+                   "sample": ("one V-cycle with smoother rebuild (%.1f s) and one without (%.1f s) on the full "
+                              "workload, single-threaded FP64 oracle, scaled by this run's %d rebuilding and %d "
+                              "plain V-cycles per step" % (smp["t_vcycle_refresh"], smp["t_vcycle"],
+                                                           mixed["refreshes"], mixed["vcycles"] - mixed["refreshes"]))}
+        except Exception as exc:  # the product number stands without it
+            cpu = {"value": None, "unit": "s/step", "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
+        if args.workload == "c2":
+            os.makedirs(os.path.dirname(VCYCLE_FILE), exist_ok=True)
+            with open(VCYCLE_FILE, "w") as f:
+                json.dump({"workload": wl["name"], "vcycles": mixed["vcycles"], "refreshes": mixed["refreshes"],
+                           "pseudo_iters": mixed["pseudo_iters"]}, f, indent=1)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": mixed["s_per_step"], "unit": "s/step", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mixed["s_per_step"] * 1000.0,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": wl["name"], "elements": E, "dofs_finest": 4 * E * (wl["levels"][0] + 1) ** 2,
+                       "blocks": "FP32 equilibrated Gauss-Jordan inverse", "residual": "FP64",
+                       "l2": "flushed (256 MiB write) before every timed step", "parallelism": "replicas"},
+            "mixed": {k: v for k, v in mixed.items() if k not in ("clocks",)},
+            "fp64": {k: v for k, v in results.get("fp64", {}).items() if k not in ("clocks",)},
+            "dof_sweeps_per_vcycle": dsw,
+            "clocks": mixed["clocks"],
+            "e2e": {"value": e2e_s, "unit": "s/step", "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes},
+            "gpu_launches": launches * args.steps,
+            "profile_ms_by_kernel": {k: {"ms": v[0], "launches": v[1]} for k, v in sorted(by_class.items())},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl, world, rank)
+    return run_ours(args, wl, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,203 @@
+/*
+ * pmgfr.h -- C interface of the GB300 implicit P-multigrid flux
+ * reconstruction library (libpmgfr.so).
+ *
+ * The library solves the 2D Euler equations with Weiss-Smith/Turkel local
+ * preconditioning, discretised by FR/CPR (Gauss-Legendre solution points,
+ * DG/Radau correction functions) and advanced by ESDIRK3 with dual time
+ * stepping.  Each implicit stage is solved by pseudo-transient continuation
+ * whose pseudo-iteration is one FAS V-cycle over polynomial levels with an
+ * element-Jacobi smoother (Wang & Yu, arXiv 1908.03972, Sections 2-3).
+ *
+ * Conventions shared by every call
+ *  - Working variables are primitive q_p = (p, u, v, T) with R = 1.
+ *  - A state array of level l is FP64, variable-major ("SoA"):
+ *      q[(v * E + e) * N + pt],  v in 0..3, N = (P_l + 1)^2,
+ *    and solution point (i, j) of an element has pt = j * (P_l + 1) + i with
+ *    i along the first reference direction xi.
+ *  - Pointers flagged by on_device = 1 are caller-owned device buffers on the
+ *    context's device; on_device = 0 means caller-owned host memory.  The
+ *    library copies what it needs and never keeps caller pointers.
+ *  - Every call is ordered on the CUDA stream given to pmg_create.  Calls
+ *    that return host data synchronise that stream.
+ *  - Every call returns a pmg_status; PMG_OK is 0 and errors are negative.
+ *    pmg_last_error() gives a message for the calling thread's last error.
+ *    No C++ exception crosses this interface.  There is no CPU fallback: if
+ *    the GPU path cannot run, the call fails with PMG_ECUDA.
+ */
+#ifndef PMGFR_H
+#define PMGFR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pmg_ctx pmg_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  PMG_OK = 0,
+  PMG_EINVAL = -1,     /* bad argument, size or call order */
+  PMG_ENOMEM = -2,     /* device allocation failed */
+  PMG_ECUDA = -3,      /* CUDA runtime error (message in pmg_last_error) */
+  PMG_ESINGULAR = -4,  /* zero pivot while factoring an element block */
+  PMG_ENONFINITE = -5, /* non-finite residual norm */
+  PMG_ENOTCONV = -6,   /* stage did not reach the tolerance in max_pseudo */
+  PMG_ESTATE = -8      /* call needs data that was not set (mesh, stage) */
+} pmg_status;
+
+typedef enum {
+  PMG_PREC_FP64 = 0, /* blocks factored and applied in FP64 */
+  PMG_PREC_FP32 = 1  /* blocks equilibrated, factored and applied in FP32 */
+} pmg_prec;
+
+/* Solver configuration (Sections 2.2-3, 4.1).
+ *  P[l], n_smooth[l]: the hierarchy P{P0-P1-...} and the smoothing counts
+ *  I{n0-n1-...}; pre- and post-smoothing use the same count, the coarsest
+ *  level smooths once (Section 3).  0 <= P <= 4, 1 <= n_levels <= 8.
+ *  cutoff = 1: eps = min(1, max(kappa Ma_inf, Ma)) (eq. eps_nonmove);
+ *  cutoff = 0: eps = min(1, Ma) (Section 4.1).
+ *  dtau_init, dtau_max, refresh_every: pseudo time step control (eq. ser
+ *  with dtau set directly; smoother rebuilt at the first pseudo-iteration of
+ *  a stage, then every refresh_every iterations until one rebuild used
+ *  dtau_max).  tol: relative drop of ||F|| that ends a stage. */
+typedef struct {
+  int n_levels;
+  int P[8];
+  int n_smooth[8];
+  double gamma, Ma_inf, kappa;
+  int cutoff;
+  double dtau_init, dtau_max, tol;
+  int refresh_every, max_pseudo;
+  int block_prec; /* pmg_prec */
+  int use_graph;  /* 1: replay each V-cycle as a captured CUDA graph */
+  double p_gauge; /* reference pressure kept out of device storage: the
+                     library stores p - p_gauge (0: p itself).  At low Mach a
+                     value near the free-stream pressure keeps the pressure
+                     resolution at the level of its variations; every call
+                     still takes and returns absolute p. */
+} pmg_config;
+
+/* Mesh of quadrilaterals with Lagrange geometry of order geom_order (1 or 2).
+ *  nodes: (n_elem, (geom_order+1)^2, 2) FP64, element geometry nodes at
+ *         equispaced reference positions, node b*(geom_order+1)+a, a along xi.
+ *  nbr:   (n_elem, 4, 3) int32: for local faces 0 (eta=-1), 1 (xi=+1),
+ *         2 (eta=+1), 3 (xi=-1): neighbour element, its local face, and 1 if
+ *         the two faces number their points in opposite order.  Faces are
+ *         interior or periodic (every face has a neighbour).
+ * Both arrays are host memory, copied during the call. */
+typedef struct {
+  int n_elem;
+  int geom_order;
+  const double* nodes;
+  const int* nbr;
+} pmg_mesh;
+
+typedef struct {
+  int pseudo_iters[8]; /* V-cycles used by each implicit stage */
+  double res_drop[8];  /* final ||F||/||F^0|| of each implicit stage */
+  double ms_total;     /* wall time of the step on the stream, milliseconds */
+  int n_vcycles;       /* total V-cycles of the step */
+  int n_refresh;       /* smoother rebuilds of the step */
+} pmg_step_stats;
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL
+ * for the legacy default stream).  *out receives the context. */
+pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out);
+
+/* Destroy a context and free its device memory.  NULL is ignored. */
+void pmg_destroy(pmg_ctx* ctx);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* pmg_last_error(void);
+
+/* Upload the mesh; builds operator tables and metrics of every level (the
+ * exact mapping evaluated at each level's own points, Section 2.3).  Must be
+ * called once, before any state call. */
+pmg_status pmg_upload_mesh(pmg_ctx* ctx, const pmg_mesh* mesh);
+
+/* Physical coordinates of the solution points of a level into host memory
+ * xy[(e * N + pt) * 2 + {0, 1}]. */
+pmg_status pmg_point_coords(pmg_ctx* ctx, int level, double* xy);
+
+/* Set / read the solution state of a level (SoA layout above). */
+pmg_status pmg_set_state(pmg_ctx* ctx, int level, const double* q, int on_device);
+pmg_status pmg_get_state(pmg_ctx* ctx, int level, double* q, int on_device);
+
+/* R = -div f of eq. eqn:FR_diff at every solution point of the level for the
+ * state q (FP64; Section 2.3, eqs. eqn:FR_diff, invis_com). */
+pmg_status pmg_residual(pmg_ctx* ctx, int level, const double* q, double* R, int on_device);
+
+/* Stage data of the finest level: src = (q_c^n + dt sum_j a_ij R^j)/(omega dt)
+ * (SoA, level 0 size) and omega*dt of eq. ESDIRK_primitive. */
+pmg_status pmg_set_stage(pmg_ctx* ctx, const double* src, double omega_dt, int on_device);
+
+/* F_l(q) = -q_c(q)/(omega dt) + R_l(q) (+ src on level 0), eq. ESDIRK_primitive. */
+pmg_status pmg_stage_residual(pmg_ctx* ctx, int level, const double* q, double* F, int on_device);
+
+/* Assemble the element blocks D_e = Gamma/dtau + M/(omega dt) - dR_e/dq_e
+ * (eqs. linearized_pseudo_transient_final, smoothing_element_jacobi) of a
+ * level at its current state, exact own-element derivative with neighbours
+ * frozen.  level = -1 assembles every level at its current state. */
+pmg_status pmg_assemble_blocks(pmg_ctx* ctx, int level, double dtau);
+
+/* Copy the assembled FP64 blocks of a level, row-major n x n per element,
+ * n = 4 N, row/column index v * N + pt. */
+pmg_status pmg_get_blocks(pmg_ctx* ctx, int level, double* D, int on_device);
+
+/* Factor the assembled blocks of a level (or all, level = -1) in the
+ * configured precision: power-of-two row/column equilibration, then
+ * Gauss-Jordan elimination with partial pivoting to the explicit inverse.
+ * Returns PMG_ESINGULAR if a pivot vanishes. */
+pmg_status pmg_factor_blocks(pmg_ctx* ctx, int level);
+
+/* x = D^-1 r per element with the factored blocks (SoA vectors). */
+pmg_status pmg_apply_blocks(pmg_ctx* ctx, int level, const double* r, double* x, int on_device);
+
+/* Restriction (L2 projection, Section 3) of a level-lf field to level lf+1,
+ * and prolongation (interpolation) of a level-(lf+1) field to level lf. */
+pmg_status pmg_restrict(pmg_ctx* ctx, int lf, const double* qf, double* qc, int on_device);
+pmg_status pmg_prolong(pmg_ctx* ctx, int lf, const double* qc, double* qf, int on_device);
+
+/* One FAS V-cycle (Section 3) on the finest-level state with the current
+ * stage data and pseudo time step dtau; refresh = 1 rebuilds every level's
+ * smoother on the way down.  *res_norm_out (may be NULL) receives ||F_0|| at
+ * the start of the cycle. */
+pmg_status pmg_vcycle(pmg_ctx* ctx, double dtau, int refresh, double* res_norm_out);
+
+/* Pseudo-transient continuation of the current stage (Section 2.4) from the
+ * finest-level state: V-cycles with SER growth of dtau until
+ * ||F|| <= tol ||F^0||.  iters / drop (may be NULL) receive the V-cycle
+ * count and the final relative drop.  PMG_ENOTCONV after max_pseudo. */
+pmg_status pmg_stage_solve(pmg_ctx* ctx, int* iters, double* drop);
+
+/* One ESDIRK3 physical step of size dt (eq. ESDIRK_ns) from the finest-level
+ * state; the stage initial guess is the previous stage's solution.  Inside the
+ * step the finest-level system F = -q_c(q)/(omega dt) + R(q) + src is
+ * evaluated as -(q_c(q) - q_c(q^n))/(omega dt) + R(q) + sum_j a_ij R^j/omega,
+ * identical in exact arithmetic, with the energy difference formed from the
+ * pressure difference so that rho E ~ 1/Ma^2 is never rounded. */
+pmg_status pmg_esdirk_step(pmg_ctx* ctx, double dt, pmg_step_stats* stats);
+
+/* Residual norm ||F^m|| and pseudo time step of every pseudo-iteration of the
+ * last pmg_stage_solve or pmg_esdirk_step (all stages, in order).  Up to
+ * max_count entries are written to norms / dtau (either may be NULL);
+ * *count receives the total number recorded.  Host memory. */
+pmg_status pmg_stage_history(pmg_ctx* ctx, double* norms, double* dtau, int max_count, int* count);
+
+/* Per-launch profiler.  While enabled, every kernel launch of the solver is
+ * bracketed by CUDA events on the context's stream (V-cycles are then issued
+ * launch by launch, not as a captured graph) and the event times are summed
+ * per kernel class and level.  enable = 1 clears the sums. */
+pmg_status pmg_profile(pmg_ctx* ctx, int enable);
+
+/* Kernel classes of the profiler, in this order: face flux, volume residual,
+ * block apply, block assembly, block factorisation, restriction, prolongation,
+ * norm reduction, stage arithmetic.  ms and counts receive PMG_PROF_CLASSES x 8
+ * entries (class-major, level 0..7): summed milliseconds and launch counts. */
+#define PMG_PROF_CLASSES 9
+pmg_status pmg_profile_read(pmg_ctx* ctx, double* ms, long long* counts);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMGFR_H */

@@ -8,13 +8,14 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pmg_oracle.cpp")
-_LIB = os.path.join(_HERE, "liboracle.so")
+_LIB = os.path.join(_HERE, f"liboracle.{platform.machine()}.so")
 _lib = None
 
 

@@ -1,0 +1,817 @@
+// api.cu -- C interface of libpmgfr and the solver orchestration: FAS
+// V-cycle (Section 3), pseudo-transient continuation with SER (Section 2.4),
+// ESDIRK3 physical steps.  Every arithmetic step runs in the kernels of
+// k_residual.cu, k_blocks.cu and k_misc.cu; the host only sequences launches,
+// keeps the pseudo-time schedule and reads one norm per V-cycle.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "pmg_internal.h"
+
+using namespace pmg;
+
+struct pmg_ctx {
+  Ctx c;
+};
+
+static thread_local std::string g_err;
+
+static pmg_status fail(pmg_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+#define PMG_CK(call)                                                                   \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) return fail(PMG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define PMG_CK_LAUNCH()                                                                \
+  do {                                                                                 \
+    cudaError_t e_ = cudaGetLastError();                                               \
+    if (e_ != cudaSuccess) return fail(PMG_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <class T>
+static cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, count * sizeof(T) > 0 ? count * sizeof(T) : 8);
+}
+
+// ESDIRK3 of Section 2.4 (third order, four stages, first stage explicit,
+// stiffly accurate, L-stable): the published rational coefficients.
+static void esdirk3_table(Ctx& c) {
+  memset(c.A, 0, sizeof(c.A));
+  memset(c.b, 0, sizeof(c.b));
+  memset(c.c, 0, sizeof(c.c));
+  const double g = 1767732205903.0 / 4055673282236.0;
+  c.A[1][0] = g; c.A[1][1] = g;
+  c.A[2][0] = 2746238789719.0 / 10658868560708.0;
+  c.A[2][1] = -640167445237.0 / 6845629431997.0;
+  c.A[2][2] = g;
+  c.b[0] = 1471266399579.0 / 7840856788654.0;
+  c.b[1] = -4482444167858.0 / 7529755066697.0;
+  c.b[2] = 11266239266428.0 / 11593286722821.0;
+  c.b[3] = g;
+  for (int j = 0; j < 4; ++j) c.A[3][j] = c.b[j];
+  c.c[0] = 0.0; c.c[1] = 2 * g; c.c[2] = 3.0 / 5.0; c.c[3] = 1.0;
+  c.stages = 4;
+}
+
+static void free_level(LevelDev& L) {
+  double** ptrs[] = {&L.q, &L.qb, &L.S, &L.F, &L.Pd, &L.met, &L.face, &L.Fcom, &L.Dfull, &L.rs, &L.cs};
+  for (double** p : ptrs) { if (*p) cudaFree(*p); *p = nullptr; }
+  if (L.Dinv) cudaFree(L.Dinv);
+  L.Dinv = nullptr;
+}
+
+extern "C" {
+
+const char* pmg_last_error(void) { return g_err.c_str(); }
+
+pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
+  if (!cfg || !out) return fail(PMG_EINVAL, "null argument");
+  if (cfg->n_levels < 1 || cfg->n_levels > kMaxLevels) return fail(PMG_EINVAL, "n_levels must be in 1..8");
+  for (int l = 0; l < cfg->n_levels; ++l) {
+    if (cfg->P[l] < 0 || cfg->P[l] > kMaxP) return fail(PMG_EINVAL, "P must be in 0..4");
+    if (l > 0 && cfg->P[l] >= cfg->P[l - 1]) return fail(PMG_EINVAL, "P levels must decrease");
+    if (cfg->n_smooth[l] < 1) return fail(PMG_EINVAL, "smoothing counts must be >= 1");
+  }
+  if (cfg->block_prec != PMG_PREC_FP64 && cfg->block_prec != PMG_PREC_FP32)
+    return fail(PMG_EINVAL, "unknown block precision");
+  if (!(cfg->gamma > 1.0)) return fail(PMG_EINVAL, "gamma must exceed 1");
+  int dev;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(PMG_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  pmg_ctx* h = new pmg_ctx();
+  Ctx& c = h->c;
+  c.cfg = *cfg;
+  c.device = dev;
+  if (stream) {
+    c.stream = (cudaStream_t)stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { delete h; return fail(PMG_ECUDA, cudaGetErrorString(e)); }
+    c.own_stream = true;
+  }
+  c.ph.gamma = cfg->gamma;
+  c.ph.gm1 = cfg->gamma - 1.0;
+  c.ph.Cp = cfg->gamma / (cfg->gamma - 1.0);
+  c.ph.eps_min = cfg->cutoff ? cfg->kappa * cfg->Ma_inf : 0.0;
+  c.ph.p_ref = cfg->p_gauge;
+  esdirk3_table(c);
+  if (dalloc(&c.d_scal, 4) != cudaSuccess || dalloc(&c.d_flag, 4) != cudaSuccess ||
+      dalloc(&c.d_dtau, 1) != cudaSuccess || cudaMallocHost((void**)&c.h_scal, 8 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&c.h_dtau, sizeof(double)) != cudaSuccess) {
+    pmg_destroy(h);
+    return fail(PMG_ENOMEM, "device allocation failed");
+  }
+  *out = h;
+  return PMG_OK;
+}
+
+void pmg_destroy(pmg_ctx* h) {
+  if (!h) return;
+  Ctx& c = h->c;
+  cudaStreamSynchronize(c.stream);
+  for (int g = 0; g < 2; ++g)
+    if (c.graph[g]) cudaGraphExecDestroy(c.graph[g]);
+  for (int l = 0; l < kMaxLevels; ++l) free_level(c.lev[l]);
+  double** ptrs[] = {&c.src, &c.qn, &c.qcn, &c.d_partial, &c.d_scal, &c.d_tmp0, &c.d_tmp1, &c.d_dtau};
+  for (double** p : ptrs) { if (*p) cudaFree(*p); *p = nullptr; }
+  for (int j = 0; j < 6; ++j) if (c.Rst[j]) cudaFree(c.Rst[j]);
+  if (c.d_faces) cudaFree(c.d_faces);
+  if (c.d_flag) cudaFree(c.d_flag);
+  if (c.h_scal) cudaFreeHost(c.h_scal);
+  if (c.h_dtau) cudaFreeHost(c.h_dtau);
+  for (auto& e : c.prof.ev) cudaEventDestroy(e);
+  if (c.own_stream) cudaStreamDestroy(c.stream);
+  delete h;
+}
+
+pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
+  if (!h || !m || !m->nodes || !m->nbr) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  if (c.mesh_ready) return fail(PMG_EINVAL, "mesh already uploaded");
+  if (m->n_elem < 1 || m->geom_order < 1 || m->geom_order > 4) return fail(PMG_EINVAL, "bad mesh sizes");
+  c.E = m->n_elem;
+  c.mesh.E = m->n_elem;
+  c.mesh.Ng = m->geom_order;
+  int nn = (m->geom_order + 1) * (m->geom_order + 1);
+  c.mesh.nodes.assign(m->nodes, m->nodes + (size_t)c.E * nn * 2);
+  c.mesh.nbr.assign(m->nbr, m->nbr + (size_t)c.E * 12);
+  std::vector<Ref1D> refs;
+  std::vector<LevelGeomHost> geo(c.cfg.n_levels);
+  try {
+    build_faces(c.mesh);
+    for (int l = 0; l < c.cfg.n_levels; ++l) {
+      refs.push_back(make_ref1d(c.cfg.P[l]));
+      build_level_geometry(c.mesh, refs[l], geo[l]);
+    }
+  } catch (const std::exception& ex) {
+    return fail(PMG_EINVAL, ex.what());
+  }
+  c.n_faces = (int)c.mesh.faces.size();
+  // face list followed by the neighbour table
+  std::vector<int> fbuf((size_t)c.n_faces * 5 + (size_t)c.E * 12);
+  for (int f = 0; f < c.n_faces; ++f) {
+    const FaceRec& r = c.mesh.faces[f];
+    int* o = &fbuf[(size_t)f * 5];
+    o[0] = r.eL; o[1] = r.fL; o[2] = r.eR; o[3] = r.fR; o[4] = r.rev;
+  }
+  memcpy(&fbuf[(size_t)c.n_faces * 5], c.mesh.nbr.data(), sizeof(int) * c.E * 12);
+  PMG_CK(dalloc(&c.d_faces, fbuf.size()));
+  PMG_CK(cudaMemcpy(c.d_faces, fbuf.data(), sizeof(int) * fbuf.size(), cudaMemcpyHostToDevice));
+  size_t maxtot = 0;
+  int maxblocks = 1;
+  size_t wbytes = c.cfg.block_prec == PMG_PREC_FP64 ? 8 : 4;
+  for (int l = 0; l < c.cfg.n_levels; ++l) {
+    LevelDev& L = c.lev[l];
+    const Ref1D& r = refs[l];
+    L.P = r.P; L.n1 = r.P + 1; L.N = L.n1 * L.n1; L.n = 4 * L.N;
+    L.tot = (size_t)4 * c.E * L.N;
+    maxtot = std::max(maxtot, L.tot);
+    memset(&L.op, 0, sizeof(L.op));
+    for (int i = 0; i < L.n1; ++i) {
+      for (int k = 0; k < L.n1; ++k) L.op.D[i][k] = r.D[i * L.n1 + k];
+      L.op.lm[i] = r.lm[i]; L.op.lp[i] = r.lp[i]; L.op.gL[i] = r.gL[i]; L.op.gR[i] = r.gR[i];
+    }
+    size_t nn2 = (size_t)c.E * L.n * L.n;
+    if (dalloc(&L.q, L.tot) || dalloc(&L.qb, L.tot) || dalloc(&L.S, L.tot) || dalloc(&L.F, L.tot) ||
+        dalloc(&L.Pd, L.tot) || dalloc(&L.met, geo[l].met.size()) || dalloc(&L.face, geo[l].face.size()) ||
+        dalloc(&L.Fcom, (size_t)4 * c.E * 4 * L.n1) || dalloc(&L.Dfull, nn2) ||
+        cudaMalloc(&L.Dinv, nn2 * wbytes) || dalloc(&L.rs, (size_t)c.E * L.n) || dalloc(&L.cs, (size_t)c.E * L.n))
+      return fail(PMG_ENOMEM, "device allocation failed for level data");
+    PMG_CK(cudaMemset(L.S, 0, L.tot * 8));
+    PMG_CK(cudaMemset(L.q, 0, L.tot * 8));
+    PMG_CK(cudaMemcpy(L.met, geo[l].met.data(), geo[l].met.size() * 8, cudaMemcpyHostToDevice));
+    PMG_CK(cudaMemcpy(L.face, geo[l].face.data(), geo[l].face.size() * 8, cudaMemcpyHostToDevice));
+    L.xy_host = geo[l].xy;
+    int blocks = (c.E * L.N + 31) / 32;   // upper bound on residual CTAs
+    maxblocks = std::max(maxblocks, blocks);
+  }
+  for (int l = 0; l + 1 < c.cfg.n_levels; ++l) {
+    std::vector<double> R, I;
+    make_transfer(refs[l], refs[l + 1], R, I);
+    int nf = refs[l].P + 1, nc = refs[l + 1].P + 1;
+    memset(&c.xfer[l], 0, sizeof(XferTab));
+    for (int i = 0; i < nc; ++i)
+      for (int q = 0; q < nf; ++q) c.xfer[l].R[i][q] = R[i * nf + q];
+    for (int i = 0; i < nf; ++i)
+      for (int k = 0; k < nc; ++k) c.xfer[l].I[i][k] = I[i * nc + k];
+  }
+  size_t tot0 = c.lev[0].tot;
+  c.tmp_size = maxtot;
+  if (dalloc(&c.src, tot0) || dalloc(&c.qn, tot0) || dalloc(&c.qcn, tot0) || dalloc(&c.d_tmp0, maxtot) ||
+      dalloc(&c.d_tmp1, maxtot) || dalloc(&c.d_partial, (size_t)maxblocks))
+    return fail(PMG_ENOMEM, "device allocation failed for stage data");
+  for (int j = 0; j < c.stages; ++j)
+    if (dalloc(&c.Rst[j], tot0)) return fail(PMG_ENOMEM, "device allocation failed for stage data");
+  PMG_CK(cudaMemset(c.src, 0, tot0 * 8));
+  c.n_partial = maxblocks;
+  PMG_CK(prepare_kernels(c));
+  c.mesh_ready = true;
+  return PMG_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ helpers
+static pmg_status check_level(const Ctx& c, int level) {
+  if (!c.mesh_ready) return fail(PMG_ESTATE, "mesh not uploaded");
+  if (level < 0 || level >= c.cfg.n_levels) return fail(PMG_EINVAL, "level out of range");
+  return PMG_OK;
+}
+
+static cudaError_t copy_in(const Ctx& c, double* dst, const double* src, size_t count, int on_device) {
+  return cudaMemcpyAsync(dst, src, count * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                         c.stream);
+}
+
+static cudaError_t copy_out(const Ctx& c, double* dst, const double* src, size_t count, int on_device) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, count * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  c.stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(c.stream);
+}
+
+static int residual_block_count(const Ctx& c, int l) { return residual_blocks_for(c.lev[l].P, c.E); }
+
+// ------------------------------------------------------------- profiler
+// Event pairs around individual launches (only outside graph capture).
+static void prof_harvest(Ctx& c) {
+  Profiler& p = c.prof;
+  if (p.used == 0) return;
+  cudaEventSynchronize(p.ev[2 * (p.used - 1) + 1]);
+  for (int k = 0; k < p.used; ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.ev[2 * k], p.ev[2 * k + 1]) == cudaSuccess) {
+      int cls = p.tag[k] / kMaxLevels, lvl = p.tag[k] % kMaxLevels;
+      p.ms[cls][lvl] += ms;
+      p.count[cls][lvl] += 1;
+    }
+  }
+  p.used = 0;
+}
+
+static int prof_begin(Ctx& c, int cls, int level) {
+  Profiler& p = c.prof;
+  if (!p.on) return -1;
+  if (p.used == (int)p.tag.size()) prof_harvest(c);
+  int k = p.used++;
+  p.tag[k] = cls * kMaxLevels + level;
+  cudaEventRecord(p.ev[2 * k], c.stream);
+  return k;
+}
+
+static void prof_end(Ctx& c, int k) {
+  if (k >= 0) cudaEventRecord(c.prof.ev[2 * k + 1], c.stream);
+}
+
+struct ProfScope {
+  Ctx& c;
+  int k;
+  ProfScope(Ctx& cc, int cls, int level) : c(cc), k(prof_begin(cc, cls, level)) {}
+  ~ProfScope() { prof_end(c, k); }
+};
+
+// Level system residual F_l(q_l) - S_l into lev[l].F (norm into d_scal[0] if asked).
+static void system_residual(Ctx& c, int l, bool norm) {
+  LevelDev& L = c.lev[l];
+  {
+    ProfScope ps(c, K_FACE, l);
+    launch_face_flux(c, L, L.q, c.stream);
+  }
+  {
+    ProfScope ps(c, K_VOLUME, l);
+    const double* qref = l > 0 ? L.qb : (c.split_stage ? c.qn : nullptr);
+    launch_volume(c, L, l, L.q, L.F, RES_SYSTEM, 1.0 / c.omega_dt, l == 0 ? c.src : nullptr, l > 0 ? L.S : nullptr,
+                  nullptr, nullptr, norm ? c.d_partial : nullptr, c.stream, qref);
+  }
+  if (norm) {
+    ProfScope ps(c, K_NORM, l);
+    launch_norm_final(c.d_partial, residual_block_count(c, l), c.d_scal, c.stream);
+  }
+}
+
+static void refresh_level(Ctx& c, int l) {
+  LevelDev& L = c.lev[l];
+  {
+    ProfScope ps(c, K_ASSEMBLE, l);
+    launch_assemble(c, L, L.q, c.d_dtau, 1.0 / c.omega_dt, c.stream);
+  }
+  {
+    ProfScope ps(c, K_FACTOR, l);
+    launch_factor(c, L, c.cfg.block_prec, c.d_flag, c.stream);
+  }
+  L.assembled = L.factored = true;
+}
+
+// n element-Jacobi sweeps q += D^-1 F with F kept equal to F_l(q) - S_l.
+static void sweeps(Ctx& c, int l, int n, bool final_residual, bool final_norm) {
+  LevelDev& L = c.lev[l];
+  for (int s = 0; s < n; ++s) {
+    {
+      ProfScope ps(c, K_APPLY, l);
+      launch_apply(c, L, c.cfg.block_prec, L.F, L.q, 1, c.stream);
+    }
+    if (s < n - 1) system_residual(c, l, false);
+    else if (final_residual) system_residual(c, l, final_norm);
+  }
+}
+
+// FAS V-cycle from level l (Section 3).  On entry lev[l].F = F_l(q) - S_l.
+static void vcycle_level(Ctx& c, int l, bool refresh) {
+  LevelDev& L = c.lev[l];
+  if (refresh) refresh_level(c, l);
+  const int nl = c.cfg.n_levels;
+  if (l == nl - 1) {
+    sweeps(c, l, c.cfg.n_smooth[l], false, false);
+    return;
+  }
+  sweeps(c, l, c.cfg.n_smooth[l], true, false);   // pre-smoothing, ends with F(q^a)
+  LevelDev& C = c.lev[l + 1];
+  const XferTab& X = c.xfer[l];
+  {
+    ProfScope ps(c, K_RESTRICT, l + 1);
+    launch_restrict(c, L, C, X, L.q, C.q, C.qb, 1.0, c.stream);       // q^b = P q^a
+    launch_restrict(c, L, C, X, L.F, C.Pd, nullptr, -1.0, c.stream);  // P d = -P (F - S)
+  }
+  {
+    ProfScope ps(c, K_FACE, l + 1);
+    launch_face_flux(c, C, C.q, c.stream);                             // S = F(q^b) + P d
+  }
+  {
+    ProfScope ps(c, K_VOLUME, l + 1);
+    launch_volume(c, C, l + 1, C.q, C.F, RES_FORCING, 1.0 / c.omega_dt, nullptr, nullptr, C.S, C.Pd, nullptr,
+                  c.stream, C.qb);
+  }
+  vcycle_level(c, l + 1, refresh);
+  {
+    ProfScope ps(c, K_PROLONG, l);
+    launch_prolong_add(c, L, C, X, C.q, C.qb, L.q, c.stream);         // q += I (q^a_c - q^b_c)
+  }
+  system_residual(c, l, false);
+  sweeps(c, l, c.cfg.n_smooth[l], l == 0, l == 0);                 // post-smoothing
+}
+
+static pmg_status launch_vcycle(Ctx& c, bool refresh) {
+  if (!c.cfg.use_graph || c.prof.on) {
+    vcycle_level(c, 0, refresh);
+    PMG_CK_LAUNCH();
+    return PMG_OK;
+  }
+  int g = refresh ? 1 : 0;
+  if (!c.graph[g] || c.graph_inv_odt[g] != 1.0 / c.omega_dt) {
+    if (c.graph[g]) { cudaGraphExecDestroy(c.graph[g]); c.graph[g] = nullptr; }
+    cudaGraph_t graph;
+    PMG_CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+    vcycle_level(c, 0, refresh);
+    cudaError_t le = cudaGetLastError();
+    cudaError_t ee = cudaStreamEndCapture(c.stream, &graph);
+    if (le != cudaSuccess) return fail(PMG_ECUDA, std::string("capture launch: ") + cudaGetErrorString(le));
+    if (ee != cudaSuccess) return fail(PMG_ECUDA, std::string("capture: ") + cudaGetErrorString(ee));
+    cudaError_t ie = cudaGraphInstantiate(&c.graph[g], graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return fail(PMG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+    c.graph_inv_odt[g] = 1.0 / c.omega_dt;
+  }
+  PMG_CK(cudaGraphLaunch(c.graph[g], c.stream));
+  return PMG_OK;
+}
+
+static pmg_status read_norm(Ctx& c, double* out) {
+  PMG_CK(cudaMemcpyAsync(c.h_scal, c.d_scal, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  PMG_CK(cudaStreamSynchronize(c.stream));
+  *out = std::sqrt(c.h_scal[0]);
+  if (c.prof.on) prof_harvest(c);
+  return PMG_OK;
+}
+
+static pmg_status set_dtau(Ctx& c, double dtau) {
+  // the pinned mirror is only rewritten after the stream has consumed it
+  PMG_CK(cudaStreamSynchronize(c.stream));
+  *c.h_dtau = dtau;
+  PMG_CK(cudaMemcpyAsync(c.d_dtau, c.h_dtau, sizeof(double), cudaMemcpyHostToDevice, c.stream));
+  return PMG_OK;
+}
+
+static pmg_status check_singular(Ctx& c) {
+  int flag = 0;
+  PMG_CK(cudaMemcpyAsync(&flag, c.d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  PMG_CK(cudaStreamSynchronize(c.stream));
+  if (flag) {
+    cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.stream);
+    return fail(PMG_ESINGULAR, "zero pivot in element block " + std::to_string(flag - 1));
+  }
+  return PMG_OK;
+}
+
+// Pseudo-transient continuation of the current stage (Section 2.4).
+static pmg_status stage_solve(Ctx& c, int* iters, double* drop, int* n_refresh) {
+  if (!c.F0_valid) {
+    system_residual(c, 0, true);
+    PMG_CK_LAUNCH();
+    c.F0_valid = true;
+  }
+  double nm;
+  pmg_status st = read_norm(c, &nm);
+  if (st) return st;
+  double n0 = nm, prev = nm, dtau = c.cfg.dtau_init, built = 0.0;
+  for (int m = 0;; ++m) {
+    if (m == 0) n0 = nm;
+    c.hist_norm.push_back(nm);
+    c.hist_dtau.push_back(m > 0 ? std::min(dtau * std::pow(prev / nm, 1.5), c.cfg.dtau_max) : dtau);
+    if (nm <= c.cfg.tol * n0 || n0 == 0.0) {
+      if (iters) *iters = m;
+      if (drop) *drop = n0 > 0 ? nm / n0 : 0.0;
+      return PMG_OK;
+    }
+    if (!std::isfinite(nm)) {
+      if (iters) *iters = m;
+      if (drop) *drop = nm;
+      return fail(PMG_ENONFINITE, "non-finite residual norm");
+    }
+    if (m >= c.cfg.max_pseudo) {
+      if (iters) *iters = m;
+      if (drop) *drop = nm / n0;
+      return fail(PMG_ENOTCONV, "stage not converged within max_pseudo V-cycles");
+    }
+    if (m > 0) dtau = std::min(dtau * std::pow(prev / nm, 1.5), c.cfg.dtau_max);
+    bool refresh = (m == 0) || (m % c.cfg.refresh_every == 0 && built < c.cfg.dtau_max);
+    if (refresh) {
+      built = dtau;
+      st = set_dtau(c, dtau);
+      if (st) return st;
+      if (n_refresh) ++*n_refresh;
+    }
+    st = launch_vcycle(c, refresh);
+    if (st) return st;
+    if (refresh) {
+      st = check_singular(c);
+      if (st) return st;
+    }
+    prev = nm;
+    st = read_norm(c, &nm);
+    if (st) return st;
+  }
+}
+
+extern "C" {
+
+pmg_status pmg_point_coords(pmg_ctx* h, int level, double* xy) {
+  if (!h || !xy) return fail(PMG_EINVAL, "null argument");
+  pmg_status st = check_level(h->c, level);
+  if (st) return st;
+  const LevelDev& L = h->c.lev[level];
+  memcpy(xy, L.xy_host.data(), L.xy_host.size() * 8);
+  return PMG_OK;
+}
+
+pmg_status pmg_set_state(pmg_ctx* h, int level, const double* q, int on_device) {
+  if (!h || !q) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  pmg_status st = check_level(c, level);
+  if (st) return st;
+  PMG_CK(copy_in(c, c.lev[level].q, q, c.lev[level].tot, on_device));
+  launch_shift_pressure(c.lev[level].tot / 4, -c.ph.p_ref, c.lev[level].q, c.stream);
+  PMG_CK_LAUNCH();
+  PMG_CK(cudaStreamSynchronize(c.stream));
+  if (level == 0) c.F0_valid = false;
+  return PMG_OK;
+}
+
+pmg_status pmg_get_state(pmg_ctx* h, int level, double* q, int on_device) {
+  if (!h || !q) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  pmg_status st = check_level(c, level);
+  if (st) return st;
+  const LevelDev& L = c.lev[level];
+  PMG_CK(cudaMemcpyAsync(c.d_tmp0, L.q, L.tot * 8, cudaMemcpyDeviceToDevice, c.stream));
+  launch_shift_pressure(L.tot / 4, c.ph.p_ref, c.d_tmp0, c.stream);
+  PMG_CK_LAUNCH();
+  PMG_CK(copy_out(c, q, c.d_tmp0, L.tot, on_device));
+  return PMG_OK;
+}
+
+pmg_status pmg_residual(pmg_ctx* h, int level, const double* q, double* R, int on_device) {
+  if (!h || !q || !R) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  pmg_status st = check_level(c, level);
+  if (st) return st;
+  LevelDev& L = c.lev[level];
+  PMG_CK(copy_in(c, c.d_tmp0, q, L.tot, on_device));
+  launch_shift_pressure(L.tot / 4, -c.ph.p_ref, c.d_tmp0, c.stream);
+  const double* qd = c.d_tmp0;
+  double* Rd = on_device ? R : c.d_tmp1;
+  launch_face_flux(c, L, qd, c.stream);
+  launch_volume(c, L, level, qd, Rd, RES_PURE, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr, c.stream);
+  PMG_CK_LAUNCH();
+  if (!on_device) PMG_CK(copy_out(c, R, Rd, L.tot, 0));
+  else PMG_CK(cudaStreamSynchronize(c.stream));
+  return PMG_OK;
+}
+
+pmg_status pmg_set_stage(pmg_ctx* h, const double* src, double omega_dt, int on_device) {
+  if (!h || !src) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  if (!c.mesh_ready) return fail(PMG_ESTATE, "mesh not uploaded");
+  if (!(omega_dt > 0.0)) return fail(PMG_EINVAL, "omega_dt must be positive");
+  PMG_CK(copy_in(c, c.src, src, c.lev[0].tot, on_device));
+  PMG_CK(cudaStreamSynchronize(c.stream));
+  c.omega_dt = omega_dt;
+  c.stage_ready = true;
+  c.split_stage = false;
+  c.F0_valid = false;
+  return PMG_OK;
+}
+
+pmg_status pmg_stage_residual(pmg_ctx* h, int level, const double* q, double* F, int on_device) {
+  if (!h || !q || !F) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  pmg_status st = check_level(c, level);
+  if (st) return st;
+  if (!c.stage_ready) return fail(PMG_ESTATE, "stage data not set");
+  LevelDev& L = c.lev[level];
+  PMG_CK(copy_in(c, c.d_tmp0, q, L.tot, on_device));
+  launch_shift_pressure(L.tot / 4, -c.ph.p_ref, c.d_tmp0, c.stream);
+  const double* qd = c.d_tmp0;
+  double* Fd = on_device ? F : c.d_tmp1;
+  launch_face_flux(c, L, qd, c.stream);
+  launch_volume(c, L, level, qd, Fd, RES_STAGEF, 1.0 / c.omega_dt, level == 0 ? c.src : nullptr, nullptr, nullptr,
+                nullptr, nullptr, c.stream);
+  PMG_CK_LAUNCH();
+  if (!on_device) PMG_CK(copy_out(c, F, Fd, L.tot, 0));
+  else PMG_CK(cudaStreamSynchronize(c.stream));
+  return PMG_OK;
+}
+
+pmg_status pmg_assemble_blocks(pmg_ctx* h, int level, double dtau) {
+  if (!h) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  if (!c.mesh_ready) return fail(PMG_ESTATE, "mesh not uploaded");
+  if (level < -1 || level >= c.cfg.n_levels) return fail(PMG_EINVAL, "level out of range");
+  if (!(dtau > 0.0)) return fail(PMG_EINVAL, "dtau must be positive");
+  pmg_status st = set_dtau(c, dtau);
+  if (st) return st;
+  for (int l = 0; l < c.cfg.n_levels; ++l) {
+    if (level >= 0 && l != level) continue;
+    launch_assemble(c, c.lev[l], c.lev[l].q, c.d_dtau, 1.0 / c.omega_dt, c.stream);
+    c.lev[l].assembled = true;
+    c.lev[l].factored = false;
+  }
+  PMG_CK_LAUNCH();
+  PMG_CK(cudaStreamSynchronize(c.stream));
+  return PMG_OK;
+}
+
+pmg_status pmg_get_blocks(pmg_ctx* h, int level, double* D, int on_device) {
+  if (!h || !D) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  pmg_status st = check_level(c, level);
+  if (st) return st;
+  if (!c.lev[level].assembled) return fail(PMG_ESTATE, "blocks not assembled");
+  const LevelDev& L = c.lev[level];
+  PMG_CK(copy_out(c, D, L.Dfull, (size_t)c.E * L.n * L.n, on_device));
+  return PMG_OK;
+}
+
+pmg_status pmg_factor_blocks(pmg_ctx* h, int level) {
+  if (!h) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  if (!c.mesh_ready) return fail(PMG_ESTATE, "mesh not uploaded");
+  if (level < -1 || level >= c.cfg.n_levels) return fail(PMG_EINVAL, "level out of range");
+  for (int l = 0; l < c.cfg.n_levels; ++l) {
+    if (level >= 0 && l != level) continue;
+    if (!c.lev[l].assembled) return fail(PMG_ESTATE, "blocks not assembled");
+    launch_factor(c, c.lev[l], c.cfg.block_prec, c.d_flag, c.stream);
+    c.lev[l].factored = true;
+  }
+  PMG_CK_LAUNCH();
+  return check_singular(c);
+}
+
+pmg_status pmg_apply_blocks(pmg_ctx* h, int level, const double* r, double* x, int on_device) {
+  if (!h || !r || !x) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  pmg_status st = check_level(c, level);
+  if (st) return st;
+  LevelDev& L = c.lev[level];
+  if (!L.factored) return fail(PMG_ESTATE, "blocks not factored");
+  const double* rd = r;
+  double* xd = x;
+  if (!on_device) {
+    PMG_CK(copy_in(c, c.d_tmp0, r, L.tot, 0));
+    rd = c.d_tmp0;
+    xd = c.d_tmp1;
+  }
+  launch_apply(c, L, c.cfg.block_prec, rd, xd, 0, c.stream);
+  PMG_CK_LAUNCH();
+  if (!on_device) PMG_CK(copy_out(c, x, xd, L.tot, 0));
+  else PMG_CK(cudaStreamSynchronize(c.stream));
+  return PMG_OK;
+}
+
+pmg_status pmg_restrict(pmg_ctx* h, int lf, const double* qf, double* qc, int on_device) {
+  if (!h || !qf || !qc) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  pmg_status st = check_level(c, lf);
+  if (st) return st;
+  if (lf + 1 >= c.cfg.n_levels) return fail(PMG_EINVAL, "no coarser level");
+  LevelDev& F = c.lev[lf];
+  LevelDev& C = c.lev[lf + 1];
+  const double* in = qf;
+  double* out = qc;
+  if (!on_device) {
+    PMG_CK(copy_in(c, c.d_tmp0, qf, F.tot, 0));
+    in = c.d_tmp0;
+    out = c.d_tmp1;
+  }
+  launch_restrict(c, F, C, c.xfer[lf], in, out, nullptr, 1.0, c.stream);
+  PMG_CK_LAUNCH();
+  if (!on_device) PMG_CK(copy_out(c, qc, out, C.tot, 0));
+  else PMG_CK(cudaStreamSynchronize(c.stream));
+  return PMG_OK;
+}
+
+pmg_status pmg_prolong(pmg_ctx* h, int lf, const double* qc, double* qf, int on_device) {
+  if (!h || !qf || !qc) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  pmg_status st = check_level(c, lf);
+  if (st) return st;
+  if (lf + 1 >= c.cfg.n_levels) return fail(PMG_EINVAL, "no coarser level");
+  LevelDev& F = c.lev[lf];
+  LevelDev& C = c.lev[lf + 1];
+  const double* in = qc;
+  double* out = qf;
+  if (!on_device) {
+    PMG_CK(copy_in(c, c.d_tmp0, qc, C.tot, 0));
+    in = c.d_tmp0;
+    out = c.d_tmp1;
+  }
+  launch_prolong(c, F, C, c.xfer[lf], in, out, c.stream);
+  PMG_CK_LAUNCH();
+  if (!on_device) PMG_CK(copy_out(c, qf, out, F.tot, 0));
+  else PMG_CK(cudaStreamSynchronize(c.stream));
+  return PMG_OK;
+}
+
+pmg_status pmg_vcycle(pmg_ctx* h, double dtau, int refresh, double* res_norm_out) {
+  if (!h) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  if (!c.mesh_ready) return fail(PMG_ESTATE, "mesh not uploaded");
+  if (!c.stage_ready) return fail(PMG_ESTATE, "stage data not set");
+  if (!(dtau > 0.0)) return fail(PMG_EINVAL, "dtau must be positive");
+  if (!refresh)
+    for (int l = 0; l < c.cfg.n_levels; ++l)
+      if (!c.lev[l].factored) return fail(PMG_ESTATE, "smoother not built: call with refresh = 1 first");
+  if (!c.F0_valid) {
+    system_residual(c, 0, true);
+    c.F0_valid = true;
+  }
+  double nm;
+  pmg_status st = read_norm(c, &nm);
+  if (st) return st;
+  if (res_norm_out) *res_norm_out = nm;
+  st = set_dtau(c, dtau);
+  if (st) return st;
+  st = launch_vcycle(c, refresh != 0);
+  if (st) return st;
+  if (refresh) {
+    st = check_singular(c);
+    if (st) return st;
+  }
+  PMG_CK(cudaStreamSynchronize(c.stream));
+  return PMG_OK;
+}
+
+pmg_status pmg_stage_solve(pmg_ctx* h, int* iters, double* drop) {
+  if (!h) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  if (!c.mesh_ready) return fail(PMG_ESTATE, "mesh not uploaded");
+  if (!c.stage_ready) return fail(PMG_ESTATE, "stage data not set");
+  c.hist_norm.clear();
+  c.hist_dtau.clear();
+  return stage_solve(c, iters, drop, nullptr);
+}
+
+pmg_status pmg_profile(pmg_ctx* h, int enable) {
+  if (!h) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  Profiler& p = c.prof;
+  PMG_CK(cudaStreamSynchronize(c.stream));
+  if (enable && p.ev.empty()) {
+    const int pairs = 4096;
+    p.ev.resize(2 * pairs);
+    p.tag.resize(pairs);
+    for (auto& e : p.ev) PMG_CK(cudaEventCreate(&e));
+  }
+  if (!enable && p.on) prof_harvest(c);
+  p.on = enable != 0;
+  if (enable) {
+    p.used = 0;
+    memset(p.ms, 0, sizeof(p.ms));
+    memset(p.count, 0, sizeof(p.count));
+  }
+  return PMG_OK;
+}
+
+pmg_status pmg_profile_read(pmg_ctx* h, double* ms, long long* counts) {
+  if (!h || !ms || !counts) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  PMG_CK(cudaStreamSynchronize(c.stream));
+  prof_harvest(c);
+  for (int k = 0; k < K_COUNT; ++k)
+    for (int l = 0; l < kMaxLevels; ++l) {
+      ms[k * kMaxLevels + l] = c.prof.ms[k][l];
+      counts[k * kMaxLevels + l] = c.prof.count[k][l];
+    }
+  return PMG_OK;
+}
+
+pmg_status pmg_stage_history(pmg_ctx* h, double* norms, double* dtau, int max_count, int* count) {
+  if (!h || !count) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  int n = (int)c.hist_norm.size();
+  *count = n;
+  for (int i = 0; i < n && i < max_count; ++i) {
+    if (norms) norms[i] = c.hist_norm[i];
+    if (dtau) dtau[i] = c.hist_dtau[i];
+  }
+  return PMG_OK;
+}
+
+pmg_status pmg_esdirk_step(pmg_ctx* h, double dt, pmg_step_stats* stats) {
+  if (!h) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  if (!c.mesh_ready) return fail(PMG_ESTATE, "mesh not uploaded");
+  if (!(dt > 0.0)) return fail(PMG_EINVAL, "dt must be positive");
+  pmg_step_stats local;
+  memset(&local, 0, sizeof(local));
+  cudaEvent_t ev0, ev1;
+  PMG_CK(cudaEventCreate(&ev0));
+  PMG_CK(cudaEventCreate(&ev1));
+  PMG_CK(cudaEventRecord(ev0, c.stream));
+  LevelDev& L0 = c.lev[0];
+  const int N0 = L0.N;
+  c.hist_norm.clear();
+  c.hist_dtau.clear();
+  PMG_CK(cudaMemcpyAsync(c.qn, L0.q, L0.tot * 8, cudaMemcpyDeviceToDevice, c.stream));
+  {
+    ProfScope ps(c, K_FACE, 0);
+    launch_face_flux(c, L0, L0.q, c.stream);
+  }
+  {
+    ProfScope ps(c, K_VOLUME, 0);
+    launch_volume(c, L0, 0, L0.q, c.Rst[0], RES_PURE, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr, c.stream);
+  }
+  PMG_CK_LAUNCH();
+  const double omega = c.A[1][1];
+  c.omega_dt = omega * dt;
+  c.stage_ready = true;
+  c.split_stage = true;   // level-0 system uses q_c(q) - q_c(q^n) and src = sum_j a_ij R^j / omega
+  pmg_status st = PMG_OK;
+  for (int i = 1; i < c.stages; ++i) {
+    double a[6];
+    for (int j = 0; j < i; ++j) a[j] = c.A[i][j];
+    {
+      ProfScope ps(c, K_STAGE, 0);
+      launch_stage_src(c, N0, nullptr, c.Rst, a, i, dt, 1.0 / c.omega_dt, c.src, c.stream);
+    }
+    c.F0_valid = false;
+    int it = 0;
+    double dr = 0.0;
+    st = stage_solve(c, &it, &dr, &local.n_refresh);
+    local.pseudo_iters[i - 1] = it;
+    local.res_drop[i - 1] = dr;
+    local.n_vcycles += it;
+    if (st) break;
+    {
+      ProfScope ps(c, K_FACE, 0);
+      launch_face_flux(c, L0, L0.q, c.stream);
+    }
+    {
+      ProfScope ps(c, K_VOLUME, 0);
+      launch_volume(c, L0, 0, L0.q, c.Rst[i], RES_PURE, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr, c.stream);
+    }
+  }
+  if (st == PMG_OK) {
+    ProfScope ps(c, K_STAGE, 0);
+    launch_bsum_update(c, N0, c.qn, c.Rst, c.b, c.stages, dt, L0.q, c.stream);
+    PMG_CK_LAUNCH();
+  }
+  c.F0_valid = false;
+  PMG_CK(cudaEventRecord(ev1, c.stream));
+  PMG_CK(cudaEventSynchronize(ev1));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  local.ms_total = ms;
+  if (c.prof.on) prof_harvest(c);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  if (stats) *stats = local;
+  return st;
+}
+
+}  // extern "C"

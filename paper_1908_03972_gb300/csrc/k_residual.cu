@@ -1,0 +1,298 @@
+// k_residual.cu -- FP64 FR/CPR residual on the GPU (Section 2.3).
+//
+// Two launches per evaluation:
+//  * face_flux: one thread per face flux point.  It extrapolates both
+//    neighbouring solution polynomials along the line normal to the face,
+//    evaluates the preconditioned Roe flux once and writes it, with opposite
+//    signs, into both elements' face slots (no atomics, exact conservation).
+//  * volume: one thread per solution point, several elements per CTA.
+//    Contravariant fluxes go to shared memory; the Lagrange derivative, the
+//    face jumps (common minus extrapolated flux polynomial) and the DG
+//    correction are applied there, followed by the epilogue of the requested
+//    mode (pure R, level system residual, FAS forcing) and an optional
+//    deterministic per-CTA sum of squares for the residual norm.
+//
+// Both kernels are bound by FP64 arithmetic on GB300 (about 1.2 TFLOP/s).
+#include "pmg_internal.h"
+
+namespace pmg {
+
+template <int P>
+struct ElemsPerBlock {
+  static constexpr int N = (P + 1) * (P + 1);
+  static constexpr int value = (P == 0) ? 128 : 256 / N;
+};
+
+// Trace of the solution polynomial along the line through face point k of
+// face f, extrapolated from the line's solution points minus a reference
+// value ref[v] (the weights sum to one, so trace = ref + returned value).
+// Subtracting a common reference before the sum keeps the rounding of
+// p ~ T ~ 1/Ma^2 out of the jumps p+ - p-, T+ - T- that the preconditioned
+// dissipation amplifies.
+template <int P>
+__device__ __forceinline__ void line_trace(const double* __restrict__ q, size_t plane, int e, int f, int k,
+                                           const double* lm, const double* lp, const double ref[4],
+                                           double out[4]) {
+  constexpr int n1 = P + 1, N = n1 * n1;
+  const bool plus = (f == 1 || f == 2);
+  const bool eta = (f == 0 || f == 2);
+  const double* base = q + (size_t)e * N + (eta ? k : k * n1);
+  const int stride = eta ? n1 : 1;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    double s = 0.0;
+#pragma unroll
+    for (int m = 0; m < n1; ++m) s = fma(plus ? lp[m] : lm[m], __ldg(base + v * plane + m * stride) - ref[v], s);
+    out[v] = s;
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) face_flux_kernel(const int* __restrict__ faces, int n_faces, int E,
+                                                        const double* __restrict__ q,
+                                                        const double* __restrict__ face,
+                                                        double* __restrict__ Fcom, OpTab op, Phys ph) {
+  constexpr int n1 = P + 1, N = n1 * n1;
+  int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= n_faces * n1) return;
+  int fc = tid / n1, k = tid - fc * n1;
+  const int* fr = faces + fc * 5;
+  int eL = fr[0], fL = fr[1], eR = fr[2], fR = fr[3], rev = fr[4];
+  int kR = rev ? P - k : k;
+  size_t plane = (size_t)E * N;
+  double lm[n1], lp[n1];
+#pragma unroll
+  for (int m = 0; m < n1; ++m) { lm[m] = op.lm[m]; lp[m] = op.lp[m]; }
+  // reference: (gauge) pressure and temperature at the left element's first solution point
+  double ref[4] = {__ldg(q + (size_t)eL * N), 0.0, 0.0, __ldg(q + 3 * plane + (size_t)eL * N)};
+  double sm[4], sp[4];
+  line_trace<P>(q, plane, eL, fL, k, lm, lp, ref, sm);
+  line_trace<P>(q, plane, eR, fR, kR, lm, lp, ref, sp);
+  double qm[4], qp[4], dq[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    qm[v] = ref[v] + sm[v];
+    qp[v] = ref[v] + sp[v];
+    dq[v] = sp[v] - sm[v];
+  }
+  qm[0] += ph.p_ref;   // absolute pressure for the fluxes and the averaged state
+  qp[0] += ph.p_ref;
+  const double* g = face + (((size_t)eL * 4 + fL) * n1 + k) * 3;
+  double out[4];
+  roe_flux_jump(qm, qp, dq, __ldg(g), __ldg(g + 1), __ldg(g + 2), ph, out);
+  size_t fplane = (size_t)E * 4 * n1;
+  size_t iL = ((size_t)eL * 4 + fL) * n1 + k, iR = ((size_t)eR * 4 + fR) * n1 + kR;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    Fcom[v * fplane + iL] = out[v];
+    Fcom[v * fplane + iR] = -out[v];
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) volume_kernel(int E, const double* __restrict__ q,
+                                                     const double* __restrict__ met,
+                                                     const double* __restrict__ Fcom, OpTab op, Phys ph,
+                                                     double* __restrict__ out, int mode, double inv_odt,
+                                                     const double* __restrict__ src,
+                                                     const double* __restrict__ S, double* __restrict__ Sout,
+                                                     const double* __restrict__ Pd,
+                                                     const double* __restrict__ qn,
+                                                     double* __restrict__ partial) {
+  constexpr int n1 = P + 1, N = n1 * n1, EPB = ElemsPerBlock<P>::value;
+  __shared__ double sFt[EPB][4][N];
+  __shared__ double sGt[EPB][4][N];
+  __shared__ double sJ[EPB][4][4][n1];   // [face][var][k]
+  __shared__ double sD[n1][n1], sgL[n1], sgR[n1], slm[n1], slp[n1];
+  __shared__ double sred[256 / 32];
+
+  const int le = threadIdx.x / N, pt = threadIdx.x - le * N;
+  const int e = blockIdx.x * EPB + le;
+  const bool active = (le < EPB) && (e < E);
+  const size_t plane = (size_t)E * N;
+  if (threadIdx.x < n1 * n1) sD[threadIdx.x / n1][threadIdx.x % n1] = op.D[threadIdx.x / n1][threadIdx.x % n1];
+  if (threadIdx.x < n1) {
+    sgL[threadIdx.x] = op.gL[threadIdx.x];
+    sgR[threadIdx.x] = op.gR[threadIdx.x];
+    slm[threadIdx.x] = op.lm[threadIdx.x];
+    slp[threadIdx.x] = op.lp[threadIdx.x];
+  }
+
+  double qq[4] = {0, 0, 0, 0}, invJ = 0.0;
+  size_t gi = (size_t)e * N + pt;
+  if (active) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) qq[v] = __ldg(q + v * plane + gi);
+    double a = __ldg(met + gi), b = __ldg(met + plane + gi);
+    double c = __ldg(met + 2 * plane + gi), d = __ldg(met + 3 * plane + gi);
+    invJ = __ldg(met + 4 * plane + gi);
+    double qa[4] = {qq[0] + ph.p_ref, qq[1], qq[2], qq[3]};   // absolute pressure
+    double f[4], g[4];
+    flux_xy(qa, ph, f, g);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      sFt[le][v][pt] = fma(a, f[v], b * g[v]);
+      sGt[le][v][pt] = fma(c, f[v], d * g[v]);
+    }
+  }
+  __syncthreads();
+  if (active) {
+    // face jumps: common (reference-direction) minus extrapolated flux polynomial
+    const size_t fplane = (size_t)E * 4 * n1;
+    for (int it = pt; it < 16 * n1; it += N) {
+      int f = it / (4 * n1), r = it - f * 4 * n1, v = r / n1, k = r - v * n1;
+      const bool xi = (f == 1 || f == 3);
+      const bool plus = (f == 1 || f == 2);
+      double loc = 0.0;
+#pragma unroll
+      for (int m = 0; m < n1; ++m) {
+        double fv = xi ? sFt[le][v][k * n1 + m] : sGt[le][v][m * n1 + k];
+        loc = fma(plus ? slp[m] : slm[m], fv, loc);
+      }
+      double com = __ldg(Fcom + v * fplane + ((size_t)e * 4 + f) * n1 + k);
+      sJ[le][f][v][k] = (plus ? com : -com) - loc;
+    }
+  }
+  __syncthreads();
+  double ssq = 0.0;
+  if (active) {
+    const int i = pt % n1, j = pt / n1;
+    double qc[4];
+    if (qn) {
+      // q_c(q) - q_c(q_ref) with the energy difference taken through
+      // rho E = p/(gamma-1) + rho|v|^2/2 and the gauge pressures, so that no
+      // p ~ rho E ~ 1/Ma^2 is rounded (q_ref = q^n on the finest level, q^b on
+      // coarser levels, where the constant q_c(q^b)/(omega dt) cancels in F - S)
+      double qo[4] = {__ldg(qn + gi), __ldg(qn + plane + gi), __ldg(qn + 2 * plane + gi), __ldg(qn + 3 * plane + gi)};
+      double rho = (qq[0] + ph.p_ref) / qq[3], rhoo = (qo[0] + ph.p_ref) / qo[3];
+      qc[0] = rho - rhoo;
+      qc[1] = rho * qq[1] - rhoo * qo[1];
+      qc[2] = rho * qq[2] - rhoo * qo[2];
+      qc[3] = (qq[0] - qo[0]) / ph.gm1 +
+              0.5 * (rho * (qq[1] * qq[1] + qq[2] * qq[2]) - rhoo * (qo[1] * qo[1] + qo[2] * qo[2]));
+    } else {
+      double qa[4] = {qq[0] + ph.p_ref, qq[1], qq[2], qq[3]};
+      cons(qa, ph, qc);
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      double acc = 0.0;
+#pragma unroll
+      for (int m = 0; m < n1; ++m) {
+        acc = fma(sD[i][m], sFt[le][v][j * n1 + m], acc);
+        acc = fma(sD[j][m], sGt[le][v][m * n1 + i], acc);
+      }
+      acc = fma(sgL[i], sJ[le][3][v][j], acc);
+      acc = fma(sgR[i], sJ[le][1][v][j], acc);
+      acc = fma(sgL[j], sJ[le][0][v][i], acc);
+      acc = fma(sgR[j], sJ[le][2][v][i], acc);
+      double R = -acc * invJ;
+      size_t o = v * plane + gi;
+      if (mode == RES_PURE) {
+        out[o] = R;
+      } else if (mode == RES_FORCING) {
+        double Fraw = fma(-qc[v], inv_odt, R);
+        double pd = Pd[o];
+        Sout[o] = Fraw + pd;
+        out[o] = -pd;
+        ssq = fma(pd, pd, ssq);
+      } else {
+        double F = fma(-qc[v], inv_odt, R);
+        if (src) F += src[o];
+        if (mode == RES_SYSTEM && S) F -= S[o];
+        out[o] = F;
+        ssq = fma(F, F, ssq);
+      }
+    }
+  }
+  if (partial) {
+    // deterministic block sum of squares
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) ssq += __shfl_down_sync(0xffffffffu, ssq, off);
+    if ((threadIdx.x & 31) == 0) sred[threadIdx.x >> 5] = ssq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) s += sred[w];
+      partial[blockIdx.x] = s;
+    }
+  }
+}
+
+__global__ void norm_final_kernel(const double* __restrict__ partial, int n, double* __restrict__ out) {
+  __shared__ double s[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) acc += partial[i];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = s[0];
+}
+
+// Whole warps only: threads beyond EPB * N idle (the block reduction uses
+// full-warp shuffles).
+int residual_threads_per_block(int P) {
+  int t;
+  switch (P) {
+    case 0: t = ElemsPerBlock<0>::value * 1; break;
+    case 1: t = ElemsPerBlock<1>::value * 4; break;
+    case 2: t = ElemsPerBlock<2>::value * 9; break;
+    case 3: t = ElemsPerBlock<3>::value * 16; break;
+    default: t = ElemsPerBlock<4>::value * 25; break;
+  }
+  return (t + 31) / 32 * 32;
+}
+
+static int elems_per_block(int P) {
+  switch (P) {
+    case 0: return ElemsPerBlock<0>::value;
+    case 1: return ElemsPerBlock<1>::value;
+    case 2: return ElemsPerBlock<2>::value;
+    case 3: return ElemsPerBlock<3>::value;
+    default: return ElemsPerBlock<4>::value;
+  }
+}
+
+int residual_blocks_for(int P, int E) { int epb = elems_per_block(P); return (E + epb - 1) / epb; }
+
+void launch_face_flux(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s) {
+  int total = c.n_faces * L.n1;
+  int threads = 128, blocks = (total + threads - 1) / threads;
+#define PMG_FACE(PP) face_flux_kernel<PP><<<blocks, threads, 0, s>>>(c.d_faces, c.n_faces, c.E, q, L.face, L.Fcom, L.op, c.ph)
+  switch (L.P) {
+    case 0: PMG_FACE(0); break;
+    case 1: PMG_FACE(1); break;
+    case 2: PMG_FACE(2); break;
+    case 3: PMG_FACE(3); break;
+    default: PMG_FACE(4); break;
+  }
+#undef PMG_FACE
+}
+
+void launch_volume(const Ctx& c, const LevelDev& L, int level, const double* q, double* out, ResMode mode,
+                   double inv_odt, const double* src, const double* S, double* Sout, const double* Pd,
+                   double* partial, cudaStream_t s, const double* qn) {
+  (void)level;
+  int threads = residual_threads_per_block(L.P);
+  int blocks = residual_blocks_for(L.P, c.E);
+#define PMG_VOL(PP)                                                                                   \
+  volume_kernel<PP><<<blocks, threads, 0, s>>>(c.E, q, L.met, L.Fcom, L.op, c.ph, out, (int)mode, inv_odt, \
+                                               src, S, Sout, Pd, qn, partial)
+  switch (L.P) {
+    case 0: PMG_VOL(0); break;
+    case 1: PMG_VOL(1); break;
+    case 2: PMG_VOL(2); break;
+    case 3: PMG_VOL(3); break;
+    default: PMG_VOL(4); break;
+  }
+#undef PMG_VOL
+}
+
+void launch_norm_final(const double* partial, int n, double* out, cudaStream_t s) {
+  norm_final_kernel<<<1, 256, 0, s>>>(partial, n, out);
+}
+
+}  // namespace pmg

@@ -1,0 +1,168 @@
+// pmg_internal.h -- internal data structures of libpmgfr.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pmgfr.h"
+#include "physics.cuh"
+
+namespace pmg {
+
+constexpr int kMaxP = 4;
+constexpr int kMaxLevels = 8;
+
+// ----------------------------------------------------------------- host side
+struct Ref1D {
+  int P;
+  std::vector<double> x, w, D, lm, lp, gL, gR;
+};
+
+struct FaceRec {
+  int eL, fL, eR, fR, rev;
+};
+
+struct MeshHost {
+  int E = 0, Ng = 0;
+  std::vector<double> nodes;
+  std::vector<int> nbr;
+  std::vector<FaceRec> faces;
+};
+
+struct LevelGeomHost {
+  std::vector<double> met;   // 5 planes of E*N: a, b, c, d, 1/|J|
+  std::vector<double> xy;    // (E, N, 2)
+  std::vector<double> face;  // (E, 4, n1, 3): unit outward normal, area factor
+};
+
+Ref1D make_ref1d(int P);
+void make_transfer(const Ref1D& f, const Ref1D& c, std::vector<double>& R, std::vector<double>& I);
+void build_faces(MeshHost& m);
+void build_level_geometry(const MeshHost& m, const Ref1D& r, LevelGeomHost& g);
+
+// --------------------------------------------------------------- device side
+// Operator tables of one level, passed to kernels by value.
+struct OpTab {
+  double D[kMaxP + 1][kMaxP + 1];
+  double lm[kMaxP + 1], lp[kMaxP + 1], gL[kMaxP + 1], gR[kMaxP + 1];
+};
+
+// Restriction (nc x nf) and prolongation (nf x nc) 1D operators, by value.
+struct XferTab {
+  double R[kMaxP + 1][kMaxP + 1];
+  double I[kMaxP + 1][kMaxP + 1];
+};
+
+struct LevelDev {
+  int P = 0, n1 = 0, N = 0, n = 0;
+  size_t tot = 0;              // 4 * E * N
+  OpTab op;
+  double* q = nullptr;         // state
+  double* qb = nullptr;        // state at entry of the level in the V-cycle
+  double* S = nullptr;         // FAS forcing
+  double* F = nullptr;         // level system residual F_l(q) - S_l
+  double* Pd = nullptr;        // restricted defect (coarse levels)
+  double* met = nullptr;       // 5 * E * N
+  double* face = nullptr;      // E * 4 * n1 * 3
+  double* Fcom = nullptr;      // 4 * E * 4 * n1 common fluxes, outward
+  double* Dfull = nullptr;     // E * n * n assembled FP64 blocks (row-major)
+  void* Dinv = nullptr;        // E * n * n factored inverse (column-major), FP32 or FP64
+  double* rs = nullptr;        // E * n row scales
+  double* cs = nullptr;        // E * n column scales
+  bool assembled = false, factored = false;
+  std::vector<double> xy_host;
+};
+
+// Residual kernel epilogues.
+enum ResMode : int {
+  RES_PURE = 0,     // out = R
+  RES_SYSTEM = 1,   // out = -q_c/(omega dt) + R (+ src) - S   (level system residual)
+  RES_FORCING = 2,  // S = -q_c/(omega dt) + R + Pd;  out = -Pd
+  RES_STAGEF = 3    // out = -q_c/(omega dt) + R (+ src), no S
+};
+
+// Kernel classes timed by the optional per-launch event profiler.
+enum KClass : int { K_FACE = 0, K_VOLUME, K_APPLY, K_ASSEMBLE, K_FACTOR, K_RESTRICT, K_PROLONG, K_NORM, K_STAGE,
+                    K_COUNT };
+
+struct Profiler {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;       // pairs (start, end)
+  std::vector<int> tag;              // class * kMaxLevels + level of each pair
+  int used = 0;                      // pairs recorded since the last harvest
+  double ms[K_COUNT][kMaxLevels] = {};
+  long long count[K_COUNT][kMaxLevels] = {};
+};
+
+struct Ctx {
+  pmg_config cfg;
+  Profiler prof;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  Phys ph;
+  MeshHost mesh;
+  bool mesh_ready = false;
+  int E = 0, n_faces = 0;
+  int* d_faces = nullptr;      // n_faces * 5
+  LevelDev lev[kMaxLevels];
+  XferTab xfer[kMaxLevels];
+  // stage data (finest level)
+  double* src = nullptr;
+  double* qn = nullptr;        // state at the start of the physical step
+  double* qcn = nullptr;       // conservative state at the start of the step
+  double* Rst[6] = {nullptr};  // R(q^j) of the stages
+  double omega_dt = 1.0;
+  bool stage_ready = false;
+  bool split_stage = false;    // src holds sum_j a_ij R^j / omega and q^n is in qn
+  std::vector<double> hist_norm, hist_dtau;   // pseudo-iteration history of the last step
+  bool F0_valid = false;       // lev[0].F holds F_0(q) for the current q
+  // reductions
+  double* d_partial = nullptr; // per-block partial sums
+  int n_partial = 0;
+  double* d_scal = nullptr;    // device scalars: [0] ||F||^2, [1] status flags
+  double* h_scal = nullptr;    // pinned host mirror
+  int* d_flag = nullptr;       // singular-pivot / error flags
+  // scratch vectors for API calls with host or device I/O
+  double* d_tmp0 = nullptr;
+  double* d_tmp1 = nullptr;
+  size_t tmp_size = 0;
+  // CUDA graphs of the V-cycle (0: plain, 1: with refresh)
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  double graph_inv_odt[2] = {0.0, 0.0};
+  double* d_dtau = nullptr;    // pseudo time step read by the assembly kernel
+  double* h_dtau = nullptr;
+  // ESDIRK3 tableau
+  double A[6][6], b[6], c[6];
+  int stages = 4;
+};
+
+// ---------------------------------------------------------- kernel launchers
+void launch_face_flux(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s);
+void launch_volume(const Ctx& c, const LevelDev& L, int level, const double* q, double* out, ResMode mode,
+                   double inv_odt, const double* src, const double* S, double* Sout, const double* Pd,
+                   double* partial, cudaStream_t s, const double* qn = nullptr);
+void launch_norm_final(const double* partial, int n, double* out, cudaStream_t s);
+void launch_assemble(const Ctx& c, const LevelDev& L, const double* q, const double* d_dtau, double inv_odt,
+                     cudaStream_t s);
+void launch_factor(const Ctx& c, LevelDev& L, int prec, int* flag, cudaStream_t s);
+void launch_apply(const Ctx& c, const LevelDev& L, int prec, const double* r, double* x, int accumulate,
+                  cudaStream_t s);
+void launch_restrict(const Ctx& c, const LevelDev& Lf, const LevelDev& Lc, const XferTab& X, const double* in,
+                     double* out, double* out2, double scale, cudaStream_t s);
+void launch_prolong_add(const Ctx& c, const LevelDev& Lf, const LevelDev& Lc, const XferTab& X, const double* qc,
+                        const double* qcb, double* qf, cudaStream_t s);
+void launch_prolong(const Ctx& c, const LevelDev& Lf, const LevelDev& Lc, const XferTab& X, const double* in,
+                    double* out, cudaStream_t s);
+void launch_cons(const Ctx& c, int N, const double* q, double* qc, cudaStream_t s);
+void launch_stage_src(const Ctx& c, int N, const double* qcn, double* const* R, const double* a, int nr,
+                      double dt, double inv_odt, double* src, cudaStream_t s);
+void launch_bsum_update(const Ctx& c, int N, const double* qn, double* const* R, const double* b, int nr,
+                        double dt, double* q, cudaStream_t s);
+void launch_shift_pressure(size_t plane, double delta, double* q, cudaStream_t s);
+int residual_threads_per_block(int P);
+int residual_blocks_for(int P, int E);
+cudaError_t prepare_kernels(const Ctx& c);
+
+}  // namespace pmg

@@ -1,0 +1,393 @@
+"""Python binding of libpmgfr (argument marshalling only).
+
+Functions carry the names of the C interface in ``include/pmgfr.h``.  Arrays
+may be NumPy arrays (host memory) or CUDA ``torch.Tensor`` objects (device
+memory on the context's device); every computation runs in the library's
+CUDA kernels.  There is no CPU fallback: if the library is missing the import
+of this module's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libpmgfr.so")
+
+PMG_OK = 0
+PMG_EINVAL, PMG_ENOMEM, PMG_ECUDA, PMG_ESINGULAR, PMG_ENONFINITE, PMG_ENOTCONV, PMG_ESTATE = (
+    -1, -2, -3, -4, -5, -6, -8)
+PMG_PREC_FP64, PMG_PREC_FP32 = 0, 1
+
+
+class PmgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libpmgfr status {status}: {msg}")
+        self.status = status
+
+
+class pmg_config(ctypes.Structure):
+    _fields_ = [
+        ("n_levels", ctypes.c_int),
+        ("P", ctypes.c_int * 8),
+        ("n_smooth", ctypes.c_int * 8),
+        ("gamma", ctypes.c_double),
+        ("Ma_inf", ctypes.c_double),
+        ("kappa", ctypes.c_double),
+        ("cutoff", ctypes.c_int),
+        ("dtau_init", ctypes.c_double),
+        ("dtau_max", ctypes.c_double),
+        ("tol", ctypes.c_double),
+        ("refresh_every", ctypes.c_int),
+        ("max_pseudo", ctypes.c_int),
+        ("block_prec", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+        ("p_gauge", ctypes.c_double),
+    ]
+
+
+class pmg_mesh(ctypes.Structure):
+    _fields_ = [
+        ("n_elem", ctypes.c_int),
+        ("geom_order", ctypes.c_int),
+        ("nodes", ctypes.POINTER(ctypes.c_double)),
+        ("nbr", ctypes.POINTER(ctypes.c_int)),
+    ]
+
+
+class pmg_step_stats(ctypes.Structure):
+    _fields_ = [
+        ("pseudo_iters", ctypes.c_int * 8),
+        ("res_drop", ctypes.c_double * 8),
+        ("ms_total", ctypes.c_double),
+        ("n_vcycles", ctypes.c_int),
+        ("n_refresh", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def load():
+    """Load libpmgfr.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libpmgfr.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    pd = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "pmg_create": ([ctypes.POINTER(pmg_config), vp, ctypes.POINTER(vp)], ci),
+        "pmg_destroy": ([vp], None),
+        "pmg_last_error": ([], ctypes.c_char_p),
+        "pmg_upload_mesh": ([vp, ctypes.POINTER(pmg_mesh)], ci),
+        "pmg_point_coords": ([vp, ci, pd], ci),
+        "pmg_set_state": ([vp, ci, vp, ci], ci),
+        "pmg_get_state": ([vp, ci, vp, ci], ci),
+        "pmg_residual": ([vp, ci, vp, vp, ci], ci),
+        "pmg_set_stage": ([vp, vp, cd, ci], ci),
+        "pmg_stage_residual": ([vp, ci, vp, vp, ci], ci),
+        "pmg_assemble_blocks": ([vp, ci, cd], ci),
+        "pmg_get_blocks": ([vp, ci, vp, ci], ci),
+        "pmg_factor_blocks": ([vp, ci], ci),
+        "pmg_apply_blocks": ([vp, ci, vp, vp, ci], ci),
+        "pmg_restrict": ([vp, ci, vp, vp, ci], ci),
+        "pmg_prolong": ([vp, ci, vp, vp, ci], ci),
+        "pmg_vcycle": ([vp, cd, ci, pd], ci),
+        "pmg_stage_solve": ([vp, ctypes.POINTER(ci), pd], ci),
+        "pmg_esdirk_step": ([vp, cd, ctypes.POINTER(pmg_step_stats)], ci),
+        "pmg_stage_history": ([vp, pd, pd, ci, ctypes.POINTER(ci)], ci),
+        "pmg_profile": ([vp, ci], ci),
+        "pmg_profile_read": ([vp, pd, ctypes.POINTER(ctypes.c_longlong)], ci),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != PMG_OK:
+        raise PmgError(status, load().pmg_last_error().decode())
+
+
+def _ptr(x, writable=False):
+    """(pointer, on_device) of a NumPy array or CUDA torch tensor."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError("host arrays must be C-contiguous float64")
+        if writable and not x.flags["WRITEABLE"]:
+            raise TypeError("output array is read-only")
+        return ctypes.c_void_p(x.ctypes.data), 0
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        return ctypes.c_void_p(x.data_ptr()), 1 if x.is_cuda else 0
+    raise TypeError("expected numpy.ndarray or torch.Tensor")
+
+
+def make_config(P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutoff=0, dtau_init=0.01,
+                dtau_max=10.0, tol=1e-8, refresh_every=10, max_pseudo=2000, block_prec=PMG_PREC_FP64,
+                use_graph=1, p_gauge=0.0) -> pmg_config:
+    cfg = pmg_config()
+    cfg.n_levels = len(P_levels)
+    for l, (P, n) in enumerate(zip(P_levels, n_smooth)):
+        cfg.P[l] = P
+        cfg.n_smooth[l] = n
+    cfg.gamma, cfg.Ma_inf, cfg.kappa, cfg.cutoff = gamma, Ma_inf, kappa, cutoff
+    cfg.dtau_init, cfg.dtau_max, cfg.tol = dtau_init, dtau_max, tol
+    cfg.refresh_every, cfg.max_pseudo = refresh_every, max_pseudo
+    cfg.block_prec, cfg.use_graph = block_prec, use_graph
+    cfg.p_gauge = p_gauge
+    return cfg
+
+
+def pmg_create(cfg: pmg_config, stream=None):
+    h = ctypes.c_void_p()
+    s = ctypes.c_void_p(stream) if stream else None
+    _check(load().pmg_create(ctypes.byref(cfg), s, ctypes.byref(h)))
+    return h
+
+
+def pmg_destroy(h):
+    if h:
+        load().pmg_destroy(h)
+
+
+def pmg_upload_mesh(h, nodes, nbr):
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+    nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+    nn = nodes.shape[1]
+    Ng = int(round(nn ** 0.5)) - 1
+    m = pmg_mesh(nodes.shape[0], Ng, nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                 nbr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    _check(load().pmg_upload_mesh(h, ctypes.byref(m)))
+
+
+def pmg_point_coords(h, level, E, N):
+    xy = np.zeros((E, N, 2))
+    _check(load().pmg_point_coords(h, level, xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return xy
+
+
+def pmg_set_state(h, level, q):
+    p, dev = _ptr(q)
+    _check(load().pmg_set_state(h, level, p, dev))
+
+
+def pmg_get_state(h, level, out):
+    p, dev = _ptr(out, True)
+    _check(load().pmg_get_state(h, level, p, dev))
+    return out
+
+
+def pmg_residual(h, level, q, out):
+    pq, d1 = _ptr(q)
+    pr, d2 = _ptr(out, True)
+    if d1 != d2:
+        raise TypeError("q and R must both be host or both device arrays")
+    _check(load().pmg_residual(h, level, pq, pr, d1))
+    return out
+
+
+def pmg_set_stage(h, src, omega_dt):
+    p, dev = _ptr(src)
+    _check(load().pmg_set_stage(h, p, float(omega_dt), dev))
+
+
+def pmg_stage_residual(h, level, q, out):
+    pq, d1 = _ptr(q)
+    pr, d2 = _ptr(out, True)
+    if d1 != d2:
+        raise TypeError("q and F must both be host or both device arrays")
+    _check(load().pmg_stage_residual(h, level, pq, pr, d1))
+    return out
+
+
+def pmg_assemble_blocks(h, level, dtau):
+    _check(load().pmg_assemble_blocks(h, level, float(dtau)))
+
+
+def pmg_get_blocks(h, level, out):
+    p, dev = _ptr(out, True)
+    _check(load().pmg_get_blocks(h, level, p, dev))
+    return out
+
+
+def pmg_factor_blocks(h, level):
+    _check(load().pmg_factor_blocks(h, level))
+
+
+def pmg_apply_blocks(h, level, r, out):
+    pr, d1 = _ptr(r)
+    px, d2 = _ptr(out, True)
+    if d1 != d2:
+        raise TypeError("r and x must both be host or both device arrays")
+    _check(load().pmg_apply_blocks(h, level, pr, px, d1))
+    return out
+
+
+def pmg_restrict(h, lf, qf, out):
+    pa, d1 = _ptr(qf)
+    pb, d2 = _ptr(out, True)
+    if d1 != d2:
+        raise TypeError("mixed host/device arguments")
+    _check(load().pmg_restrict(h, lf, pa, pb, d1))
+    return out
+
+
+def pmg_prolong(h, lf, qc, out):
+    pa, d1 = _ptr(qc)
+    pb, d2 = _ptr(out, True)
+    if d1 != d2:
+        raise TypeError("mixed host/device arguments")
+    _check(load().pmg_prolong(h, lf, pa, pb, d1))
+    return out
+
+
+def pmg_vcycle(h, dtau, refresh=True):
+    nm = ctypes.c_double()
+    _check(load().pmg_vcycle(h, float(dtau), int(refresh), ctypes.byref(nm)))
+    return nm.value
+
+
+def pmg_stage_solve(h):
+    it = ctypes.c_int()
+    dr = ctypes.c_double()
+    _check(load().pmg_stage_solve(h, ctypes.byref(it), ctypes.byref(dr)))
+    return it.value, dr.value
+
+
+def pmg_esdirk_step(h, dt, raise_on_error=True):
+    st = pmg_step_stats()
+    status = load().pmg_esdirk_step(h, float(dt), ctypes.byref(st))
+    if raise_on_error:
+        _check(status)
+    return st if raise_on_error else (status, st)
+
+
+def pmg_stage_history(h):
+    n = ctypes.c_int()
+    _check(load().pmg_stage_history(h, None, None, 0, ctypes.byref(n)))
+    norms = np.zeros(max(n.value, 1))
+    dtau = np.zeros(max(n.value, 1))
+    pd = ctypes.POINTER(ctypes.c_double)
+    _check(load().pmg_stage_history(h, norms.ctypes.data_as(pd), dtau.ctypes.data_as(pd), n.value, ctypes.byref(n)))
+    return norms[: n.value], dtau[: n.value]
+
+
+class Solver:
+    """Owns one context: mesh, levels and stage data (convenience wrapper)."""
+
+    def __init__(self, nodes, nbr, P_levels, n_smooth, stream=None, **cfg_kw):
+        self.cfg = make_config(P_levels, n_smooth, **cfg_kw)
+        self.P = list(P_levels)
+        self.E = int(np.asarray(nodes).shape[0])
+        self.h = None
+        self.h = pmg_create(self.cfg, stream)
+        pmg_upload_mesh(self.h, nodes, nbr)
+
+    def close(self):
+        if self.h is not None:
+            pmg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def N(self, level=0):
+        return (self.P[level] + 1) ** 2
+
+    def shape(self, level=0):
+        return (4, self.E, self.N(level))
+
+    def n(self, level=0):
+        return 4 * self.N(level)
+
+    def coords(self, level=0):
+        return pmg_point_coords(self.h, level, self.E, self.N(level))
+
+    def set_state(self, q, level=0):
+        pmg_set_state(self.h, level, q)
+
+    def get_state(self, level=0):
+        return pmg_get_state(self.h, level, np.zeros(self.shape(level)))
+
+    def residual(self, q, level=0):
+        return pmg_residual(self.h, level, np.ascontiguousarray(q, dtype=np.float64), np.zeros(self.shape(level)))
+
+    def set_stage(self, src, omega_dt):
+        pmg_set_stage(self.h, np.ascontiguousarray(src, dtype=np.float64), omega_dt)
+
+    def stage_F(self, q, level=0):
+        return pmg_stage_residual(self.h, level, np.ascontiguousarray(q, dtype=np.float64),
+                                  np.zeros(self.shape(level)))
+
+    def blocks(self, q, dtau, level=0):
+        self.set_state(np.ascontiguousarray(q, dtype=np.float64), level)
+        pmg_assemble_blocks(self.h, level, dtau)
+        n = self.n(level)
+        return pmg_get_blocks(self.h, level, np.zeros((self.E, n, n)))
+
+    def factor(self, level=0):
+        pmg_factor_blocks(self.h, level)
+
+    def apply(self, r, level=0):
+        return pmg_apply_blocks(self.h, level, np.ascontiguousarray(r, dtype=np.float64),
+                                np.zeros(self.shape(level)))
+
+    def restrict(self, qf, lf):
+        return pmg_restrict(self.h, lf, np.ascontiguousarray(qf, dtype=np.float64), np.zeros(self.shape(lf + 1)))
+
+    def prolong(self, qc, lf):
+        return pmg_prolong(self.h, lf, np.ascontiguousarray(qc, dtype=np.float64), np.zeros(self.shape(lf)))
+
+    def vcycle(self, q, dtau, refresh=True):
+        self.set_state(np.ascontiguousarray(q, dtype=np.float64))
+        nm = pmg_vcycle(self.h, dtau, refresh)
+        return self.get_state(), nm
+
+    def stage_solve(self, q):
+        self.set_state(np.ascontiguousarray(q, dtype=np.float64))
+        it, dr = pmg_stage_solve(self.h)
+        return self.get_state(), it, dr
+
+    def esdirk_step(self, q, dt):
+        self.set_state(np.ascontiguousarray(q, dtype=np.float64))
+        st = pmg_esdirk_step(self.h, dt)
+        return self.get_state(), st
+
+
+def pmg_last_error() -> str:
+    return load().pmg_last_error().decode()
+
+
+PROF_CLASSES = ["face_flux", "volume", "apply", "assemble", "factor", "restrict", "prolong", "norm", "stage"]
+
+
+def pmg_profile(h, enable=True):
+    _check(load().pmg_profile(h, int(enable)))
+
+
+def pmg_profile_read(h):
+    """{(class, level): (ms, launches)} of the per-launch profiler."""
+    ms = np.zeros(len(PROF_CLASSES) * 8)
+    cnt = np.zeros(len(PROF_CLASSES) * 8, dtype=np.int64)
+    _check(load().pmg_profile_read(h, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong))))
+    out = {}
+    for k, name in enumerate(PROF_CLASSES):
+        for l in range(8):
+            if cnt[k * 8 + l]:
+                out[(name, l)] = (float(ms[k * 8 + l]), int(cnt[k * 8 + l]))
+    return out
