@@ -256,8 +256,27 @@ def run_ours(args, wl, world, rank, local):
         torch.cuda.synchronize(device)
         return e0.elapsed_time(e1), st
 
+    if args.ncu_window:
+        # Profiling window for ncu: the stage-2 system of the first step and
+        # N V-cycles of it (99.9% of a step's launches are V-cycle launches).
+        s = solver
+        A = 1767732205903.0 / 4055673282236.0
+        odt = A * wl["dt"]
+        pmgfr.pmg_set_state(s.h, 0, q0_dev)
+        R = s.residual(q0)
+        rho = q0[0] / q0[3]
+        qc = np.stack([rho, rho * q0[1], rho * q0[2], rho * (q0[3] / 0.4 + 0.5 * (q0[1] ** 2 + q0[2] ** 2))])
+        s.set_stage((qc + wl["dt"] * A * R) / odt, odt)
+        s.set_state(q0)
+        norms = [pmgfr.pmg_vcycle(s.h, 0.01 if k == 0 else 1.0, k % 10 == 0) for k in range(args.ncu_window)]
+        torch.cuda.synchronize(device)
+        if rank == 0:
+            print(json.dumps({"ncu_window_vcycles": args.ncu_window, "first_norm": norms[0], "last_norm": norms[-1]}))
+        solver.close()
+        return 0
+
     results = {}
-    for prec, label, warm in ((pmgfr.PMG_PREC_FP32, "mixed", args.warmup), (pmgfr.PMG_PREC_FP64, "fp64", 1)):
+    for prec, label, warm in ((pmgfr.PMG_PREC_FP32, "mixed", args.warmup), (pmgfr.PMG_PREC_FP64, "fp64", 0)):
         if args.skip_fp64 and label == "fp64":
             continue
         s = solver if label == "mixed" else make(prec)
@@ -393,6 +412,8 @@ def main():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--ncu-window", type=int, default=0,
+                    help="profiling helper: run N V-cycles of the first stage and exit (no bench line)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     wl = WORKLOADS[args.workload]
