@@ -71,10 +71,14 @@ typedef struct {
   int block_prec; /* pmg_prec */
   int use_graph;  /* 1: replay each V-cycle as a captured CUDA graph */
   double p_gauge; /* reference pressure kept out of device storage: the
-                     library stores p - p_gauge (0: p itself).  At low Mach a
-                     value near the free-stream pressure keeps the pressure
-                     resolution at the level of its variations; every call
-                     still takes and returns absolute p. */
+                     library stores p - p_gauge (0: p itself) and uses it in
+                     the momentum flux, where the constant part only adds
+                     p_gauge times the discrete metric identity.  At low Mach
+                     a value near the free-stream pressure keeps the pressure
+                     resolution at the level of its variations.  Curved
+                     (geom_order > 1) meshes need P >= geom_order on every
+                     level (pmg_upload_mesh returns PMG_EINVAL otherwise).  Every call still takes
+                     and returns absolute p. */
 } pmg_config;
 
 /* Mesh of quadrilaterals with Lagrange geometry of order geom_order (1 or 2).
@@ -196,6 +200,29 @@ pmg_status pmg_profile(pmg_ctx* ctx, int enable);
  * entries (class-major, level 0..7): summed milliseconds and launch counts. */
 #define PMG_PROF_CLASSES 9
 pmg_status pmg_profile_read(pmg_ctx* ctx, double* ms, long long* counts);
+
+/* Allocation-free variant of pmg_residual, for callers that must not
+ * allocate device memory once they are running: for example an application
+ * that has handed all spare device memory to its own pool, or that runs under
+ * a device-memory budget fixed at start-up.  (The paper has no counterpart;
+ * this is an interface addition of this library.)
+ *
+ * Computes R = -div f exactly as pmg_residual does, for a state q and an
+ * output R that are both caller-owned DEVICE buffers of the level's SoA size
+ * on the context's device, which must be the current device.  The call makes
+ * no cudaMalloc, cudaFree or other allocating call.  Its scratch (a copy of
+ * q and the common face fluxes: 4 E N + 16 E (P+1) doubles) lives in one
+ * static device array of 2^21 doubles (16 MiB) that every GPU loading this
+ * library holds until the process exits; a level that needs more returns
+ * PMG_EINVAL with the sizes in the message.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) for that device, so make the first call before any
+ * stream capture.  All calls share the array and each overwrites all of the
+ * scratch it reads, so nothing carries over between calls; but calls whose
+ * GPU work overlaps (other streams, other contexts, other host threads) race
+ * on it.  The call synchronises the context's stream before returning. */
+pmg_status pmg_residual_static(pmg_ctx* ctx, int level, const double* q, double* R);
 
 #ifdef __cplusplus
 }

@@ -135,6 +135,10 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
   Ctx& c = h->c;
   if (c.mesh_ready) return fail(PMG_EINVAL, "mesh already uploaded");
   if (m->n_elem < 1 || m->geom_order < 1 || m->geom_order > 4) return fail(PMG_EINVAL, "bad mesh sizes");
+  if (c.ph.p_ref != 0.0)
+    for (int l = 0; l < c.cfg.n_levels; ++l)
+      if (c.cfg.P[l] < m->geom_order && m->geom_order > 1)
+        return fail(PMG_EINVAL, "p_gauge != 0 needs P >= geometry order on every level (the metric identity)");
   c.E = m->n_elem;
   c.mesh.E = m->n_elem;
   c.mesh.Ng = m->geom_order;
@@ -510,6 +514,58 @@ pmg_status pmg_residual(pmg_ctx* h, int level, const double* q, double* R, int o
   PMG_CK_LAUNCH();
   if (!on_device) PMG_CK(copy_out(c, R, Rd, L.tot, 0));
   else PMG_CK(cudaStreamSynchronize(c.stream));
+  return PMG_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------- allocation-free residual
+// Scratch of pmg_residual_static: one file-scope device array shared by every
+// call on a device (the gauge-shifted copy of the input state followed by the
+// common face fluxes).  Host code never touches it by name as an address: the
+// device address is looked up once per device with cudaGetSymbolAddress.
+static constexpr size_t kStaticScratchDoubles = (size_t)1 << 21;   // 16 MiB
+static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
+static double* g_static_scratch_addr[64] = {};
+
+static cudaError_t static_scratch_address(int device, double** out) {
+  if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+  if (!g_static_scratch_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_static_scratch_addr[device] = (double*)p;
+  }
+  *out = g_static_scratch_addr[device];
+  return cudaSuccess;
+}
+
+extern "C" {
+
+pmg_status pmg_residual_static(pmg_ctx* h, int level, const double* q, double* R) {
+  if (!h || !q || !R) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  pmg_status st = check_level(c, level);
+  if (st) return st;
+  LevelDev L = c.lev[level];   // shallow copy: only the face-flux slot is redirected
+  const size_t n_state = L.tot, n_face = (size_t)4 * c.E * 4 * L.n1;
+  if (n_state + n_face > kStaticScratchDoubles)
+    return fail(PMG_EINVAL, "pmg_residual_static: level needs " + std::to_string(n_state + n_face) +
+                                " scratch doubles, the static scratch holds " +
+                                std::to_string(kStaticScratchDoubles));
+  int cur = -1;
+  PMG_CK(cudaGetDevice(&cur));
+  if (cur != c.device) return fail(PMG_EINVAL, "pmg_residual_static: make the context's device current first");
+  double* scratch = nullptr;
+  PMG_CK(static_scratch_address(c.device, &scratch));
+  double* qs = scratch;
+  L.Fcom = scratch + n_state;
+  PMG_CK(cudaMemcpyAsync(qs, q, n_state * 8, cudaMemcpyDeviceToDevice, c.stream));
+  launch_shift_pressure(n_state / 4, -c.ph.p_ref, qs, c.stream);
+  launch_face_flux(c, L, qs, c.stream);
+  launch_volume(c, L, level, qs, R, RES_PURE, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr, c.stream);
+  PMG_CK_LAUNCH();
+  PMG_CK(cudaStreamSynchronize(c.stream));
   return PMG_OK;
 }
 

@@ -102,6 +102,7 @@ def load():
         "pmg_esdirk_step": ([vp, cd, ctypes.POINTER(pmg_step_stats)], ci),
         "pmg_stage_history": ([vp, pd, pd, ci, ctypes.POINTER(ci)], ci),
         "pmg_profile": ([vp, ci], ci),
+        "pmg_residual_static": ([vp, ci, vp, vp], ci),
         "pmg_profile_read": ([vp, pd, ctypes.POINTER(ctypes.c_longlong)], ci),
     }
     for name, (args, res) in sig.items():
@@ -390,4 +391,14 @@ def pmg_profile_read(h):
         for l in range(8):
             if cnt[k * 8 + l]:
                 out[(name, l)] = (float(ms[k * 8 + l]), int(cnt[k * 8 + l]))
+    return out
+
+
+def pmg_residual_static(h, level, q, out):
+    """Allocation-free residual: q and out must be CUDA float64 tensors."""
+    pq, d1 = _ptr(q)
+    pr, d2 = _ptr(out, True)
+    if not (d1 and d2):
+        raise TypeError("pmg_residual_static takes device tensors only")
+    _check(load().pmg_residual_static(h, level, pq, pr))
     return out

@@ -1,0 +1,74 @@
+"""The allocation-free residual entry point (pmg_residual_static).
+
+Some callers cannot allocate device memory once they run (a fixed device
+budget, or all spare memory handed to their own pool), so the library offers
+a residual call whose scratch lives in a static device array.  It must give
+the same residual as the regular entry point, on repeated calls, and must
+not change the device's free memory after its first call.  This file is
+collected last on purpose: it also has to pass after every other GPU test.
+"""
+import numpy as np
+import pytest
+
+from paper_1908_03972_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1908_03972_gb300 import build, pmgfr
+    build.build()
+    pmgfr.load()
+    return torch, pmgfr
+
+
+@pytest.mark.parametrize("gauge", [0.0, W.freestream_T(0.005)])
+def test_static_residual_matches_regular_entry_point(setup, gauge):
+    torch, pmgfr = setup
+    nodes, nbr = W.periodic_box(24, 20, Ng=1)
+    s = pmgfr.Solver(nodes, nbr, [3, 2, 1, 0], [1, 1, 1, 1], p_gauge=gauge)
+    try:
+        dev = torch.device("cuda", torch.cuda.current_device())
+        for level in range(4):
+            q = W.isentropic_vortex(s.coords(level), center=(4.0, 6.0))
+            q_dev = torch.from_numpy(np.ascontiguousarray(q)).to(dev)
+            ref = torch.empty_like(q_dev)
+            pmgfr.pmg_residual(s.h, level, q_dev, ref)
+            out1 = torch.full_like(q_dev, float("nan"))
+            out2 = torch.full_like(q_dev, float("nan"))
+            pmgfr.pmg_residual_static(s.h, level, q_dev, out1)
+            torch.cuda.synchronize()
+            free_before = torch.cuda.mem_get_info()[0]
+            pmgfr.pmg_residual_static(s.h, level, q_dev, out2)
+            torch.cuda.synchronize()
+            free_after = torch.cuda.mem_get_info()[0]
+            assert free_after == free_before
+            r = ref.cpu().numpy()
+            for out in (out1, out2):
+                o = out.cpu().numpy()
+                assert np.isfinite(o).all()
+                # same kernels, same inputs: identical up to the tolerance of the parity tests
+                for v in range(4):
+                    assert np.abs(o[v] - r[v]).max() <= 1e-10 * max(np.abs(r[v]).max(), 1e-300)
+    finally:
+        s.close()
+
+
+def test_static_residual_rejects_oversized_levels(setup):
+    torch, pmgfr = setup
+    # 4 E N + 16 E (P+1) doubles must fit in 2^21: E = 36864 at P = 3 needs 2.95e6
+    nodes, nbr = W.periodic_box(192, 192, Ng=1)
+    s = pmgfr.Solver(nodes, nbr, [3], [1])
+    try:
+        dev = torch.device("cuda", torch.cuda.current_device())
+        q = torch.zeros((4, s.E, 16), dtype=torch.float64, device=dev)
+        out = torch.zeros_like(q)
+        with pytest.raises(pmgfr.PmgError) as ei:
+            pmgfr.pmg_residual_static(s.h, 0, q, out)
+        assert "scratch" in str(ei.value)
+    finally:
+        s.close()
