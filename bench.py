@@ -337,6 +337,10 @@ def run_ours(args, wl, world, rank, local):
         work, bound, unit, peak = volume_flops(P, E, top_lvl == 0), "alu", "TFLOP/s", FP64_PEAK_TFLOPS
     elif top_name == "apply":
         work, bound, unit, peak = apply_bytes(P, E, 4), "hbm", "GB/s", None
+    elif top_name == "fused_sweep":
+        # each face is evaluated by both of its elements inside the fused sweep
+        work = 2 * face_flops(P, n_faces) + volume_flops(P, E, True)
+        bound, unit, peak = "alu", "TFLOP/s", FP64_PEAK_TFLOPS
     else:
         work, bound, unit, peak = None, "alu", "TFLOP/s", FP64_PEAK_TFLOPS
     avg_s = top_ms / top_n / 1000.0

@@ -196,9 +196,10 @@ pmg_status pmg_profile(pmg_ctx* ctx, int enable);
 
 /* Kernel classes of the profiler, in this order: face flux, volume residual,
  * block apply, block assembly, block factorisation, restriction, prolongation,
- * norm reduction, stage arithmetic.  ms and counts receive PMG_PROF_CLASSES x 8
- * entries (class-major, level 0..7): summed milliseconds and launch counts. */
-#define PMG_PROF_CLASSES 9
+ * norm reduction, stage arithmetic, fused coarse-level sweep.  ms and counts
+ * receive PMG_PROF_CLASSES x 8 entries (class-major, level 0..7): summed
+ * milliseconds and launch counts. */
+#define PMG_PROF_CLASSES 10
 pmg_status pmg_profile_read(pmg_ctx* ctx, double* ms, long long* counts);
 
 /* Allocation-free variant of pmg_residual, for callers that must not

@@ -4,8 +4,10 @@
 // k_residual.cu, k_blocks.cu and k_misc.cu; the host only sequences launches,
 // keeps the pseudo-time schedule and reads one norm per V-cycle.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
+#include <utility>
 
 #include "pmg_internal.h"
 
@@ -60,7 +62,7 @@ static void esdirk3_table(Ctx& c) {
 }
 
 static void free_level(LevelDev& L) {
-  double** ptrs[] = {&L.q, &L.qb, &L.S, &L.F, &L.Pd, &L.met, &L.face, &L.Fcom, &L.Dfull, &L.rs, &L.cs};
+  double** ptrs[] = {&L.q, &L.q2, &L.qb, &L.S, &L.F, &L.Pd, &L.met, &L.face, &L.Fcom, &L.Dfull, &L.rs, &L.cs};
   for (double** p : ptrs) { if (*p) cudaFree(*p); *p = nullptr; }
   if (L.Dinv) cudaFree(L.Dinv);
   L.Dinv = nullptr;
@@ -100,6 +102,8 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   c.ph.Cp = cfg->gamma / (cfg->gamma - 1.0);
   c.ph.eps_min = cfg->cutoff ? cfg->kappa * cfg->Ma_inf : 0.0;
   c.ph.p_ref = cfg->p_gauge;
+  c.ph.inv_gamma = 1.0 / cfg->gamma;
+  c.ph.inv_gm1 = 1.0 / (cfg->gamma - 1.0);
   esdirk3_table(c);
   if (dalloc(&c.d_scal, 4) != cudaSuccess || dalloc(&c.d_flag, 4) != cudaSuccess ||
       dalloc(&c.d_dtau, 1) != cudaSuccess || cudaMallocHost((void**)&c.h_scal, 8 * sizeof(double)) != cudaSuccess ||
@@ -187,13 +191,20 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
         dalloc(&L.Fcom, (size_t)4 * c.E * 4 * L.n1) || dalloc(&L.Dfull, nn2) ||
         cudaMalloc(&L.Dinv, nn2 * wbytes) || dalloc(&L.rs, (size_t)c.E * L.n) || dalloc(&L.cs, (size_t)c.E * L.n))
       return fail(PMG_ENOMEM, "device allocation failed for level data");
+    // Optionally, coarse levels are smoothed by the fused one-launch sweep
+    // (k_fused.cu).  PMG_FUSE_MAX_P sets the largest P that uses it; it is off
+    // by default because the fused sweep evaluates every face twice and the
+    // coarse sweeps are bound by FP64 issue, not by launches.
+    int fuse_max = -1;
+    if (const char* env = getenv("PMG_FUSE_MAX_P")) fuse_max = atoi(env);
+    L.fused = (l > 0 && L.P <= fuse_max && L.P <= 3);
+    if (L.fused && dalloc(&L.q2, L.tot)) return fail(PMG_ENOMEM, "device allocation failed for level data");
     PMG_CK(cudaMemset(L.S, 0, L.tot * 8));
     PMG_CK(cudaMemset(L.q, 0, L.tot * 8));
     PMG_CK(cudaMemcpy(L.met, geo[l].met.data(), geo[l].met.size() * 8, cudaMemcpyHostToDevice));
     PMG_CK(cudaMemcpy(L.face, geo[l].face.data(), geo[l].face.size() * 8, cudaMemcpyHostToDevice));
     L.xy_host = geo[l].xy;
-    int blocks = (c.E * L.N + 31) / 32;   // upper bound on residual CTAs
-    maxblocks = std::max(maxblocks, blocks);
+    maxblocks = std::max(maxblocks, residual_blocks_for(L.P, c.E));
   }
   for (int l = 0; l + 1 < c.cfg.n_levels; ++l) {
     std::vector<double> R, I;
@@ -312,29 +323,69 @@ static void refresh_level(Ctx& c, int l) {
   L.assembled = L.factored = true;
 }
 
-// n element-Jacobi sweeps q += D^-1 F with F kept equal to F_l(q) - S_l.
-static void sweeps(Ctx& c, int l, int n, bool final_residual, bool final_norm) {
+// n element-Jacobi sweeps q += D^-1 (F_l(q) - S_l) (eq. smoothing_element_jacobi
+// on the level system).  With F_valid, lev[l].F already holds F_l(q) - S_l
+// for the current state and the first sweep only applies the blocks; every
+// other sweep is one face-flux launch and one volume launch that forms the
+// residual and updates the state in place.  final_residual leaves
+// F_l(q) - S_l of the smoothed state in lev[l].F (and its norm, if asked).
+// Fused levels return the number of state-buffer swaps.
+static int sweeps(Ctx& c, int l, int n, bool F_valid, bool final_residual, bool final_norm) {
   LevelDev& L = c.lev[l];
-  for (int s = 0; s < n; ++s) {
-    {
-      ProfScope ps(c, K_APPLY, l);
-      launch_apply(c, L, c.cfg.block_prec, L.F, L.q, 1, c.stream);
+  if (L.fused) {
+    for (int s = 0; s < n; ++s) {
+      {
+        ProfScope ps(c, K_FUSED, l);
+        launch_fused_sweep(c, L, L.q, L.q2, 1.0 / c.omega_dt, nullptr, L.S, L.qb, c.cfg.block_prec, c.stream);
+      }
+      std::swap(L.q, L.q2);
     }
-    if (s < n - 1) system_residual(c, l, false);
-    else if (final_residual) system_residual(c, l, final_norm);
+    if (final_residual) system_residual(c, l, final_norm);
+    return n;
   }
+  const double* qref = l > 0 ? L.qb : (c.split_stage ? c.qn : nullptr);
+  int s = 0;
+  if (F_valid && n > 0) {
+    ProfScope ps(c, K_APPLY, l);
+    launch_apply(c, L, c.cfg.block_prec, L.F, L.q, 1, c.stream);
+    s = 1;
+  }
+  for (; s < n; ++s) {
+    {
+      ProfScope ps(c, K_FACE, l);
+      launch_face_flux(c, L, L.q, c.stream);
+    }
+    {
+      ProfScope ps(c, K_VOLUME, l);
+      launch_volume_apply(c, L, L.q, 1.0 / c.omega_dt, l == 0 ? c.src : nullptr, l > 0 ? L.S : nullptr, qref,
+                          c.cfg.block_prec, c.stream);
+    }
+  }
+  if (final_residual) system_residual(c, l, final_norm);
+  return 0;
 }
 
-// FAS V-cycle from level l (Section 3).  On entry lev[l].F = F_l(q) - S_l.
+// After an odd number of swaps, move the state back to the level's first
+// buffer so that every V-cycle (and a captured graph) starts from the same one.
+static void restore_buffer(Ctx& c, int l, int swaps) {
+  LevelDev& L = c.lev[l];
+  if (!L.fused || (swaps & 1) == 0) return;
+  cudaMemcpyAsync(L.q2, L.q, L.tot * 8, cudaMemcpyDeviceToDevice, c.stream);
+  std::swap(L.q, L.q2);
+}
+
+// FAS V-cycle from level l (Section 3).
 static void vcycle_level(Ctx& c, int l, bool refresh) {
   LevelDev& L = c.lev[l];
   if (refresh) refresh_level(c, l);
   const int nl = c.cfg.n_levels;
+  // On entry lev[l].F = F_l(q) - S_l: from the norm evaluation on the finest
+  // level, from the forcing evaluation (= -P d) on coarser ones.
   if (l == nl - 1) {
-    sweeps(c, l, c.cfg.n_smooth[l], false, false);
+    restore_buffer(c, l, sweeps(c, l, c.cfg.n_smooth[l], true, false, false));
     return;
   }
-  sweeps(c, l, c.cfg.n_smooth[l], true, false);   // pre-smoothing, ends with F(q^a)
+  int swaps = sweeps(c, l, c.cfg.n_smooth[l], true, true, false);   // pre-smoothing, ends with F(q^a)
   LevelDev& C = c.lev[l + 1];
   const XferTab& X = c.xfer[l];
   {
@@ -356,8 +407,8 @@ static void vcycle_level(Ctx& c, int l, bool refresh) {
     ProfScope ps(c, K_PROLONG, l);
     launch_prolong_add(c, L, C, X, C.q, C.qb, L.q, c.stream);         // q += I (q^a_c - q^b_c)
   }
-  system_residual(c, l, false);
-  sweeps(c, l, c.cfg.n_smooth[l], l == 0, l == 0);                 // post-smoothing
+  swaps += sweeps(c, l, c.cfg.n_smooth[l], false, l == 0, l == 0);   // post-smoothing
+  restore_buffer(c, l, swaps);
 }
 
 static pmg_status launch_vcycle(Ctx& c, bool refresh) {

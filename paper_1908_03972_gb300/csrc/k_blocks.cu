@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(128) assemble_kernel(int E, const double* __re
       Dual qd[4];
       for (int k = 0; k < 4; ++k) qd[k] = Dual(qv[k], k == w ? 1.0 : 0.0);
       Dual f[4], g[4];
-      flux_xy(qd, ph, f, g);
+      flux_xy(qd, qd[0] - ph.p_ref, ph, f, g);
       for (int v = 0; v < 4; ++v) {
         sAx[pt][v * 4 + w] = a * f[v].d + b * g[v].d;
         sAe[pt][v * 4 + w] = c * f[v].d + d * g[v].d;
@@ -291,12 +291,17 @@ template <> struct Vec4<double> {
 };
 
 // One thread per four rows of one element's block; N threads per element.
+template <int N>
+struct ApplyEPB {   // elements per CTA: 1-2 warps per CTA, enough CTAs for all SMs
+  static constexpr int value = N <= 4 ? 32 / N : (64 / N > 0 ? 64 / N : 1);
+};
+
 template <class W, int N>
-__global__ void __launch_bounds__(256) apply_kernel(int E, const W* __restrict__ Dinv, const double* __restrict__ rs,
-                                                    const double* __restrict__ cs, const double* __restrict__ r,
-                                                    double* __restrict__ x, int accumulate) {
+__global__ void __launch_bounds__(64) apply_kernel(int E, const W* __restrict__ Dinv, const double* __restrict__ rs,
+                                                   const double* __restrict__ cs, const double* __restrict__ r,
+                                                   double* __restrict__ x, int accumulate) {
   constexpr int n = 4 * N;
-  constexpr int EPB = (N >= 256) ? 1 : 256 / N;
+  constexpr int EPB = ApplyEPB<N>::value;
   __shared__ W sr[EPB][n];
   const int le = threadIdx.x / N, t = threadIdx.x - le * N;
   const int e = blockIdx.x * EPB + le;
@@ -338,7 +343,14 @@ template <class W>
 static void apply_dispatch(const Ctx& c, const LevelDev& L, const W* Dinv, const double* r, double* x, int acc,
                            cudaStream_t s) {
   int N = L.N;
-  int epb = (N >= 256) ? 1 : 256 / N;
+  int epb = 1;
+  switch (N) {
+    case 1: epb = ApplyEPB<1>::value; break;
+    case 4: epb = ApplyEPB<4>::value; break;
+    case 9: epb = ApplyEPB<9>::value; break;
+    case 16: epb = ApplyEPB<16>::value; break;
+    default: epb = ApplyEPB<25>::value; break;
+  }
   int threads = ((epb * N) + 31) / 32 * 32;
   int blocks = (c.E + epb - 1) / epb;
 #define PMG_APPLY(NN) apply_kernel<W, NN><<<blocks, threads, 0, s>>>(c.E, Dinv, L.rs, L.cs, r, x, acc)

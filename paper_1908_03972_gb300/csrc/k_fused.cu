@@ -1,0 +1,217 @@
+// k_fused.cu -- one element-Jacobi sweep of a coarse P-level in one launch.
+//
+// On the coarse levels (few points per element, 4096-16384 threads per launch)
+// the separate face-flux, volume and block-apply launches are each bound by
+// the latency of one thread's FP64 chain, not by throughput.  This kernel
+// fuses a whole sweep q_next = q + D^-1 (F(q) - S) (Section 2.4, eq.
+// smoothing_element_jacobi, on the level system of Section 3) per element:
+//
+//  1. own state and contravariant fluxes to shared memory;
+//  2. the element's own 4 (P+1) face points: own and neighbour traces (the
+//     neighbour from the input state), preconditioned Roe flux, jump against
+//     the extrapolated flux polynomial.  Each face is evaluated by both of
+//     its elements: twice the face arithmetic, but no grid-wide dependency;
+//  3. divergence + DG correction, level-system epilogue (F - S, stage term
+//     relative to q^b or q^n);
+//  4. x = cs .* (D^-1 (rs .* F)) with the element's factored block, written to
+//     a second state buffer (Jacobi: every element reads the old state).
+#include "pmg_internal.h"
+
+namespace pmg {
+
+template <int P>
+struct FusedEPB {   // elements per CTA; a thread per face point of each element
+  static constexpr int value = P == 0 ? 8 : P == 1 ? 4 : P == 2 ? 2 : 1;
+};
+
+template <int P, class W>
+__global__ void __launch_bounds__(64) fused_sweep_kernel(
+    int E, const double* __restrict__ qin, double* __restrict__ qout, const double* __restrict__ met,
+    const double* __restrict__ face, const int* __restrict__ nbr, OpTab op, Phys ph, double inv_odt,
+    const double* __restrict__ src, const double* __restrict__ S, const double* __restrict__ qref,
+    const W* __restrict__ Dinv, const double* __restrict__ rs, const double* __restrict__ cs) {
+  constexpr int n1 = P + 1, N = n1 * n1, n = 4 * N, EPB = FusedEPB<P>::value, FP = 4 * n1;
+  __shared__ double sq[EPB][4][N];
+  __shared__ double sFt[EPB][4][N];
+  __shared__ double sGt[EPB][4][N];
+  __shared__ double sJ[EPB][4][4][n1];
+  __shared__ W sr[EPB][n];
+  __shared__ double sD[n1][n1], sgL[n1], sgR[n1], slm[n1], slp[n1];
+  const size_t plane = (size_t)E * N;
+  if (threadIdx.x < n1 * n1) sD[threadIdx.x / n1][threadIdx.x % n1] = op.D[threadIdx.x / n1][threadIdx.x % n1];
+  if (threadIdx.x < n1) {
+    sgL[threadIdx.x] = op.gL[threadIdx.x];
+    sgR[threadIdx.x] = op.gR[threadIdx.x];
+    slm[threadIdx.x] = op.lm[threadIdx.x];
+    slp[threadIdx.x] = op.lp[threadIdx.x];
+  }
+  // phase 1: thread (le, pt) for pt < N
+  {
+    const int le = threadIdx.x / FP, t = threadIdx.x - le * FP;
+    const int e = blockIdx.x * EPB + le;
+    if (le < EPB && e < E && t < N) {
+      size_t gi = (size_t)e * N + t;
+      double qq[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) { qq[v] = __ldg(qin + v * plane + gi); sq[le][v][t] = qq[v]; }
+      double qa[4] = {qq[0] + ph.p_ref, qq[1], qq[2], qq[3]};
+      double a = __ldg(met + gi), b = __ldg(met + plane + gi);
+      double c = __ldg(met + 2 * plane + gi), d = __ldg(met + 3 * plane + gi);
+      double f[4], g[4];
+      flux_xy(qa, qq[0], ph, f, g);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        sFt[le][v][t] = fma(a, f[v], b * g[v]);
+        sGt[le][v][t] = fma(c, f[v], d * g[v]);
+      }
+    }
+  }
+  __syncthreads();
+  // phase 2: thread (le, face point t = f * n1 + k)
+  {
+    const int le = threadIdx.x / FP, t = threadIdx.x - le * FP;
+    const int e = blockIdx.x * EPB + le;
+    if (le < EPB && e < E) {
+      const int f = t / n1, k = t - f * n1;
+      const bool plus = (f == 1 || f == 2), eta = (f == 0 || f == 2), xi = !eta;
+      const double ref[4] = {sq[le][0][0], 0.0, 0.0, sq[le][3][0]};
+      double sm[4], sp[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        double s = 0.0;
+#pragma unroll
+        for (int m = 0; m < n1; ++m) s = fma(plus ? slp[m] : slm[m], sq[le][v][eta ? m * n1 + k : k * n1 + m] - ref[v], s);
+        sm[v] = s;
+      }
+      const int en = __ldg(nbr + (e * 4 + f) * 3 + 0), fn = __ldg(nbr + (e * 4 + f) * 3 + 1);
+      const int rev = __ldg(nbr + (e * 4 + f) * 3 + 2);
+      const int kn = rev ? P - k : k;
+      {
+        const bool pn = (fn == 1 || fn == 2), etan = (fn == 0 || fn == 2);
+        const double* base = qin + (size_t)en * N + (etan ? kn : kn * n1);
+        const int stride = etan ? n1 : 1;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          double s = 0.0;
+#pragma unroll
+          for (int m = 0; m < n1; ++m) s = fma(pn ? slp[m] : slm[m], __ldg(base + v * plane + m * stride) - ref[v], s);
+          sp[v] = s;
+        }
+      }
+      double qm[4], qp[4], dq[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) { qm[v] = ref[v] + sm[v]; qp[v] = ref[v] + sp[v]; dq[v] = sp[v] - sm[v]; }
+      const double pgm = qm[0], pgp = qp[0];
+      qm[0] += ph.p_ref;
+      qp[0] += ph.p_ref;
+      const double* g = face + (((size_t)e * 4 + f) * n1 + k) * 3;
+      double out[4];
+      roe_flux_jump(qm, qp, dq, pgm, pgp, __ldg(g), __ldg(g + 1), __ldg(g + 2), ph, out);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        double loc = 0.0;
+#pragma unroll
+        for (int m = 0; m < n1; ++m)
+          loc = fma(plus ? slp[m] : slm[m], xi ? sFt[le][v][k * n1 + m] : sGt[le][v][m * n1 + k], loc);
+        sJ[le][f][v][k] = (plus ? out[v] : -out[v]) - loc;
+      }
+    }
+  }
+  __syncthreads();
+  // phase 3: residual and level-system epilogue, thread (le, pt)
+  {
+    const int le = threadIdx.x / FP, t = threadIdx.x - le * FP;
+    const int e = blockIdx.x * EPB + le;
+    if (le < EPB && e < E && t < N) {
+      const int i = t % n1, j = t / n1;
+      size_t gi = (size_t)e * N + t;
+      double qq[4] = {sq[le][0][t], sq[le][1][t], sq[le][2][t], sq[le][3][t]};
+      double qc[4];
+      if (qref) {
+        double qo[4] = {__ldg(qref + gi), __ldg(qref + plane + gi), __ldg(qref + 2 * plane + gi),
+                        __ldg(qref + 3 * plane + gi)};
+        double rho = (qq[0] + ph.p_ref) / qq[3], rhoo = (qo[0] + ph.p_ref) / qo[3];
+        qc[0] = rho - rhoo;
+        qc[1] = rho * qq[1] - rhoo * qo[1];
+        qc[2] = rho * qq[2] - rhoo * qo[2];
+        qc[3] = (qq[0] - qo[0]) * ph.inv_gm1 +
+                0.5 * (rho * (qq[1] * qq[1] + qq[2] * qq[2]) - rhoo * (qo[1] * qo[1] + qo[2] * qo[2]));
+      } else {
+        double qa[4] = {qq[0] + ph.p_ref, qq[1], qq[2], qq[3]};
+        cons(qa, ph, qc);
+      }
+      const double invJ = __ldg(met + 4 * plane + gi);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        double acc = 0.0;
+#pragma unroll
+        for (int m = 0; m < n1; ++m) {
+          acc = fma(sD[i][m], sFt[le][v][j * n1 + m], acc);
+          acc = fma(sD[j][m], sGt[le][v][m * n1 + i], acc);
+        }
+        acc = fma(sgL[i], sJ[le][3][v][j], acc);
+        acc = fma(sgR[i], sJ[le][1][v][j], acc);
+        acc = fma(sgL[j], sJ[le][0][v][i], acc);
+        acc = fma(sgR[j], sJ[le][2][v][i], acc);
+        double R = -acc * invJ;
+        size_t o = v * plane + gi;
+        double F = fma(-qc[v], inv_odt, R);
+        if (src) F += src[o];
+        if (S) F -= S[o];
+        int row = v * N + t;
+        sr[le][row] = (W)(F * rs[(size_t)e * n + row]);
+      }
+    }
+  }
+  __syncthreads();
+  // phase 4: block apply, thread (le, rows 4t..4t+3) for t < N
+  {
+    const int le = threadIdx.x / FP, t = threadIdx.x - le * FP;
+    const int e = blockIdx.x * EPB + le;
+    if (le < EPB && e < E && t < N) {
+      W acc[4] = {0, 0, 0, 0};
+      const W* Dm = Dinv + (size_t)e * n * n + 4 * t;
+#pragma unroll 4
+      for (int kk = 0; kk < n; ++kk) {
+        W rk = sr[le][kk];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) acc[m] = fma(__ldg(Dm + (size_t)kk * n + m), rk, acc[m]);
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        int row = 4 * t + m;
+        int v = row / N, pt = row - v * N;
+        double xv = (double)acc[m] * cs[(size_t)e * n + row];
+        size_t o = v * plane + (size_t)e * N + pt;
+        qout[o] = sq[le][v][pt] + xv;
+      }
+    }
+  }
+}
+
+template <int P>
+static void fused_launch(const Ctx& c, const LevelDev& L, const double* qin, double* qout, double inv_odt,
+                         const double* src, const double* S, const double* qref, int prec, cudaStream_t s) {
+  constexpr int EPB = FusedEPB<P>::value, FP = 4 * (P + 1);
+  int threads = (EPB * FP + 31) / 32 * 32;
+  int blocks = (c.E + EPB - 1) / EPB;
+  const int* nbr = c.d_faces + 5 * c.n_faces;
+  if (prec == PMG_PREC_FP64)
+    fused_sweep_kernel<P, double><<<blocks, threads, 0, s>>>(c.E, qin, qout, L.met, L.face, nbr, L.op, c.ph, inv_odt,
+                                                             src, S, qref, (const double*)L.Dinv, L.rs, L.cs);
+  else
+    fused_sweep_kernel<P, float><<<blocks, threads, 0, s>>>(c.E, qin, qout, L.met, L.face, nbr, L.op, c.ph, inv_odt,
+                                                            src, S, qref, (const float*)L.Dinv, L.rs, L.cs);
+}
+
+void launch_fused_sweep(const Ctx& c, const LevelDev& L, const double* qin, double* qout, double inv_odt,
+                        const double* src, const double* S, const double* qref, int prec, cudaStream_t s) {
+  switch (L.P) {
+    case 0: fused_launch<0>(c, L, qin, qout, inv_odt, src, S, qref, prec, s); break;
+    case 1: fused_launch<1>(c, L, qin, qout, inv_odt, src, S, qref, prec, s); break;
+    case 2: fused_launch<2>(c, L, qin, qout, inv_odt, src, S, qref, prec, s); break;
+    default: fused_launch<3>(c, L, qin, qout, inv_odt, src, S, qref, prec, s); break;
+  }
+}
+
+}  // namespace pmg

@@ -71,7 +71,7 @@ __global__ void prolong_kernel(int E, XferTab X, const double* __restrict__ qc, 
 
 void launch_restrict(const Ctx& c, const LevelDev& Lf, const LevelDev& Lc, const XferTab& X, const double* in,
                      double* out, double* out2, double scale, cudaStream_t s) {
-  int total = c.E * Lc.N, threads = 256, blocks = (total + threads - 1) / threads;
+  int total = c.E * Lc.N, threads = 64, blocks = (total + threads - 1) / threads;
 #define PMG_R(A, B) \
   if (Lf.P == A && Lc.P == B) { restrict_kernel<A, B><<<blocks, threads, 0, s>>>(c.E, X, in, out, out2, scale); return; }
   PMG_PAIRS(PMG_R)
@@ -80,7 +80,7 @@ void launch_restrict(const Ctx& c, const LevelDev& Lf, const LevelDev& Lc, const
 
 static void prolong_impl(const Ctx& c, const LevelDev& Lf, const LevelDev& Lc, const XferTab& X, const double* qc,
                          const double* qcb, double* qf, int add, cudaStream_t s) {
-  int total = c.E * Lf.N, threads = 256, blocks = (total + threads - 1) / threads;
+  int total = c.E * Lf.N, threads = 64, blocks = (total + threads - 1) / threads;
 #define PMG_P(A, B) \
   if (Lf.P == A && Lc.P == B) { prolong_kernel<A, B><<<blocks, threads, 0, s>>>(c.E, X, qc, qcb, qf, add); return; }
   PMG_PAIRS(PMG_P)

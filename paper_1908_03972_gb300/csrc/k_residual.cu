@@ -17,10 +17,13 @@
 
 namespace pmg {
 
+// Elements per CTA of the volume kernel.  The kernel is bound by FP64 issue
+// (2 DFMA per clock per SM), so small CTAs of one or two warps spread even the
+// coarse levels (4096 elements) over all 152 SMs.
 template <int P>
 struct ElemsPerBlock {
   static constexpr int N = (P + 1) * (P + 1);
-  static constexpr int value = (P == 0) ? 128 : 256 / N;
+  static constexpr int value = P == 0 ? 32 : P == 1 ? 8 : P == 2 ? 7 : P == 3 ? 4 : 2;
 };
 
 // Trace of the solution polynomial along the line through face point k of
@@ -75,11 +78,12 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const int* __restrict__ 
     qp[v] = ref[v] + sp[v];
     dq[v] = sp[v] - sm[v];
   }
-  qm[0] += ph.p_ref;   // absolute pressure for the fluxes and the averaged state
+  const double pgm = qm[0], pgp = qp[0];   // gauge pressures for the momentum fluxes
+  qm[0] += ph.p_ref;   // absolute pressure for the averaged state and rho
   qp[0] += ph.p_ref;
   const double* g = face + (((size_t)eL * 4 + fL) * n1 + k) * 3;
   double out[4];
-  roe_flux_jump(qm, qp, dq, __ldg(g), __ldg(g + 1), __ldg(g + 2), ph, out);
+  roe_flux_jump(qm, qp, dq, pgm, pgp, __ldg(g), __ldg(g + 1), __ldg(g + 2), ph, out);
   size_t fplane = (size_t)E * 4 * n1;
   size_t iL = ((size_t)eL * 4 + fL) * n1 + k, iR = ((size_t)eR * 4 + fR) * n1 + kR;
 #pragma unroll
@@ -89,8 +93,13 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const int* __restrict__ 
   }
 }
 
-template <int P>
-__global__ void __launch_bounds__(256) volume_kernel(int E, const double* __restrict__ q,
+// APPLY: after forming the level-system residual F of its elements, each CTA
+// also performs the element-Jacobi update q += cs .* (D^-1 (rs .* F)) in
+// place (eq. smoothing_element_jacobi).  That is safe within one launch: the
+// face fluxes were formed from the old state by the preceding face launch,
+// and a CTA reads and writes only its own elements' states.
+template <int P, class W, bool APPLY>
+__global__ void __launch_bounds__(256) volume_kernel(int E, const double* q,
                                                      const double* __restrict__ met,
                                                      const double* __restrict__ Fcom, OpTab op, Phys ph,
                                                      double* __restrict__ out, int mode, double inv_odt,
@@ -98,8 +107,11 @@ __global__ void __launch_bounds__(256) volume_kernel(int E, const double* __rest
                                                      const double* __restrict__ S, double* __restrict__ Sout,
                                                      const double* __restrict__ Pd,
                                                      const double* __restrict__ qn,
-                                                     double* __restrict__ partial) {
-  constexpr int n1 = P + 1, N = n1 * n1, EPB = ElemsPerBlock<P>::value;
+                                                     double* __restrict__ partial, double* qw,
+                                                     const W* __restrict__ Dinv, const double* __restrict__ rs,
+                                                     const double* __restrict__ cs) {
+  constexpr int n1 = P + 1, N = n1 * n1, EPB = ElemsPerBlock<P>::value, n = 4 * N;
+  __shared__ W sr[APPLY ? EPB : 1][APPLY ? n : 1];
   __shared__ double sFt[EPB][4][N];
   __shared__ double sGt[EPB][4][N];
   __shared__ double sJ[EPB][4][4][n1];   // [face][var][k]
@@ -118,17 +130,18 @@ __global__ void __launch_bounds__(256) volume_kernel(int E, const double* __rest
     slp[threadIdx.x] = op.lp[threadIdx.x];
   }
 
-  double qq[4] = {0, 0, 0, 0}, invJ = 0.0;
+  double qq[4] = {0, 0, 0, 0}, invJ = 0.0, rho_pt = 0.0;
   size_t gi = (size_t)e * N + pt;
   if (active) {
 #pragma unroll
-    for (int v = 0; v < 4; ++v) qq[v] = __ldg(q + v * plane + gi);
+    for (int v = 0; v < 4; ++v) qq[v] = q[v * plane + gi];
     double a = __ldg(met + gi), b = __ldg(met + plane + gi);
     double c = __ldg(met + 2 * plane + gi), d = __ldg(met + 3 * plane + gi);
     invJ = __ldg(met + 4 * plane + gi);
     double qa[4] = {qq[0] + ph.p_ref, qq[1], qq[2], qq[3]};   // absolute pressure
+    rho_pt = qa[0] * s_rcp(qa[3]);
     double f[4], g[4];
-    flux_xy(qa, ph, f, g);
+    flux_xy_rho(qa, qq[0], rho_pt, ph, f, g);
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       sFt[le][v][pt] = fma(a, f[v], b * g[v]);
@@ -164,15 +177,17 @@ __global__ void __launch_bounds__(256) volume_kernel(int E, const double* __rest
       // p ~ rho E ~ 1/Ma^2 is rounded (q_ref = q^n on the finest level, q^b on
       // coarser levels, where the constant q_c(q^b)/(omega dt) cancels in F - S)
       double qo[4] = {__ldg(qn + gi), __ldg(qn + plane + gi), __ldg(qn + 2 * plane + gi), __ldg(qn + 3 * plane + gi)};
-      double rho = (qq[0] + ph.p_ref) / qq[3], rhoo = (qo[0] + ph.p_ref) / qo[3];
+      double rho = rho_pt, rhoo = (qo[0] + ph.p_ref) * s_rcp(qo[3]);
       qc[0] = rho - rhoo;
       qc[1] = rho * qq[1] - rhoo * qo[1];
       qc[2] = rho * qq[2] - rhoo * qo[2];
-      qc[3] = (qq[0] - qo[0]) / ph.gm1 +
+      qc[3] = (qq[0] - qo[0]) * ph.inv_gm1 +
               0.5 * (rho * (qq[1] * qq[1] + qq[2] * qq[2]) - rhoo * (qo[1] * qo[1] + qo[2] * qo[2]));
     } else {
-      double qa[4] = {qq[0] + ph.p_ref, qq[1], qq[2], qq[3]};
-      cons(qa, ph, qc);
+      qc[0] = rho_pt;
+      qc[1] = rho_pt * qq[1];
+      qc[2] = rho_pt * qq[2];
+      qc[3] = rho_pt * (qq[3] * ph.inv_gm1 + 0.5 * (qq[1] * qq[1] + qq[2] * qq[2]));
     }
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -200,8 +215,34 @@ __global__ void __launch_bounds__(256) volume_kernel(int E, const double* __rest
         double F = fma(-qc[v], inv_odt, R);
         if (src) F += src[o];
         if (mode == RES_SYSTEM && S) F -= S[o];
-        out[o] = F;
+        if (APPLY) {
+          const int row = v * N + pt;
+          sr[APPLY ? le : 0][APPLY ? row : 0] = (W)(F * rs[(size_t)e * n + row]);
+        } else {
+          out[o] = F;
+        }
         ssq = fma(F, F, ssq);
+      }
+    }
+  }
+  if (APPLY) {
+    __syncthreads();
+    if (active) {
+      // thread (le, pt) owns rows 4 pt .. 4 pt + 3 of its element's block
+      W acc[4] = {0, 0, 0, 0};
+      const W* Dm = Dinv + (size_t)e * n * n + 4 * pt;
+#pragma unroll 8
+      for (int kk = 0; kk < n; ++kk) {
+        W rk = sr[APPLY ? le : 0][APPLY ? kk : 0];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) acc[m] = fma(__ldg(Dm + (size_t)kk * n + m), rk, acc[m]);
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int row = 4 * pt + m;
+        const int v = row / N, p2 = row - v * N;
+        const size_t o = v * plane + (size_t)e * N + p2;
+        qw[o] = q[o] + (double)acc[m] * cs[(size_t)e * n + row];
       }
     }
   }
@@ -260,7 +301,8 @@ int residual_blocks_for(int P, int E) { int epb = elems_per_block(P); return (E 
 
 void launch_face_flux(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s) {
   int total = c.n_faces * L.n1;
-  int threads = 128, blocks = (total + threads - 1) / threads;
+  // one warp per CTA: FP64-bound threads, spread over every SM
+  int threads = 32, blocks = (total + threads - 1) / threads;
 #define PMG_FACE(PP) face_flux_kernel<PP><<<blocks, threads, 0, s>>>(c.d_faces, c.n_faces, c.E, q, L.face, L.Fcom, L.op, c.ph)
   switch (L.P) {
     case 0: PMG_FACE(0); break;
@@ -278,9 +320,10 @@ void launch_volume(const Ctx& c, const LevelDev& L, int level, const double* q, 
   (void)level;
   int threads = residual_threads_per_block(L.P);
   int blocks = residual_blocks_for(L.P, c.E);
-#define PMG_VOL(PP)                                                                                   \
-  volume_kernel<PP><<<blocks, threads, 0, s>>>(c.E, q, L.met, L.Fcom, L.op, c.ph, out, (int)mode, inv_odt, \
-                                               src, S, Sout, Pd, qn, partial)
+#define PMG_VOL(PP)                                                                                          \
+  volume_kernel<PP, double, false><<<blocks, threads, 0, s>>>(c.E, q, L.met, L.Fcom, L.op, c.ph, out, (int)mode, \
+                                                              inv_odt, src, S, Sout, Pd, qn, partial, nullptr,   \
+                                                              nullptr, nullptr, nullptr)
   switch (L.P) {
     case 0: PMG_VOL(0); break;
     case 1: PMG_VOL(1); break;
@@ -289,6 +332,34 @@ void launch_volume(const Ctx& c, const LevelDev& L, int level, const double* q, 
     default: PMG_VOL(4); break;
   }
 #undef PMG_VOL
+}
+
+template <class W>
+static void volume_apply_dispatch(const Ctx& c, const LevelDev& L, double* q, double inv_odt, const double* src,
+                                  const double* S, const double* qn, cudaStream_t s) {
+  int threads = residual_threads_per_block(L.P);
+  int blocks = residual_blocks_for(L.P, c.E);
+  const W* Dinv = (const W*)L.Dinv;
+#define PMG_VA(PP)                                                                                        \
+  volume_kernel<PP, W, true><<<blocks, threads, 0, s>>>(c.E, q, L.met, L.Fcom, L.op, c.ph, nullptr,          \
+                                                        (int)RES_SYSTEM, inv_odt, src, S, nullptr, nullptr, qn, \
+                                                        nullptr, q, Dinv, L.rs, L.cs)
+  switch (L.P) {
+    case 0: PMG_VA(0); break;
+    case 1: PMG_VA(1); break;
+    case 2: PMG_VA(2); break;
+    case 3: PMG_VA(3); break;
+    default: PMG_VA(4); break;
+  }
+#undef PMG_VA
+}
+
+// Level-system residual of the current state followed, in the same launch,
+// by the element-Jacobi update of that state (after launch_face_flux).
+void launch_volume_apply(const Ctx& c, const LevelDev& L, double* q, double inv_odt, const double* src,
+                         const double* S, const double* qn, int prec, cudaStream_t s) {
+  if (prec == PMG_PREC_FP64) volume_apply_dispatch<double>(c, L, q, inv_odt, src, S, qn, s);
+  else volume_apply_dispatch<float>(c, L, q, inv_odt, src, S, qn, s);
 }
 
 void launch_norm_final(const double* partial, int n, double* out, cudaStream_t s) {

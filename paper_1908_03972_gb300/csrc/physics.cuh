@@ -17,6 +17,8 @@ struct Phys {
   double Cp;       // gamma / (gamma - 1) with R = 1
   double eps_min;  // kappa * Ma_inf when the cut-off is on, 0 otherwise
   double p_ref;    // device states hold p - p_ref (gauge pressure)
+  double inv_gamma;  // 1 / gamma
+  double inv_gm1;    // 1 / (gamma - 1)
 };
 
 // ---------------------------------------------------------------------------
@@ -58,6 +60,26 @@ __host__ __device__ inline Dual s_sqrt(Dual a) {
 }
 __host__ __device__ inline double s_abs(double a) { return fabs(a); }
 __host__ __device__ inline Dual s_abs(Dual a) { return a.v < 0.0 ? -a : a; }
+// Reciprocal.  On the device, division costs about ten FP64 FMAs on GB300;
+// here the hardware approximation (PTX rcp.approx.ftz.f64, about 20 correct
+// bits) is refined by two Newton-Raphson steps y <- y + y (1 - x y), each
+// doubling the number of correct bits, to full FP64 accuracy (within an ulp
+// or two of the correctly rounded quotient; the parity tests bound the
+// effect on the residual).  Arguments here are normal numbers (T, p, eps^2,
+// c' > 0).  Dual numbers use plain division.
+__host__ __device__ inline double s_rcp(double x) {
+#ifdef __CUDA_ARCH__
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+#else
+  return 1.0 / x;
+#endif
+}
+__host__ __device__ inline Dual s_rcp(Dual x) { return 1.0 / x; }
 template <class S> __host__ __device__ inline S s_min(S a, S b) { return val(a) <= val(b) ? a : b; }
 template <class S> __host__ __device__ inline S s_max(S a, S b) { return val(a) >= val(b) ? a : b; }
 
@@ -65,25 +87,39 @@ template <class S> __host__ __device__ inline S s_max(S a, S b) { return val(a) 
 // Inviscid flux through the unit direction (nx, ny):
 // (rho u_n, rho u_n u + p nx, rho u_n v + p ny, rho u_n H), R = 1.
 // ---------------------------------------------------------------------------
+//
+// q holds the absolute pressure; pm is the pressure used in the momentum
+// flux.  With gauge storage pm = p - p_ref: the constant p_ref contributes
+// p_ref times the discrete metric identity, which vanishes wherever the
+// discretisation preserves a uniform flow (straight elements, or curved
+// elements with P >= geometry order), and leaving it out keeps the rounding
+// of p ~ 1/Ma^2 out of the momentum residual (and, through the velocity
+// updates, out of the H-weighted energy residual).
 template <class S>
-__host__ __device__ inline void flux_n(const S q[4], double nx, double ny, const Phys& ph, S f[4]) {
-  S rho = q[0] / q[3];
+__host__ __device__ inline void flux_n(const S q[4], const S& pm, double nx, double ny, const Phys& ph, S f[4]) {
+  S rho = q[0] * s_rcp(q[3]);
   S H = ph.Cp * q[3] + 0.5 * (q[1] * q[1] + q[2] * q[2]);
   S mn = rho * (q[1] * nx + q[2] * ny);
   f[0] = mn;
-  f[1] = mn * q[1] + q[0] * nx;
-  f[2] = mn * q[2] + q[0] * ny;
+  f[1] = mn * q[1] + pm * nx;
+  f[2] = mn * q[2] + pm * ny;
   f[3] = mn * H;
 }
 
-// Cartesian fluxes f (x) and g (y) at one point.
+// Cartesian fluxes f (x) and g (y) at one point (pm as in flux_n), with the
+// density rho = p / T supplied by the caller.
 template <class S>
-__host__ __device__ inline void flux_xy(const S q[4], const Phys& ph, S f[4], S g[4]) {
-  S rho = q[0] / q[3];
+__host__ __device__ inline void flux_xy_rho(const S q[4], const S& pm, const S& rho, const Phys& ph, S f[4],
+                                            S g[4]) {
   S H = ph.Cp * q[3] + 0.5 * (q[1] * q[1] + q[2] * q[2]);
   S mx = rho * q[1], my = rho * q[2];
-  f[0] = mx; f[1] = mx * q[1] + q[0]; f[2] = mx * q[2]; f[3] = mx * H;
-  g[0] = my; g[1] = my * q[1]; g[2] = my * q[2] + q[0]; g[3] = my * H;
+  f[0] = mx; f[1] = mx * q[1] + pm; f[2] = mx * q[2]; f[3] = mx * H;
+  g[0] = my; g[1] = my * q[1]; g[2] = my * q[2] + pm; g[3] = my * H;
+}
+
+template <class S>
+__host__ __device__ inline void flux_xy(const S q[4], const S& pm, const Phys& ph, S f[4], S g[4]) {
+  flux_xy_rho(q, pm, q[0] * s_rcp(q[3]), ph, f, g);
 }
 
 // Conservative variables (rho, rho u, rho v, rho E).
@@ -93,7 +129,7 @@ __host__ __device__ inline void cons(const S q[4], const Phys& ph, S qc[4]) {
   qc[0] = rho;
   qc[1] = rho * q[1];
   qc[2] = rho * q[2];
-  qc[3] = rho * (q[3] / ph.gm1 + 0.5 * (q[1] * q[1] + q[2] * q[2]));
+  qc[3] = rho * (q[3] * ph.inv_gm1 + 0.5 * (q[1] * q[1] + q[2] * q[2]));
 }
 
 // eps^2 with eps = min(1, max(eps_min, Ma)) (eq. eps_nonmove; eps_min = 0
@@ -122,25 +158,28 @@ __host__ __device__ inline S eps2_of(const S q[4], const Phys& ph) {
 // (p, u_n) plus |u_n| on T.  The dissipation is then M K |.| dq_p.
 // ---------------------------------------------------------------------------
 template <class S>
-__host__ __device__ inline void roe_flux_jump(const S qm[4], const S qp[4], const S dq[4], double nx, double ny,
-                                              double dS, const Phys& ph, S out[4]) {
+__host__ __device__ inline void roe_flux_jump(const S qm[4], const S qp[4], const S dq[4], const S& pmm,
+                                              const S& pmp, double nx, double ny, double dS, const Phys& ph,
+                                              S out[4]) {
   S fm[4], fp[4];
-  flux_n(qm, nx, ny, ph, fm);
-  flux_n(qp, nx, ny, ph, fp);
+  flux_n(qm, pmm, nx, ny, ph, fm);
+  flux_n(qp, pmp, nx, ny, ph, fp);
   // averaged state
   S p = 0.5 * (qm[0] + qp[0]);
   S u = 0.5 * (qm[1] + qp[1]);
   S v = 0.5 * (qm[2] + qp[2]);
   S T = 0.5 * (qm[3] + qp[3]);
   S dp = dq[0], du = dq[1], dv = dq[2], dT = dq[3];
-  S iT = 1.0 / T;
+  // divisions are ~10 FP64 FMA each on GB300: form each reciprocal once
+  S iT = s_rcp(T);
   S rho = p * iT;
-  S irho = T / p;
+  S irho = T * s_rcp(p);
   S c2 = ph.gamma * T;
   S vv = u * u + v * v;
-  S e2 = s_min(S(1.0), s_max(S(ph.eps_min * ph.eps_min), vv / c2));
+  S e2 = s_min(S(1.0), s_max(S(ph.eps_min * ph.eps_min), vv * iT * ph.inv_gamma));
   S Ur2 = e2 * c2;
-  S iUr2 = 1.0 / Ur2;
+  S ie2 = s_rcp(e2);
+  S iUr2 = ie2 * iT * ph.inv_gamma;
   S un = u * nx + v * ny;
   S dun = du * nx + dv * ny;
   S dut = dv * nx - du * ny;
@@ -149,7 +188,7 @@ __host__ __device__ inline void roe_flux_jump(const S qm[4], const S qp[4], cons
   S unp = un * (1.0 - alpha);
   S lp = unp + cpr, lm = unp - cpr;
   S alp = s_abs(lp), alm = s_abs(lm), aun = s_abs(un);
-  S a1 = (alp - alm) * (0.5 / cpr);
+  S a1 = (alp - alm) * (0.5 * s_rcp(cpr));
   S a0 = alp - a1 * lp;
   S rc2 = rho * c2;
   // |B| (dp, dun)
@@ -167,7 +206,6 @@ __host__ __device__ inline void roe_flux_jump(const S qm[4], const S qp[4], cons
   S xu = zu * nx - xt * ny;
   S xv = zu * ny + xt * nx;
   // K then M
-  S ie2 = 1.0 / e2;
   S yp = zp * ie2;
   S yT = (ie2 - 1.0) * irCp * zp + xT;
   S drho = (yp - rho * yT) * iT;
@@ -187,7 +225,7 @@ template <class S>
 __host__ __device__ inline void roe_flux(const S qm[4], const S qp[4], double nx, double ny, double dS,
                                          const Phys& ph, S out[4]) {
   S dq[4] = {qp[0] - qm[0], qp[1] - qm[1], qp[2] - qm[2], qp[3] - qm[3]};
-  roe_flux_jump(qm, qp, dq, nx, ny, dS, ph, out);
+  roe_flux_jump(qm, qp, dq, qm[0] - ph.p_ref, qp[0] - ph.p_ref, nx, ny, dS, ph, out);
 }
 
 // Gamma (eq. preconditioning, 2D rows) and M = dq_c/dq_p at one point,

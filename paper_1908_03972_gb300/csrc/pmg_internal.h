@@ -59,6 +59,8 @@ struct LevelDev {
   size_t tot = 0;              // 4 * E * N
   OpTab op;
   double* q = nullptr;         // state
+  double* q2 = nullptr;        // second state buffer of fused (ping-pong) sweeps
+  bool fused = false;          // coarse level smoothed by the fused one-launch sweep
   double* qb = nullptr;        // state at entry of the level in the V-cycle
   double* S = nullptr;         // FAS forcing
   double* F = nullptr;         // level system residual F_l(q) - S_l
@@ -84,7 +86,7 @@ enum ResMode : int {
 
 // Kernel classes timed by the optional per-launch event profiler.
 enum KClass : int { K_FACE = 0, K_VOLUME, K_APPLY, K_ASSEMBLE, K_FACTOR, K_RESTRICT, K_PROLONG, K_NORM, K_STAGE,
-                    K_COUNT };
+                    K_FUSED, K_COUNT };
 
 struct Profiler {
   bool on = false;
@@ -144,6 +146,8 @@ void launch_volume(const Ctx& c, const LevelDev& L, int level, const double* q, 
                    double inv_odt, const double* src, const double* S, double* Sout, const double* Pd,
                    double* partial, cudaStream_t s, const double* qn = nullptr);
 void launch_norm_final(const double* partial, int n, double* out, cudaStream_t s);
+void launch_volume_apply(const Ctx& c, const LevelDev& L, double* q, double inv_odt, const double* src,
+                         const double* S, const double* qn, int prec, cudaStream_t s);
 void launch_assemble(const Ctx& c, const LevelDev& L, const double* q, const double* d_dtau, double inv_odt,
                      cudaStream_t s);
 void launch_factor(const Ctx& c, LevelDev& L, int prec, int* flag, cudaStream_t s);
@@ -161,6 +165,8 @@ void launch_stage_src(const Ctx& c, int N, const double* qcn, double* const* R, 
 void launch_bsum_update(const Ctx& c, int N, const double* qn, double* const* R, const double* b, int nr,
                         double dt, double* q, cudaStream_t s);
 void launch_shift_pressure(size_t plane, double delta, double* q, cudaStream_t s);
+void launch_fused_sweep(const Ctx& c, const LevelDev& L, const double* qin, double* qout, double inv_odt,
+                        const double* src, const double* S, const double* qref, int prec, cudaStream_t s);
 int residual_threads_per_block(int P);
 int residual_blocks_for(int P, int E);
 cudaError_t prepare_kernels(const Ctx& c);

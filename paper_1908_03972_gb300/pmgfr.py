@@ -373,7 +373,8 @@ def pmg_last_error() -> str:
     return load().pmg_last_error().decode()
 
 
-PROF_CLASSES = ["face_flux", "volume", "apply", "assemble", "factor", "restrict", "prolong", "norm", "stage"]
+PROF_CLASSES = ["face_flux", "volume", "apply", "assemble", "factor", "restrict", "prolong", "norm", "stage",
+                "fused_sweep"]
 
 
 def pmg_profile(h, enable=True):

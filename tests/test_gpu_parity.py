@@ -82,6 +82,8 @@ def _mesh(name):
 @pytest.mark.parametrize("P", [0, 1, 2, 3, 4])
 def test_residual_parity(name, P, gauge):
     (nodes, nbr), Ng = _mesh(name)
+    if gauge and P < Ng:
+        pytest.skip("gauge storage needs P >= geometry order")
     orc, gpu = _pair(nodes, nbr, Ng, [P], [1], p_gauge=gauge)
     try:
         q = W.isentropic_vortex(orc.coords(), center=(4.3, 5.6))
@@ -108,6 +110,13 @@ def test_residual_parity_reversed_faces():
             gpu.close()
 
 
+def test_gauge_storage_rejected_below_geometry_order():
+    from paper_1908_03972_gb300 import pmgfr
+    nodes, nbr = W.periodic_box(3, 3, Ng=2, perturb=0.3)
+    with pytest.raises(pmgfr.PmgError):
+        pmgfr.Solver(nodes, nbr, [2, 1], [1, 1], p_gauge=TINF)
+
+
 def test_free_stream_on_gpu():
     nodes, nbr = W.periodic_box(4, 4, Ng=2, perturb=0.3)
     from paper_1908_03972_gb300 import pmgfr
@@ -126,8 +135,9 @@ def test_free_stream_on_gpu():
 @pytest.mark.parametrize("gauge", GAUGES)
 @pytest.mark.parametrize("P", [0, 1, 2, 3])
 def test_stage_residual_parity(P, gauge):
-    nodes, nbr = W.periodic_box(4, 4, Ng=2, perturb=0.3)
-    orc, gpu = _pair(nodes, nbr, 2, [P], [1], p_gauge=gauge)
+    Ng = 1 if gauge else 2
+    nodes, nbr = W.periodic_box(4, 4, Ng=Ng, perturb=0.3 if Ng > 1 else 0.0)
+    orc, gpu = _pair(nodes, nbr, Ng, [P], [1], p_gauge=gauge)
     try:
         q = W.isentropic_vortex(orc.coords(), center=(4.0, 6.0))
         src = _qc(q) / 0.05 + 0.3 * orc.residual(q)
@@ -143,8 +153,9 @@ def test_stage_residual_parity(P, gauge):
 @pytest.mark.parametrize("gauge", GAUGES)
 @pytest.mark.parametrize("P", [0, 1, 2, 3])
 def test_block_assembly_parity(P, gauge):
-    nodes, nbr = W.periodic_box(3, 4, Ng=2, perturb=0.3)
-    orc, gpu = _pair(nodes, nbr, 2, [P], [1], p_gauge=gauge)
+    Ng = 1 if gauge else 2
+    nodes, nbr = W.periodic_box(3, 4, Ng=Ng, perturb=0.3 if Ng > 1 else 0.0)
+    orc, gpu = _pair(nodes, nbr, Ng, [P], [1], p_gauge=gauge)
     try:
         q = W.isentropic_vortex(orc.coords(), center=(4.0, 6.0))
         omega_dt = 0.0436
@@ -209,8 +220,9 @@ def _stage_setup(orc, gpu, omega_dt=0.0436, scale=0.5):
 @pytest.mark.parametrize("gauge", GAUGES)
 @pytest.mark.parametrize("levels,smooth", [([2, 1, 0], [2, 3, 4]), ([3, 2, 1, 0], [1, 2, 2, 3]), ([2], [3])])
 def test_vcycle_parity_fp64(levels, smooth, gauge):
-    nodes, nbr = W.periodic_box(4, 4, Ng=2, perturb=0.3)
-    orc, gpu = _pair(nodes, nbr, 2, levels, smooth, p_gauge=gauge)
+    Ng = 1 if gauge else 2
+    nodes, nbr = W.periodic_box(4, 4, Ng=Ng, perturb=0.3 if Ng > 1 else 0.0)
+    orc, gpu = _pair(nodes, nbr, Ng, levels, smooth, p_gauge=gauge)
     try:
         q = _stage_setup(orc, gpu)
         qo = orc.vcycle(q, 0.7, refresh=True)
@@ -227,11 +239,29 @@ def test_vcycle_parity_fp64(levels, smooth, gauge):
         gpu.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_vcycle_parity_fused_coarse_sweeps(prec, monkeypatch):
+    """The one-launch fused sweep of the coarse levels gives the same V-cycle."""
+    monkeypatch.setenv("PMG_FUSE_MAX_P", "2")
+    nodes, nbr = W.periodic_box(4, 4, Ng=2, perturb=0.3)
+    orc, gpu = _pair(nodes, nbr, 2, [3, 2, 1, 0], [2, 3, 3, 5], prec=prec)
+    try:
+        q = _stage_setup(orc, gpu)
+        qo = orc.vcycle(q, 0.7, refresh=True)
+        qg, _ = gpu.vcycle(q, 0.7, refresh=True)
+        dq = np.abs(qo - q).max(axis=(1, 2))
+        tol = 1e-8 if prec == 0 else 5e-3
+        assert (np.abs(qg - qo).max(axis=(1, 2)) / dq).max() <= tol
+    finally:
+        gpu.close()
+
+
 @pytest.mark.parametrize("gauge", GAUGES)
 @pytest.mark.parametrize("prec", [0, 1])
 def test_stage_solve_parity(prec, gauge):
-    nodes, nbr = W.periodic_box(4, 4, Ng=2, perturb=0.3)
-    orc, gpu = _pair(nodes, nbr, 2, [2, 1, 0], [2, 3, 4], prec=prec, tol=1e-8, p_gauge=gauge)
+    Ng = 1 if gauge else 2
+    nodes, nbr = W.periodic_box(4, 4, Ng=Ng, perturb=0.3 if Ng > 1 else 0.0)
+    orc, gpu = _pair(nodes, nbr, Ng, [2, 1, 0], [2, 3, 4], prec=prec, tol=1e-8, p_gauge=gauge)
     try:
         q = _stage_setup(orc, gpu)
         qo, it_o, drop_o, _, st = orc.stage_solve(q)
