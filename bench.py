@@ -85,6 +85,32 @@ def apply_flops(P, E):
 
 
 # ------------------------------------------------------------------ helpers
+def csrc_fingerprint():
+    import hashlib
+    src = os.path.join(ROOT, "paper_1908_03972_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(src)):
+        h.update(f.encode())
+        with open(os.path.join(src, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(key):
+    """DRAM bytes per launch of a kernel from the committed ncu capture, or
+    None when there is none or the kernel sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic_c2.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    if rec.get("csrc_sha256_prefix") != csrc_fingerprint():
+        return None
+    k = rec.get("kernels", {}).get(key)
+    return k["dram_bytes_per_launch"] if k else None
+
+
+
 class ClockSampler:
     """nvidia-smi samples every 200 ms while the timed region runs."""
 
@@ -355,9 +381,10 @@ def run_ours(args, wl, world, rank, local):
     else:
         achieved = work / avg_s / 1e12 if work else None
         peak_note = "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz"
-    roofline = {"kernel": f"{top_name}[level {top_lvl}, P={P}]", "bound": bound, "achieved": achieved,
+    key = f"{top_name}[level {top_lvl}, P={P}]"
+    roofline = {"kernel": key, "bound": bound, "achieved": achieved,
                 "peak": peak, "unit": unit, "frac": (achieved / peak) if achieved else None,
-                "traffic": None, "peak_source": peak_note,
+                "traffic": ncu_traffic(key), "peak_source": peak_note,
                 "share_of_step": top_ms / total_ms if total_ms else None,
                 "avg_launch_us": avg_s * 1e6, "launches_per_step": top_n}
 
