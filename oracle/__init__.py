@@ -56,6 +56,8 @@ class OrcConfig(ctypes.Structure):
         ("tol", ctypes.c_double),
         ("refresh_every", ctypes.c_int),
         ("max_pseudo", ctypes.c_int),
+        ("mu", ctypes.c_double),
+        ("Pr", ctypes.c_double),
     ]
 
 
@@ -159,7 +161,7 @@ class Oracle:
 
     def __init__(self, nodes, nbr, Ng, P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005,
                  kappa=1.0, cutoff=0, dtau_init=0.01, dtau_max=10.0, tol=1e-8,
-                 refresh_every=10, max_pseudo=2000):
+                 refresh_every=10, max_pseudo=2000, mu=0.0, Pr=0.72):
         cfg = OrcConfig()
         cfg.n_levels = len(P_levels)
         for l, P in enumerate(P_levels):
@@ -169,6 +171,7 @@ class Oracle:
         cfg.esdirk_stages = 4
         cfg.dtau_init, cfg.dtau_max, cfg.tol = dtau_init, dtau_max, tol
         cfg.refresh_every, cfg.max_pseudo = refresh_every, max_pseudo
+        cfg.mu, cfg.Pr = mu, Pr
         self.cfg = cfg
         self.nodes = _f64(nodes)
         self.nbr = np.ascontiguousarray(nbr, dtype=np.int32)

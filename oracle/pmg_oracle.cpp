@@ -1,8 +1,12 @@
 // pmg_oracle.cpp -- TEST INFRASTRUCTURE ONLY.
 //
 // A plain, slow, FP64 CPU restatement of the implicit P-multigrid flux
-// reconstruction solver of Wang & Yu (arXiv 1908.03972) for the 2D Euler
-// equations with Weiss-Smith/Turkel local preconditioning.  It exists only to
+// reconstruction solver of Wang & Yu (arXiv 1908.03972) for the 2D Euler and
+// (constant mu, Section 2.1) Navier-Stokes equations with Weiss-Smith/Turkel
+// local preconditioning.  Viscous terms follow Section 2.3: q_com of eq.
+// com_q, common gradient of eq. com_grad_q with BR2 liftings.  The paper does
+// not state the BR2 penalty; eta_f = 4 (faces per element) is the reading
+// taken, and its value is parity unpinned (every pin holds for any eta_f > 0).  It exists only to
 // check the CUDA library: tests, the smoke check and the CPU-baseline leg of
 // the benchmark may load it; the product path never does.  It shares no code,
 // header, table or constant generator with the CUDA library.
@@ -204,6 +208,7 @@ static std::vector<double> make_prolongation(const Basis1D& f, const Basis1D& c)
 struct Phys {
   double gamma, Ma_inf, kappa;
   int cutoff;  // 1: eps = min(1, max(kappa Ma_inf, Ma)); 0: eps = min(1, Ma)
+  double mu = 0.0, Pr = 0.72;   // constant dynamic viscosity (0: Euler), Prandtl number
 };
 
 template <class S> static void cons_from_prim(const S q[4], const Phys& ph, S qc[4]) {
@@ -387,6 +392,7 @@ struct LevelGeom {
   Basis1D b;
   std::vector<double> met;   // per (e, pt): x_xi, x_eta, y_xi, y_eta, |J|
   std::vector<double> fS;    // per (e, face, k): outward area-scaled normal (Sx, Sy)
+  std::vector<double> fJ;    // per (e, face, k): |J| of the element map at the face point
 };
 
 static void map_derivs(int Ng, const double* xn, double xi, double eta,
@@ -416,6 +422,7 @@ struct OrcConfig {
   int esdirk_stages;      // 4 = ESDIRK3 (the scheme implemented)
   double dtau_init, dtau_max, tol;
   int refresh_every, max_pseudo;
+  double mu, Pr;
 };
 
 struct Level {
@@ -448,6 +455,7 @@ static void build_level_geom(Oracle* o, int P, LevelGeom* g) {
   int n1 = P + 1, E = o->E, Ng = o->Ng, nn = (Ng + 1) * (Ng + 1);
   g->met.assign((size_t)E * g->N * 5, 0.0);
   g->fS.assign((size_t)E * 4 * n1 * 2, 0.0);
+  g->fJ.assign((size_t)E * 4 * n1, 0.0);
   for (int e = 0; e < E; ++e) {
     const double* xn = &o->nodes[(size_t)e * nn * 2];
     for (int j = 0; j < n1; ++j)
@@ -473,6 +481,7 @@ static void build_level_geom(Oracle* o, int P, LevelGeom* g) {
         else { Sx = -y_eta; Sy = x_eta; }               // -(grad xi)|J|
         double* s = &g->fS[(((size_t)e * 4 + f) * n1 + k) * 2];
         s[0] = Sx; s[1] = Sy;
+        g->fJ[((size_t)e * 4 + f) * n1 + k] = x_xi * y_eta - x_eta * y_xi;
       }
   }
 }
@@ -498,43 +507,139 @@ static void trace_state(const Basis1D& b, const S* qe, int N, int f, int k, S ou
   }
 }
 
-// Neighbour traces for every element face point from a real state array.
+// Broken (uncorrected) gradient of one element's state at its solution
+// points: reference derivatives by the Lagrange derivative matrix, then the
+// chain rule with the exact metric terms.  g[(c*4 + v)*N + pt], c = x, y.
+template <class S>
+static void broken_gradient(const Level& L, int e, const S* qe, S* g) {
+  const Basis1D& b = L.g.b;
+  int n1 = b.P + 1, N = L.g.N;
+  for (int v = 0; v < 4; ++v)
+    for (int j = 0; j < n1; ++j)
+      for (int i = 0; i < n1; ++i) {
+        S qx = 0.0, qy = 0.0;
+        for (int m = 0; m < n1; ++m) {
+          qx += b.D[i * n1 + m] * qe[v * N + j * n1 + m];
+          qy += b.D[j * n1 + m] * qe[v * N + m * n1 + i];
+        }
+        const double* mt = &L.g.met[((size_t)e * N + j * n1 + i) * 5];
+        int pt = j * n1 + i;
+        g[(0 * 4 + v) * N + pt] = (mt[3] * qx - mt[2] * qy) / mt[4];
+        g[(1 * 4 + v) * N + pt] = (-mt[1] * qx + mt[0] * qy) / mt[4];
+      }
+}
+
+// Frozen neighbour data at every element face point, NT values each: the
+// neighbour's state trace (4), its broken-gradient trace (8, x then y per
+// variable) and its |J| at that face point.
+static const int NT = 13;
+
 static void neighbour_traces(const Oracle* o, const Level& L, const double* q, std::vector<double>& tr) {
   int P = L.g.P, n1 = P + 1, N = L.g.N, E = o->E;
-  tr.assign((size_t)E * 4 * n1 * 4, 0.0);
-  std::vector<double> qe(4 * N);
+  tr.assign((size_t)E * 4 * n1 * NT, 0.0);
+  std::vector<double> qe(4 * N), g(8 * N);
   for (int e = 0; e < E; ++e)
     for (int f = 0; f < 4; ++f) {
       int en = o->nbr[(e * 4 + f) * 3 + 0], fn = o->nbr[(e * 4 + f) * 3 + 1];
       int rev = o->nbr[(e * 4 + f) * 3 + 2];
       for (int v = 0; v < 4; ++v)
         for (int p = 0; p < N; ++p) qe[v * N + p] = q[((size_t)v * E + en) * N + p];
+      if (o->ph.mu > 0.0) broken_gradient<double>(L, en, qe.data(), g.data());
       for (int k = 0; k < n1; ++k) {
         int kn = rev ? P - k : k;
-        double t[4];
+        double* t = &tr[(((size_t)e * 4 + f) * n1 + k) * NT];
         trace_state(L.g.b, qe.data(), N, fn, kn, t);
-        for (int v = 0; v < 4; ++v) tr[(((size_t)e * 4 + f) * n1 + k) * 4 + v] = t[v];
+        if (o->ph.mu > 0.0) {
+          trace_state(L.g.b, g.data(), N, fn, kn, t + 4);
+          trace_state(L.g.b, g.data() + 4 * N, N, fn, kn, t + 8);
+        }
+        t[12] = L.g.fJ[((size_t)en * 4 + fn) * n1 + kn];
       }
     }
+}
+
+// Viscous fluxes (Section 2.1) in x and y from the state and the gradients
+// d = (dp/dx, du/dx, dv/dx, dT/dx, dp/dy, du/dy, dv/dy, dT/dy): stress
+// tau_ij = mu (du_i/dx_j + du_j/dx_i - 2/3 div u delta_ij), heat flux
+// K_j = -(mu Cp / Pr) dT/dx_j, energy flux u_i tau_ij - K_j.
+template <class S>
+static void viscous_flux(const S q[4], const S d[8], const Phys& ph, S fv[4], S gv[4]) {
+  double Cp = ph.gamma / (ph.gamma - 1.0);
+  S ux = d[1], vx = d[2], Tx = d[3], uy = d[5], vy = d[6], Ty = d[7];
+  S dv = ux + vy;
+  S txx = ph.mu * (2.0 * ux - (2.0 / 3.0) * dv);
+  S tyy = ph.mu * (2.0 * vy - (2.0 / 3.0) * dv);
+  S txy = ph.mu * (uy + vx);
+  double k = ph.mu * Cp / ph.Pr;
+  fv[0] = 0.0; fv[1] = txx; fv[2] = txy; fv[3] = q[1] * txx + q[2] * txy + k * Tx;
+  gv[0] = 0.0; gv[1] = txy; gv[2] = tyy; gv[3] = q[1] * txy + q[2] * tyy + k * Ty;
 }
 
 // FR/CPR residual R = -div f of one element (Section 2.3, eq. eqn:FR_diff):
 // contravariant fluxes at solution points, Lagrange derivative, and the DG
 // correction of the jumps between the common and the local (extrapolated flux
-// polynomial) normal fluxes at the flux points.  Neighbour traces are frozen.
+// polynomial) normal fluxes at the flux points.  Neighbour data are frozen.
+//
+// With mu > 0 the flux is f_inv - f_vis (Section 2.1).  The viscous flux at a
+// solution point takes the corrected gradient: the reference derivatives of
+// the state plus the DG correction of the jumps q_com - q^- (eq. com_q) at the
+// flux points of the same line, then the chain rule.  At a flux point it takes
+// q_com and the common gradient of eq. com_grad_q, with the BR2 liftings
+// r^(+-) = eta_f g'(face) (q_com - q^(+-)) S^(+-) / |J|^(+-): the correction
+// of that face alone, evaluated at the face point (g'_R(1) = (P+1)^2 / 2 for
+// the DG correction; S the outward face normal scaled by the face metric).
 template <class S>
 static void element_residual(const Oracle* o, const Level& L, int e, const S* qe,
                              const double* ntr, S* Re) {
   const Basis1D& b = L.g.b;
   int P = b.P, n1 = P + 1, N = L.g.N;
   const Phys& ph = o->ph;
+  const bool visc = ph.mu > 0.0;
+  const double eta_f = 4.0, gface = 0.5 * n1 * n1;
   std::vector<S> Ft(4 * N), Gt(4 * N);
+  // Viscous preliminaries: traces, common states, corrected gradients.
+  std::vector<S> qm_all(4 * n1 * 4), qc_all(4 * n1 * 4), gb(8 * N), gc(8 * N);
+  for (int f = 0; f < 4; ++f)
+    for (int k = 0; k < n1; ++k) {
+      S* qm = &qm_all[(f * n1 + k) * 4];
+      trace_state(b, qe, N, f, k, qm);
+      const double* t = &ntr[(((size_t)e * 4 + f) * n1 + k) * NT];
+      for (int v = 0; v < 4; ++v) qc_all[(f * n1 + k) * 4 + v] = 0.5 * (qm[v] + t[v]);
+    }
+  if (visc) {
+    broken_gradient<S>(L, e, qe, gb.data());
+    for (int v = 0; v < 4; ++v)
+      for (int j = 0; j < n1; ++j)
+        for (int i = 0; i < n1; ++i) {
+          S qx = 0.0, qy = 0.0;
+          for (int m = 0; m < n1; ++m) {
+            qx += b.D[i * n1 + m] * qe[v * N + j * n1 + m];
+            qy += b.D[j * n1 + m] * qe[v * N + m * n1 + i];
+          }
+          // xi faces 3 (xi = -1) and 1 (xi = +1) at face point j; eta faces
+          // 0 (eta = -1) and 2 (eta = +1) at face point i.
+          qx += b.gL[i] * (qc_all[(3 * n1 + j) * 4 + v] - qm_all[(3 * n1 + j) * 4 + v]) +
+                b.gR[i] * (qc_all[(1 * n1 + j) * 4 + v] - qm_all[(1 * n1 + j) * 4 + v]);
+          qy += b.gL[j] * (qc_all[(0 * n1 + i) * 4 + v] - qm_all[(0 * n1 + i) * 4 + v]) +
+                b.gR[j] * (qc_all[(2 * n1 + i) * 4 + v] - qm_all[(2 * n1 + i) * 4 + v]);
+          const double* mt = &L.g.met[((size_t)e * N + j * n1 + i) * 5];
+          int pt = j * n1 + i;
+          gc[(0 * 4 + v) * N + pt] = (mt[3] * qx - mt[2] * qy) / mt[4];
+          gc[(1 * 4 + v) * N + pt] = (-mt[1] * qx + mt[0] * qy) / mt[4];
+        }
+  }
   for (int pt = 0; pt < N; ++pt) {
     const double* m = &L.g.met[((size_t)e * N + pt) * 5];
     S q[4] = {qe[0 * N + pt], qe[1 * N + pt], qe[2 * N + pt], qe[3 * N + pt]};
     S fx[4], fy[4];
     euler_flux_n(q, 1.0, 0.0, ph, fx);
     euler_flux_n(q, 0.0, 1.0, ph, fy);
+    if (visc) {
+      S d[8], fv[4], gv[4];
+      for (int c = 0; c < 8; ++c) d[c] = gc[c * N + pt];
+      viscous_flux(q, d, ph, fv, gv);
+      for (int v = 0; v < 4; ++v) { fx[v] -= fv[v]; fy[v] -= gv[v]; }
+    }
     for (int v = 0; v < 4; ++v) {
       Ft[v * N + pt] = m[3] * fx[v] - m[1] * fy[v];    //  y_eta f - x_eta g
       Gt[v * N + pt] = -m[2] * fx[v] + m[0] * fy[v];   // -y_xi f + x_xi g
@@ -552,10 +657,29 @@ static void element_residual(const Oracle* o, const Level& L, int e, const S* qe
   for (int f = 0; f < 4; ++f)
     for (int k = 0; k < n1; ++k) {
       S qm[4], qp[4], fo[4];
-      trace_state(b, qe, N, f, k, qm);
-      for (int v = 0; v < 4; ++v) qp[v] = ntr[(((size_t)e * 4 + f) * n1 + k) * 4 + v];
+      for (int v = 0; v < 4; ++v) qm[v] = qm_all[(f * n1 + k) * 4 + v];
+      const double* t = &ntr[(((size_t)e * 4 + f) * n1 + k) * NT];
+      for (int v = 0; v < 4; ++v) qp[v] = t[v];
       const double* Sv = &L.g.fS[(((size_t)e * 4 + f) * n1 + k) * 2];
       roe_flux(qm, qp, Sv[0], Sv[1], ph, fo);
+      if (visc) {
+        // Common gradient, eq. com_grad_q: broken gradients of both sides
+        // at the face point plus their BR2 liftings.
+        double Jm = L.g.fJ[((size_t)e * 4 + f) * n1 + k], Jp = t[12];
+        S gm[8], dcom[8], qcm[4], fv[4], gv[4];
+        trace_state(b, gb.data(), N, f, k, gm);
+        trace_state(b, gb.data() + 4 * N, N, f, k, gm + 4);
+        for (int v = 0; v < 4; ++v) {
+          S qcv = qc_all[(f * n1 + k) * 4 + v];
+          qcm[v] = qcv;
+          S rm = eta_f * gface * (qcv - qm[v]) / Jm;    // times S_out
+          S rp = eta_f * gface * (qcv - qp[v]) / Jp;    // times -S_out
+          dcom[v] = 0.5 * (gm[v] + t[4 + v] + (rm - rp) * Sv[0]);
+          dcom[4 + v] = 0.5 * (gm[4 + v] + t[8 + v] + (rm - rp) * Sv[1]);
+        }
+        viscous_flux(qcm, dcom, ph, fv, gv);
+        for (int v = 0; v < 4; ++v) fo[v] -= fv[v] * Sv[0] + gv[v] * Sv[1];
+      }
       double sg = (f == 1 || f == 2) ? 1.0 : -1.0;        // outward -> reference-direction
       const std::vector<double>& l = (f == 1 || f == 2) ? b.lp : b.lm;
       const std::vector<double>& gp = (f == 1 || f == 2) ? b.gR : b.gL;
@@ -844,6 +968,8 @@ void* orc_create(const OrcConfig* cfg, int E, int Ng, const double* nodes, const
   Oracle* o = new Oracle();
   o->cfg = *cfg;
   o->ph = {cfg->gamma, cfg->Ma_inf, cfg->kappa, cfg->cutoff};
+  o->ph.mu = cfg->mu;
+  o->ph.Pr = cfg->Pr;
   o->E = E; o->Ng = Ng;
   int nn = (Ng + 1) * (Ng + 1);
   o->nodes.assign(nodes, nodes + (size_t)E * nn * 2);
