@@ -79,6 +79,14 @@ typedef struct {
                      (geom_order > 1) meshes need P >= geom_order on every
                      level (pmg_upload_mesh returns PMG_EINVAL otherwise).  Every call still takes
                      and returns absolute p. */
+  double mu;      /* constant dynamic viscosity (Section 2.1); 0: Euler.
+                     mu > 0 adds the viscous fluxes with the common
+                     solution of eq. com_q and the BR2 common gradient of
+                     eq. com_grad_q (penalty eta_f = 4, the number of faces
+                     of a quadrilateral) to the residual and to the element
+                     blocks.  The fused coarse sweep is not used then. */
+  double Pr;      /* Prandtl number of the heat flux K_j = -(mu Cp / Pr)
+                     dT/dx_j (0.72 in the paper); read when mu > 0 */
 } pmg_config;
 
 /* Mesh of quadrilaterals with Lagrange geometry of order geom_order (1 or 2).

@@ -62,7 +62,8 @@ static void esdirk3_table(Ctx& c) {
 }
 
 static void free_level(LevelDev& L) {
-  double** ptrs[] = {&L.q, &L.q2, &L.qb, &L.S, &L.F, &L.Pd, &L.met, &L.face, &L.Fcom, &L.Dfull, &L.rs, &L.cs};
+  double** ptrs[] = {&L.q,     &L.q2, &L.qb, &L.S,  &L.F,  &L.Pd, &L.met,  &L.face,
+                     &L.Fcom,  &L.Dfull, &L.rs, &L.cs, &L.Gb, &L.Qj, &L.fJinv};
   for (double** p : ptrs) { if (*p) cudaFree(*p); *p = nullptr; }
   if (L.Dinv) cudaFree(L.Dinv);
   L.Dinv = nullptr;
@@ -83,6 +84,9 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   if (cfg->block_prec != PMG_PREC_FP64 && cfg->block_prec != PMG_PREC_FP32)
     return fail(PMG_EINVAL, "unknown block precision");
   if (!(cfg->gamma > 1.0)) return fail(PMG_EINVAL, "gamma must exceed 1");
+  if (!(cfg->mu >= 0.0) || !std::isfinite(cfg->mu)) return fail(PMG_EINVAL, "mu must be finite and >= 0");
+  if (cfg->mu > 0.0 && !(cfg->Pr > 0.0 && std::isfinite(cfg->Pr)))
+    return fail(PMG_EINVAL, "Pr must be finite and > 0 when mu > 0");
   int dev;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(PMG_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
@@ -104,6 +108,8 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   c.ph.p_ref = cfg->p_gauge;
   c.ph.inv_gamma = 1.0 / cfg->gamma;
   c.ph.inv_gm1 = 1.0 / (cfg->gamma - 1.0);
+  c.ph.mu = cfg->mu;
+  c.ph.kT = cfg->mu > 0.0 ? cfg->mu * c.ph.Cp / cfg->Pr : 0.0;
   esdirk3_table(c);
   if (dalloc(&c.d_scal, 4) != cudaSuccess || dalloc(&c.d_flag, 4) != cudaSuccess ||
       dalloc(&c.d_dtau, 1) != cudaSuccess || cudaMallocHost((void**)&c.h_scal, 8 * sizeof(double)) != cudaSuccess ||
@@ -185,6 +191,9 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
       for (int k = 0; k < L.n1; ++k) L.op.D[i][k] = r.D[i * L.n1 + k];
       L.op.lm[i] = r.lm[i]; L.op.lp[i] = r.lp[i]; L.op.gL[i] = r.gL[i]; L.op.gR[i] = r.gR[i];
     }
+    // BR2 lifting factor: penalty eta_f = 4 (faces of a quadrilateral) times
+    // the DG correction's g_R'(1) = (P+1)^2 / 2
+    L.op.pen = 4.0 * 0.5 * L.n1 * L.n1;
     size_t nn2 = (size_t)c.E * L.n * L.n;
     if (dalloc(&L.q, L.tot) || dalloc(&L.qb, L.tot) || dalloc(&L.S, L.tot) || dalloc(&L.F, L.tot) ||
         dalloc(&L.Pd, L.tot) || dalloc(&L.met, geo[l].met.size()) || dalloc(&L.face, geo[l].face.size()) ||
@@ -197,8 +206,14 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
     // coarse sweeps are bound by FP64 issue, not by launches.
     int fuse_max = -1;
     if (const char* env = getenv("PMG_FUSE_MAX_P")) fuse_max = atoi(env);
-    L.fused = (l > 0 && L.P <= fuse_max && L.P <= 3);
+    L.fused = (l > 0 && L.P <= fuse_max && L.P <= 3 && c.ph.mu == 0.0);
     if (L.fused && dalloc(&L.q2, L.tot)) return fail(PMG_ENOMEM, "device allocation failed for level data");
+    if (c.ph.mu > 0.0) {
+      if (dalloc(&L.Gb, (size_t)6 * c.E * L.N) || dalloc(&L.Qj, (size_t)3 * c.E * 4 * L.n1) ||
+          dalloc(&L.fJinv, geo[l].fJinv.size()))
+        return fail(PMG_ENOMEM, "device allocation failed for level data");
+      PMG_CK(cudaMemcpy(L.fJinv, geo[l].fJinv.data(), geo[l].fJinv.size() * 8, cudaMemcpyHostToDevice));
+    }
     PMG_CK(cudaMemset(L.S, 0, L.tot * 8));
     PMG_CK(cudaMemset(L.q, 0, L.tot * 8));
     PMG_CK(cudaMemcpy(L.met, geo[l].met.data(), geo[l].met.size() * 8, cudaMemcpyHostToDevice));
@@ -598,10 +613,12 @@ pmg_status pmg_residual_static(pmg_ctx* h, int level, const double* q, double* R
   Ctx& c = h->c;
   pmg_status st = check_level(c, level);
   if (st) return st;
-  LevelDev L = c.lev[level];   // shallow copy: only the face-flux slot is redirected
+  LevelDev L = c.lev[level];   // shallow copy: only the scratch slots are redirected
+  const bool visc = c.ph.mu > 0.0;
   const size_t n_state = L.tot, n_face = (size_t)4 * c.E * 4 * L.n1;
-  if (n_state + n_face > kStaticScratchDoubles)
-    return fail(PMG_EINVAL, "pmg_residual_static: level needs " + std::to_string(n_state + n_face) +
+  const size_t n_visc = visc ? (size_t)6 * c.E * L.N + (size_t)3 * c.E * 4 * L.n1 : 0;
+  if (n_state + n_face + n_visc > kStaticScratchDoubles)
+    return fail(PMG_EINVAL, "pmg_residual_static: level needs " + std::to_string(n_state + n_face + n_visc) +
                                 " scratch doubles, the static scratch holds " +
                                 std::to_string(kStaticScratchDoubles));
   int cur = -1;
@@ -611,6 +628,10 @@ pmg_status pmg_residual_static(pmg_ctx* h, int level, const double* q, double* R
   PMG_CK(static_scratch_address(c.device, &scratch));
   double* qs = scratch;
   L.Fcom = scratch + n_state;
+  if (visc) {   // broken gradients and face jumps of the viscous terms
+    L.Gb = scratch + n_state + n_face;
+    L.Qj = L.Gb + (size_t)6 * c.E * L.N;
+  }
   PMG_CK(cudaMemcpyAsync(qs, q, n_state * 8, cudaMemcpyDeviceToDevice, c.stream));
   launch_shift_pressure(n_state / 4, -c.ph.p_ref, qs, c.stream);
   launch_face_flux(c, L, qs, c.stream);

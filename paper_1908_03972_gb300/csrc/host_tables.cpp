@@ -192,6 +192,7 @@ void build_level_geometry(const MeshHost& m, const Ref1D& r, LevelGeomHost& g) {
   g.met.assign((size_t)5 * E * N, 0.0);
   g.xy.assign((size_t)E * N * 2, 0.0);
   g.face.assign((size_t)E * 4 * n1 * 3, 0.0);
+  g.fJinv.assign((size_t)E * 4 * n1, 0.0);
   for (int e = 0; e < E; ++e) {
     const double* xn = &m.nodes[(size_t)e * nn * 2];
     for (int j = 0; j < n1; ++j)
@@ -226,6 +227,9 @@ void build_level_geometry(const MeshHost& m, const Ref1D& r, LevelGeomHost& g) {
         double dS = std::sqrt(sx * sx + sy * sy);
         double* o = &g.face[(((size_t)e * 4 + f) * n1 + k) * 3];
         o[0] = sx / dS; o[1] = sy / dS; o[2] = dS;
+        double det = J[0] * J[3] - J[1] * J[2];
+        if (!(det > 0.0)) throw std::runtime_error("non-positive element Jacobian on a face");
+        g.fJinv[((size_t)e * 4 + f) * n1 + k] = 1.0 / det;
       }
   }
   // Both sides of a face must see the same normal flux: copy the owner's

@@ -143,6 +143,7 @@ void launch_assemble(const Ctx& c, const LevelDev& L, const double* q, const dou
     default: PMG_ASM(4); break;
   }
 #undef PMG_ASM
+  if (c.ph.mu > 0.0) launch_assemble_visc(c, L, q, s);
 }
 
 // -------------------------------------------------------------------- factor

@@ -13,6 +13,16 @@
 //    deterministic per-CTA sum of squares for the residual norm.
 //
 // Both kernels are bound by FP64 arithmetic on GB300 (about 1.2 TFLOP/s).
+//
+// Viscous terms (mu > 0, Section 2.1 fluxes, Section 2.3 common viscous flux):
+// a gradient launch (k_viscous.cu) first forms the broken gradients of
+// (u, v, T) at the solution points.  The face launch extrapolates them from
+// both sides, adds the BR2 liftings of the jump to form the common gradient of
+// eq. com_grad_q, evaluates the viscous flux at q_com (eq. com_q) and
+// subtracts it from the Roe flux; it also stores q_com - q_own for both
+// elements.  The volume launch forms the corrected gradient at each solution
+// point (derivative plus DG correction of those jumps) and subtracts the
+// viscous flux from the inviscid one before the divergence.
 #include "pmg_internal.h"
 
 namespace pmg {
@@ -50,11 +60,32 @@ __device__ __forceinline__ void line_trace(const double* __restrict__ q, size_t 
   }
 }
 
+// Trace of the six broken-gradient planes of element e at face point (f, k).
 template <int P>
+__device__ __forceinline__ void grad_trace(const double* __restrict__ Gb, size_t plane, int e, int f, int k,
+                                           const double* lm, const double* lp, double out[6]) {
+  constexpr int n1 = P + 1, N = n1 * n1;
+  const bool plus = (f == 1 || f == 2);
+  const bool eta = (f == 0 || f == 2);
+  const double* base = Gb + (size_t)e * N + (eta ? k : k * n1);
+  const int stride = eta ? n1 : 1;
+#pragma unroll
+  for (int v = 0; v < 6; ++v) {
+    double s = 0.0;
+#pragma unroll
+    for (int m = 0; m < n1; ++m) s = fma(plus ? lp[m] : lm[m], __ldg(base + v * plane + m * stride), s);
+    out[v] = s;
+  }
+}
+
+template <int P, bool VISC>
 __global__ void __launch_bounds__(256) face_flux_kernel(const int* __restrict__ faces, int n_faces, int E,
                                                         const double* __restrict__ q,
                                                         const double* __restrict__ face,
-                                                        double* __restrict__ Fcom, OpTab op, Phys ph) {
+                                                        double* __restrict__ Fcom, OpTab op, Phys ph,
+                                                        const double* __restrict__ Gb,
+                                                        const double* __restrict__ fJinv,
+                                                        double* __restrict__ Qj) {
   constexpr int n1 = P + 1, N = n1 * n1;
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= n_faces * n1) return;
@@ -86,6 +117,30 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const int* __restrict__ 
   roe_flux_jump(qm, qp, dq, pgm, pgp, __ldg(g), __ldg(g + 1), __ldg(g + 2), ph, out);
   size_t fplane = (size_t)E * 4 * n1;
   size_t iL = ((size_t)eL * 4 + fL) * n1 + k, iR = ((size_t)eR * 4 + fR) * n1 + kR;
+  if (VISC) {
+    // common gradient: mean of the two broken-gradient traces plus the BR2
+    // liftings r^- + r^+ = pen (q_com - q^-) (1/|J|^- + 1/|J|^+) n dS, with
+    // q_com - q^- = dq / 2
+    double gm[6], gp[6], gc[6];
+    grad_trace<P>(Gb, plane, eL, fL, k, lm, lp, gm);
+    grad_trace<P>(Gb, plane, eR, fR, kR, lm, lp, gp);
+    const double nx = __ldg(g), ny = __ldg(g + 1), dS = __ldg(g + 2);
+    const double wl = 0.25 * op.pen * (__ldg(fJinv + iL) + __ldg(fJinv + iR)) * dS;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      gc[v] = fma(wl * nx, dq[v + 1], 0.5 * (gm[v] + gp[v]));
+      gc[3 + v] = fma(wl * ny, dq[v + 1], 0.5 * (gm[3 + v] + gp[3 + v]));
+    }
+    double fv[4], gv[4];
+    viscous_flux(0.5 * (qm[1] + qp[1]), 0.5 * (qm[2] + qp[2]), gc, ph, fv, gv);
+#pragma unroll
+    for (int v = 1; v < 4; ++v) out[v] -= fma(fv[v], nx, gv[v] * ny) * dS;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      Qj[v * fplane + iL] = 0.5 * dq[v + 1];
+      Qj[v * fplane + iR] = -0.5 * dq[v + 1];
+    }
+  }
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     Fcom[v * fplane + iL] = out[v];
@@ -98,7 +153,7 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const int* __restrict__ 
 // place (eq. smoothing_element_jacobi).  That is safe within one launch: the
 // face fluxes were formed from the old state by the preceding face launch,
 // and a CTA reads and writes only its own elements' states.
-template <int P, class W, bool APPLY>
+template <int P, class W, bool APPLY, bool VISC>
 __global__ void __launch_bounds__(256) volume_kernel(int E, const double* q,
                                                      const double* __restrict__ met,
                                                      const double* __restrict__ Fcom, OpTab op, Phys ph,
@@ -109,9 +164,11 @@ __global__ void __launch_bounds__(256) volume_kernel(int E, const double* q,
                                                      const double* __restrict__ qn,
                                                      double* __restrict__ partial, double* qw,
                                                      const W* __restrict__ Dinv, const double* __restrict__ rs,
-                                                     const double* __restrict__ cs) {
+                                                     const double* __restrict__ cs,
+                                                     const double* __restrict__ Qj) {
   constexpr int n1 = P + 1, N = n1 * n1, EPB = ElemsPerBlock<P>::value, n = 4 * N;
   __shared__ W sr[APPLY ? EPB : 1][APPLY ? n : 1];
+  __shared__ double sV[VISC ? EPB : 1][3][VISC ? N : 1];   // (u, v, T) for the gradients
   __shared__ double sFt[EPB][4][N];
   __shared__ double sGt[EPB][4][N];
   __shared__ double sJ[EPB][4][4][n1];   // [face][var][k]
@@ -132,6 +189,13 @@ __global__ void __launch_bounds__(256) volume_kernel(int E, const double* q,
 
   double qq[4] = {0, 0, 0, 0}, invJ = 0.0, rho_pt = 0.0;
   size_t gi = (size_t)e * N + pt;
+  if (VISC) {
+    if (active) {
+#pragma unroll
+      for (int v = 1; v < 4; ++v) sV[VISC ? le : 0][v - 1][VISC ? pt : 0] = q[v * plane + gi];
+    }
+    __syncthreads();
+  }
   if (active) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) qq[v] = q[v * plane + gi];
@@ -142,6 +206,33 @@ __global__ void __launch_bounds__(256) volume_kernel(int E, const double* q,
     rho_pt = qa[0] * s_rcp(qa[3]);
     double f[4], g[4];
     flux_xy_rho(qa, qq[0], rho_pt, ph, f, g);
+    if (VISC) {
+      // corrected gradient: reference derivatives plus the DG correction of
+      // the jumps q_com - q_own at the four faces' points on this point's lines
+      const int i = pt % n1, j = pt / n1;
+      const size_t fplane = (size_t)E * 4 * n1;
+      const double* Qe = Qj + (size_t)e * 4 * n1;
+      double gr[6], fv[4], gv[4];
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        double ax = 0.0, ae = 0.0;
+#pragma unroll
+        for (int m = 0; m < n1; ++m) {   // differences to the line's first value
+          ax = fma(sD[i][m], sV[VISC ? le : 0][v][VISC ? j * n1 + m : 0] - sV[VISC ? le : 0][v][VISC ? j * n1 : 0], ax);
+          ae = fma(sD[j][m], sV[VISC ? le : 0][v][VISC ? m * n1 + i : 0] - sV[VISC ? le : 0][v][VISC ? i : 0], ae);
+        }
+        const double* Qv = Qe + v * fplane;
+        ax = fma(sgL[i], __ldg(Qv + 3 * n1 + j), ax);
+        ax = fma(sgR[i], __ldg(Qv + 1 * n1 + j), ax);
+        ae = fma(sgL[j], __ldg(Qv + 0 * n1 + i), ae);
+        ae = fma(sgR[j], __ldg(Qv + 2 * n1 + i), ae);
+        gr[v] = invJ * fma(a, ax, c * ae);
+        gr[3 + v] = invJ * fma(b, ax, d * ae);
+      }
+      viscous_flux(qq[1], qq[2], gr, ph, fv, gv);
+#pragma unroll
+      for (int v = 1; v < 4; ++v) { f[v] -= fv[v]; g[v] -= gv[v]; }
+    }
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       sFt[le][v][pt] = fma(a, f[v], b * g[v]);
@@ -303,7 +394,17 @@ void launch_face_flux(const Ctx& c, const LevelDev& L, const double* q, cudaStre
   int total = c.n_faces * L.n1;
   // one warp per CTA: FP64-bound threads, spread over every SM
   int threads = 32, blocks = (total + threads - 1) / threads;
-#define PMG_FACE(PP) face_flux_kernel<PP><<<blocks, threads, 0, s>>>(c.d_faces, c.n_faces, c.E, q, L.face, L.Fcom, L.op, c.ph)
+  const bool visc = c.ph.mu > 0.0;
+  if (visc) launch_grad(c, L, q, s);
+#define PMG_FACE(PP)                                                                                       \
+  do {                                                                                                     \
+    if (visc)                                                                                              \
+      face_flux_kernel<PP, true><<<blocks, threads, 0, s>>>(c.d_faces, c.n_faces, c.E, q, L.face, L.Fcom, \
+                                                            L.op, c.ph, L.Gb, L.fJinv, L.Qj);             \
+    else                                                                                                   \
+      face_flux_kernel<PP, false><<<blocks, threads, 0, s>>>(c.d_faces, c.n_faces, c.E, q, L.face, L.Fcom, \
+                                                             L.op, c.ph, nullptr, nullptr, nullptr);       \
+  } while (0)
   switch (L.P) {
     case 0: PMG_FACE(0); break;
     case 1: PMG_FACE(1); break;
@@ -321,9 +422,16 @@ void launch_volume(const Ctx& c, const LevelDev& L, int level, const double* q, 
   int threads = residual_threads_per_block(L.P);
   int blocks = residual_blocks_for(L.P, c.E);
 #define PMG_VOL(PP)                                                                                          \
-  volume_kernel<PP, double, false><<<blocks, threads, 0, s>>>(c.E, q, L.met, L.Fcom, L.op, c.ph, out, (int)mode, \
-                                                              inv_odt, src, S, Sout, Pd, qn, partial, nullptr,   \
-                                                              nullptr, nullptr, nullptr)
+  do {                                                                                                       \
+    if (c.ph.mu > 0.0)                                                                                       \
+      volume_kernel<PP, double, false, true><<<blocks, threads, 0, s>>>(                                     \
+          c.E, q, L.met, L.Fcom, L.op, c.ph, out, (int)mode, inv_odt, src, S, Sout, Pd, qn, partial, nullptr, \
+          nullptr, nullptr, nullptr, L.Qj);                                                                  \
+    else                                                                                                     \
+      volume_kernel<PP, double, false, false><<<blocks, threads, 0, s>>>(                                    \
+          c.E, q, L.met, L.Fcom, L.op, c.ph, out, (int)mode, inv_odt, src, S, Sout, Pd, qn, partial, nullptr, \
+          nullptr, nullptr, nullptr, nullptr);                                                               \
+  } while (0)
   switch (L.P) {
     case 0: PMG_VOL(0); break;
     case 1: PMG_VOL(1); break;
@@ -340,10 +448,19 @@ static void volume_apply_dispatch(const Ctx& c, const LevelDev& L, double* q, do
   int threads = residual_threads_per_block(L.P);
   int blocks = residual_blocks_for(L.P, c.E);
   const W* Dinv = (const W*)L.Dinv;
-#define PMG_VA(PP)                                                                                        \
-  volume_kernel<PP, W, true><<<blocks, threads, 0, s>>>(c.E, q, L.met, L.Fcom, L.op, c.ph, nullptr,          \
-                                                        (int)RES_SYSTEM, inv_odt, src, S, nullptr, nullptr, qn, \
-                                                        nullptr, q, Dinv, L.rs, L.cs)
+#define PMG_VA(PP)                                                                                          \
+  do {                                                                                                        \
+    if (c.ph.mu > 0.0)                                                                                        \
+      volume_kernel<PP, W, true, true><<<blocks, threads, 0, s>>>(c.E, q, L.met, L.Fcom, L.op, c.ph, nullptr,  \
+                                                                  (int)RES_SYSTEM, inv_odt, src, S, nullptr,   \
+                                                                  nullptr, qn, nullptr, q, Dinv, L.rs, L.cs,   \
+                                                                  L.Qj);                                       \
+    else                                                                                                      \
+      volume_kernel<PP, W, true, false><<<blocks, threads, 0, s>>>(c.E, q, L.met, L.Fcom, L.op, c.ph, nullptr, \
+                                                                   (int)RES_SYSTEM, inv_odt, src, S, nullptr,  \
+                                                                   nullptr, qn, nullptr, q, Dinv, L.rs, L.cs,  \
+                                                                   nullptr);                                   \
+  } while (0)
   switch (L.P) {
     case 0: PMG_VA(0); break;
     case 1: PMG_VA(1); break;

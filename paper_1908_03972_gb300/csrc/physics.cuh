@@ -19,6 +19,8 @@ struct Phys {
   double p_ref;    // device states hold p - p_ref (gauge pressure)
   double inv_gamma;  // 1 / gamma
   double inv_gm1;    // 1 / (gamma - 1)
+  double mu;         // constant dynamic viscosity (0: Euler)
+  double kT;         // heat conductivity mu Cp / Pr
 };
 
 // ---------------------------------------------------------------------------
@@ -251,6 +253,26 @@ __host__ __device__ inline void gamma_and_M(const double q[4], const Phys& ph, d
   G[14] = M[14] = rho * v;
   G[15] += rho * ph.Cp;
   M[15] += rho * ph.Cp;
+}
+
+// Viscous fluxes (Section 2.1, constant mu) in x and y from the velocity and
+// the gradients g = (du/dx, dv/dx, dT/dx, du/dy, dv/dy, dT/dy):
+// tau_ij = mu (du_i/dx_j + du_j/dx_i) - (2/3) mu div(u) delta_ij, and the
+// energy flux u_i tau_ij - K_j with K_j = -kT dT/dx_j.  Mass rows are zero.
+template <class S>
+__host__ __device__ inline void viscous_flux(S u, S v, const S g[6], const Phys& ph, S fv[4], S gv[4]) {
+  const S div3 = (g[0] + g[4]) * (2.0 / 3.0);
+  const S txx = ph.mu * (2.0 * g[0] - div3);
+  const S tyy = ph.mu * (2.0 * g[4] - div3);
+  const S txy = ph.mu * (g[3] + g[1]);
+  fv[0] = 0.0;
+  fv[1] = txx;
+  fv[2] = txy;
+  fv[3] = u * txx + v * txy + ph.kT * g[2];
+  gv[0] = 0.0;
+  gv[1] = txy;
+  gv[2] = tyy;
+  gv[3] = u * txy + v * tyy + ph.kT * g[5];
 }
 
 }  // namespace pmg

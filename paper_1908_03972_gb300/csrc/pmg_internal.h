@@ -34,6 +34,7 @@ struct LevelGeomHost {
   std::vector<double> met;   // 5 planes of E*N: a, b, c, d, 1/|J|
   std::vector<double> xy;    // (E, N, 2)
   std::vector<double> face;  // (E, 4, n1, 3): unit outward normal, area factor
+  std::vector<double> fJinv; // (E, 4, n1): 1/|J| at the face points
 };
 
 Ref1D make_ref1d(int P);
@@ -46,6 +47,7 @@ void build_level_geometry(const MeshHost& m, const Ref1D& r, LevelGeomHost& g);
 struct OpTab {
   double D[kMaxP + 1][kMaxP + 1];
   double lm[kMaxP + 1], lp[kMaxP + 1], gL[kMaxP + 1], gR[kMaxP + 1];
+  double pen;   // BR2 lifting factor eta_f g_R'(1) = 4 (P+1)^2 / 2
 };
 
 // Restriction (nc x nf) and prolongation (nf x nc) 1D operators, by value.
@@ -68,6 +70,10 @@ struct LevelDev {
   double* met = nullptr;       // 5 * E * N
   double* face = nullptr;      // E * 4 * n1 * 3
   double* Fcom = nullptr;      // 4 * E * 4 * n1 common fluxes, outward
+  // viscous terms (mu > 0 only)
+  double* Gb = nullptr;        // 6 * E * N broken gradients of (u, v, T): x planes, then y
+  double* Qj = nullptr;        // 3 * E * 4 * n1: q_com - q_own of (u, v, T) at each element face point
+  double* fJinv = nullptr;     // E * 4 * n1: 1/|J| at the face points
   double* Dfull = nullptr;     // E * n * n assembled FP64 blocks (row-major)
   void* Dinv = nullptr;        // E * n * n factored inverse (column-major), FP32 or FP64
   double* rs = nullptr;        // E * n row scales
@@ -165,6 +171,8 @@ void launch_stage_src(const Ctx& c, int N, const double* qcn, double* const* R, 
 void launch_bsum_update(const Ctx& c, int N, const double* qn, double* const* R, const double* b, int nr,
                         double dt, double* q, cudaStream_t s);
 void launch_shift_pressure(size_t plane, double delta, double* q, cudaStream_t s);
+void launch_grad(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s);
+void launch_assemble_visc(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s);
 void launch_fused_sweep(const Ctx& c, const LevelDev& L, const double* qin, double* qout, double inv_odt,
                         const double* src, const double* S, const double* qref, int prec, cudaStream_t s);
 int residual_threads_per_block(int P);

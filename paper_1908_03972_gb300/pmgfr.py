@@ -45,6 +45,8 @@ class pmg_config(ctypes.Structure):
         ("block_prec", ctypes.c_int),
         ("use_graph", ctypes.c_int),
         ("p_gauge", ctypes.c_double),
+        ("mu", ctypes.c_double),
+        ("Pr", ctypes.c_double),
     ]
 
 
@@ -136,7 +138,7 @@ def _ptr(x, writable=False):
 
 def make_config(P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutoff=0, dtau_init=0.01,
                 dtau_max=10.0, tol=1e-8, refresh_every=10, max_pseudo=2000, block_prec=PMG_PREC_FP64,
-                use_graph=1, p_gauge=0.0) -> pmg_config:
+                use_graph=1, p_gauge=0.0, mu=0.0, Pr=0.72) -> pmg_config:
     cfg = pmg_config()
     cfg.n_levels = len(P_levels)
     for l, (P, n) in enumerate(zip(P_levels, n_smooth)):
@@ -147,6 +149,7 @@ def make_config(P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutof
     cfg.refresh_every, cfg.max_pseudo = refresh_every, max_pseudo
     cfg.block_prec, cfg.use_graph = block_prec, use_graph
     cfg.p_gauge = p_gauge
+    cfg.mu, cfg.Pr = mu, Pr
     return cfg
 
 
