@@ -5,11 +5,13 @@ and the plain FP64 element-Jacobi P-multigrid V-cycle, plus DOF-sweeps/s.
 
 Workload (default "c2"): isentropic vortex, Ma_inf = 0.005, periodic
 [0,10]^2, 64x64 straight quads, P{3-2-1-0}, I{5-10-20-40}, ESDIRK3,
-dt = 0.1, dtau 0.01 -> 10, smoother refresh every 10 pseudo-iterations.
-Every step is the first physical step from the analytic vortex (the state is
-reset before each step, outside the timed region); inputs are synthetic and
-resident in HBM when a timed step starts.  L2 is flushed before every timed
-step by writing a 256 MiB buffer.
+dt = 0.1, dtau 0.01 -> 10, smoother refresh every 10 pseudo-iterations, the
+residual norm with each equation divided by its free-stream convective flux
+scale.  The vortex is advanced by consecutive physical steps from the
+analytic state: W untimed warm-up steps, then K timed steps (the defaults,
+3 + 2, are the configuration's five steps); both block precisions advance
+the same steps.  Inputs are synthetic and resident in HBM when a timed step
+starts.  L2 is flushed before every timed step by writing a 256 MiB buffer.
 
 One JSON line is printed by rank 0.  Under torchrun (N > 1) every rank runs
 an independent replica (weak scaling, no data-path collective).
@@ -34,17 +36,18 @@ VCYCLE_FILE = os.path.join(ROOT, "profiles", "c2_step_vcycles.json")
 
 WORKLOADS = {
     "c2": dict(name="2D Euler isentropic vortex, Ma_inf=0.005, periodic [0,10]^2, 64x64 straight quads, "
-                    "P{3-2-1-0} (64 DOFs/elem), I{5-10-20-40}, ESDIRK3 dt=0.1, first step from the analytic "
-                    "state, each stage to a 1e-8 relative drop",
+                    "P{3-2-1-0} (64 DOFs/elem), I{5-10-20-40}, ESDIRK3 dt=0.1, consecutive steps from the "
+                    "analytic state, each stage to a 1e-8 relative drop of the free-stream-scaled norm",
                n=64, levels=[3, 2, 1, 0], smooth=[5, 10, 20, 40], dt=0.1),
     "c1": dict(name="2D Euler isentropic vortex, Ma_inf=0.005, periodic [0,10]^2, 8x8 straight quads, "
-                    "P{2-1-0} (36 DOFs/elem), I{5-10-20}, ESDIRK3 dt=0.1, first step from the analytic state, "
-                    "each stage to a 1e-8 relative drop",
+                    "P{2-1-0} (36 DOFs/elem), I{5-10-20}, ESDIRK3 dt=0.1, consecutive steps from the analytic "
+                    "state, each stage to a 1e-8 relative drop of the free-stream-scaled norm",
                n=8, levels=[2, 1, 0], smooth=[5, 10, 20], dt=0.1),
 }
 
-# FP64 arithmetic peak of one GB300: 2 FP64 FMA per clock per SM (measured:
-# 1.20 TFLOP/s of dependent-free DFMA at 2.0 GHz), 152 SMs, 2.07 GHz max clock.
+# FP64 arithmetic peak of one GB300 from its unit counts: 2 FP64 FMA per clock
+# per SM, 152 SMs, 2.07 GHz maximum clock (a DFMA microbenchmark sustains
+# 1.005 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
@@ -190,7 +193,7 @@ def oracle_sample(wl, n_ref, n_plain):
     import oracle as O
     from paper_1908_03972_gb300 import workloads as W
     nodes, nbr = W.periodic_box(wl["n"], wl["n"], Ng=1)
-    orc = O.Oracle(nodes, nbr, 1, wl["levels"], wl["smooth"], tol=1e-8)
+    orc = O.Oracle(nodes, nbr, 1, wl["levels"], wl["smooth"], tol=1e-8, res_scale=W.freestream_scales(0.005))
     q = W.isentropic_vortex(orc.coords())
     A, b, c = O.esdirk3()
     dt = wl["dt"]
@@ -258,7 +261,7 @@ def run_ours(args, wl, world, rank, local):
     E = nodes.shape[0]
     stream = torch.cuda.current_stream(device)
     kw = dict(tol=1e-8, dtau_init=0.01, dtau_max=10.0, refresh_every=10, max_pseudo=20000, use_graph=1,
-              p_gauge=W.freestream_T(0.005))
+              p_gauge=W.freestream_T(0.005), res_scale=W.freestream_scales(0.005))
     dsw = dof_sweeps_per_vcycle(E, wl["levels"], wl["smooth"])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
 
@@ -271,7 +274,7 @@ def run_ours(args, wl, world, rank, local):
     state_bytes = q0.nbytes
 
     def one_step(s, timed):
-        pmgfr.pmg_set_state(s.h, 0, q0_dev)
+        """Advance the solver's state by one physical step (events on its stream)."""
         if timed:
             flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -302,12 +305,16 @@ def run_ours(args, wl, world, rank, local):
         return 0
 
     results = {}
-    for prec, label, warm in ((pmgfr.PMG_PREC_FP32, "mixed", args.warmup), (pmgfr.PMG_PREC_FP64, "fp64", 0)):
+    q_warm = None   # state after the warm-up steps (host), start of the timed steps
+    for prec, label in ((pmgfr.PMG_PREC_FP32, "mixed"), (pmgfr.PMG_PREC_FP64, "fp64")):
         if args.skip_fp64 and label == "fp64":
             continue
         s = solver if label == "mixed" else make(prec)
-        for _ in range(warm):
+        pmgfr.pmg_set_state(s.h, 0, q0_dev)
+        for _ in range(args.warmup):
             one_step(s, False)
+        if label == "mixed":
+            q_warm = np.ascontiguousarray(s.get_state())
         sampler = ClockSampler(local) if label == "mixed" else None
         if sampler:
             sampler.start()
@@ -315,31 +322,41 @@ def run_ours(args, wl, world, rank, local):
             import torch.distributed as dist
             dist.barrier()
         torch.cuda.synchronize(device)
-        ms, stats = [], None
+        ms, its, drops, nvs, nrs = [], [], [], [], []
         for _ in range(args.steps):
             t, stats = one_step(s, True)
             ms.append(t)
+            its.append(list(stats.pseudo_iters)[:3])
+            drops.append(max(float(x) for x in list(stats.res_drop)[:3]))
+            nvs.append(stats.n_vcycles)
+            nrs.append(stats.n_refresh)
         torch.cuda.synchronize(device)
         clocks = sampler.stop() if sampler else None
         mean_ms = barrier_max(float(np.mean(ms)), world, device)
-        nv = stats.n_vcycles
-        results[label] = dict(s_per_step=mean_ms / 1000.0, ms=ms, vcycles=nv, refreshes=stats.n_refresh,
-                              pseudo_iters=list(stats.pseudo_iters)[:3],
-                              res_drop=[float(x) for x in list(stats.res_drop)[:3]],
+        nv = float(np.mean(nvs))
+        results[label] = dict(s_per_step=mean_ms / 1000.0, ms=ms, vcycles=nv, refreshes=float(np.mean(nrs)),
+                              pseudo_iters=its, max_res_drop=drops,
                               dof_sweeps_per_s=dsw * nv * world / (mean_ms / 1000.0), clocks=clocks)
         if label != "mixed":
             s.close()
 
     mixed = results["mixed"]
-    # end to end through the C interface with host buffers: H2D state, step, D2H state
-    qh = np.ascontiguousarray(q0)
-    out = np.empty_like(qh)
-    torch.cuda.synchronize(device)
-    t0 = time.perf_counter()
-    pmgfr.pmg_set_state(solver.h, 0, qh)
-    pmgfr.pmg_esdirk_step(solver.h, wl["dt"])
-    pmgfr.pmg_get_state(solver.h, 0, out)
-    e2e_s = barrier_max(time.perf_counter() - t0, world, device)
+    # End to end through the C interface with host buffers: the same K steps
+    # from the state after the warm-ups, each step taking its state from pinned
+    # host memory and returning the new state there.
+    qh = torch.from_numpy(q_warm).pin_memory().numpy()
+    out = torch.empty(qh.shape, dtype=torch.float64).pin_memory().numpy()
+    e2e = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        pmgfr.pmg_set_state(solver.h, 0, qh)
+        pmgfr.pmg_esdirk_step(solver.h, wl["dt"])
+        pmgfr.pmg_get_state(solver.h, 0, out)
+        e2e.append(time.perf_counter() - t0)
+        qh[...] = out
+    e2e_s = barrier_max(float(np.mean(e2e)), world, device)
 
     # per-launch profile of one step (launch by launch, CUDA events on the solver stream)
     pmgfr.pmg_profile(solver.h, True)
@@ -397,14 +414,15 @@ def run_ours(args, wl, world, rank, local):
                    "sample": ("one V-cycle with smoother rebuild (%.1f s) and one without (%.1f s) on the full "
                               "workload, single-threaded FP64 oracle, scaled by this run's %d rebuilding and %d "
                               "plain V-cycles per step" % (smp["t_vcycle_refresh"], smp["t_vcycle"],
-                                                           mixed["refreshes"], mixed["vcycles"] - mixed["refreshes"]))}
+                                                           round(mixed["refreshes"]),
+                                                           round(mixed["vcycles"] - mixed["refreshes"])))}
         except Exception as exc:  # the product number stands without it
             cpu = {"value": None, "unit": "s/step", "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
         if args.workload == "c2":
             os.makedirs(os.path.dirname(VCYCLE_FILE), exist_ok=True)
             with open(VCYCLE_FILE, "w") as f:
                 json.dump({"workload": wl["name"], "vcycles": mixed["vcycles"], "refreshes": mixed["refreshes"],
-                           "pseudo_iters": mixed["pseudo_iters"]}, f, indent=1)
+                           "pseudo_iters": mixed["pseudo_iters"], "warmup_steps": args.warmup}, f, indent=1)
 
     if rank == 0:
         line = {
@@ -437,7 +455,7 @@ def run_ours(args, wl, world, rank, local):
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))

@@ -87,6 +87,16 @@ typedef struct {
                      blocks.  The fused coarse sweep is not used then. */
   double Pr;      /* Prandtl number of the heat flux K_j = -(mu Cp / Pr)
                      dT/dx_j (0.72 in the paper); read when mu > 0 */
+  double res_scale[4]; /* reference scale of each equation (mass, x and y
+                     momentum, energy) in ||F||, the norm of eq. ser and of
+                     the stopping test: ||F||^2 = sum_v sum_pts
+                     (F_v / res_scale[v])^2 over the finest level.  The paper
+                     leaves the weighting open; a value <= 0 counts as 1.
+                     The free-stream convective flux scales (rho U, rho U^2,
+                     rho U^2, rho U H) make the equations commensurate at low
+                     Mach, where the unweighted norm is the energy residual,
+                     H ~ 1/Ma^2 times any mass imbalance, and stages that
+                     start near their solution stall. */
 } pmg_config;
 
 /* Mesh of quadrilaterals with Lagrange geometry of order geom_order (1 or 2).

@@ -58,6 +58,7 @@ class OrcConfig(ctypes.Structure):
         ("max_pseudo", ctypes.c_int),
         ("mu", ctypes.c_double),
         ("Pr", ctypes.c_double),
+        ("res_scale", ctypes.c_double * 4),
     ]
 
 
@@ -161,7 +162,7 @@ class Oracle:
 
     def __init__(self, nodes, nbr, Ng, P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005,
                  kappa=1.0, cutoff=0, dtau_init=0.01, dtau_max=10.0, tol=1e-8,
-                 refresh_every=10, max_pseudo=2000, mu=0.0, Pr=0.72):
+                 refresh_every=10, max_pseudo=2000, mu=0.0, Pr=0.72, res_scale=(1.0, 1.0, 1.0, 1.0)):
         cfg = OrcConfig()
         cfg.n_levels = len(P_levels)
         for l, P in enumerate(P_levels):
@@ -172,6 +173,8 @@ class Oracle:
         cfg.dtau_init, cfg.dtau_max, cfg.tol = dtau_init, dtau_max, tol
         cfg.refresh_every, cfg.max_pseudo = refresh_every, max_pseudo
         cfg.mu, cfg.Pr = mu, Pr
+        for v in range(4):
+            cfg.res_scale[v] = res_scale[v]
         self.cfg = cfg
         self.nodes = _f64(nodes)
         self.nbr = np.ascontiguousarray(nbr, dtype=np.int32)

@@ -87,6 +87,8 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   if (!(cfg->mu >= 0.0) || !std::isfinite(cfg->mu)) return fail(PMG_EINVAL, "mu must be finite and >= 0");
   if (cfg->mu > 0.0 && !(cfg->Pr > 0.0 && std::isfinite(cfg->Pr)))
     return fail(PMG_EINVAL, "Pr must be finite and > 0 when mu > 0");
+  for (int v = 0; v < 4; ++v)
+    if (!std::isfinite(cfg->res_scale[v])) return fail(PMG_EINVAL, "res_scale must be finite");
   int dev;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(PMG_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
@@ -110,6 +112,7 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   c.ph.inv_gm1 = 1.0 / (cfg->gamma - 1.0);
   c.ph.mu = cfg->mu;
   c.ph.kT = cfg->mu > 0.0 ? cfg->mu * c.ph.Cp / cfg->Pr : 0.0;
+  for (int v = 0; v < 4; ++v) c.ph.nw[v] = cfg->res_scale[v] > 0.0 ? 1.0 / cfg->res_scale[v] : 1.0;
   esdirk3_table(c);
   if (dalloc(&c.d_scal, 4) != cudaSuccess || dalloc(&c.d_flag, 4) != cudaSuccess ||
       dalloc(&c.d_dtau, 1) != cudaSuccess || cudaMallocHost((void**)&c.h_scal, 8 * sizeof(double)) != cudaSuccess ||

@@ -312,7 +312,10 @@ __global__ void __launch_bounds__(256) volume_kernel(int E, const double* q,
         } else {
           out[o] = F;
         }
-        ssq = fma(F, F, ssq);
+        if (partial) {   // weighted sum of squares of the norm of eq. ser
+          const double Fw = F * ph.nw[v];
+          ssq = fma(Fw, Fw, ssq);
+        }
       }
     }
   }

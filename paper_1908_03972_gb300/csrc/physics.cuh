@@ -21,6 +21,7 @@ struct Phys {
   double inv_gm1;    // 1 / (gamma - 1)
   double mu;         // constant dynamic viscosity (0: Euler)
   double kT;         // heat conductivity mu Cp / Pr
+  double nw[4];      // weights 1 / res_scale of the equations in the residual norm
 };
 
 // ---------------------------------------------------------------------------

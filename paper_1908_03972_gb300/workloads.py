@@ -107,6 +107,15 @@ def freestream_T(Ma_inf: float, speed: float = math.sqrt(2.0), gamma: float = GA
     return c * c / gamma
 
 
+def freestream_scales(Ma_inf: float, rho: float = 1.0, speed: float = math.sqrt(2.0),
+                      gamma: float = GAMMA) -> tuple:
+    """Convective flux scales (rho U, rho U^2, rho U^2, rho U H) of the free
+    stream, one per equation: the reference scales of the residual norm."""
+    T = freestream_T(Ma_inf, speed, gamma)
+    H = gamma / (gamma - 1.0) * T + 0.5 * speed * speed
+    return (rho * speed, rho * speed * speed, rho * speed * speed, rho * speed * H)
+
+
 def isentropic_vortex(xy: np.ndarray, t: float = 0.0, Ma_inf: float = 0.005,
                       strength: float = 5.0, phi: float = 0.5,
                       center=(5.0, 5.0), period=(10.0, 10.0),

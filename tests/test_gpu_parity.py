@@ -278,39 +278,52 @@ def test_stage_solve_parity(prec, gauge):
         gpu.close()
 
 
+_C1_STEPS = 3
+_C1_KW = dict(tol=1e-8, dtau_init=0.01, dtau_max=10.0, refresh_every=10, max_pseudo=4000,
+              res_scale=W.freestream_scales(0.005))
+_c1_oracle_cache = {}
+
+
+def _c1_oracle_steps():
+    """The oracle's first three ESDIRK3 steps of C1 (computed once per module)."""
+    if "steps" not in _c1_oracle_cache:
+        nodes, nbr = W.periodic_box(8, 8, Ng=1)
+        orc = O.Oracle(nodes, nbr, 1, [2, 1, 0], [5, 10, 20], **_C1_KW)
+        q = W.isentropic_vortex(orc.coords())
+        out = []
+        for _ in range(_C1_STEPS):
+            q, its, _ = orc.esdirk_step(q, 0.1)
+            out.append((q.copy(), its))
+        _c1_oracle_cache["steps"] = out
+    return _c1_oracle_cache["steps"]
+
+
 @pytest.mark.parametrize("gauge", GAUGES)
 @pytest.mark.parametrize("prec", [0, 1])
 def test_esdirk_c1_parity(prec, gauge):
     """Vortex, 8x8 straight quads on [0,10]^2, P{2-1-0}, I{5-10-20}, ESDIRK3,
-    dt = 0.1, tol 1e-8: the first physical step from the analytic state against
-    the oracle.  From the second step on the stage residuals start small and
-    the first V-cycle raises them ~100x through the energy equation, after
-    which SER shrinks dtau until the stage stalls, in both codes."""
+    dt = 0.1, tol 1e-8 of the free-stream-scaled norm: three consecutive
+    physical steps from the analytic state, each against the oracle's."""
+    from paper_1908_03972_gb300 import pmgfr
     nodes, nbr = W.periodic_box(8, 8, Ng=1)
-    kw = dict(tol=1e-8, dtau_init=0.01, dtau_max=10.0, refresh_every=10)
-    orc, gpu = _pair(nodes, nbr, 1, [2, 1, 0], [5, 10, 20], prec=prec, p_gauge=gauge, **kw)
+    ref = _c1_oracle_steps()
+    gpu = pmgfr.Solver(nodes, nbr, [2, 1, 0], [5, 10, 20], block_prec=prec, p_gauge=gauge, **_C1_KW)
     try:
-        q = W.isentropic_vortex(orc.coords())
-        qo, qg = q.copy(), q.copy()
-        for step in range(1):
-            qo, its_o, drops_o = orc.esdirk_step(qo, 0.1)
+        qg = W.isentropic_vortex(gpu.coords())
+        for step, (qo, its_o) in enumerate(ref):
             qg, st = gpu.esdirk_step(qg, 0.1)
             its_g = list(st.pseudo_iters)[:3]
             assert max(st.res_drop[:3]) <= 1e-8
             if prec == 0:
-                # The last decades converge at ~0.99 per V-cycle, so where 1e-8 is
-                # crossed depends on rounding: the GPU forms pressure and energy
-                # differences without rounding p ~ rho E ~ 1/Ma^2 (the oracle does
-                # not) and may need fewer V-cycles.  Stage 2 is decided before the
-                # tail and must agree closely.
-                assert abs(its_o[0] - its_g[0]) <= max(3, 0.02 * its_o[0]), (its_o, its_g)
-                assert all(b <= 1.05 * a + 3 for a, b in zip(its_o, its_g)), (its_o, its_g)
-        # The 1e-8 stopping test bounds ||F||, dominated by the energy equation
-        # (rho E ~ 1/Ma^2); a remaining energy residual of 1e-8 ||F^0|| allows
-        # pressure differences of order (gamma-1) omega dt 1e-8 ||F^0|| ~ 1e-6
-        # rho_inf |v_inf|^2 between two converged solutions.
-        dp = np.abs(qg[0] - qo[0]).max() / 2.0
-        du = np.abs(qg[1:3] - qo[1:3]).max()
-        assert dp <= 2e-6 and du <= 1e-7, (dp, du)
+                # the last decades converge slowly, so where 1e-8 is crossed
+                # depends on rounding; the GPU forms pressure and energy
+                # differences without rounding p ~ rho E ~ 1/Ma^2
+                assert all(b <= 1.1 * a + 5 and a <= 1.1 * b + 5 for a, b in zip(its_o, its_g)), (step, its_o, its_g)
+            # Two states that both meet the stopping test differ by up to the
+            # error it allows; for the pressure that is of order
+            # (gamma-1) omega dt tol ||F^0|| ~ 1e-6 rho_inf |v_inf|^2 per step.
+            dp = np.abs(qg[0] - qo[0]).max() / 2.0
+            du = np.abs(qg[1:3] - qo[1:3]).max()
+            assert dp <= 2e-6 * (step + 1) and du <= 1e-7 * (step + 1), (step, dp, du)
     finally:
         gpu.close()
