@@ -243,6 +243,21 @@ pmg_status pmg_profile_read(pmg_ctx* ctx, double* ms, long long* counts);
  * on it.  The call synchronises the context's stream before returning. */
 pmg_status pmg_residual_static(pmg_ctx* ctx, int level, const double* q, double* R);
 
+/* Checkpoint and restore of the finest-level state (no counterpart in the
+ * paper).  pmg_checkpoint writes a binary file at `path` (a host string): a
+ * header (magic "PMGFRCK1", version, element count, geometry order, P of
+ * every level, hashes of the mesh and of the discretisation settings gamma,
+ * Ma_inf, kappa, cutoff, p_gauge, mu, Pr, res_scale and the P hierarchy) and
+ * the state as stored on the device (variable-major FP64, pressure relative
+ * to p_gauge).  Everything else a physical step uses (stage data, blocks,
+ * coarse states) is rebuilt by the step, so a restored context repeats the
+ * next pmg_esdirk_step bit for bit on the same GPU.  pmg_restore checks the
+ * header against the context and returns PMG_EINVAL for another mesh, P
+ * hierarchy or setting, a truncated or foreign file; PMG_ESTATE without a
+ * mesh.  Both synchronise the context's stream. */
+pmg_status pmg_checkpoint(pmg_ctx* ctx, const char* path);
+pmg_status pmg_restore(pmg_ctx* ctx, const char* path);
+
 #ifdef __cplusplus
 }
 #endif

@@ -4,6 +4,8 @@
 // k_residual.cu, k_blocks.cu and k_misc.cu; the host only sequences launches,
 // keeps the pseudo-time schedule and reads one norm per V-cycle.
 #include <cmath>
+#include <cstdint>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -552,6 +554,102 @@ pmg_status pmg_set_state(pmg_ctx* h, int level, const double* q, int on_device) 
   PMG_CK_LAUNCH();
   PMG_CK(cudaStreamSynchronize(c.stream));
   if (level == 0) c.F0_valid = false;
+  return PMG_OK;
+}
+
+// ------------------------------------------------------- checkpoint / restore
+// File: 72-byte header (magic, version, E, P of every level, geometry order,
+// a hash of the mesh and of the discretisation settings), then the finest
+// state as stored on the device (variable-major FP64, pressure relative to
+// p_gauge), so that a restored run repeats the next step bit for bit.
+namespace {
+constexpr char kCkptMagic[8] = {'P', 'M', 'G', 'F', 'R', 'C', 'K', '1'};
+struct CkptHeader {
+  char magic[8];
+  int32_t version, n_elem, geom_order, n_levels;
+  int32_t P[8];
+  uint64_t mesh_hash, config_hash;
+};
+static_assert(sizeof(CkptHeader) == 72, "checkpoint header layout");
+
+uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
+  const unsigned char* b = (const unsigned char*)data;
+  for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ull; }
+  return h;
+}
+
+uint64_t mesh_hash(const Ctx& c) {
+  uint64_t h = 1469598103934665603ull;
+  h = fnv1a(h, c.mesh.nodes.data(), c.mesh.nodes.size() * sizeof(double));
+  return fnv1a(h, c.mesh.nbr.data(), c.mesh.nbr.size() * sizeof(int));
+}
+
+uint64_t config_hash(const Ctx& c) {
+  // the settings that define the discrete system (not the solver schedule)
+  const pmg_config& g = c.cfg;
+  double d[8 + 4] = {g.gamma, g.Ma_inf, g.kappa, (double)g.cutoff, g.p_gauge, g.mu, g.Pr, (double)g.n_levels,
+                     g.res_scale[0], g.res_scale[1], g.res_scale[2], g.res_scale[3]};
+  uint64_t h = fnv1a(1469598103934665603ull, d, sizeof(d));
+  return fnv1a(h, g.P, sizeof(g.P));
+}
+
+CkptHeader make_header(const Ctx& c) {
+  CkptHeader hd;
+  memset(&hd, 0, sizeof(hd));
+  memcpy(hd.magic, kCkptMagic, 8);
+  hd.version = 1;
+  hd.n_elem = c.E;
+  hd.geom_order = c.mesh.Ng;
+  hd.n_levels = c.cfg.n_levels;
+  for (int l = 0; l < c.cfg.n_levels; ++l) hd.P[l] = c.cfg.P[l];
+  hd.mesh_hash = mesh_hash(c);
+  hd.config_hash = config_hash(c);
+  return hd;
+}
+}  // namespace
+
+pmg_status pmg_checkpoint(pmg_ctx* h, const char* path) {
+  if (!h || !path) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  if (!c.mesh_ready) return fail(PMG_ESTATE, "no mesh uploaded");
+  const LevelDev& L = c.lev[0];
+  std::vector<double> buf(L.tot);
+  PMG_CK(cudaMemcpyAsync(buf.data(), L.q, L.tot * 8, cudaMemcpyDeviceToHost, c.stream));
+  PMG_CK(cudaStreamSynchronize(c.stream));
+  CkptHeader hd = make_header(c);
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(PMG_EINVAL, std::string("cannot open ") + path + " for writing");
+  bool ok = fwrite(&hd, sizeof(hd), 1, f) == 1 && fwrite(buf.data(), 8, buf.size(), f) == buf.size();
+  ok = (fclose(f) == 0) && ok;
+  if (!ok) return fail(PMG_EINVAL, std::string("write failed: ") + path);
+  return PMG_OK;
+}
+
+pmg_status pmg_restore(pmg_ctx* h, const char* path) {
+  if (!h || !path) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  if (!c.mesh_ready) return fail(PMG_ESTATE, "no mesh uploaded");
+  LevelDev& L = c.lev[0];
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(PMG_EINVAL, std::string("cannot open ") + path);
+  CkptHeader hd;
+  std::vector<double> buf(L.tot);
+  bool ok = fread(&hd, sizeof(hd), 1, f) == 1;
+  ok = ok && fread(buf.data(), 8, buf.size(), f) == buf.size();
+  char extra;
+  ok = ok && fread(&extra, 1, 1, f) == 0;   // nothing after the state
+  fclose(f);
+  if (!ok) return fail(PMG_EINVAL, std::string("not a checkpoint of this size: ") + path);
+  CkptHeader want = make_header(c);
+  if (memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != 1)
+    return fail(PMG_EINVAL, std::string("not a pmgfr checkpoint: ") + path);
+  if (hd.n_elem != want.n_elem || hd.geom_order != want.geom_order || hd.n_levels != want.n_levels ||
+      memcmp(hd.P, want.P, sizeof(hd.P)) != 0 || hd.mesh_hash != want.mesh_hash)
+    return fail(PMG_EINVAL, "checkpoint is for another mesh or P hierarchy");
+  if (hd.config_hash != want.config_hash) return fail(PMG_EINVAL, "checkpoint is for other discretisation settings");
+  PMG_CK(cudaMemcpyAsync(L.q, buf.data(), L.tot * 8, cudaMemcpyHostToDevice, c.stream));
+  PMG_CK(cudaStreamSynchronize(c.stream));
+  c.F0_valid = false;
   return PMG_OK;
 }
 

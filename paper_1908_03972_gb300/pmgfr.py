@@ -106,6 +106,8 @@ def load():
         "pmg_stage_history": ([vp, pd, pd, ci, ctypes.POINTER(ci)], ci),
         "pmg_profile": ([vp, ci], ci),
         "pmg_residual_static": ([vp, ci, vp, vp], ci),
+        "pmg_checkpoint": ([vp, ctypes.c_char_p], ci),
+        "pmg_restore": ([vp, ctypes.c_char_p], ci),
         "pmg_profile_read": ([vp, pd, ctypes.POINTER(ctypes.c_longlong)], ci),
     }
     for name, (args, res) in sig.items():
@@ -409,3 +411,11 @@ def pmg_residual_static(h, level, q, out):
         raise TypeError("pmg_residual_static takes device tensors only")
     _check(load().pmg_residual_static(h, level, pq, pr))
     return out
+
+
+def pmg_checkpoint(h, path):
+    _check(load().pmg_checkpoint(h, os.fsencode(path)))
+
+
+def pmg_restore(h, path):
+    _check(load().pmg_restore(h, os.fsencode(path)))
