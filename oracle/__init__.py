@@ -59,6 +59,7 @@ class OrcConfig(ctypes.Structure):
         ("mu", ctypes.c_double),
         ("Pr", ctypes.c_double),
         ("res_scale", ctypes.c_double * 4),
+        ("q_inf", ctypes.c_double * 4),
     ]
 
 
@@ -162,7 +163,8 @@ class Oracle:
 
     def __init__(self, nodes, nbr, Ng, P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005,
                  kappa=1.0, cutoff=0, dtau_init=0.01, dtau_max=10.0, tol=1e-8,
-                 refresh_every=10, max_pseudo=2000, mu=0.0, Pr=0.72, res_scale=(1.0, 1.0, 1.0, 1.0)):
+                 refresh_every=10, max_pseudo=2000, mu=0.0, Pr=0.72, res_scale=(1.0, 1.0, 1.0, 1.0),
+                 q_inf=(0.0, 0.0, 0.0, 0.0)):
         cfg = OrcConfig()
         cfg.n_levels = len(P_levels)
         for l, P in enumerate(P_levels):
@@ -175,6 +177,7 @@ class Oracle:
         cfg.mu, cfg.Pr = mu, Pr
         for v in range(4):
             cfg.res_scale[v] = res_scale[v]
+            cfg.q_inf[v] = q_inf[v]
         self.cfg = cfg
         self.nodes = _f64(nodes)
         self.nbr = np.ascontiguousarray(nbr, dtype=np.int32)
@@ -183,6 +186,9 @@ class Oracle:
         self.P = list(P_levels)
         self.h = lib().orc_create(ctypes.byref(cfg), self.E, Ng, _p(self.nodes),
                                   self.nbr.ctypes.data_as(_i))
+        if not self.h:
+            raise ValueError("invalid neighbour table (or a slip wall with mu > 0, "
+                             "or a no-slip wall without the eps cut-off)")
 
     def __del__(self):
         if getattr(self, "h", None):

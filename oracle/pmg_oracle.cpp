@@ -6,7 +6,9 @@
 // local preconditioning.  Viscous terms follow Section 2.3: q_com of eq.
 // com_q, common gradient of eq. com_grad_q with BR2 liftings.  The paper does
 // not state the BR2 penalty; eta_f = 4 (faces per element) is the reading
-// taken, and its value is parity unpinned (every pin holds for any eta_f > 0).  It exists only to
+// taken, and its value is parity unpinned (every pin holds for any eta_f > 0).
+// Boundary faces (slip wall, no-slip adiabatic wall, far field) use ghost
+// states through the same common fluxes; the paper states none (reading).  It exists only to
 // check the CUDA library: tests, the smoke check and the CPU-baseline leg of
 // the benchmark may load it; the product path never does.  It shares no code,
 // header, table or constant generator with the CUDA library.
@@ -22,7 +24,9 @@
 //   an element block row/column index is v*N + pt;
 //   faces: 0 eta=-1, 1 xi=+1, 2 eta=+1, 3 xi=-1; face points are ordered by the
 //   tangential reference coordinate increasing.
-//   nbr[(e*4+f)*3 + {0,1,2}] = (neighbour element, neighbour face, reversed?).
+//   nbr[(e*4+f)*3 + {0,1,2}] = (neighbour element, neighbour face, reversed?);
+//   a boundary face has neighbour element -1 and the boundary type in the
+//   second slot: 2 slip wall, 3 no-slip adiabatic wall, 4 far field.
 //   Element geometry: (Ng+1)^2 Lagrange nodes at equispaced reference
 //   positions, index b*(Ng+1)+a, a along xi; nodes[(e*(Ng+1)^2 + node)*2 + {x,y}].
 #include <complex>
@@ -424,6 +428,7 @@ struct OrcConfig {
   int refresh_every, max_pseudo;
   double mu, Pr;
   double res_scale[4];    // reference scale of each equation in ||F|| (0: 1)
+  double q_inf[4];        // free-stream primitive state (p, u, v, T) of far-field faces
 };
 
 struct Level {
@@ -543,6 +548,7 @@ static void neighbour_traces(const Oracle* o, const Level& L, const double* q, s
     for (int f = 0; f < 4; ++f) {
       int en = o->nbr[(e * 4 + f) * 3 + 0], fn = o->nbr[(e * 4 + f) * 3 + 1];
       int rev = o->nbr[(e * 4 + f) * 3 + 2];
+      if (en < 0) continue;   // boundary face: the ghost state follows the own trace
       for (int v = 0; v < 4; ++v)
         for (int p = 0; p < N; ++p) qe[v * N + p] = q[((size_t)v * E + en) * N + p];
       if (o->ph.mu > 0.0) broken_gradient<double>(L, en, qe.data(), g.data());
@@ -576,6 +582,32 @@ static void viscous_flux(const S q[4], const S d[8], const Phys& ph, S fv[4], S 
   gv[0] = 0.0; gv[1] = txy; gv[2] = tyy; gv[3] = q[1] * txy + q[2] * tyy + k * Ty;
 }
 
+// Boundary faces (the paper states no boundary treatment; reading: a ghost
+// state enters the same common fluxes).  From the own trace q^- and the unit
+// outward normal: slip wall (p, u - 2 u_n n, T); no-slip adiabatic wall
+// (p, -u, T); far field the free stream.  For the viscous terms the ghost
+// side mirrors the element (its broken-gradient trace and |J| are the own
+// ones), which makes eq. com_grad_q the standard one-sided BR2 gradient
+// grad q^- + eta_f g'(1) (q_com - q^-) S/|J|; walls carry no viscous energy
+// flux (u_com = 0 on a no-slip wall and the wall is adiabatic).
+template <class S>
+static void ghost_state(int bc, const S qm[4], double nx, double ny, const double qinf[4], S qg[4]) {
+  if (bc == 4) {
+    for (int v = 0; v < 4; ++v) qg[v] = qinf[v];
+    return;
+  }
+  qg[0] = qm[0];
+  qg[3] = qm[3];
+  if (bc == 3) {
+    qg[1] = -qm[1];
+    qg[2] = -qm[2];
+  } else {
+    S un = qm[1] * nx + qm[2] * ny;
+    qg[1] = qm[1] - 2.0 * un * nx;
+    qg[2] = qm[2] - 2.0 * un * ny;
+  }
+}
+
 // FR/CPR residual R = -div f of one element (Section 2.3, eq. eqn:FR_diff):
 // contravariant fluxes at solution points, Lagrange derivative, and the DG
 // correction of the jumps between the common and the local (extrapolated flux
@@ -600,13 +632,24 @@ static void element_residual(const Oracle* o, const Level& L, int e, const S* qe
   std::vector<S> Ft(4 * N), Gt(4 * N);
   // Viscous preliminaries: traces, common states, corrected gradients.
   std::vector<S> qm_all(4 * n1 * 4), qc_all(4 * n1 * 4), gb(8 * N), gc(8 * N);
-  for (int f = 0; f < 4; ++f)
+  std::vector<S> qp_all(4 * n1 * 4);
+  for (int f = 0; f < 4; ++f) {
+    const int en = o->nbr[(e * 4 + f) * 3 + 0], bc = o->nbr[(e * 4 + f) * 3 + 1];
     for (int k = 0; k < n1; ++k) {
       S* qm = &qm_all[(f * n1 + k) * 4];
+      S* qp = &qp_all[(f * n1 + k) * 4];
       trace_state(b, qe, N, f, k, qm);
       const double* t = &ntr[(((size_t)e * 4 + f) * n1 + k) * NT];
-      for (int v = 0; v < 4; ++v) qc_all[(f * n1 + k) * 4 + v] = 0.5 * (qm[v] + t[v]);
+      if (en < 0) {
+        const double* Sv = &L.g.fS[(((size_t)e * 4 + f) * n1 + k) * 2];
+        const double dS = std::sqrt(Sv[0] * Sv[0] + Sv[1] * Sv[1]);
+        ghost_state(bc, qm, Sv[0] / dS, Sv[1] / dS, o->cfg.q_inf, qp);
+      } else {
+        for (int v = 0; v < 4; ++v) qp[v] = t[v];
+      }
+      for (int v = 0; v < 4; ++v) qc_all[(f * n1 + k) * 4 + v] = 0.5 * (qm[v] + qp[v]);
     }
+  }
   if (visc) {
     broken_gradient<S>(L, e, qe, gb.data());
     for (int v = 0; v < 4; ++v)
@@ -658,28 +701,32 @@ static void element_residual(const Oracle* o, const Level& L, int e, const S* qe
   for (int f = 0; f < 4; ++f)
     for (int k = 0; k < n1; ++k) {
       S qm[4], qp[4], fo[4];
+      const bool bnd = o->nbr[(e * 4 + f) * 3 + 0] < 0;
+      const int bc = o->nbr[(e * 4 + f) * 3 + 1];
       for (int v = 0; v < 4; ++v) qm[v] = qm_all[(f * n1 + k) * 4 + v];
       const double* t = &ntr[(((size_t)e * 4 + f) * n1 + k) * NT];
-      for (int v = 0; v < 4; ++v) qp[v] = t[v];
+      for (int v = 0; v < 4; ++v) qp[v] = qp_all[(f * n1 + k) * 4 + v];
       const double* Sv = &L.g.fS[(((size_t)e * 4 + f) * n1 + k) * 2];
       roe_flux(qm, qp, Sv[0], Sv[1], ph, fo);
       if (visc) {
         // Common gradient, eq. com_grad_q: broken gradients of both sides
         // at the face point plus their BR2 liftings.
-        double Jm = L.g.fJ[((size_t)e * 4 + f) * n1 + k], Jp = t[12];
-        S gm[8], dcom[8], qcm[4], fv[4], gv[4];
+        double Jm = L.g.fJ[((size_t)e * 4 + f) * n1 + k], Jp = bnd ? Jm : t[12];
+        S gm[8], gp[8], dcom[8], qcm[4], fv[4], gv[4];
         trace_state(b, gb.data(), N, f, k, gm);
         trace_state(b, gb.data() + 4 * N, N, f, k, gm + 4);
+        for (int c = 0; c < 8; ++c) gp[c] = bnd ? gm[c] : S(t[4 + c]);
         for (int v = 0; v < 4; ++v) {
           S qcv = qc_all[(f * n1 + k) * 4 + v];
           qcm[v] = qcv;
           S rm = eta_f * gface * (qcv - qm[v]) / Jm;    // times S_out
           S rp = eta_f * gface * (qcv - qp[v]) / Jp;    // times -S_out
-          dcom[v] = 0.5 * (gm[v] + t[4 + v] + (rm - rp) * Sv[0]);
-          dcom[4 + v] = 0.5 * (gm[4 + v] + t[8 + v] + (rm - rp) * Sv[1]);
+          dcom[v] = 0.5 * (gm[v] + gp[v] + (rm - rp) * Sv[0]);
+          dcom[4 + v] = 0.5 * (gm[4 + v] + gp[4 + v] + (rm - rp) * Sv[1]);
         }
         viscous_flux(qcm, dcom, ph, fv, gv);
-        for (int v = 0; v < 4; ++v) fo[v] -= fv[v] * Sv[0] + gv[v] * Sv[1];
+        const int nv = (bnd && bc != 4) ? 3 : 4;   // walls: no viscous energy flux
+        for (int v = 0; v < nv; ++v) fo[v] -= fv[v] * Sv[0] + gv[v] * Sv[1];
       }
       double sg = (f == 1 || f == 2) ? 1.0 : -1.0;        // outward -> reference-direction
       const std::vector<double>& l = (f == 1 || f == 2) ? b.lp : b.lm;
@@ -988,6 +1035,15 @@ void* orc_create(const OrcConfig* cfg, int E, int Ng, const double* nodes, const
   int nn = (Ng + 1) * (Ng + 1);
   o->nodes.assign(nodes, nodes + (size_t)E * nn * 2);
   o->nbr.assign(nbr, nbr + (size_t)E * 12);
+  for (int i = 0; i < E * 4; ++i) {
+    int en = nbr[i * 3], fn = nbr[i * 3 + 1];
+    // slip walls are for inviscid runs only; a no-slip wall state has u = 0,
+    // where eps = min(1, max(kappa Ma_inf, Ma)) needs the cut-off
+    bool ok = en >= 0 ? (en < E && fn >= 0 && fn < 4)
+                      : (en == -1 && fn >= 2 && fn <= 4 && !(fn == 2 && cfg->mu > 0) &&
+                         !(fn == 3 && !(cfg->cutoff && cfg->kappa * cfg->Ma_inf > 0)));
+    if (!ok) { delete o; return nullptr; }
+  }
   o->lev.resize(cfg->n_levels);
   for (int l = 0; l < cfg->n_levels; ++l) {
     build_level_geom(o, cfg->P[l], &o->lev[l].g);

@@ -11,7 +11,9 @@ Mesh conventions (the library's C interface documents the same layout):
   ``a`` along the first reference direction xi.
 * ``nbr``: int32 ``(E, 4, 3)``: for each local face (0: eta=-1, 1: xi=+1,
   2: eta=+1, 3: xi=-1) the neighbour element, its local face and a flag that
-  is 1 when the two faces number their points in opposite order.
+  is 1 when the two faces number their points in opposite order.  A boundary
+  face has neighbour element -1 and its boundary type in the second slot
+  (``BC_SLIP_WALL``, ``BC_NOSLIP_WALL`` adiabatic, ``BC_FARFIELD``).
 """
 from __future__ import annotations
 
@@ -20,6 +22,7 @@ import math
 import numpy as np
 
 GAMMA = 1.4
+BC_SLIP_WALL, BC_NOSLIP_WALL, BC_FARFIELD = 2, 3, 4
 
 
 def periodic_box(nx: int, ny: int, x0: float = 0.0, x1: float = 10.0,
@@ -72,6 +75,89 @@ def periodic_box(nx: int, ny: int, x0: float = 0.0, x1: float = 10.0,
             nbr[e, 1] = (jy * nx + (ix + 1) % nx, 3, 0)
             nbr[e, 2] = (((jy + 1) % ny) * nx + ix, 0, 0)
             nbr[e, 3] = (jy * nx + (ix - 1) % nx, 1, 0)
+    return nodes, nbr
+
+
+def channel(nx: int, ny: int, x0: float = 0.0, x1: float = 10.0, y0: float = 0.0, y1: float = 2.0,
+            Ng: int = 1, perturb: float = 0.0, seed: int = 1234,
+            bottom: int = BC_NOSLIP_WALL, top: int = BC_NOSLIP_WALL):
+    """``nx`` x ``ny`` quadrilaterals of a rectangle, periodic in x, with
+    boundary faces of type ``bottom`` at y0 and ``top`` at y1.
+
+    With ``perturb > 0`` interior nodes move by seeded smooth modes that are
+    periodic in x and vanish in y at both walls, so the walls stay straight.
+    """
+    Lx, Ly = x1 - x0, y1 - y0
+    rng = np.random.default_rng(seed)
+    modes = []
+    if perturb > 0.0:
+        for _ in range(3):
+            kx = int(rng.integers(1, 3))
+            ax, ay = rng.uniform(-1.0, 1.0, size=2)
+            ph = rng.uniform(0.0, 2 * math.pi, size=2)
+            modes.append((kx, ax, ay, ph))
+    hx, hy = Lx / nx, Ly / ny
+    r = np.linspace(0.0, 1.0, Ng + 1)
+    E = nx * ny
+    nodes = np.zeros((E, (Ng + 1) ** 2, 2))
+    for jy in range(ny):
+        for ix in range(nx):
+            e = jy * nx + ix
+            A, B = np.meshgrid(r, r, indexing="xy")
+            X = x0 + (ix + A) * hx
+            Y = y0 + (jy + B) * hy
+            eta = (Y - y0) / Ly
+            dX = np.zeros_like(X)
+            dY = np.zeros_like(Y)
+            for kx, ax, ay, ph in modes:
+                arg = 2 * math.pi * kx * (X - x0) / Lx
+                dX += ax * np.sin(arg + ph[0]) * np.sin(math.pi * eta)
+                dY += ay * np.sin(arg + ph[1]) * np.sin(math.pi * eta)
+            sc = perturb * min(hx, hy) / max(1, len(modes))
+            nodes[e, :, 0] = (X + sc * dX).reshape(-1)
+            nodes[e, :, 1] = (Y + sc * dY).reshape(-1)
+    nbr = np.zeros((E, 4, 3), dtype=np.int32)
+    for jy in range(ny):
+        for ix in range(nx):
+            e = jy * nx + ix
+            nbr[e, 0] = ((jy - 1) * nx + ix, 2, 0) if jy > 0 else (-1, bottom, 0)
+            nbr[e, 1] = (jy * nx + (ix + 1) % nx, 3, 0)
+            nbr[e, 2] = ((jy + 1) * nx + ix, 0, 0) if jy < ny - 1 else (-1, top, 0)
+            nbr[e, 3] = (jy * nx + (ix - 1) % nx, 1, 0)
+    return nodes, nbr
+
+
+def cylinder_omesh(n_r: int, n_theta: int, r_in: float = 0.5, r_out: float = 50.0, Ng: int = 2,
+                   wall: int = BC_NOSLIP_WALL, outer: int = BC_FARFIELD):
+    """O-mesh around a circular cylinder centred at the origin.
+
+    Radii r_k = r_in (r_out/r_in)^(k/n_r), k = 0..n_r; angles 2 pi j/n_theta.
+    Element e = j*n_r + i spans [r_i, r_i+1] x [theta_j, theta_j+1], xi along
+    r and eta along theta; its Lagrange nodes sit at equispaced radius and
+    angle, so every node lies exactly on its circle.  Faces at r_in carry
+    ``wall``, faces at r_out ``outer``; the angular direction is periodic.
+    """
+    rk = r_in * (r_out / r_in) ** (np.arange(n_r + 1) / n_r)
+    dth = 2 * math.pi / n_theta
+    t = np.linspace(0.0, 1.0, Ng + 1)
+    E = n_r * n_theta
+    nodes = np.zeros((E, (Ng + 1) ** 2, 2))
+    for j in range(n_theta):
+        for i in range(n_r):
+            e = j * n_r + i
+            A, B = np.meshgrid(t, t, indexing="xy")   # A along xi = r, B along eta = theta
+            R = rk[i] + A * (rk[i + 1] - rk[i])
+            TH = (j + B) * dth
+            nodes[e, :, 0] = (R * np.cos(TH)).reshape(-1)
+            nodes[e, :, 1] = (R * np.sin(TH)).reshape(-1)
+    nbr = np.zeros((E, 4, 3), dtype=np.int32)
+    for j in range(n_theta):
+        for i in range(n_r):
+            e = j * n_r + i
+            nbr[e, 0] = (((j - 1) % n_theta) * n_r + i, 2, 0)
+            nbr[e, 1] = (j * n_r + i + 1, 3, 0) if i < n_r - 1 else (-1, outer, 0)
+            nbr[e, 2] = (((j + 1) % n_theta) * n_r + i, 0, 0)
+            nbr[e, 3] = (j * n_r + i - 1, 1, 0) if i > 0 else (-1, wall, 0)
     return nodes, nbr
 
 
