@@ -97,15 +97,31 @@ typedef struct {
                      Mach, where the unweighted norm is the energy residual,
                      H ~ 1/Ma^2 times any mass imbalance, and stages that
                      start near their solution stall. */
+  double q_inf[4]; /* free-stream primitive state (p absolute, u, v, T) that
+                     far-field boundary faces see as their outer state */
 } pmg_config;
+
+/* Boundary types, in the second slot of a boundary face's neighbour entry
+ * (whose element slot is -1).  The paper states no boundary treatment; a
+ * ghost state enters the same common fluxes (Section 2.3):
+ *  slip wall: (p, u - 2 u_n n, T), inviscid runs only (mu = 0);
+ *  no-slip adiabatic wall: (p, -u, -v, T); its mean state has u = 0, so it
+ *    needs the eps cut-off (cutoff = 1, kappa Ma_inf > 0);
+ *  far field: q_inf.
+ * For the viscous terms the ghost side mirrors the element (one-sided BR2
+ * gradient), and walls carry no viscous energy flux. */
+enum { PMG_BC_SLIP_WALL = 2, PMG_BC_NOSLIP_WALL = 3, PMG_BC_FARFIELD = 4 };
 
 /* Mesh of quadrilaterals with Lagrange geometry of order geom_order (1 or 2).
  *  nodes: (n_elem, (geom_order+1)^2, 2) FP64, element geometry nodes at
  *         equispaced reference positions, node b*(geom_order+1)+a, a along xi.
  *  nbr:   (n_elem, 4, 3) int32: for local faces 0 (eta=-1), 1 (xi=+1),
  *         2 (eta=+1), 3 (xi=-1): neighbour element, its local face, and 1 if
- *         the two faces number their points in opposite order.  Faces are
- *         interior or periodic (every face has a neighbour).
+ *         the two faces number their points in opposite order.  A
+ *         boundary face has neighbour element -1 and a PMG_BC_* type in the
+ *         face slot (0 in the third); pmg_upload_mesh returns PMG_EINVAL for
+ *         an unknown type, a slip wall with mu > 0, or a no-slip wall
+ *         without the eps cut-off.
  * Both arrays are host memory, copied during the call. */
 typedef struct {
   int n_elem;

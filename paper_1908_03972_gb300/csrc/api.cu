@@ -115,6 +115,7 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   c.ph.mu = cfg->mu;
   c.ph.kT = cfg->mu > 0.0 ? cfg->mu * c.ph.Cp / cfg->Pr : 0.0;
   for (int v = 0; v < 4; ++v) c.ph.nw[v] = cfg->res_scale[v] > 0.0 ? 1.0 / cfg->res_scale[v] : 1.0;
+  for (int v = 0; v < 4; ++v) c.ph.qinf[v] = cfg->q_inf[v];
   esdirk3_table(c);
   if (dalloc(&c.d_scal, 4) != cudaSuccess || dalloc(&c.d_flag, 4) != cudaSuccess ||
       dalloc(&c.d_dtau, 1) != cudaSuccess || cudaMallocHost((void**)&c.h_scal, 8 * sizeof(double)) != cudaSuccess ||
@@ -154,6 +155,15 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
     for (int l = 0; l < c.cfg.n_levels; ++l)
       if (c.cfg.P[l] < m->geom_order && m->geom_order > 1)
         return fail(PMG_EINVAL, "p_gauge != 0 needs P >= geometry order on every level (the metric identity)");
+  for (int i = 0; i < m->n_elem * 4; ++i) {
+    if (m->nbr[i * 3] != -1) continue;
+    const int bc = m->nbr[i * 3 + 1];
+    if (bc == PMG_BC_SLIP_WALL && c.ph.mu > 0.0) return fail(PMG_EINVAL, "slip walls are for mu = 0 only");
+    if (bc == PMG_BC_NOSLIP_WALL && !(c.ph.eps_min > 0.0))
+      return fail(PMG_EINVAL, "a no-slip wall needs the eps cut-off (cutoff = 1, kappa Ma_inf > 0)");
+    if (bc == PMG_BC_FARFIELD && !(c.ph.qinf[0] > 0.0 && c.ph.qinf[3] > 0.0))
+      return fail(PMG_EINVAL, "far-field faces need q_inf with p > 0 and T > 0");
+  }
   c.E = m->n_elem;
   c.mesh.E = m->n_elem;
   c.mesh.Ng = m->geom_order;
@@ -211,7 +221,9 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
     // coarse sweeps are bound by FP64 issue, not by launches.
     int fuse_max = -1;
     if (const char* env = getenv("PMG_FUSE_MAX_P")) fuse_max = atoi(env);
-    L.fused = (l > 0 && L.P <= fuse_max && L.P <= 3 && c.ph.mu == 0.0);
+    bool boundary = false;
+    for (const FaceRec& fr : c.mesh.faces) boundary = boundary || fr.eR < 0;
+    L.fused = (l > 0 && L.P <= fuse_max && L.P <= 3 && c.ph.mu == 0.0 && !boundary);
     if (L.fused && dalloc(&L.q2, L.tot)) return fail(PMG_ENOMEM, "device allocation failed for level data");
     if (c.ph.mu > 0.0) {
       if (dalloc(&L.Gb, (size_t)6 * c.E * L.N) || dalloc(&L.Qj, (size_t)3 * c.E * 4 * L.n1) ||

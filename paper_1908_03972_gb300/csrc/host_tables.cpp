@@ -235,6 +235,7 @@ void build_level_geometry(const MeshHost& m, const Ref1D& r, LevelGeomHost& g) {
   // Both sides of a face must see the same normal flux: copy the owner's
   // normal, negated, to the neighbour's matching points.
   for (const FaceRec& fr : m.faces) {
+    if (fr.eR < 0) continue;   // boundary faces have one side
     for (int k = 0; k < n1; ++k) {
       int kr = fr.rev ? P - k : k;
       const double* a = &g.face[(((size_t)fr.eL * 4 + fr.fL) * n1 + k) * 3];
@@ -249,6 +250,11 @@ void build_faces(MeshHost& m) {
   for (int e = 0; e < m.E; ++e)
     for (int f = 0; f < 4; ++f) {
       int en = m.nbr[(e * 4 + f) * 3 + 0], fn = m.nbr[(e * 4 + f) * 3 + 1], rev = m.nbr[(e * 4 + f) * 3 + 2];
+      if (en == -1) {   // boundary face: fn is the boundary type
+        if (fn < PMG_BC_SLIP_WALL || fn > PMG_BC_FARFIELD) throw std::runtime_error("bad boundary type");
+        m.faces.push_back(FaceRec{e, f, -1, fn, 0});
+        continue;
+      }
       if (en < 0 || en >= m.E || fn < 0 || fn > 3) throw std::runtime_error("bad neighbour table");
       const int* back = &m.nbr[(en * 4 + fn) * 3];
       if (back[0] != e || back[1] != f || back[2] != rev) throw std::runtime_error("neighbour table is not symmetric");

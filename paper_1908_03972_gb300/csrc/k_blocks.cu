@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(128) assemble_kernel(int E, const double* __re
     int f = t / n1, k = t - f * n1;
     const bool plus = (f == 1 || f == 2);
     const bool eta = (f == 0 || f == 2);
-    double qm[4], qp[4];
+    double qm[4], qp[4] = {0.0, 0.0, 0.0, 0.0};
     for (int v = 0; v < 4; ++v) {
       double s = 0.0;
       for (int m = 0; m < n1; ++m) s += (plus ? slp[m] : slm[m]) * sq[v][eta ? m * n1 + k : k * n1 + m];
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(128) assemble_kernel(int E, const double* __re
     }
     int en = nbr[(e * 4 + f) * 3 + 0], fn = nbr[(e * 4 + f) * 3 + 1], rev = nbr[(e * 4 + f) * 3 + 2];
     int kn = rev ? P - k : k;
-    {
+    if (en >= 0) {
       const bool pn = (fn == 1 || fn == 2);
       const bool en_eta = (fn == 0 || fn == 2);
       for (int v = 0; v < 4; ++v) {
@@ -91,14 +91,16 @@ __global__ void __launch_bounds__(128) assemble_kernel(int E, const double* __re
           s += (pn ? slp[m] : slm[m]) * q[v * plane + (size_t)en * N + (en_eta ? m * n1 + kn : kn * n1 + m)];
         qp[v] = s;
       }
+      qp[0] += ph.p_ref;
     }
     qm[0] += ph.p_ref;
-    qp[0] += ph.p_ref;
     const double* g = face + (((size_t)e * 4 + f) * n1 + k) * 3;
     double sg = plus ? 1.0 : -1.0;
     for (int w = 0; w < 4; ++w) {
       Dual dm[4], dp[4], o[4];
       for (int v = 0; v < 4; ++v) { dm[v] = Dual(qm[v], v == w ? 1.0 : 0.0); dp[v] = Dual(qp[v], 0.0); }
+      // a boundary face's ghost state follows the own trace (fn = boundary type)
+      if (en < 0) ghost_state(fn, dm, g[0], g[1], ph, dp);
       roe_flux(dm, dp, g[0], g[1], g[2], ph, o);
       for (int v = 0; v < 4; ++v) sC[f][k][v * 4 + w] = sg * o[v].d;
     }

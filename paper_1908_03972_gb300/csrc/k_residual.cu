@@ -5,6 +5,8 @@
 //    neighbouring solution polynomials along the line normal to the face,
 //    evaluates the preconditioned Roe flux once and writes it, with opposite
 //    signs, into both elements' face slots (no atomics, exact conservation).
+//    On a boundary face the outer state is the ghost state of the boundary
+//    type (physics.cuh ghost_state), formed here relative to the reference.
 //  * volume: one thread per solution point, several elements per CTA.
 //    Contravariant fluxes go to shared memory; the Lagrange derivative, the
 //    face jumps (common minus extrapolated flux polynomial) and the DG
@@ -99,9 +101,30 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const int* __restrict__ 
   for (int m = 0; m < n1; ++m) { lm[m] = op.lm[m]; lp[m] = op.lp[m]; }
   // reference: (gauge) pressure and temperature at the left element's first solution point
   double ref[4] = {__ldg(q + (size_t)eL * N), 0.0, 0.0, __ldg(q + 3 * plane + (size_t)eL * N)};
+  const double* g = face + (((size_t)eL * 4 + fL) * n1 + k) * 3;
+  const double nx = __ldg(g), ny = __ldg(g + 1), dS = __ldg(g + 2);
+  const bool bnd = eR < 0;   // boundary face: fR holds the boundary type
   double sm[4], sp[4];
   line_trace<P>(q, plane, eL, fL, k, lm, lp, ref, sm);
-  line_trace<P>(q, plane, eR, fR, kR, lm, lp, ref, sp);
+  if (!bnd) {
+    line_trace<P>(q, plane, eR, fR, kR, lm, lp, ref, sp);
+  } else if (fR == PMG_BC_FARFIELD) {   // ghost = free stream, relative to the reference
+    sp[0] = (ph.qinf[0] - ph.p_ref) - ref[0];
+    sp[1] = ph.qinf[1];
+    sp[2] = ph.qinf[2];
+    sp[3] = ph.qinf[3] - ref[3];
+  } else {   // walls: same p and T, velocity reflected (slip) or reversed (no-slip)
+    sp[0] = sm[0];
+    sp[3] = sm[3];
+    if (fR == PMG_BC_NOSLIP_WALL) {
+      sp[1] = -sm[1];
+      sp[2] = -sm[2];
+    } else {
+      const double un = fma(sm[1], nx, sm[2] * ny);
+      sp[1] = fma(-2.0 * un, nx, sm[1]);
+      sp[2] = fma(-2.0 * un, ny, sm[2]);
+    }
+  }
   double qm[4], qp[4], dq[4];
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
@@ -112,19 +135,24 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const int* __restrict__ 
   const double pgm = qm[0], pgp = qp[0];   // gauge pressures for the momentum fluxes
   qm[0] += ph.p_ref;   // absolute pressure for the averaged state and rho
   qp[0] += ph.p_ref;
-  const double* g = face + (((size_t)eL * 4 + fL) * n1 + k) * 3;
   double out[4];
-  roe_flux_jump(qm, qp, dq, pgm, pgp, __ldg(g), __ldg(g + 1), __ldg(g + 2), ph, out);
-  size_t fplane = (size_t)E * 4 * n1;
-  size_t iL = ((size_t)eL * 4 + fL) * n1 + k, iR = ((size_t)eR * 4 + fR) * n1 + kR;
+  roe_flux_jump(qm, qp, dq, pgm, pgp, nx, ny, dS, ph, out);
+  const size_t fplane = (size_t)E * 4 * n1;
+  const size_t iL = ((size_t)eL * 4 + fL) * n1 + k;
+  const size_t iR = bnd ? iL : ((size_t)eR * 4 + fR) * n1 + kR;
   if (VISC) {
     // common gradient: mean of the two broken-gradient traces plus the BR2
     // liftings r^- + r^+ = pen (q_com - q^-) (1/|J|^- + 1/|J|^+) n dS, with
-    // q_com - q^- = dq / 2
+    // q_com - q^- = dq / 2.  A boundary face mirrors the element (its
+    // gradient trace and |J|): the one-sided BR2 gradient.
     double gm[6], gp[6], gc[6];
     grad_trace<P>(Gb, plane, eL, fL, k, lm, lp, gm);
-    grad_trace<P>(Gb, plane, eR, fR, kR, lm, lp, gp);
-    const double nx = __ldg(g), ny = __ldg(g + 1), dS = __ldg(g + 2);
+    if (!bnd) {
+      grad_trace<P>(Gb, plane, eR, fR, kR, lm, lp, gp);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) gp[c] = gm[c];
+    }
     const double wl = 0.25 * op.pen * (__ldg(fJinv + iL) + __ldg(fJinv + iR)) * dS;
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
@@ -133,18 +161,20 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const int* __restrict__ 
     }
     double fv[4], gv[4];
     viscous_flux(0.5 * (qm[1] + qp[1]), 0.5 * (qm[2] + qp[2]), gc, ph, fv, gv);
+    const int nv = (bnd && fR != PMG_BC_FARFIELD) ? 3 : 4;   // walls: no viscous energy flux
 #pragma unroll
-    for (int v = 1; v < 4; ++v) out[v] -= fma(fv[v], nx, gv[v] * ny) * dS;
+    for (int v = 1; v < 4; ++v)
+      if (v < nv) out[v] -= fma(fv[v], nx, gv[v] * ny) * dS;
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
       Qj[v * fplane + iL] = 0.5 * dq[v + 1];
-      Qj[v * fplane + iR] = -0.5 * dq[v + 1];
+      if (!bnd) Qj[v * fplane + iR] = -0.5 * dq[v + 1];
     }
   }
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     Fcom[v * fplane + iL] = out[v];
-    Fcom[v * fplane + iR] = -out[v];
+    if (!bnd) Fcom[v * fplane + iR] = -out[v];
   }
 }
 

@@ -11,7 +11,11 @@
 //    exact tangents (dual numbers through the same viscous flux code as the
 //    residual) of the element's viscous residual with neighbour data frozen:
 //    corrected gradients at the solution points, BR2 common gradient and
-//    q_com at the flux points, divergence and DG correction.
+//    q_com at the flux points, divergence and DG correction.  On boundary
+//    faces the ghost state follows the own trace: q_com - q^- changes by
+//    kappa dq^- (kappa = -1/2 for interior and far-field faces, -1 for the
+//    velocity and 0 for the temperature at no-slip adiabatic walls), and the
+//    mirrored gradient trace doubles the own gradient's share.
 #include "pmg_internal.h"
 
 namespace pmg {
@@ -86,7 +90,9 @@ __global__ void __launch_bounds__(256) assemble_visc_kernel(int E, const double*
   __shared__ double sQc[FP][2];     // q_com velocities
   __shared__ double sGf[FP][6];     // common gradient (values)
   __shared__ double sS[FP][4];      // nx, ny, dS, lifting weight
-  __shared__ double sD[n1][n1], sDc[n1][n1], sgL[n1], sgR[n1], slm[n1], slp[n1];
+  __shared__ double sD[n1][n1], sgL[n1], sgR[n1], slm[n1], slp[n1];
+  __shared__ double sKap[4][3];     // d(q_com - q^-)/dq^- per face and variable (u, v, T)
+  __shared__ int sBc[4];            // boundary type per face, 0 for interior faces
   __shared__ double sdF[C][3][N], sdG[C][3][N];   // tangents of the total contravariant fluxes, rows 1..3
   __shared__ double sdJ[C][4][3][n1];             // tangents of the face jumps
   const int e = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
@@ -100,9 +106,13 @@ __global__ void __launch_bounds__(256) assemble_visc_kernel(int E, const double*
   if (tid < n1 * n1) {
     const int i = tid / n1, m = tid % n1;
     sD[i][m] = op.D[i][m];
-    // derivative of the corrected reference derivative with respect to the
-    // own state: D - (g_L l_- + g_R l_+) / 2  (q_com - q^- = (q^+ - q^-) / 2)
-    sDc[i][m] = op.D[i][m] - 0.5 * (op.gL[i] * op.lm[m] + op.gR[i] * op.lp[m]);
+  }
+  if (tid < 4) {
+    const int en = nbr[(e * 4 + tid) * 3 + 0], bc = nbr[(e * 4 + tid) * 3 + 1];
+    sBc[tid] = en < 0 ? bc : 0;
+    const bool wall = en < 0 && bc == PMG_BC_NOSLIP_WALL;
+    sKap[tid][0] = sKap[tid][1] = wall ? -1.0 : -0.5;
+    sKap[tid][2] = wall ? 0.0 : -0.5;
   }
   if (tid < n1) {
     sgL[tid] = op.gL[tid];
@@ -129,10 +139,12 @@ __global__ void __launch_bounds__(256) assemble_visc_kernel(int E, const double*
     const int f = t / n1, k = t - f * n1;
     const bool plus = (f == 1 || f == 2), eta = (f == 0 || f == 2);
     const int en = nbr[(e * 4 + f) * 3 + 0], fn = nbr[(e * 4 + f) * 3 + 1], rev = nbr[(e * 4 + f) * 3 + 2];
+    const bool bnd = en < 0;
     const int kn = rev ? P - k : k;
     const bool pn = (fn == 1 || fn == 2), etan = (fn == 0 || fn == 2);
     const int stride = etan ? n1 : 1;
-    const size_t nbase = (size_t)en * N + (etan ? kn : kn * n1);
+    const size_t nbase = bnd ? 0 : (size_t)en * N + (etan ? kn : kn * n1);
+    const double* g = face + (((size_t)e * 4 + f) * n1 + k) * 3;
     double qm[3], qp[3];
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
@@ -140,25 +152,39 @@ __global__ void __launch_bounds__(256) assemble_visc_kernel(int E, const double*
       const double ref = sV[v][0];
       for (int m = 0; m < n1; ++m) {
         sm = fma(plus ? slp[m] : slm[m], sV[v][eta ? m * n1 + k : k * n1 + m] - ref, sm);
-        sp = fma(pn ? slp[m] : slm[m], q[(v + 1) * plane + nbase + m * stride] - ref, sp);
+        if (!bnd) sp = fma(pn ? slp[m] : slm[m], q[(v + 1) * plane + nbase + m * stride] - ref, sp);
       }
-      sDq[t][v] = sp - sm;
       qm[v] = ref + sm;
       qp[v] = ref + sp;
+      sDq[t][v] = sp - sm;
+    }
+    if (bnd) {   // ghost of (u, v, T); walls keep T, the far field is the free stream
+      if (fn == PMG_BC_FARFIELD) {
+        qp[0] = ph.qinf[1];
+        qp[1] = ph.qinf[2];
+        qp[2] = ph.qinf[3];
+      } else {
+        qp[0] = -qm[0];
+        qp[1] = -qm[1];
+        qp[2] = qm[2];
+      }
+      for (int v = 0; v < 3; ++v) sDq[t][v] = qp[v] - qm[v];
     }
     sQc[t][0] = 0.5 * (qm[0] + qp[0]);
     sQc[t][1] = 0.5 * (qm[1] + qp[1]);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {   // neighbour's broken-gradient trace, for now
       double s = 0.0;
-      for (int m = 0; m < n1; ++m) s = fma(pn ? slp[m] : slm[m], Gb[c * plane + nbase + m * stride], s);
+      if (!bnd)
+        for (int m = 0; m < n1; ++m) s = fma(pn ? slp[m] : slm[m], Gb[c * plane + nbase + m * stride], s);
       sGf[t][c] = s;
     }
-    const double* g = face + (((size_t)e * 4 + f) * n1 + k) * 3;
     sS[t][0] = g[0];
     sS[t][1] = g[1];
     sS[t][2] = g[2];
-    sS[t][3] = 0.25 * op.pen * (fJinv[((size_t)e * 4 + f) * n1 + k] + fJinv[((size_t)en * 4 + fn) * n1 + kn]) * g[2];
+    const double iJm = fJinv[((size_t)e * 4 + f) * n1 + k];
+    const double iJp = bnd ? iJm : fJinv[((size_t)en * 4 + fn) * n1 + kn];
+    sS[t][3] = 0.25 * op.pen * (iJm + iJp) * g[2];
   }
   __syncthreads();
   // values: corrected gradients at the solution points, common gradients
@@ -187,7 +213,8 @@ __global__ void __launch_bounds__(256) assemble_visc_kernel(int E, const double*
       double s = 0.0;
       for (int m = 0; m < n1; ++m) s = fma(plus ? slp[m] : slm[m], sGb[c][eta ? m * n1 + k : k * n1 + m], s);
       const double nc = c < 3 ? sS[t][0] : sS[t][1];
-      sGf[t][c] = fma(sS[t][3] * nc, sDq[t][c % 3], 0.5 * (s + sGf[t][c]));
+      const double other = sBc[f] ? s : sGf[t][c];   // a boundary mirrors the element
+      sGf[t][c] = fma(sS[t][3] * nc, sDq[t][c % 3], 0.5 * (s + other));
     }
   }
   __syncthreads();
@@ -200,8 +227,12 @@ __global__ void __launch_bounds__(256) assemble_visc_kernel(int E, const double*
       if (col >= 3 * N) continue;
       const int w = col / N, cp = col - w * N, ci = cp % n1, cj = cp / n1;
       const int i = pt % n1, j = pt / n1;
-      const double dax = (cj == j) ? sDc[i][ci] : 0.0;
-      const double dae = (ci == i) ? sDc[j][cj] : 0.0;
+      // d(corrected reference derivative)/dq: D plus the DG correction of
+      // d(q_com - q^-) = kappa dq^- on the two faces of each line
+      const double dax =
+          (cj == j) ? sD[i][ci] + sgL[i] * sKap[3][w] * slm[ci] + sgR[i] * sKap[1][w] * slp[ci] : 0.0;
+      const double dae =
+          (ci == i) ? sD[j][cj] + sgL[j] * sKap[0][w] * slm[cj] + sgR[j] * sKap[2][w] * slp[cj] : 0.0;
       const double a = sM[0][pt], b = sM[1][pt], c = sM[2][pt], d = sM[3][pt], iJ = sM[4][pt];
       Dual gr[6];
 #pragma unroll
@@ -240,21 +271,24 @@ __global__ void __launch_bounds__(256) assemble_visc_kernel(int E, const double*
         dgx = fma(l[m], sM[4][p2] * fma(sM[0][p2], bx, sM[2][p2] * be), dgx);
         dgy = fma(l[m], sM[4][p2] * fma(sM[1][p2], bx, sM[3][p2] * be), dgy);
       }
-      // d(grad q_com) = d(grad q^-)/2 + lifting of d(q_com - q^-) = -dq^-/2
+      // d(grad q_com) = gfac d(grad q^-) + lifting of d(q_com - q^-) = kappa dq^-
+      // (gfac = 1/2, or 1 where the ghost side mirrors the element)
       const double wl = sS[fp][3], nx = sS[fp][0], ny = sS[fp][1], dS = sS[fp][2];
+      const double kap = sKap[f][w], gfac = sBc[f] ? 1.0 : 0.5;
       Dual gr[6];
 #pragma unroll
       for (int v = 0; v < 3; ++v) {
-        gr[v] = Dual(sGf[fp][v], v == w ? fma(-wl * nx, dqm, 0.5 * dgx) : 0.0);
-        gr[3 + v] = Dual(sGf[fp][3 + v], v == w ? fma(-wl * ny, dqm, 0.5 * dgy) : 0.0);
+        gr[v] = Dual(sGf[fp][v], v == w ? fma(2.0 * kap * wl * nx, dqm, gfac * dgx) : 0.0);
+        gr[3 + v] = Dual(sGf[fp][3 + v], v == w ? fma(2.0 * kap * wl * ny, dqm, gfac * dgy) : 0.0);
       }
-      const Dual u(sQc[fp][0], w == 0 ? 0.5 * dqm : 0.0);
-      const Dual vv(sQc[fp][1], w == 1 ? 0.5 * dqm : 0.0);
+      const Dual u(sQc[fp][0], w == 0 ? (1.0 + kap) * dqm : 0.0);
+      const Dual vv(sQc[fp][1], w == 1 ? (1.0 + kap) * dqm : 0.0);
       Dual fv[4], gv[4];
       viscous_flux(u, vv, gr, ph, fv, gv);
+      const int nr = (sBc[f] && sBc[f] != PMG_BC_FARFIELD) ? 2 : 3;   // walls: no viscous energy flux
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        const double dcom = -fma(fv[r + 1].d, nx, gv[r + 1].d * ny) * dS;   // outward, total flux
+        const double dcom = r < nr ? -fma(fv[r + 1].d, nx, gv[r + 1].d * ny) * dS : 0.0;   // outward, total flux
         double loc = 0.0;
         for (int m = 0; m < n1; ++m) loc = fma(l[m], xi ? sdF[cc][r][k * n1 + m] : sdG[cc][r][m * n1 + k], loc);
         sdJ[cc][f][r][k] = (plus ? dcom : -dcom) - loc;

@@ -22,6 +22,7 @@ struct Phys {
   double mu;         // constant dynamic viscosity (0: Euler)
   double kT;         // heat conductivity mu Cp / Pr
   double nw[4];      // weights 1 / res_scale of the equations in the residual norm
+  double qinf[4];    // free stream of far-field faces (p absolute, u, v, T)
 };
 
 // ---------------------------------------------------------------------------
@@ -274,6 +275,29 @@ __host__ __device__ inline void viscous_flux(S u, S v, const S g[6], const Phys&
   gv[1] = txy;
   gv[2] = tyy;
   gv[3] = u * txy + v * tyy + ph.kT * g[5];
+}
+
+// Ghost state of a boundary face (the paper states no boundary treatment;
+// reading: a ghost state enters the same common fluxes).  q holds absolute
+// pressure; (nx, ny) is the unit outward normal.  bc 2: slip wall
+// (p, u - 2 u_n n, T); 3: no-slip adiabatic wall (p, -u, -v, T); 4: far
+// field (the free stream).
+template <class S>
+__host__ __device__ inline void ghost_state(int bc, const S qm[4], double nx, double ny, const Phys& ph, S qg[4]) {
+  if (bc == 4) {
+    for (int v = 0; v < 4; ++v) qg[v] = S(ph.qinf[v]);
+    return;
+  }
+  qg[0] = qm[0];
+  qg[3] = qm[3];
+  if (bc == 3) {
+    qg[1] = -qm[1];
+    qg[2] = -qm[2];
+  } else {
+    const S un = qm[1] * nx + qm[2] * ny;
+    qg[1] = qm[1] - 2.0 * un * nx;
+    qg[2] = qm[2] - 2.0 * un * ny;
+  }
 }
 
 }  // namespace pmg

@@ -48,6 +48,7 @@ class pmg_config(ctypes.Structure):
         ("mu", ctypes.c_double),
         ("Pr", ctypes.c_double),
         ("res_scale", ctypes.c_double * 4),
+        ("q_inf", ctypes.c_double * 4),
     ]
 
 
@@ -141,7 +142,8 @@ def _ptr(x, writable=False):
 
 def make_config(P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutoff=0, dtau_init=0.01,
                 dtau_max=10.0, tol=1e-8, refresh_every=10, max_pseudo=2000, block_prec=PMG_PREC_FP64,
-                use_graph=1, p_gauge=0.0, mu=0.0, Pr=0.72, res_scale=(1.0, 1.0, 1.0, 1.0)) -> pmg_config:
+                use_graph=1, p_gauge=0.0, mu=0.0, Pr=0.72, res_scale=(1.0, 1.0, 1.0, 1.0),
+                q_inf=(0.0, 0.0, 0.0, 0.0)) -> pmg_config:
     cfg = pmg_config()
     cfg.n_levels = len(P_levels)
     for l, (P, n) in enumerate(zip(P_levels, n_smooth)):
@@ -155,6 +157,7 @@ def make_config(P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutof
     cfg.mu, cfg.Pr = mu, Pr
     for v in range(4):
         cfg.res_scale[v] = res_scale[v]
+        cfg.q_inf[v] = q_inf[v]
     return cfg
 
 

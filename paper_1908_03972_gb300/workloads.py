@@ -237,6 +237,17 @@ def to_soa(field: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(field, dtype=np.float64)
 
 
+def freestream_noise_state(xy: np.ndarray, Ma_inf: float, speed: float = 1.0, noise: float = 1e-3,
+                           seed: int = 7, gamma: float = GAMMA) -> np.ndarray:
+    """Free stream (rho = 1, u = speed, v = 0) with seeded Gaussian noise of
+    relative size ``noise`` in v: the start of the cylinder case."""
+    T = freestream_T(Ma_inf, speed, gamma)
+    rng = np.random.default_rng(seed)
+    shape = xy.shape[:-1]
+    return np.stack([np.full(shape, T), np.full(shape, speed),
+                     noise * speed * rng.standard_normal(shape), np.full(shape, T)])
+
+
 def uniform_state(E: int, N: int, p: float, u: float, v: float, T: float) -> np.ndarray:
     q = np.empty((4, E, N))
     q[0], q[1], q[2], q[3] = p, u, v, T
