@@ -60,6 +60,9 @@ class OrcConfig(ctypes.Structure):
         ("Pr", ctypes.c_double),
         ("res_scale", ctypes.c_double * 4),
         ("q_inf", ctypes.c_double * 4),
+        ("cfl_mode", ctypes.c_int),
+        ("cfl_init", ctypes.c_double),
+        ("cfl_max", ctypes.c_double),
     ]
 
 
@@ -75,6 +78,9 @@ def _declare(L):
     L.orc_roe.argtypes = [_d, _d, cd, cd, cd, cd, cd, ci, _d]
     L.orc_cons_from_prim.argtypes = [_d, cd, _d]
     L.orc_prim_from_cons.argtypes = [_d, cd, _d]
+    L.orc_element_dx.argtypes = [vp, _d]
+    L.orc_dtau_min.argtypes = [vp, _d]
+    L.orc_dtau_min.restype = cd
     L.orc_create.argtypes = [ctypes.POINTER(OrcConfig), ci, ci, _d, _i]
     L.orc_create.restype = vp
     L.orc_destroy.argtypes = [vp]
@@ -164,7 +170,7 @@ class Oracle:
     def __init__(self, nodes, nbr, Ng, P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005,
                  kappa=1.0, cutoff=0, dtau_init=0.01, dtau_max=10.0, tol=1e-8,
                  refresh_every=10, max_pseudo=2000, mu=0.0, Pr=0.72, res_scale=(1.0, 1.0, 1.0, 1.0),
-                 q_inf=(0.0, 0.0, 0.0, 0.0)):
+                 q_inf=(0.0, 0.0, 0.0, 0.0), cfl_mode=0, cfl_init=1e2, cfl_max=1e5):
         cfg = OrcConfig()
         cfg.n_levels = len(P_levels)
         for l, P in enumerate(P_levels):
@@ -178,6 +184,7 @@ class Oracle:
         for v in range(4):
             cfg.res_scale[v] = res_scale[v]
             cfg.q_inf[v] = q_inf[v]
+        cfg.cfl_mode, cfg.cfl_init, cfg.cfl_max = cfl_mode, cfl_init, cfl_max
         self.cfg = cfg
         self.nodes = _f64(nodes)
         self.nbr = np.ascontiguousarray(nbr, dtype=np.int32)
@@ -200,6 +207,14 @@ class Oracle:
 
     def shape(self, level=0):
         return (4, self.E, self.N(level))
+
+    def element_dx(self):
+        dx = np.zeros(self.E)
+        lib().orc_element_dx(self.h, _p(dx))
+        return dx
+
+    def dtau_min(self, q):
+        return lib().orc_dtau_min(self.h, _p(_f64(q)))
 
     def coords(self, level=0):
         xy = np.zeros((self.E, self.N(level), 2))

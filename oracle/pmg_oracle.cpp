@@ -414,6 +414,58 @@ static void map_derivs(int Ng, const double* xn, double xi, double eta,
     }
 }
 
+// Point of the element map at (xi, eta).
+static void map_point(int Ng, const double* xn, double xi, double eta, double* x, double* y) {
+  std::vector<double> r(Ng + 1);
+  for (int a = 0; a <= Ng; ++a) r[a] = -1.0 + 2.0 * a / (Ng > 0 ? Ng : 1);
+  *x = *y = 0.0;
+  for (int b = 0; b <= Ng; ++b)
+    for (int a = 0; a <= Ng; ++a) {
+      double phi = lagrange(r, a, xi) * lagrange(r, b, eta);
+      *x += phi * xn[(b * (Ng + 1) + a) * 2];
+      *y += phi * xn[(b * (Ng + 1) + a) * 2 + 1];
+    }
+}
+
+// Element size of the CFL definition (Section 2.4): twice the minimum distance
+// from the element's barycentre to its faces.  Reading: the barycentre is the
+// area centroid (8-point Gauss quadrature of the mapped element); each face
+// curve is sampled at 65 equispaced reference points and the distance is the
+// smallest point-to-segment distance of that polyline.
+static double element_dx(int Ng, const double* xn) {
+  const Basis1D q8 = make_basis(7);
+  double A = 0.0, cx = 0.0, cy = 0.0;
+  for (int j = 0; j < 8; ++j)
+    for (int i = 0; i < 8; ++i) {
+      double a, b, c, d, x, y;
+      map_derivs(Ng, xn, q8.x[i], q8.x[j], &a, &b, &c, &d);
+      map_point(Ng, xn, q8.x[i], q8.x[j], &x, &y);
+      double w = q8.w[i] * q8.w[j] * (a * d - b * c);
+      A += w; cx += w * x; cy += w * y;
+    }
+  cx /= A; cy /= A;
+  const int K = 64;
+  double best = 1e300;
+  for (int f = 0; f < 4; ++f) {
+    double px = 0, py = 0;
+    for (int k = 0; k <= K; ++k) {
+      double t = -1.0 + 2.0 * k / K, xi, eta, x, y;
+      if (f == 0) { xi = t; eta = -1.0; } else if (f == 1) { xi = 1.0; eta = t; }
+      else if (f == 2) { xi = t; eta = 1.0; } else { xi = -1.0; eta = t; }
+      map_point(Ng, xn, xi, eta, &x, &y);
+      if (k > 0) {   // distance from (cx, cy) to the segment (px, py)-(x, y)
+        double ex = x - px, ey = y - py, L2 = ex * ex + ey * ey;
+        double s = L2 > 0 ? ((cx - px) * ex + (cy - py) * ey) / L2 : 0.0;
+        s = std::min(1.0, std::max(0.0, s));
+        double dx = px + s * ex - cx, dy = py + s * ey - cy;
+        best = std::min(best, std::sqrt(dx * dx + dy * dy));
+      }
+      px = x; py = y;
+    }
+  }
+  return 2.0 * best;
+}
+
 // ---------------------------------------------------------------------------
 // Solver context
 // ---------------------------------------------------------------------------
@@ -429,6 +481,8 @@ struct OrcConfig {
   double mu, Pr;
   double res_scale[4];    // reference scale of each equation in ||F|| (0: 1)
   double q_inf[4];        // free-stream primitive state (p, u, v, T) of far-field faces
+  int cfl_mode;           // 1: dtau = CFL dtau_min (eq. CFL), SER on the CFL number
+  double cfl_init, cfl_max;
 };
 
 struct Level {
@@ -446,6 +500,7 @@ struct Oracle {
   std::vector<int> nbr;
   std::vector<Level> lev;
   std::vector<std::vector<double>> Rm, Pm;   // restriction / prolongation 1D, level l -> l+1
+  std::vector<double> dx;                    // element size of eq. CFL (twice barycentre-to-face distance)
   // stage data (finest level)
   std::vector<double> src;                   // (q_c^n + dt sum a_ij R^j)/(omega dt)
   double omega_dt;
@@ -1044,6 +1099,8 @@ void* orc_create(const OrcConfig* cfg, int E, int Ng, const double* nodes, const
                          !(fn == 3 && !(cfg->cutoff && cfg->kappa * cfg->Ma_inf > 0)));
     if (!ok) { delete o; return nullptr; }
   }
+  o->dx.resize(E);
+  for (int e = 0; e < E; ++e) o->dx[e] = element_dx(Ng, &o->nodes[(size_t)e * nn * 2]);
   o->lev.resize(cfg->n_levels);
   for (int l = 0; l < cfg->n_levels; ++l) {
     build_level_geom(o, cfg->P[l], &o->lev[l].g);
@@ -1074,6 +1131,16 @@ int orc_metrics(void* h, int level, double* met, double* fS) {
 }
 
 // Physical coordinates of the solution points of a level, (E, N, 2).
+static double dtau_min(const Oracle* o, const double* q);
+
+int orc_element_dx(void* h, double* dx) {
+  Oracle* o = (Oracle*)h;
+  for (int e = 0; e < o->E; ++e) dx[e] = o->dx[e];
+  return 0;
+}
+
+double orc_dtau_min(void* h, const double* q) { return dtau_min((Oracle*)h, q); }
+
 int orc_coords(void* h, int level, double* xy) {
   Oracle* o = (Oracle*)h;
   const Level& L = o->lev[level];
@@ -1161,6 +1228,29 @@ int orc_vcycle(void* h, double* q, double dtau, int refresh) {
   return st;
 }
 
+// dtau_min of the CFL definition (Section 2.4): the smaller of
+// min_e (dx_e/(P+1)) / (c + |v|)_e and min_e (dx_e/(P+1))^2 / (mu/rho)_e on the
+// finest level.  Reading: (c + |v|)_e is the largest and rho_e the smallest
+// value over the element's solution points.
+static double dtau_min(const Oracle* o, const double* q) {
+  const Level& L = o->lev[0];
+  int N = L.g.N, E = o->E, P = L.g.P;
+  double best = 1e300;
+  for (int e = 0; e < E; ++e) {
+    double smax = 0.0, rmin = 1e300;
+    for (int p = 0; p < N; ++p) {
+      double pr = q[((size_t)0 * E + e) * N + p], u = q[((size_t)1 * E + e) * N + p];
+      double v = q[((size_t)2 * E + e) * N + p], T = q[((size_t)3 * E + e) * N + p];
+      smax = std::max(smax, std::sqrt(o->ph.gamma * T) + std::sqrt(u * u + v * v));
+      rmin = std::min(rmin, pr / T);
+    }
+    double hP = o->dx[e] / (P + 1);
+    best = std::min(best, hP / smax);
+    if (o->ph.mu > 0.0) best = std::min(best, hP * hP * rmin / o->ph.mu);
+  }
+  return best;
+}
+
 // Pseudo-transient continuation of one implicit stage (Section 2.4): a
 // V-cycle per pseudo-iteration, SER growth of dtau (eq. ser, exponent 1.5),
 // smoother refresh at m = 0 and every refresh_every iterations while
@@ -1190,7 +1280,13 @@ static int stage_solve(Oracle* o, double* q, int* iters, double* drop, double* n
   Level& L = o->lev[0];
   size_t tot = L.q.size();
   std::vector<double> F(tot);
-  double dtau = o->cfg.dtau_init, n0 = 0.0, prev = 0.0, dtau_built = 0.0;
+  double dtau_init = o->cfg.dtau_init, dtau_max = o->cfg.dtau_max;
+  if (o->cfg.cfl_mode) {   // eq. CFL: dtau = CFL dtau_min, SER acting on the CFL number
+    double dm = dtau_min(o, q);
+    dtau_init = o->cfg.cfl_init * dm;
+    dtau_max = o->cfg.cfl_max * dm;
+  }
+  double dtau = dtau_init, n0 = 0.0, prev = 0.0, dtau_built = 0.0;
   for (int m = 0;; ++m) {
     level_F(o, 0, q, true, false, F.data());
     double nm = residual_norm(o, F);
@@ -1199,8 +1295,8 @@ static int stage_solve(Oracle* o, double* q, int* iters, double* drop, double* n
     if (nm <= o->cfg.tol * n0 || n0 == 0.0) { *iters = m; *drop = n0 > 0 ? nm / n0 : 0.0; return 0; }
     if (!std::isfinite(nm)) { *iters = m; *drop = nm; return -5; }
     if (m >= o->cfg.max_pseudo) { *iters = m; *drop = nm / n0; return -6; }
-    if (m > 0) dtau = ser_next(dtau, prev, nm, o->cfg.dtau_max);
-    bool refresh = refresh_due(m, o->cfg.refresh_every, dtau_built, o->cfg.dtau_max);
+    if (m > 0) dtau = ser_next(dtau, prev, nm, dtau_max);
+    bool refresh = refresh_due(m, o->cfg.refresh_every, dtau_built, dtau_max);
     if (refresh) dtau_built = dtau;
     int st = orc_vcycle(o, q, dtau, refresh);
     if (st) return st;
