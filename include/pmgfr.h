@@ -99,6 +99,16 @@ typedef struct {
                      start near their solution stall. */
   double q_inf[4]; /* free-stream primitive state (p absolute, u, v, T) that
                      far-field boundary faces see as their outer state */
+  int cfl_mode;   /* 0: dtau_init/dtau_max as given.  1: the CFL form of
+                     Section 2.4: at the start of every stage dtau_init =
+                     cfl_init dtau_min and dtau_max = cfl_max dtau_min, with
+                     dtau_min = min over elements of min((dx/(P+1))/(c+|v|),
+                     (dx/(P+1))^2 rho/mu) on the finest level (dx: twice the
+                     distance from the element's barycentre to its nearest
+                     face; c + |v| the largest and rho the smallest value over
+                     the element's points), so that SER acts on the CFL number.
+                     The paper's wall-bounded cases use 1e2 and 1e5. */
+  double cfl_init, cfl_max;
 } pmg_config;
 
 /* Boundary types, in the second slot of a boundary face's neighbour entry
@@ -271,6 +281,11 @@ pmg_status pmg_residual_static(pmg_ctx* ctx, int level, const double* q, double*
  * header against the context and returns PMG_EINVAL for another mesh, P
  * hierarchy or setting, a truncated or foreign file; PMG_ESTATE without a
  * mesh.  Both synchronise the context's stream. */
+/* dtau_min of the CFL form (see cfl_mode) for the current finest-level state,
+ * into *out (host).  Synchronises the context's stream.  PMG_ESTATE without a
+ * mesh. */
+pmg_status pmg_dtau_min(pmg_ctx* ctx, double* out);
+
 pmg_status pmg_checkpoint(pmg_ctx* ctx, const char* path);
 pmg_status pmg_restore(pmg_ctx* ctx, const char* path);
 

@@ -86,6 +86,8 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   if (cfg->block_prec != PMG_PREC_FP64 && cfg->block_prec != PMG_PREC_FP32)
     return fail(PMG_EINVAL, "unknown block precision");
   if (!(cfg->gamma > 1.0)) return fail(PMG_EINVAL, "gamma must exceed 1");
+  if (cfg->cfl_mode && !(cfg->cfl_init > 0.0 && cfg->cfl_max >= cfg->cfl_init))
+    return fail(PMG_EINVAL, "cfl_mode needs 0 < cfl_init <= cfl_max");
   if (!(cfg->mu >= 0.0) || !std::isfinite(cfg->mu)) return fail(PMG_EINVAL, "mu must be finite and >= 0");
   if (cfg->mu > 0.0 && !(cfg->Pr > 0.0 && std::isfinite(cfg->Pr)))
     return fail(PMG_EINVAL, "Pr must be finite and > 0 when mu > 0");
@@ -134,7 +136,7 @@ void pmg_destroy(pmg_ctx* h) {
   for (int g = 0; g < 2; ++g)
     if (c.graph[g]) cudaGraphExecDestroy(c.graph[g]);
   for (int l = 0; l < kMaxLevels; ++l) free_level(c.lev[l]);
-  double** ptrs[] = {&c.src, &c.qn, &c.qcn, &c.d_partial, &c.d_scal, &c.d_tmp0, &c.d_tmp1, &c.d_dtau};
+  double** ptrs[] = {&c.src, &c.qn, &c.qcn, &c.d_partial, &c.d_scal, &c.d_tmp0, &c.d_tmp1, &c.d_dtau, &c.d_dx};
   for (double** p : ptrs) { if (*p) cudaFree(*p); *p = nullptr; }
   for (int j = 0; j < 6; ++j) if (c.Rst[j]) cudaFree(c.Rst[j]);
   if (c.d_faces) cudaFree(c.d_faces);
@@ -180,6 +182,11 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
     }
   } catch (const std::exception& ex) {
     return fail(PMG_EINVAL, ex.what());
+  }
+  {
+    std::vector<double> dx = element_sizes(c.mesh);
+    PMG_CK(dalloc(&c.d_dx, dx.size()));
+    PMG_CK(cudaMemcpy(c.d_dx, dx.data(), dx.size() * 8, cudaMemcpyHostToDevice));
   }
   c.n_faces = (int)c.mesh.faces.size();
   // face list followed by the neighbour table
@@ -476,6 +483,16 @@ static pmg_status read_norm(Ctx& c, double* out) {
   return PMG_OK;
 }
 
+// dtau_min of the CFL form for the current finest state (d_scal[2]).
+static pmg_status compute_dtau_min(Ctx& c, double* out) {
+  launch_dtau_min(c, c.d_partial, c.d_scal + 2, c.stream);
+  PMG_CK_LAUNCH();
+  PMG_CK(cudaMemcpyAsync(c.h_scal + 2, c.d_scal + 2, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  PMG_CK(cudaStreamSynchronize(c.stream));
+  *out = c.h_scal[2];
+  return PMG_OK;
+}
+
 static pmg_status set_dtau(Ctx& c, double dtau) {
   // the pinned mirror is only rewritten after the stream has consumed it
   PMG_CK(cudaStreamSynchronize(c.stream));
@@ -505,11 +522,20 @@ static pmg_status stage_solve(Ctx& c, int* iters, double* drop, int* n_refresh) 
   double nm;
   pmg_status st = read_norm(c, &nm);
   if (st) return st;
-  double n0 = nm, prev = nm, dtau = c.cfg.dtau_init, built = 0.0;
+  double dtau_init = c.cfg.dtau_init, dtau_max = c.cfg.dtau_max;
+  if (c.cfg.cfl_mode) {   // Section 2.4: dtau = CFL dtau_min, SER acting on the CFL number
+    double dm;
+    st = compute_dtau_min(c, &dm);
+    if (st) return st;
+    if (!(dm > 0.0) || !std::isfinite(dm)) return fail(PMG_ENONFINITE, "dtau_min is not a positive number");
+    dtau_init = c.cfg.cfl_init * dm;
+    dtau_max = c.cfg.cfl_max * dm;
+  }
+  double n0 = nm, prev = nm, dtau = dtau_init, built = 0.0;
   for (int m = 0;; ++m) {
     if (m == 0) n0 = nm;
     c.hist_norm.push_back(nm);
-    c.hist_dtau.push_back(m > 0 ? std::min(dtau * std::pow(prev / nm, 1.5), c.cfg.dtau_max) : dtau);
+    c.hist_dtau.push_back(m > 0 ? std::min(dtau * std::pow(prev / nm, 1.5), dtau_max) : dtau);
     if (nm <= c.cfg.tol * n0 || n0 == 0.0) {
       if (iters) *iters = m;
       if (drop) *drop = n0 > 0 ? nm / n0 : 0.0;
@@ -525,8 +551,8 @@ static pmg_status stage_solve(Ctx& c, int* iters, double* drop, int* n_refresh) 
       if (drop) *drop = nm / n0;
       return fail(PMG_ENOTCONV, "stage not converged within max_pseudo V-cycles");
     }
-    if (m > 0) dtau = std::min(dtau * std::pow(prev / nm, 1.5), c.cfg.dtau_max);
-    bool refresh = (m == 0) || (m % c.cfg.refresh_every == 0 && built < c.cfg.dtau_max);
+    if (m > 0) dtau = std::min(dtau * std::pow(prev / nm, 1.5), dtau_max);
+    bool refresh = (m == 0) || (m % c.cfg.refresh_every == 0 && built < dtau_max);
     if (refresh) {
       built = dtau;
       st = set_dtau(c, dtau);
@@ -619,6 +645,13 @@ CkptHeader make_header(const Ctx& c) {
   return hd;
 }
 }  // namespace
+
+pmg_status pmg_dtau_min(pmg_ctx* h, double* out) {
+  if (!h || !out) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  if (!c.mesh_ready) return fail(PMG_ESTATE, "no mesh uploaded");
+  return compute_dtau_min(c, out);
+}
 
 pmg_status pmg_checkpoint(pmg_ctx* h, const char* path) {
   if (!h || !path) return fail(PMG_EINVAL, "null argument");

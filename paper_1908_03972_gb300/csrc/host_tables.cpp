@@ -12,6 +12,7 @@
 //    each level's own solution and flux points.
 #include "pmg_internal.h"
 
+#include <algorithm>
 #include <cmath>
 #include <stdexcept>
 
@@ -243,6 +244,54 @@ void build_level_geometry(const MeshHost& m, const Ref1D& r, LevelGeomHost& g) {
       b[0] = -a[0]; b[1] = -a[1]; b[2] = a[2];
     }
   }
+}
+
+// Element size of the CFL form (Section 2.4): twice the distance from the
+// element's area centroid (8-point Gauss quadrature) to its nearest face, each
+// face curve taken as the polyline through 65 equispaced reference points.
+std::vector<double> element_sizes(const MeshHost& m) {
+  const int Ng = m.Ng, nn = (Ng + 1) * (Ng + 1);
+  std::vector<double> C = geom_monomials(Ng);
+  Ref1D q8 = make_ref1d(7);
+  std::vector<double> dx(m.E);
+  for (int e = 0; e < m.E; ++e) {
+    const double* xn = &m.nodes[(size_t)e * nn * 2];
+    double A = 0.0, cx = 0.0, cy = 0.0;
+    for (int j = 0; j < 8; ++j)
+      for (int i = 0; i < 8; ++i) {
+        double x, y, J[4];
+        map_jacobian(C, Ng, xn, q8.x[i], q8.x[j], &x, &y, J);
+        const double w = q8.w[i] * q8.w[j] * (J[0] * J[3] - J[1] * J[2]);
+        A += w;
+        cx += w * x;
+        cy += w * y;
+      }
+    cx /= A;
+    cy /= A;
+    double best = 1e300;
+    const int K = 64;
+    for (int f = 0; f < 4; ++f) {
+      double px = 0.0, py = 0.0;
+      for (int k = 0; k <= K; ++k) {
+        const double t = -1.0 + 2.0 * k / K;
+        const double xi = (f == 1) ? 1.0 : (f == 3) ? -1.0 : t;
+        const double eta = (f == 2) ? 1.0 : (f == 0) ? -1.0 : t;
+        double x, y, J[4];
+        map_jacobian(C, Ng, xn, xi, eta, &x, &y, J);
+        if (k > 0) {
+          const double ex = x - px, ey = y - py, L2 = ex * ex + ey * ey;
+          double sgm = L2 > 0.0 ? ((cx - px) * ex + (cy - py) * ey) / L2 : 0.0;
+          sgm = std::min(1.0, std::max(0.0, sgm));
+          const double ddx = px + sgm * ex - cx, ddy = py + sgm * ey - cy;
+          best = std::min(best, std::sqrt(ddx * ddx + ddy * ddy));
+        }
+        px = x;
+        py = y;
+      }
+    }
+    dx[e] = 2.0 * best;
+  }
+  return dx;
 }
 
 void build_faces(MeshHost& m) {

@@ -182,4 +182,54 @@ void launch_bsum_update(const Ctx& c, int N, const double* qn, double* const* R,
   bsum_kernel<<<(unsigned)((plane + 255) / 256), 256, 0, s>>>(plane, c.ph, qn, rp, nr, dt, q);
 }
 
+// dtau_min of the CFL form (Section 2.4) on the finest level: per element
+// (dx/(P+1)) / max(c + |v|) and (dx/(P+1))^2 min(rho) / mu, then the minimum
+// over all elements (per-block minima, then one block).
+__global__ void dtau_elem_kernel(int E, int N, int P, const double* __restrict__ q, const double* __restrict__ dx,
+                                 Phys ph, double* __restrict__ partial) {
+  __shared__ double red[128];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  double best = 1e300;
+  if (e < E) {
+    const size_t plane = (size_t)E * N;
+    double smax = 0.0, rmin = 1e300;
+    for (int p = 0; p < N; ++p) {
+      const size_t i = (size_t)e * N + p;
+      const double pr = q[i] + ph.p_ref, u = q[plane + i], v = q[2 * plane + i], T = q[3 * plane + i];
+      smax = fmax(smax, sqrt(ph.gamma * T) + sqrt(u * u + v * v));
+      rmin = fmin(rmin, pr / T);
+    }
+    const double hP = dx[e] / (P + 1);
+    best = hP / smax;
+    if (ph.mu > 0.0) best = fmin(best, hP * hP * rmin / ph.mu);
+  }
+  red[threadIdx.x] = best;
+  __syncthreads();
+  for (int w = 64; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void min_final_kernel(const double* __restrict__ partial, int n, double* __restrict__ out) {
+  __shared__ double red[256];
+  double m = 1e300;
+  for (int i = threadIdx.x; i < n; i += 256) m = fmin(m, partial[i]);
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] = fmin(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+void launch_dtau_min(const Ctx& c, double* partial, double* out, cudaStream_t s) {
+  const LevelDev& L = c.lev[0];
+  const int blocks = (c.E + 127) / 128;
+  dtau_elem_kernel<<<blocks, 128, 0, s>>>(c.E, L.N, L.P, L.q, c.d_dx, c.ph, partial);
+  min_final_kernel<<<1, 256, 0, s>>>(partial, blocks, out);
+}
+
 }  // namespace pmg

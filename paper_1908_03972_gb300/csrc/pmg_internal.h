@@ -41,6 +41,7 @@ Ref1D make_ref1d(int P);
 void make_transfer(const Ref1D& f, const Ref1D& c, std::vector<double>& R, std::vector<double>& I);
 void build_faces(MeshHost& m);
 void build_level_geometry(const MeshHost& m, const Ref1D& r, LevelGeomHost& g);
+std::vector<double> element_sizes(const MeshHost& m);
 
 // --------------------------------------------------------------- device side
 // Operator tables of one level, passed to kernels by value.
@@ -114,6 +115,7 @@ struct Ctx {
   bool mesh_ready = false;
   int E = 0, n_faces = 0;
   int* d_faces = nullptr;      // n_faces * 5
+  double* d_dx = nullptr;      // E element sizes of the CFL form
   LevelDev lev[kMaxLevels];
   XferTab xfer[kMaxLevels];
   // stage data (finest level)
@@ -171,6 +173,7 @@ void launch_stage_src(const Ctx& c, int N, const double* qcn, double* const* R, 
 void launch_bsum_update(const Ctx& c, int N, const double* qn, double* const* R, const double* b, int nr,
                         double dt, double* q, cudaStream_t s);
 void launch_shift_pressure(size_t plane, double delta, double* q, cudaStream_t s);
+void launch_dtau_min(const Ctx& c, double* partial, double* out, cudaStream_t s);
 void launch_grad(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s);
 void launch_assemble_visc(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s);
 void launch_fused_sweep(const Ctx& c, const LevelDev& L, const double* qin, double* qout, double inv_odt,

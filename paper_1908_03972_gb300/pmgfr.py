@@ -49,6 +49,9 @@ class pmg_config(ctypes.Structure):
         ("Pr", ctypes.c_double),
         ("res_scale", ctypes.c_double * 4),
         ("q_inf", ctypes.c_double * 4),
+        ("cfl_mode", ctypes.c_int),
+        ("cfl_init", ctypes.c_double),
+        ("cfl_max", ctypes.c_double),
     ]
 
 
@@ -108,6 +111,7 @@ def load():
         "pmg_profile": ([vp, ci], ci),
         "pmg_residual_static": ([vp, ci, vp, vp], ci),
         "pmg_checkpoint": ([vp, ctypes.c_char_p], ci),
+        "pmg_dtau_min": ([vp, ctypes.POINTER(ctypes.c_double)], ci),
         "pmg_restore": ([vp, ctypes.c_char_p], ci),
         "pmg_profile_read": ([vp, pd, ctypes.POINTER(ctypes.c_longlong)], ci),
     }
@@ -143,7 +147,7 @@ def _ptr(x, writable=False):
 def make_config(P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutoff=0, dtau_init=0.01,
                 dtau_max=10.0, tol=1e-8, refresh_every=10, max_pseudo=2000, block_prec=PMG_PREC_FP64,
                 use_graph=1, p_gauge=0.0, mu=0.0, Pr=0.72, res_scale=(1.0, 1.0, 1.0, 1.0),
-                q_inf=(0.0, 0.0, 0.0, 0.0)) -> pmg_config:
+                q_inf=(0.0, 0.0, 0.0, 0.0), cfl_mode=0, cfl_init=1e2, cfl_max=1e5) -> pmg_config:
     cfg = pmg_config()
     cfg.n_levels = len(P_levels)
     for l, (P, n) in enumerate(zip(P_levels, n_smooth)):
@@ -158,6 +162,7 @@ def make_config(P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutof
     for v in range(4):
         cfg.res_scale[v] = res_scale[v]
         cfg.q_inf[v] = q_inf[v]
+    cfg.cfl_mode, cfg.cfl_init, cfg.cfl_max = cfl_mode, cfl_init, cfl_max
     return cfg
 
 
@@ -422,3 +427,9 @@ def pmg_checkpoint(h, path):
 
 def pmg_restore(h, path):
     _check(load().pmg_restore(h, os.fsencode(path)))
+
+
+def pmg_dtau_min(h):
+    out = ctypes.c_double()
+    _check(load().pmg_dtau_min(h, ctypes.byref(out)))
+    return out.value

@@ -153,3 +153,47 @@ def test_boundary_settings_checked():
     bad[0, 0] = (-1, 7, 0)
     with pytest.raises(pmgfr.PmgError):
         pmgfr.Solver(nodes, bad, [1], [1], q_inf=(1.0, 1.0, 0.0, 1.0))
+
+
+def test_cfl_form_dtau_min_parity():
+    from paper_1908_03972_gb300 import pmgfr
+    for Ma, make in ((0.001, lambda: W.cylinder_omesh(16, 64, 0.5, 50.0, Ng=2)),
+                     (0.005, lambda: W.periodic_box(8, 8, Ng=1))):
+        nodes, nbr = make()
+        Ng = 2 if nodes.shape[1] == 9 else 1
+        T = W.freestream_T(Ma, speed=1.0)
+        kw = dict(Ma_inf=Ma, mu=0.01, cutoff=1, kappa=1.0, q_inf=(T, 1.0, 0.0, T), cfl_mode=1)
+        orc = O.Oracle(nodes, nbr, Ng, [4 if Ng == 2 else 2], [1], **kw)
+        gpu = pmgfr.Solver(nodes, nbr, [4 if Ng == 2 else 2], [1], **kw)
+        try:
+            q = W.freestream_noise_state(orc.coords(), Ma, noise=0.05)
+            gpu.set_state(q)
+            a, b = pmgfr.pmg_dtau_min(gpu.h), orc.dtau_min(q)
+            assert abs(a - b) <= 1e-12 * b, (a, b)
+        finally:
+            gpu.close()
+
+
+def test_cfl_mode_stage_parity_on_the_cylinder():
+    # the paper's wall-bounded setting: CFL_init = 1e2, CFL_max = 1e5
+    from paper_1908_03972_gb300 import pmgfr
+    Ma, mu = 0.1, 0.02
+    nodes, nbr = W.cylinder_omesh(3, 12, r_in=0.5, r_out=8.0, Ng=2)
+    T = W.freestream_T(Ma, speed=1.0)
+    kw = dict(Ma_inf=Ma, mu=mu, cutoff=1, kappa=1.0, q_inf=(T, 1.0, 0.0, T), tol=1e-6, max_pseudo=3000,
+              res_scale=W.freestream_scales(Ma, speed=1.0), cfl_mode=1, cfl_init=1e2, cfl_max=1e5)
+    orc = O.Oracle(nodes, nbr, 2, [3, 2, 1], [2, 3, 4], **kw)
+    gpu = pmgfr.Solver(nodes, nbr, [3, 2, 1], [2, 3, 4], **kw)
+    try:
+        q = W.freestream_noise_state(orc.coords(), Ma)
+        omega_dt = 0.4358665215 * 0.05
+        src = _qc(q) / omega_dt + 0.5 * orc.residual(q)
+        orc.set_stage(src, omega_dt)
+        gpu.set_stage(src, omega_dt)
+        qo, it_o, _, _, st = orc.stage_solve(q)
+        assert st == 0
+        qg, it_g, drop_g = gpu.stage_solve(q)
+        assert drop_g <= 1e-6 and abs(it_g - it_o) <= max(2, 0.05 * it_o), (it_o, it_g)
+        assert np.abs(qg[1:3] - qo[1:3]).max() <= 1e-5 and np.abs(qg[0] - qo[0]).max() <= 1e-5 * T
+    finally:
+        gpu.close()
