@@ -109,6 +109,10 @@ typedef struct {
                      the element's points), so that SER acts on the CFL number.
                      The paper's wall-bounded cases use 1e2 and 1e5. */
   double cfl_init, cfl_max;
+  int esdirk_order; /* ESDIRK scheme of pmg_esdirk_step (Section 2.4): 2
+                     (three stages), 3 (four stages) or 4 (six stages);
+                     0 means 3 */
+  int reserved;   /* must be 0 */
 } pmg_config;
 
 /* Boundary types, in the second slot of a boundary face's neighbour entry

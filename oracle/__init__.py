@@ -78,6 +78,7 @@ def _declare(L):
     L.orc_roe.argtypes = [_d, _d, cd, cd, cd, cd, cd, ci, _d]
     L.orc_cons_from_prim.argtypes = [_d, cd, _d]
     L.orc_prim_from_cons.argtypes = [_d, cd, _d]
+    L.orc_esdirk.argtypes = [ci, _d, _d, _d]
     L.orc_element_dx.argtypes = [vp, _d]
     L.orc_dtau_min.argtypes = [vp, _d]
     L.orc_dtau_min.restype = cd
@@ -120,6 +121,14 @@ def transfer(Pf: int, Pc: int):
     I = np.zeros((Pf + 1, Pc + 1))
     lib().orc_transfer(Pf, Pc, _p(R), _p(I))
     return R, I
+
+
+def esdirk(order):
+    """ESDIRK tableau of the given order (2, 3 or 4): A (s x s), b, c."""
+    stages = {2: 3, 3: 4, 4: 6}[order]
+    A = np.zeros(stages * stages); b = np.zeros(stages); c = np.zeros(stages)
+    s = lib().orc_esdirk(stages, _p(A), _p(b), _p(c))
+    return A.reshape(s, s), b, c
 
 
 def esdirk3():
@@ -170,14 +179,14 @@ class Oracle:
     def __init__(self, nodes, nbr, Ng, P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005,
                  kappa=1.0, cutoff=0, dtau_init=0.01, dtau_max=10.0, tol=1e-8,
                  refresh_every=10, max_pseudo=2000, mu=0.0, Pr=0.72, res_scale=(1.0, 1.0, 1.0, 1.0),
-                 q_inf=(0.0, 0.0, 0.0, 0.0), cfl_mode=0, cfl_init=1e2, cfl_max=1e5):
+                 q_inf=(0.0, 0.0, 0.0, 0.0), cfl_mode=0, cfl_init=1e2, cfl_max=1e5, esdirk_order=3):
         cfg = OrcConfig()
         cfg.n_levels = len(P_levels)
         for l, P in enumerate(P_levels):
             cfg.P[l] = P
             cfg.n_smooth[l] = n_smooth[l]
         cfg.gamma, cfg.Ma_inf, cfg.kappa, cfg.cutoff = gamma, Ma_inf, kappa, cutoff
-        cfg.esdirk_stages = 4
+        cfg.esdirk_stages = {2: 3, 3: 4, 4: 6}[esdirk_order]
         cfg.dtau_init, cfg.dtau_max, cfg.tol = dtau_init, dtau_max, tol
         cfg.refresh_every, cfg.max_pseudo = refresh_every, max_pseudo
         cfg.mu, cfg.Pr = mu, Pr

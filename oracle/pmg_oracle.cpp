@@ -995,7 +995,59 @@ static void esdirk3_tableau(double A[6][6], double b[6], double c[6]) {
   for (int j = 0; j < 4; ++j) A[3][j] = b[j];
 }
 
+// ESDIRK2 (Section 2.4 cites Kennedy & Carpenter 2016: second order, three
+// stages): stiffly accurate, c = (0, 2g, 1), a_ii = g, last row = b.  The
+// order conditions sum b = 1 and sum b c = 1/2 give b2 = (1/2 - g)/(2g),
+// b1 = 1 - g - b2; L-stability (R(z) -> 0 as z -> -inf) fixes g = 1 - 1/sqrt 2.
+static void esdirk2_tableau(double A[6][6], double b[6], double c[6]) {
+  for (int i = 0; i < 6; ++i) { b[i] = c[i] = 0.0; for (int j = 0; j < 6; ++j) A[i][j] = 0.0; }
+  const double g = 1.0 - 1.0 / std::sqrt(2.0);
+  c[1] = 2 * g; c[2] = 1.0;
+  b[2] = g;
+  b[1] = (0.5 - g) / (2 * g);
+  b[0] = 1.0 - g - b[1];
+  A[1][0] = g; A[1][1] = g;
+  for (int j = 0; j < 3; ++j) A[2][j] = b[j];
+}
+
+// ESDIRK4 (Section 2.4 cites Bijl et al. 2002: fourth order, six stages):
+// reading = the implicit tableau of Kennedy & Carpenter's ARK4(3)6L[2]SA,
+// taken as published (gamma = 1/4, stiffly accurate).  The tests check the
+// eight fourth-order conditions and L-stability.
+static void esdirk4_tableau(double A[6][6], double b[6], double c[6]) {
+  for (int i = 0; i < 6; ++i) { b[i] = c[i] = 0.0; for (int j = 0; j < 6; ++j) A[i][j] = 0.0; }
+  const double g = 0.25;
+  const double cc[6] = {0.0, 0.5, 83.0 / 250.0, 31.0 / 50.0, 17.0 / 20.0, 1.0};
+  const double bb[6] = {82889.0 / 524892.0, 0.0, 15625.0 / 83664.0, 69875.0 / 102672.0, -2260.0 / 8211.0, 0.25};
+  for (int i = 0; i < 6; ++i) { c[i] = cc[i]; b[i] = bb[i]; }
+  for (int i = 1; i < 6; ++i) A[i][i] = g;
+  A[1][0] = g;
+  A[2][0] = 8611.0 / 62500.0; A[2][1] = -1743.0 / 31250.0;
+  A[3][0] = 5012029.0 / 34652500.0; A[3][1] = -654441.0 / 2922500.0; A[3][2] = 174375.0 / 388108.0;
+  A[4][0] = 15267082809.0 / 155376265600.0; A[4][1] = -71443401.0 / 120774400.0;
+  A[4][2] = 730878875.0 / 902184768.0; A[4][3] = 2285395.0 / 8070912.0;
+  for (int j = 0; j < 6; ++j) A[5][j] = b[j];
+}
+
+// Scheme by number of stages: 3 -> ESDIRK2, 4 -> ESDIRK3, 6 -> ESDIRK4.
+static int esdirk_tableau(int stages, double A[6][6], double b[6], double c[6]) {
+  if (stages == 3) { esdirk2_tableau(A, b, c); return 3; }
+  if (stages == 6) { esdirk4_tableau(A, b, c); return 6; }
+  esdirk3_tableau(A, b, c);
+  return 4;
+}
+
 extern "C" {
+
+int orc_esdirk(int stages, double* A, double* b, double* c) {
+  double AA[6][6], bb[6], cc[6];
+  int s = esdirk_tableau(stages, AA, bb, cc);
+  for (int i = 0; i < s; ++i) {
+    b[i] = bb[i]; c[i] = cc[i];
+    for (int j = 0; j < s; ++j) A[i * s + j] = AA[i][j];
+  }
+  return s;
+}
 
 int orc_basis(int P, double* x, double* w, double* D, double* lm, double* lp, double* gL, double* gR) {
   Basis1D b = make_basis(P);
@@ -1112,8 +1164,7 @@ void* orc_create(const OrcConfig* cfg, int E, int Ng, const double* nodes, const
     o->Rm.push_back(make_restriction(o->lev[l].g.b, o->lev[l + 1].g.b));
     o->Pm.push_back(make_prolongation(o->lev[l].g.b, o->lev[l + 1].g.b));
   }
-  esdirk3_tableau(o->A, o->b, o->c);
-  o->s = 4;
+  o->s = esdirk_tableau(cfg->esdirk_stages, o->A, o->b, o->c);
   o->omega_dt = 1.0;
   o->dtau = cfg->dtau_init;
   o->src.assign((size_t)4 * E * o->lev[0].g.N, 0.0);

@@ -43,12 +43,44 @@ static cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, count * sizeof(T) > 0 ? count * sizeof(T) : 8);
 }
 
-// ESDIRK3 of Section 2.4 (third order, four stages, first stage explicit,
-// stiffly accurate, L-stable): the published rational coefficients.
-static void esdirk3_table(Ctx& c) {
+// ESDIRK schemes of Section 2.4 (first stage explicit, stiffly accurate,
+// L-stable), with published coefficients:
+//  order 2: three stages (Kennedy & Carpenter 2016), g = 1 - 1/sqrt 2,
+//           b1 = b2 = 1/(2 sqrt 2), c = (0, 2g, 1);
+//  order 3: four stages, the implicit tableau of ARK3(2)4L[2]SA;
+//  order 4: six stages, the implicit tableau of ARK4(3)6L[2]SA (g = 1/4).
+static void esdirk_table(Ctx& c, int order) {
   memset(c.A, 0, sizeof(c.A));
   memset(c.b, 0, sizeof(c.b));
   memset(c.c, 0, sizeof(c.c));
+  if (order == 2) {
+    const double g = 1.0 - 1.0 / std::sqrt(2.0), w = 1.0 / (2.0 * std::sqrt(2.0));
+    c.A[1][0] = g; c.A[1][1] = g;
+    c.b[0] = w; c.b[1] = w; c.b[2] = g;
+    for (int j = 0; j < 3; ++j) c.A[2][j] = c.b[j];
+    c.c[1] = 2 * g; c.c[2] = 1.0;
+    c.stages = 3;
+    return;
+  }
+  if (order == 4) {
+    const double g = 0.25;
+    for (int i = 1; i < 6; ++i) c.A[i][i] = g;
+    c.A[1][0] = g;
+    c.A[2][0] = 8611.0 / 62500.0;
+    c.A[2][1] = -1743.0 / 31250.0;
+    c.A[3][0] = 5012029.0 / 34652500.0;
+    c.A[3][1] = -654441.0 / 2922500.0;
+    c.A[3][2] = 174375.0 / 388108.0;
+    c.A[4][0] = 15267082809.0 / 155376265600.0;
+    c.A[4][1] = -71443401.0 / 120774400.0;
+    c.A[4][2] = 730878875.0 / 902184768.0;
+    c.A[4][3] = 2285395.0 / 8070912.0;
+    const double b[6] = {82889.0 / 524892.0, 0.0, 15625.0 / 83664.0, 69875.0 / 102672.0, -2260.0 / 8211.0, g};
+    const double cc[6] = {0.0, 0.5, 83.0 / 250.0, 31.0 / 50.0, 17.0 / 20.0, 1.0};
+    for (int j = 0; j < 6; ++j) { c.b[j] = b[j]; c.A[5][j] = b[j]; c.c[j] = cc[j]; }
+    c.stages = 6;
+    return;
+  }
   const double g = 1767732205903.0 / 4055673282236.0;
   c.A[1][0] = g; c.A[1][1] = g;
   c.A[2][0] = 2746238789719.0 / 10658868560708.0;
@@ -86,6 +118,8 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   if (cfg->block_prec != PMG_PREC_FP64 && cfg->block_prec != PMG_PREC_FP32)
     return fail(PMG_EINVAL, "unknown block precision");
   if (!(cfg->gamma > 1.0)) return fail(PMG_EINVAL, "gamma must exceed 1");
+  if (cfg->esdirk_order != 0 && (cfg->esdirk_order < 2 || cfg->esdirk_order > 4))
+    return fail(PMG_EINVAL, "esdirk_order must be 2, 3 or 4 (0 means 3)");
   if (cfg->cfl_mode && !(cfg->cfl_init > 0.0 && cfg->cfl_max >= cfg->cfl_init))
     return fail(PMG_EINVAL, "cfl_mode needs 0 < cfl_init <= cfl_max");
   if (!(cfg->mu >= 0.0) || !std::isfinite(cfg->mu)) return fail(PMG_EINVAL, "mu must be finite and >= 0");
@@ -118,7 +152,7 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   c.ph.kT = cfg->mu > 0.0 ? cfg->mu * c.ph.Cp / cfg->Pr : 0.0;
   for (int v = 0; v < 4; ++v) c.ph.nw[v] = cfg->res_scale[v] > 0.0 ? 1.0 / cfg->res_scale[v] : 1.0;
   for (int v = 0; v < 4; ++v) c.ph.qinf[v] = cfg->q_inf[v];
-  esdirk3_table(c);
+  esdirk_table(c, cfg->esdirk_order == 0 ? 3 : cfg->esdirk_order);
   if (dalloc(&c.d_scal, 4) != cudaSuccess || dalloc(&c.d_flag, 4) != cudaSuccess ||
       dalloc(&c.d_dtau, 1) != cudaSuccess || cudaMallocHost((void**)&c.h_scal, 8 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost((void**)&c.h_dtau, sizeof(double)) != cudaSuccess) {

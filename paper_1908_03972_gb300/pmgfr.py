@@ -52,6 +52,8 @@ class pmg_config(ctypes.Structure):
         ("cfl_mode", ctypes.c_int),
         ("cfl_init", ctypes.c_double),
         ("cfl_max", ctypes.c_double),
+        ("esdirk_order", ctypes.c_int),
+        ("reserved", ctypes.c_int),
     ]
 
 
@@ -147,7 +149,8 @@ def _ptr(x, writable=False):
 def make_config(P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutoff=0, dtau_init=0.01,
                 dtau_max=10.0, tol=1e-8, refresh_every=10, max_pseudo=2000, block_prec=PMG_PREC_FP64,
                 use_graph=1, p_gauge=0.0, mu=0.0, Pr=0.72, res_scale=(1.0, 1.0, 1.0, 1.0),
-                q_inf=(0.0, 0.0, 0.0, 0.0), cfl_mode=0, cfl_init=1e2, cfl_max=1e5) -> pmg_config:
+                q_inf=(0.0, 0.0, 0.0, 0.0), cfl_mode=0, cfl_init=1e2, cfl_max=1e5,
+                esdirk_order=3) -> pmg_config:
     cfg = pmg_config()
     cfg.n_levels = len(P_levels)
     for l, (P, n) in enumerate(zip(P_levels, n_smooth)):
@@ -163,6 +166,7 @@ def make_config(P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutof
         cfg.res_scale[v] = res_scale[v]
         cfg.q_inf[v] = q_inf[v]
     cfg.cfl_mode, cfg.cfl_init, cfg.cfl_max = cfl_mode, cfl_init, cfl_max
+    cfg.esdirk_order = esdirk_order
     return cfg
 
 

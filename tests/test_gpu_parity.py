@@ -327,3 +327,27 @@ def test_esdirk_c1_parity(prec, gauge):
             assert dp <= 2e-6 * (step + 1) and du <= 1e-7 * (step + 1), (step, dp, du)
     finally:
         gpu.close()
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_esdirk2_and_esdirk4_c1_first_step_parity(order):
+    """The three- and six-stage schemes of Section 2.4 on the C1 setting, one
+    physical step from the analytic state, FP64 blocks."""
+    from paper_1908_03972_gb300 import pmgfr
+    nodes, nbr = W.periodic_box(8, 8, Ng=1)
+    kw = dict(_C1_KW, esdirk_order=order)
+    orc = O.Oracle(nodes, nbr, 1, [2, 1, 0], [5, 10, 20], **kw)
+    gpu = pmgfr.Solver(nodes, nbr, [2, 1, 0], [5, 10, 20], block_prec=0, **kw)
+    try:
+        q = W.isentropic_vortex(orc.coords())
+        qo, its_o, _ = orc.esdirk_step(q, 0.1)
+        qg, st = gpu.esdirk_step(q, 0.1)
+        n_impl = {2: 2, 4: 5}[order]
+        its_g = list(st.pseudo_iters)[:n_impl]
+        assert max(st.res_drop[:n_impl]) <= 1e-8 and min(its_g) > 0 and st.pseudo_iters[n_impl] == 0
+        assert all(b <= 1.1 * a + 5 and a <= 1.1 * b + 5 for a, b in zip(its_o, its_g)), (its_o, its_g)
+        dp = np.abs(qg[0] - qo[0]).max() / 2.0
+        du = np.abs(qg[1:3] - qo[1:3]).max()
+        assert dp <= 2e-6 and du <= 1e-7, (dp, du)
+    finally:
+        gpu.close()
