@@ -53,7 +53,7 @@ typedef enum {
 /* Solver configuration (Sections 2.2-3, 4.1).
  *  P[l], n_smooth[l]: the hierarchy P{P0-P1-...} and the smoothing counts
  *  I{n0-n1-...}; pre- and post-smoothing use the same count, the coarsest
- *  level smooths once (Section 3).  0 <= P <= 4, 1 <= n_levels <= 8.
+ *  level smooths once (Section 3).  0 <= P <= 5, 1 <= n_levels <= 8.
  *  cutoff = 1: eps = min(1, max(kappa Ma_inf, Ma)) (eq. eps_nonmove);
  *  cutoff = 0: eps = min(1, Ma) (Section 4.1).
  *  dtau_init, dtau_max, refresh_every: pseudo time step control (eq. ser

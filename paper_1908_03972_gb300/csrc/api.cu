@@ -111,7 +111,7 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   if (!cfg || !out) return fail(PMG_EINVAL, "null argument");
   if (cfg->n_levels < 1 || cfg->n_levels > kMaxLevels) return fail(PMG_EINVAL, "n_levels must be in 1..8");
   for (int l = 0; l < cfg->n_levels; ++l) {
-    if (cfg->P[l] < 0 || cfg->P[l] > kMaxP) return fail(PMG_EINVAL, "P must be in 0..4");
+    if (cfg->P[l] < 0 || cfg->P[l] > kMaxP) return fail(PMG_EINVAL, "P must be in 0..5");
     if (l > 0 && cfg->P[l] >= cfg->P[l - 1]) return fail(PMG_EINVAL, "P levels must decrease");
     if (cfg->n_smooth[l] < 1) return fail(PMG_EINVAL, "smoothing counts must be >= 1");
   }

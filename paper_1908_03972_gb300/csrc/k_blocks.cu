@@ -142,7 +142,8 @@ void launch_assemble(const Ctx& c, const LevelDev& L, const double* q, const dou
     case 1: PMG_ASM(1); break;
     case 2: PMG_ASM(2); break;
     case 3: PMG_ASM(3); break;
-    default: PMG_ASM(4); break;
+    case 4: PMG_ASM(4); break;
+    default: PMG_ASM(5); break;
   }
 #undef PMG_ASM
   if (c.ph.mu > 0.0) launch_assemble_visc(c, L, q, s);
@@ -352,7 +353,8 @@ static void apply_dispatch(const Ctx& c, const LevelDev& L, const W* Dinv, const
     case 4: epb = ApplyEPB<4>::value; break;
     case 9: epb = ApplyEPB<9>::value; break;
     case 16: epb = ApplyEPB<16>::value; break;
-    default: epb = ApplyEPB<25>::value; break;
+    case 25: epb = ApplyEPB<25>::value; break;
+    default: epb = ApplyEPB<36>::value; break;
   }
   int threads = ((epb * N) + 31) / 32 * 32;
   int blocks = (c.E + epb - 1) / epb;
@@ -362,7 +364,8 @@ static void apply_dispatch(const Ctx& c, const LevelDev& L, const W* Dinv, const
     case 4: PMG_APPLY(4); break;
     case 9: PMG_APPLY(9); break;
     case 16: PMG_APPLY(16); break;
-    default: PMG_APPLY(25); break;
+    case 25: PMG_APPLY(25); break;
+    default: PMG_APPLY(36); break;
   }
 #undef PMG_APPLY
 }

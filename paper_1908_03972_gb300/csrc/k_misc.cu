@@ -67,7 +67,8 @@ __global__ void prolong_kernel(int E, XferTab X, const double* __restrict__ qc, 
   }
 }
 
-#define PMG_PAIRS(M) M(1, 0) M(2, 0) M(2, 1) M(3, 0) M(3, 1) M(3, 2) M(4, 0) M(4, 1) M(4, 2) M(4, 3)
+#define PMG_PAIRS(M) \
+  M(1, 0) M(2, 0) M(2, 1) M(3, 0) M(3, 1) M(3, 2) M(4, 0) M(4, 1) M(4, 2) M(4, 3) M(5, 0) M(5, 1) M(5, 2) M(5, 3) M(5, 4)
 
 void launch_restrict(const Ctx& c, const LevelDev& Lf, const LevelDev& Lc, const XferTab& X, const double* in,
                      double* out, double* out2, double scale, cudaStream_t s) {

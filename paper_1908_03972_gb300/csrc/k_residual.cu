@@ -35,7 +35,7 @@ namespace pmg {
 template <int P>
 struct ElemsPerBlock {
   static constexpr int N = (P + 1) * (P + 1);
-  static constexpr int value = P == 0 ? 32 : P == 1 ? 8 : P == 2 ? 7 : P == 3 ? 4 : 2;
+  static constexpr int value = P == 0 ? 32 : P == 1 ? 8 : P == 2 ? 7 : P == 3 ? 4 : P == 4 ? 2 : 1;
 };
 
 // Trace of the solution polynomial along the line through face point k of
@@ -406,7 +406,8 @@ int residual_threads_per_block(int P) {
     case 1: t = ElemsPerBlock<1>::value * 4; break;
     case 2: t = ElemsPerBlock<2>::value * 9; break;
     case 3: t = ElemsPerBlock<3>::value * 16; break;
-    default: t = ElemsPerBlock<4>::value * 25; break;
+    case 4: t = ElemsPerBlock<4>::value * 25; break;
+    default: t = ElemsPerBlock<5>::value * 36; break;
   }
   return (t + 31) / 32 * 32;
 }
@@ -417,7 +418,8 @@ static int elems_per_block(int P) {
     case 1: return ElemsPerBlock<1>::value;
     case 2: return ElemsPerBlock<2>::value;
     case 3: return ElemsPerBlock<3>::value;
-    default: return ElemsPerBlock<4>::value;
+    case 4: return ElemsPerBlock<4>::value;
+    default: return ElemsPerBlock<5>::value;
   }
 }
 
@@ -443,7 +445,8 @@ void launch_face_flux(const Ctx& c, const LevelDev& L, const double* q, cudaStre
     case 1: PMG_FACE(1); break;
     case 2: PMG_FACE(2); break;
     case 3: PMG_FACE(3); break;
-    default: PMG_FACE(4); break;
+    case 4: PMG_FACE(4); break;
+    default: PMG_FACE(5); break;
   }
 #undef PMG_FACE
 }
@@ -470,7 +473,8 @@ void launch_volume(const Ctx& c, const LevelDev& L, int level, const double* q, 
     case 1: PMG_VOL(1); break;
     case 2: PMG_VOL(2); break;
     case 3: PMG_VOL(3); break;
-    default: PMG_VOL(4); break;
+    case 4: PMG_VOL(4); break;
+    default: PMG_VOL(5); break;
   }
 #undef PMG_VOL
 }
@@ -499,7 +503,8 @@ static void volume_apply_dispatch(const Ctx& c, const LevelDev& L, double* q, do
     case 1: PMG_VA(1); break;
     case 2: PMG_VA(2); break;
     case 3: PMG_VA(3); break;
-    default: PMG_VA(4); break;
+    case 4: PMG_VA(4); break;
+    default: PMG_VA(5); break;
   }
 #undef PMG_VA
 }

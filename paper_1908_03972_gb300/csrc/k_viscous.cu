@@ -59,7 +59,8 @@ void launch_grad(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t 
     case 1: PMG_GRAD(1); break;
     case 2: PMG_GRAD(2); break;
     case 3: PMG_GRAD(3); break;
-    default: PMG_GRAD(4); break;
+    case 4: PMG_GRAD(4); break;
+    default: PMG_GRAD(5); break;
   }
 #undef PMG_GRAD
 }
@@ -330,7 +331,8 @@ void launch_assemble_visc(const Ctx& c, const LevelDev& L, const double* q, cuda
     case 1: PMG_AV(1); break;
     case 2: PMG_AV(2); break;
     case 3: PMG_AV(3); break;
-    default: PMG_AV(4); break;
+    case 4: PMG_AV(4); break;
+    default: PMG_AV(5); break;
   }
 #undef PMG_AV
 }

@@ -10,7 +10,7 @@
 
 namespace pmg {
 
-constexpr int kMaxP = 4;
+constexpr int kMaxP = 5;
 constexpr int kMaxLevels = 8;
 
 // ----------------------------------------------------------------- host side

@@ -53,6 +53,16 @@ def _rel_per_var(a, b, orc=None, Ma=0.005):
     return max(np.abs(a[v] - b[v]).max() / (np.abs(b[v]).max() + 1e-4 * S[v]) for v in range(4))
 
 
+def _norm_bound(F, orc, Ma=0.005):
+    """2-norm of the pointwise residual bound 1e-10 (max|F_v| + 1e-4 S_v)."""
+    h, P = _h(orc), orc.P[0]
+    p = W.freestream_T(Ma)
+    vinf = 2 ** 0.5
+    S = np.array([p / vinf, p, p, (3.5 * p + 1.0) * p / vinf]) * (P + 1) ** 2 / h
+    b = np.array([1e-10 * (np.abs(F[v]).max() + 1e-4 * S[v]) for v in range(4)])
+    return float(np.sqrt((b ** 2).sum() * F[0].size))
+
+
 def _h(orc):
     met, _ = orc.metrics()
     return 2.0 * float(np.sqrt(met[:, :, 4].min()))
@@ -79,7 +89,7 @@ def _mesh(name):
 
 @pytest.mark.parametrize("gauge", GAUGES)
 @pytest.mark.parametrize("name", list(MESHES))
-@pytest.mark.parametrize("P", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("P", [0, 1, 2, 3, 4, 5])
 def test_residual_parity(name, P, gauge):
     (nodes, nbr), Ng = _mesh(name)
     if gauge and P < Ng:
@@ -151,7 +161,7 @@ def test_stage_residual_parity(P, gauge):
 
 
 @pytest.mark.parametrize("gauge", GAUGES)
-@pytest.mark.parametrize("P", [0, 1, 2, 3])
+@pytest.mark.parametrize("P", [0, 1, 2, 3, 5])
 def test_block_assembly_parity(P, gauge):
     Ng = 1 if gauge else 2
     nodes, nbr = W.periodic_box(3, 4, Ng=Ng, perturb=0.3 if Ng > 1 else 0.0)
@@ -172,7 +182,7 @@ def test_block_assembly_parity(P, gauge):
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-4)])
-@pytest.mark.parametrize("P", [0, 1, 2, 3])
+@pytest.mark.parametrize("P", [0, 1, 2, 3, 5])
 def test_factor_and_apply(P, prec, tol):
     nodes, nbr = W.periodic_box(3, 3, Ng=2, perturb=0.3)
     from paper_1908_03972_gb300 import pmgfr
@@ -193,7 +203,7 @@ def test_factor_and_apply(P, prec, tol):
         gpu.close()
 
 
-@pytest.mark.parametrize("levels", [[1, 0], [2, 1], [3, 2], [3, 1], [4, 2], [2, 0]])
+@pytest.mark.parametrize("levels", [[1, 0], [2, 1], [3, 2], [3, 1], [4, 2], [2, 0], [5, 3], [5, 1]])
 def test_transfer_parity(levels):
     nodes, nbr = W.periodic_box(3, 2, Ng=2, perturb=0.3)
     orc, gpu = _pair(nodes, nbr, 2, levels, [1, 1])
@@ -218,7 +228,8 @@ def _stage_setup(orc, gpu, omega_dt=0.0436, scale=0.5):
 
 
 @pytest.mark.parametrize("gauge", GAUGES)
-@pytest.mark.parametrize("levels,smooth", [([2, 1, 0], [2, 3, 4]), ([3, 2, 1, 0], [1, 2, 2, 3]), ([2], [3])])
+@pytest.mark.parametrize("levels,smooth", [([2, 1, 0], [2, 3, 4]), ([3, 2, 1, 0], [1, 2, 2, 3]), ([2], [3]),
+                                           ([5, 3, 1], [2, 2, 4])])
 def test_vcycle_parity_fp64(levels, smooth, gauge):
     Ng = 1 if gauge else 2
     nodes, nbr = W.periodic_box(4, 4, Ng=Ng, perturb=0.3 if Ng > 1 else 0.0)
@@ -229,7 +240,9 @@ def test_vcycle_parity_fp64(levels, smooth, gauge):
         qg, nrm = gpu.vcycle(q, 0.7, refresh=True)
         dq = np.abs(qo - q).max(axis=(1, 2))
         assert (np.abs(qg - qo).max(axis=(1, 2)) / dq).max() <= 1e-8
-        assert abs(nrm - np.linalg.norm(orc.stage_F(q))) <= 1e-10 * nrm
+        # the norm of F(q): every point within the residual bound of the module docstring
+        Fo = orc.stage_F(q)
+        assert abs(nrm - np.linalg.norm(Fo)) <= max(1e-10 * nrm, _norm_bound(Fo, orc))
         # second cycle with the frozen smoother
         qo2 = orc.vcycle(qo, 5.0, refresh=False)
         qg2, _ = gpu.vcycle(qg, 5.0, refresh=False)
