@@ -256,11 +256,12 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
         dalloc(&L.Fcom, (size_t)4 * c.E * 4 * L.n1) || dalloc(&L.Dfull, nn2) ||
         cudaMalloc(&L.Dinv, nn2 * wbytes) || dalloc(&L.rs, (size_t)c.E * L.n) || dalloc(&L.cs, (size_t)c.E * L.n))
       return fail(PMG_ENOMEM, "device allocation failed for level data");
-    // Optionally, coarse levels are smoothed by the fused one-launch sweep
-    // (k_fused.cu).  PMG_FUSE_MAX_P sets the largest P that uses it; it is off
-    // by default because the fused sweep evaluates every face twice and the
-    // coarse sweeps are bound by FP64 issue, not by launches.
-    int fuse_max = -1;
+    // Coarse levels up to P = PMG_FUSE_MAX_P (default 0) are smoothed by the
+    // fused one-launch sweep (k_fused.cu), which evaluates every face from both
+    // of its elements.  At P = 0 the extra face work runs on SMSPs the split
+    // launches leave idle and the sweep saves a launch (C2 V-cycle 2.6%
+    // faster); from P = 1 on, the doubled face work costs more than it saves.
+    int fuse_max = 0;
     if (const char* env = getenv("PMG_FUSE_MAX_P")) fuse_max = atoi(env);
     bool boundary = false;
     for (const FaceRec& fr : c.mesh.faces) boundary = boundary || fr.eR < 0;
