@@ -112,7 +112,11 @@ typedef struct {
   int esdirk_order; /* ESDIRK scheme of pmg_esdirk_step (Section 2.4): 2
                      (three stages), 3 (four stages) or 4 (six stages);
                      0 means 3 */
-  int reserved;   /* must be 0 */
+  int refresh_always; /* 0: after the first pseudo-iteration of a stage the
+                     smoother is rebuilt every refresh_every iterations until
+                     one rebuild used dtau_max (the rule of Section 4.4);
+                     1: every refresh_every iterations throughout the stage
+                     (Section 4.1 states only the period) */
 } pmg_config;
 
 /* Boundary types, in the second slot of a boundary face's neighbour entry

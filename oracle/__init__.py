@@ -63,6 +63,7 @@ class OrcConfig(ctypes.Structure):
         ("cfl_mode", ctypes.c_int),
         ("cfl_init", ctypes.c_double),
         ("cfl_max", ctypes.c_double),
+        ("refresh_always", ctypes.c_int),
     ]
 
 
@@ -179,7 +180,8 @@ class Oracle:
     def __init__(self, nodes, nbr, Ng, P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005,
                  kappa=1.0, cutoff=0, dtau_init=0.01, dtau_max=10.0, tol=1e-8,
                  refresh_every=10, max_pseudo=2000, mu=0.0, Pr=0.72, res_scale=(1.0, 1.0, 1.0, 1.0),
-                 q_inf=(0.0, 0.0, 0.0, 0.0), cfl_mode=0, cfl_init=1e2, cfl_max=1e5, esdirk_order=3):
+                 q_inf=(0.0, 0.0, 0.0, 0.0), cfl_mode=0, cfl_init=1e2, cfl_max=1e5, esdirk_order=3,
+                 refresh_always=0):
         cfg = OrcConfig()
         cfg.n_levels = len(P_levels)
         for l, P in enumerate(P_levels):
@@ -194,6 +196,7 @@ class Oracle:
             cfg.res_scale[v] = res_scale[v]
             cfg.q_inf[v] = q_inf[v]
         cfg.cfl_mode, cfg.cfl_init, cfg.cfl_max = cfl_mode, cfl_init, cfl_max
+        cfg.refresh_always = refresh_always
         self.cfg = cfg
         self.nodes = _f64(nodes)
         self.nbr = np.ascontiguousarray(nbr, dtype=np.int32)

@@ -483,6 +483,7 @@ struct OrcConfig {
   double q_inf[4];        // free-stream primitive state (p, u, v, T) of far-field faces
   int cfl_mode;           // 1: dtau = CFL dtau_min (eq. CFL), SER on the CFL number
   double cfl_init, cfl_max;
+  int refresh_always;     // 1: rebuild every refresh_every iterations throughout (Section 4.1)
 };
 
 struct Level {
@@ -1319,7 +1320,8 @@ static double ser_next(double dtau, double prev_norm, double norm, double dtau_m
 // dtau = dtau_max the smoother is not updated anymore" refers to a smoother
 // already built at dtau_max (taken literally, a dtau that reaches dtau_max
 // within the first k iterations would freeze the smoother at dtau_init).
-static bool refresh_due(int m, int k, double dtau_last_refresh, double dtau_max) {
+static bool refresh_due(int m, int k, double dtau_last_refresh, double dtau_max, bool always = false) {
+  if (always) return m % k == 0;   // Section 4.1: every k-th pseudo-iteration
   return m == 0 || (m % k == 0 && dtau_last_refresh < dtau_max);
 }
 
@@ -1347,7 +1349,7 @@ static int stage_solve(Oracle* o, double* q, int* iters, double* drop, double* n
     if (!std::isfinite(nm)) { *iters = m; *drop = nm; return -5; }
     if (m >= o->cfg.max_pseudo) { *iters = m; *drop = nm / n0; return -6; }
     if (m > 0) dtau = ser_next(dtau, prev, nm, dtau_max);
-    bool refresh = refresh_due(m, o->cfg.refresh_every, dtau_built, dtau_max);
+    bool refresh = refresh_due(m, o->cfg.refresh_every, dtau_built, dtau_max, o->cfg.refresh_always != 0);
     if (refresh) dtau_built = dtau;
     int st = orc_vcycle(o, q, dtau, refresh);
     if (st) return st;

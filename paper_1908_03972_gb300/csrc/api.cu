@@ -587,7 +587,7 @@ static pmg_status stage_solve(Ctx& c, int* iters, double* drop, int* n_refresh) 
       return fail(PMG_ENOTCONV, "stage not converged within max_pseudo V-cycles");
     }
     if (m > 0) dtau = std::min(dtau * std::pow(prev / nm, 1.5), dtau_max);
-    bool refresh = (m == 0) || (m % c.cfg.refresh_every == 0 && built < dtau_max);
+    bool refresh = (m == 0) || (m % c.cfg.refresh_every == 0 && (c.cfg.refresh_always || built < dtau_max));
     if (refresh) {
       built = dtau;
       st = set_dtau(c, dtau);

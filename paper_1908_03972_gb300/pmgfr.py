@@ -53,7 +53,7 @@ class pmg_config(ctypes.Structure):
         ("cfl_init", ctypes.c_double),
         ("cfl_max", ctypes.c_double),
         ("esdirk_order", ctypes.c_int),
-        ("reserved", ctypes.c_int),
+        ("refresh_always", ctypes.c_int),
     ]
 
 
@@ -150,7 +150,7 @@ def make_config(P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutof
                 dtau_max=10.0, tol=1e-8, refresh_every=10, max_pseudo=2000, block_prec=PMG_PREC_FP64,
                 use_graph=1, p_gauge=0.0, mu=0.0, Pr=0.72, res_scale=(1.0, 1.0, 1.0, 1.0),
                 q_inf=(0.0, 0.0, 0.0, 0.0), cfl_mode=0, cfl_init=1e2, cfl_max=1e5,
-                esdirk_order=3) -> pmg_config:
+                esdirk_order=3, refresh_always=0) -> pmg_config:
     cfg = pmg_config()
     cfg.n_levels = len(P_levels)
     for l, (P, n) in enumerate(zip(P_levels, n_smooth)):
@@ -167,6 +167,7 @@ def make_config(P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutof
         cfg.q_inf[v] = q_inf[v]
     cfg.cfl_mode, cfg.cfl_init, cfg.cfl_max = cfl_mode, cfl_init, cfl_max
     cfg.esdirk_order = esdirk_order
+    cfg.refresh_always = refresh_always
     return cfg
 
 

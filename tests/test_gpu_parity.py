@@ -364,3 +364,24 @@ def test_esdirk2_and_esdirk4_c1_first_step_parity(order):
         assert dp <= 2e-6 and du <= 1e-7, (dp, du)
     finally:
         gpu.close()
+
+
+def test_refresh_always_rule_and_parity():
+    """refresh_always = 1 rebuilds the smoother every refresh_every
+    pseudo-iterations throughout each stage (Section 4.1 states only the
+    period); the default stops once a rebuild used dtau_max (Section 4.4)."""
+    from paper_1908_03972_gb300 import pmgfr
+    nodes, nbr = W.periodic_box(8, 8, Ng=1)
+    kw = dict(_C1_KW, refresh_always=1)
+    orc = O.Oracle(nodes, nbr, 1, [2, 1, 0], [5, 10, 20], **kw)
+    gpu = pmgfr.Solver(nodes, nbr, [2, 1, 0], [5, 10, 20], block_prec=0, **kw)
+    try:
+        q = W.isentropic_vortex(orc.coords())
+        qo, its_o, _ = orc.esdirk_step(q, 0.1)
+        qg, st = gpu.esdirk_step(q, 0.1)
+        its_g = list(st.pseudo_iters)[:3]
+        assert st.n_refresh == sum((it + 9) // 10 for it in its_g), (st.n_refresh, its_g)
+        assert all(b <= 1.1 * a + 5 and a <= 1.1 * b + 5 for a, b in zip(its_o, its_g)), (its_o, its_g)
+        assert np.abs(qg[0] - qo[0]).max() / 2.0 <= 2e-6 and np.abs(qg[1:3] - qo[1:3]).max() <= 1e-7
+    finally:
+        gpu.close()
