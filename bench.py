@@ -89,10 +89,15 @@ def apply_flops(P, E):
 
 # ------------------------------------------------------------------ helpers
 def csrc_fingerprint():
+    """Hash of the kernel sources (the k_*.cu files and the device headers they
+    include); host-only files (api.cu, host_tables.cpp) do not change a
+    kernel's counters."""
     import hashlib
     src = os.path.join(ROOT, "paper_1908_03972_gb300", "csrc")
     h = hashlib.sha256()
     for f in sorted(os.listdir(src)):
+        if not (f.startswith("k_") or f.endswith(".cuh") or f == "pmg_internal.h"):
+            continue
         h.update(f.encode())
         with open(os.path.join(src, f), "rb") as fh:
             h.update(fh.read())
