@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(64) apply_kernel(int E, const W* __restrict__ 
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       int row = v * N + t;
-      sr[le][row] = (W)(r[v * plane + (size_t)e * N + t] * rs[(size_t)e * n + row]);
+      sr[le][row] = scaled_in<W>(r[v * plane + (size_t)e * N + t], rs[(size_t)e * n + row]);
     }
   }
   __syncthreads();
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(64) apply_kernel(int E, const W* __restrict__ 
   for (int m = 0; m < 4; ++m) {
     int row = 4 * t + m;
     int v = row / N, pt = row - v * N;
-    double xv = (double)acc[m] * cs[(size_t)e * n + row];
+    double xv = scaled_out<W>(acc[m], cs[(size_t)e * n + row]);
     size_t o = v * plane + (size_t)e * N + pt;
     if (accumulate) x[o] += xv;
     else x[o] = xv;

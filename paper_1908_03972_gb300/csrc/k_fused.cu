@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(64) fused_sweep_kernel(
         if (src) F += src[o];
         if (S) F -= S[o];
         int row = v * N + t;
-        sr[le][row] = (W)(F * rs[(size_t)e * n + row]);
+        sr[le][row] = scaled_in<W>(F, rs[(size_t)e * n + row]);
       }
     }
   }
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(64) fused_sweep_kernel(
       for (int m = 0; m < 4; ++m) {
         int row = 4 * t + m;
         int v = row / N, pt = row - v * N;
-        double xv = (double)acc[m] * cs[(size_t)e * n + row];
+        double xv = scaled_out<W>(acc[m], cs[(size_t)e * n + row]);
         size_t o = v * plane + (size_t)e * N + pt;
         qout[o] = sq[le][v][pt] + xv;
       }

@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(256) volume_kernel(int E, const double* q,
         if (mode == RES_SYSTEM && S) F -= S[o];
         if (APPLY) {
           const int row = v * N + pt;
-          sr[APPLY ? le : 0][APPLY ? row : 0] = (W)(F * rs[(size_t)e * n + row]);
+          sr[APPLY ? le : 0][APPLY ? row : 0] = scaled_in<W>(F, rs[(size_t)e * n + row]);
         } else {
           out[o] = F;
         }
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(256) volume_kernel(int E, const double* q,
         const int row = 4 * pt + m;
         const int v = row / N, p2 = row - v * N;
         const size_t o = v * plane + (size_t)e * N + p2;
-        qw[o] = q[o] + (double)acc[m] * cs[(size_t)e * n + row];
+        qw[o] = q[o] + scaled_out<W>(acc[m], cs[(size_t)e * n + row]);
       }
     }
   }

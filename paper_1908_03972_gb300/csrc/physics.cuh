@@ -168,12 +168,12 @@ __host__ __device__ inline void roe_flux_jump(const S qm[4], const S qp[4], cons
   S fm[4], fp[4];
   flux_n(qm, pmm, nx, ny, ph, fm);
   flux_n(qp, pmp, nx, ny, ph, fp);
-  // averaged state
-  S p = 0.5 * (qm[0] + qp[0]);
-  S u = 0.5 * (qm[1] + qp[1]);
-  S v = 0.5 * (qm[2] + qp[2]);
-  S T = 0.5 * (qm[3] + qp[3]);
+  // averaged state, formed from the jump: (q^- + q^+)/2 = q^- + dq/2
   S dp = dq[0], du = dq[1], dv = dq[2], dT = dq[3];
+  S p = qm[0] + 0.5 * dp;
+  S u = qm[1] + 0.5 * du;
+  S v = qm[2] + 0.5 * dv;
+  S T = qm[3] + 0.5 * dT;
   // divisions are ~10 FP64 FMA each on GB300: form each reciprocal once
   S iT = s_rcp(T);
   S rho = p * iT;
@@ -203,7 +203,7 @@ __host__ __device__ inline void roe_flux_jump(const S qm[4], const S qp[4], cons
   S w1 = (dp * irho + (1.0 - e2) * un * dun) * iUr2;
   // (|B| - |u_n|) w
   S y0 = (a0 - aun) * w0 + a1 * (e2 * (un * w0 + rc2 * w1));
-  S y1 = (a0 - aun) * w1 + a1 * (w0 * irho + un * w1);
+  S y1 = (a0 - aun) * w1 + a1 * (dun + un * w1);   // w0 / rho = dun
   S irCp = irho / ph.Cp;
   S xT = -(1.0 - e2) * un * irCp * y0 + e2 * ph.gm1 * T * y1 + aun * dT;
   S xt = aun * dut;
@@ -218,10 +218,11 @@ __host__ __device__ inline void roe_flux_jump(const S qm[4], const S qp[4], cons
   S d1 = u * drho + rho * xu;
   S d2 = v * drho + rho * xv;
   S d3 = H * drho - yp + rho * (u * xu + v * xv) + rho * ph.Cp * yT;
-  out[0] = (0.5 * (fm[0] + fp[0]) - 0.5 * d0) * dS;
-  out[1] = (0.5 * (fm[1] + fp[1]) - 0.5 * d1) * dS;
-  out[2] = (0.5 * (fm[2] + fp[2]) - 0.5 * d2) * dS;
-  out[3] = (0.5 * (fm[3] + fp[3]) - 0.5 * d3) * dS;
+  const double hdS = 0.5 * dS;
+  out[0] = ((fm[0] + fp[0]) - d0) * hdS;
+  out[1] = ((fm[1] + fp[1]) - d1) * hdS;
+  out[2] = ((fm[2] + fp[2]) - d2) * hdS;
+  out[3] = ((fm[3] + fp[3]) - d3) * hdS;
 }
 
 // Same flux with the jump q_p^+ - q_p^- formed from the two traces.

@@ -13,6 +13,14 @@ namespace pmg {
 constexpr int kMaxP = 5;
 constexpr int kMaxLevels = 8;
 
+// Block scales are powers of two, so applying them in the block precision W
+// after the conversion gives the same value (barring under- or overflow of
+// W) and, for W = float, keeps these multiplications off the FP64 pipe.
+template <class W>
+__device__ __forceinline__ W scaled_in(double x, double s) { return (W)x * (W)s; }
+template <class W>
+__device__ __forceinline__ double scaled_out(W a, double s) { return (double)(a * (W)s); }
+
 // ----------------------------------------------------------------- host side
 struct Ref1D {
   int P;
