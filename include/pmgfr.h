@@ -50,6 +50,20 @@ typedef enum {
   PMG_PREC_FP32 = 1  /* blocks equilibrated, factored and applied in FP32 */
 } pmg_prec;
 
+/* Arithmetic of the common Roe flux (eq. invis_com) at the face points.
+ * Double-word (float-float) arithmetic runs the same closed form on the FP32
+ * pipes at ~2^-46 relative rounding; the face traces and jumps it takes and
+ * the central pressure term stay binary64.  On the coarse levels the flux
+ * only shapes the FAS corrections; the finest level's residual defines the
+ * converged solution and the stopping norm. */
+typedef enum {
+  PMG_FLUX_FP64 = 0,      /* binary64 on every level */
+  PMG_FLUX_DW_COARSE = 1, /* double-word on the coarse levels, binary64 on
+                             the finest: the converged state solves the
+                             binary64 residual equations */
+  PMG_FLUX_DW = 2         /* double-word on every level */
+} pmg_flux_prec;
+
 /* Solver configuration (Sections 2.2-3, 4.1).
  *  P[l], n_smooth[l]: the hierarchy P{P0-P1-...} and the smoothing counts
  *  I{n0-n1-...}; pre- and post-smoothing use the same count, the coarsest
@@ -117,6 +131,8 @@ typedef struct {
                      one rebuild used dtau_max (the rule of Section 4.4);
                      1: every refresh_every iterations throughout the stage
                      (Section 4.1 states only the period) */
+  int flux_prec;  /* pmg_flux_prec of the residual's face fluxes (the
+                     element blocks are always differentiated in binary64) */
 } pmg_config;
 
 /* Boundary types, in the second slot of a boundary face's neighbour entry

@@ -117,6 +117,8 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   }
   if (cfg->block_prec != PMG_PREC_FP64 && cfg->block_prec != PMG_PREC_FP32)
     return fail(PMG_EINVAL, "unknown block precision");
+  if (cfg->flux_prec != PMG_FLUX_FP64 && cfg->flux_prec != PMG_FLUX_DW_COARSE && cfg->flux_prec != PMG_FLUX_DW)
+    return fail(PMG_EINVAL, "unknown flux precision");
   if (!(cfg->gamma > 1.0)) return fail(PMG_EINVAL, "gamma must exceed 1");
   if (cfg->esdirk_order != 0 && (cfg->esdirk_order < 2 || cfg->esdirk_order > 4))
     return fail(PMG_EINVAL, "esdirk_order must be 2, 3 or 4 (0 means 3)");
@@ -152,6 +154,7 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   c.ph.kT = cfg->mu > 0.0 ? cfg->mu * c.ph.Cp / cfg->Pr : 0.0;
   for (int v = 0; v < 4; ++v) c.ph.nw[v] = cfg->res_scale[v] > 0.0 ? 1.0 / cfg->res_scale[v] : 1.0;
   for (int v = 0; v < 4; ++v) c.ph.qinf[v] = cfg->q_inf[v];
+  c.phw = make_physw(c.ph);
   esdirk_table(c, cfg->esdirk_order == 0 ? 3 : cfg->esdirk_order);
   if (dalloc(&c.d_scal, 4) != cudaSuccess || dalloc(&c.d_flag, 4) != cudaSuccess ||
       dalloc(&c.d_dtau, 1) != cudaSuccess || cudaMallocHost((void**)&c.h_scal, 8 * sizeof(double)) != cudaSuccess ||
@@ -239,6 +242,7 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
   for (int l = 0; l < c.cfg.n_levels; ++l) {
     LevelDev& L = c.lev[l];
     const Ref1D& r = refs[l];
+    L.level = l;
     L.P = r.P; L.n1 = r.P + 1; L.N = L.n1 * L.n1; L.n = 4 * L.N;
     L.tot = (size_t)4 * c.E * L.N;
     maxtot = std::max(maxtot, L.tot);

@@ -24,10 +24,10 @@ struct FusedEPB {   // elements per CTA; a thread per face point of each element
   static constexpr int value = P == 0 ? 8 : P == 1 ? 4 : P == 2 ? 2 : 1;
 };
 
-template <int P, class W>
+template <int P, class W, bool DWF>
 __global__ void __launch_bounds__(64) fused_sweep_kernel(
     int E, const double* __restrict__ qin, double* __restrict__ qout, const double* __restrict__ met,
-    const double* __restrict__ face, const int* __restrict__ nbr, OpTab op, Phys ph, double inv_odt,
+    const double* __restrict__ face, const int* __restrict__ nbr, OpTab op, Phys ph, PhysW phw, double inv_odt,
     const double* __restrict__ src, const double* __restrict__ S, const double* __restrict__ qref,
     const W* __restrict__ Dinv, const double* __restrict__ rs, const double* __restrict__ cs) {
   constexpr int n1 = P + 1, N = n1 * n1, n = 4 * N, EPB = FusedEPB<P>::value, FP = 4 * n1;
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(64) fused_sweep_kernel(
       qp[0] += ph.p_ref;
       const double* g = face + (((size_t)e * 4 + f) * n1 + k) * 3;
       double out[4];
-      roe_flux_jump(qm, qp, dq, pgm, pgp, __ldg(g), __ldg(g + 1), __ldg(g + 2), ph, out);
+      face_roe<DWF>(qm, qp, dq, pgm, pgp, __ldg(g), __ldg(g + 1), __ldg(g + 2), ph, phw, out);
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         double loc = 0.0;
@@ -196,12 +196,18 @@ static void fused_launch(const Ctx& c, const LevelDev& L, const double* qin, dou
   int threads = (EPB * FP + 31) / 32 * 32;
   int blocks = (c.E + EPB - 1) / EPB;
   const int* nbr = c.d_faces + 5 * c.n_faces;
-  if (prec == PMG_PREC_FP64)
-    fused_sweep_kernel<P, double><<<blocks, threads, 0, s>>>(c.E, qin, qout, L.met, L.face, nbr, L.op, c.ph, inv_odt,
-                                                             src, S, qref, (const double*)L.Dinv, L.rs, L.cs);
-  else
-    fused_sweep_kernel<P, float><<<blocks, threads, 0, s>>>(c.E, qin, qout, L.met, L.face, nbr, L.op, c.ph, inv_odt,
-                                                            src, S, qref, (const float*)L.Dinv, L.rs, L.cs);
+#define PMG_FUSED(WT, D)                                                                                       \
+  fused_sweep_kernel<P, WT, D><<<blocks, threads, 0, s>>>(c.E, qin, qout, L.met, L.face, nbr, L.op, c.ph, c.phw, \
+                                                          inv_odt, src, S, qref, (const WT*)L.Dinv, L.rs, L.cs)
+  const bool dwf = flux_dw(c, L);
+  if (prec == PMG_PREC_FP64) {
+    if (dwf) PMG_FUSED(double, true);
+    else PMG_FUSED(double, false);
+  } else {
+    if (dwf) PMG_FUSED(float, true);
+    else PMG_FUSED(float, false);
+  }
+#undef PMG_FUSED
 }
 
 void launch_fused_sweep(const Ctx& c, const LevelDev& L, const double* qin, double* qout, double inv_odt,

@@ -80,11 +80,11 @@ __device__ __forceinline__ void grad_trace(const double* __restrict__ Gb, size_t
   }
 }
 
-template <int P, bool VISC>
+template <int P, bool VISC, bool DWF>
 __global__ void __launch_bounds__(256) face_flux_kernel(const int* __restrict__ faces, int n_faces, int E,
                                                         const double* __restrict__ q,
                                                         const double* __restrict__ face,
-                                                        double* __restrict__ Fcom, OpTab op, Phys ph,
+                                                        double* __restrict__ Fcom, OpTab op, Phys ph, PhysW phw,
                                                         const double* __restrict__ Gb,
                                                         const double* __restrict__ fJinv,
                                                         double* __restrict__ Qj) {
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const int* __restrict__ 
   qm[0] += ph.p_ref;   // absolute pressure for the averaged state and rho
   qp[0] += ph.p_ref;
   double out[4];
-  roe_flux_jump(qm, qp, dq, pgm, pgp, nx, ny, dS, ph, out);
+  face_roe<DWF>(qm, qp, dq, pgm, pgp, nx, ny, dS, ph, phw, out);
   const size_t fplane = (size_t)E * 4 * n1;
   const size_t iL = ((size_t)eL * 4 + fL) * n1 + k;
   const size_t iR = bnd ? iL : ((size_t)eR * 4 + fR) * n1 + kR;
@@ -429,16 +429,21 @@ void launch_face_flux(const Ctx& c, const LevelDev& L, const double* q, cudaStre
   int total = c.n_faces * L.n1;
   // one warp per CTA: FP64-bound threads, spread over every SM
   int threads = 32, blocks = (total + threads - 1) / threads;
-  const bool visc = c.ph.mu > 0.0;
+  const bool visc = c.ph.mu > 0.0, dwf = flux_dw(c, L);
   if (visc) launch_grad(c, L, q, s);
-#define PMG_FACE(PP)                                                                                       \
-  do {                                                                                                     \
-    if (visc)                                                                                              \
-      face_flux_kernel<PP, true><<<blocks, threads, 0, s>>>(c.d_faces, c.n_faces, c.E, q, L.face, L.Fcom, \
-                                                            L.op, c.ph, L.Gb, L.fJinv, L.Qj);             \
-    else                                                                                                   \
-      face_flux_kernel<PP, false><<<blocks, threads, 0, s>>>(c.d_faces, c.n_faces, c.E, q, L.face, L.Fcom, \
-                                                             L.op, c.ph, nullptr, nullptr, nullptr);       \
+#define PMG_FACE_V(PP, V, D)                                                                                 \
+  face_flux_kernel<PP, V, D><<<blocks, threads, 0, s>>>(c.d_faces, c.n_faces, c.E, q, L.face, L.Fcom, L.op, \
+                                                        c.ph, c.phw, V ? L.Gb : nullptr,                    \
+                                                        V ? L.fJinv : nullptr, V ? L.Qj : nullptr)
+#define PMG_FACE(PP)                                   \
+  do {                                                 \
+    if (visc) {                                        \
+      if (dwf) PMG_FACE_V(PP, true, true);             \
+      else PMG_FACE_V(PP, true, false);                \
+    } else {                                           \
+      if (dwf) PMG_FACE_V(PP, false, true);            \
+      else PMG_FACE_V(PP, false, false);               \
+    }                                                  \
   } while (0)
   switch (L.P) {
     case 0: PMG_FACE(0); break;
@@ -449,6 +454,7 @@ void launch_face_flux(const Ctx& c, const LevelDev& L, const double* q, cudaStre
     default: PMG_FACE(5); break;
   }
 #undef PMG_FACE
+#undef PMG_FACE_V
 }
 
 void launch_volume(const Ctx& c, const LevelDev& L, int level, const double* q, double* out, ResMode mode,

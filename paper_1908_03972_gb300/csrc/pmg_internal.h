@@ -6,7 +6,7 @@
 #include <vector>
 
 #include "../../include/pmgfr.h"
-#include "physics.cuh"
+#include "physics_dw.cuh"
 
 namespace pmg {
 
@@ -66,6 +66,7 @@ struct XferTab {
 };
 
 struct LevelDev {
+  int level = 0;               // index in the hierarchy (0: finest)
   int P = 0, n1 = 0, N = 0, n = 0;
   size_t tot = 0;              // 4 * E * N
   OpTab op;
@@ -119,6 +120,7 @@ struct Ctx {
   bool own_stream = false;
   int device = 0;
   Phys ph;
+  PhysW phw;                   // double-word copies of the gas constants
   MeshHost mesh;
   bool mesh_ready = false;
   int E = 0, n_faces = 0;
@@ -155,6 +157,12 @@ struct Ctx {
   double A[6][6], b[6], c[6];
   int stages = 4;
 };
+
+// Face-flux arithmetic of a level (pmg_config.flux_prec): double-word on the
+// coarse levels for PMG_FLUX_DW_COARSE, on every level for PMG_FLUX_DW.
+inline bool flux_dw(const Ctx& c, const LevelDev& L) {
+  return c.cfg.flux_prec == PMG_FLUX_DW || (c.cfg.flux_prec == PMG_FLUX_DW_COARSE && L.level > 0);
+}
 
 // ---------------------------------------------------------- kernel launchers
 void launch_face_flux(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s);

@@ -33,11 +33,13 @@ def _lib():
     pmgfr.load()
 
 
-def _pair(nodes, nbr, Ng, levels, smooth, prec=0, p_gauge=0.0, **kw):
-    """Oracle and GPU solver on the same mesh; the GPU may store gauge pressure."""
+def _pair(nodes, nbr, Ng, levels, smooth, prec=0, p_gauge=0.0, flux_prec=None, **kw):
+    """Oracle and GPU solver on the same mesh; the GPU may store gauge pressure
+    (its face-flux arithmetic is the binding's default unless flux_prec is given)."""
     from paper_1908_03972_gb300 import pmgfr
     orc = O.Oracle(nodes, nbr, Ng, levels, smooth, **kw)
-    gpu = pmgfr.Solver(nodes, nbr, levels, smooth, block_prec=prec, p_gauge=p_gauge, **kw)
+    gkw = dict(kw) if flux_prec is None else dict(kw, flux_prec=flux_prec)
+    gpu = pmgfr.Solver(nodes, nbr, levels, smooth, block_prec=prec, p_gauge=p_gauge, **gkw)
     return orc, gpu
 
 
@@ -385,3 +387,87 @@ def test_refresh_always_rule_and_parity():
         assert np.abs(qg[0] - qo[0]).max() / 2.0 <= 2e-6 and np.abs(qg[1:3] - qo[1:3]).max() <= 1e-7
     finally:
         gpu.close()
+
+
+@pytest.mark.parametrize("P", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("mesh,gauge", [("c1_straight_8x8", TINF), ("curved_4x4", 0.0), ("ragged_5x3", 0.0)])
+def test_residual_parity_all_flux_arithmetics(mesh, gauge, P):
+    """Every face-flux arithmetic meets the residual bound against the
+    oracle: binary64 and double-word on the finest level, and the default
+    (double-word on coarse levels) on level 1 of a two-level hierarchy.  The
+    double-word residuals stay within a tenth of that bound of the binary64
+    one (1e-11 of the same scale), and the default mode's finest level is the
+    binary64 residual bit for bit."""
+    from paper_1908_03972_gb300 import pmgfr
+    (nodes, nbr), Ng = _mesh(mesh)
+    if gauge and P < Ng:
+        pytest.skip("gauge storage needs P >= geometry order")
+    orc = O.Oracle(nodes, nbr, Ng, [P], [1])
+    q = W.isentropic_vortex(orc.coords(), center=(4.3, 5.6))
+    rng = np.random.default_rng(10 + P)
+    q = q * (1 + 1e-3 * rng.standard_normal(q.shape) * np.array([1e-3, 1, 1, 1e-5])[:, None, None])
+    R = {}
+    for name, flux, levels, lev in (("fp64", pmgfr.PMG_FLUX_FP64, [P], 0), ("dw", pmgfr.PMG_FLUX_DW, [P], 0),
+                                    ("coarse", pmgfr.PMG_FLUX_DW_COARSE, [P + 1, P], 1),
+                                    ("coarse_finest", pmgfr.PMG_FLUX_DW_COARSE, [P], 0)):
+        gpu = pmgfr.Solver(nodes, nbr, levels, [1] * len(levels), p_gauge=gauge, flux_prec=flux)
+        try:
+            R[name] = gpu.residual(q, level=lev)
+        finally:
+            gpu.close()
+    Ro = orc.residual(q)
+    for name in R:
+        assert _rel_per_var(R[name], Ro, orc) <= 1e-10, name
+    for name in ("dw", "coarse"):
+        assert _rel_per_var(R[name], R["fp64"], orc) <= 1e-11, name
+    assert np.array_equal(R["coarse_finest"], R["fp64"])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_stage_solve_parity_double_word_on_every_level(prec):
+    """PMG_FLUX_DW (double-word face fluxes on the finest level too) still
+    reaches the oracle's stage solution; its converged state solves the
+    double-word residual equations, whose rounding (~1e-12 of the residual
+    scale) sits far below the 1e-8 stopping drop."""
+    from paper_1908_03972_gb300 import pmgfr
+    nodes, nbr = W.periodic_box(4, 4, Ng=2, perturb=0.3)
+    orc, gpu = _pair(nodes, nbr, 2, [3, 2, 1, 0], [1, 2, 2, 3], prec=prec, flux_prec=pmgfr.PMG_FLUX_DW, tol=1e-8)
+    try:
+        q = _stage_setup(orc, gpu)
+        qo, it_o, _, _, st = orc.stage_solve(q)
+        assert st == 0
+        qg, it_g, drop_g = gpu.stage_solve(q)
+        assert drop_g <= 1e-8
+        if prec == 0:
+            assert abs(it_g - it_o) <= 2
+        dp = np.abs(qg[0] - qo[0]).max() / 2.0   # rho_inf |v_inf|^2
+        du = np.abs(qg[1:3] - qo[1:3]).max()
+        assert dp <= 1e-7 and du <= 1e-7, (dp, du)
+    finally:
+        gpu.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_vcycle_parity_fused_sweeps_binary64_flux(prec, monkeypatch):
+    """The fused coarse sweep with the binary64 face flux (the double-word
+    one is the default of the other V-cycle tests)."""
+    from paper_1908_03972_gb300 import pmgfr
+    monkeypatch.setenv("PMG_FUSE_MAX_P", "2")
+    nodes, nbr = W.periodic_box(4, 4, Ng=2, perturb=0.3)
+    orc, gpu = _pair(nodes, nbr, 2, [3, 2, 1, 0], [2, 3, 3, 5], prec=prec, flux_prec=pmgfr.PMG_FLUX_FP64)
+    try:
+        q = _stage_setup(orc, gpu)
+        qo = orc.vcycle(q, 0.7, refresh=True)
+        qg, _ = gpu.vcycle(q, 0.7, refresh=True)
+        dq = np.abs(qo - q).max(axis=(1, 2))
+        tol = 1e-8 if prec == 0 else 5e-3
+        assert (np.abs(qg - qo).max(axis=(1, 2)) / dq).max() <= tol
+    finally:
+        gpu.close()
+
+
+def test_flux_precision_config_checked():
+    from paper_1908_03972_gb300 import pmgfr
+    nodes, nbr = W.periodic_box(2, 2, Ng=1)
+    with pytest.raises(pmgfr.PmgError):
+        pmgfr.Solver(nodes, nbr, [1], [1], flux_prec=3)
