@@ -162,6 +162,11 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
     pmg_destroy(h);
     return fail(PMG_ENOMEM, "device allocation failed");
   }
+  // d_scal[1]: set by kernels whose bounded wait for a bulk copy gave up
+  if (cudaMemset(c.d_scal, 0, 4 * sizeof(double)) != cudaSuccess) {
+    pmg_destroy(h);
+    return fail(PMG_ECUDA, "device memset failed");
+  }
   *out = h;
   return PMG_OK;
 }
@@ -304,6 +309,7 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
   PMG_CK(cudaMemset(c.src, 0, tot0 * 8));
   c.n_partial = maxblocks;
   PMG_CK(prepare_kernels(c));
+  PMG_CK(prepare_residual_kernels(c));
   c.mesh_ready = true;
   return PMG_OK;
 }
@@ -515,8 +521,12 @@ static pmg_status launch_vcycle(Ctx& c, bool refresh) {
 }
 
 static pmg_status read_norm(Ctx& c, double* out) {
-  PMG_CK(cudaMemcpyAsync(c.h_scal, c.d_scal, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  PMG_CK(cudaMemcpyAsync(c.h_scal, c.d_scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   PMG_CK(cudaStreamSynchronize(c.stream));
+  if (c.h_scal[1] != 0.0) {
+    cudaMemsetAsync(c.d_scal + 1, 0, sizeof(double), c.stream);
+    return fail(PMG_ECUDA, "a kernel's wait for its bulk shared-memory copy timed out");
+  }
   *out = std::sqrt(c.h_scal[0]);
   if (c.prof.on) prof_harvest(c);
   return PMG_OK;

@@ -15,6 +15,13 @@
 //     relative to q^b or q^n);
 //  4. x = cs .* (D^-1 (rs .* F)) with the element's factored block, written to
 //     a second state buffer (Jacobi: every element reads the old state).
+//
+// Every global read that does not depend on an earlier phase is issued at
+// entry: the blocks and their scales as bulk asynchronous copies into shared
+// memory (waited for, with a bound, before phase 3), the neighbour's line
+// values, the face geometry and the reference state into registers.  On the
+// coarse levels one thread's latency is the kernel's time, and each of these
+// would otherwise be a separate L2 round trip.
 #include "pmg_internal.h"
 
 namespace pmg {
@@ -24,13 +31,25 @@ struct FusedEPB {   // elements per CTA; a thread per face point of each element
   static constexpr int value = P == 0 ? 8 : P == 1 ? 4 : P == 2 ? 2 : 1;
 };
 
+template <int P, class W>
+constexpr size_t fused_smem() {   // dynamic shared memory: blocks, row scales, column scales
+  constexpr size_t EPB = FusedEPB<P>::value, n = 4 * (P + 1) * (P + 1);
+  return EPB * n * n * sizeof(W) + 2 * EPB * n * sizeof(double);
+}
+
 template <int P, class W, bool DWF>
-__global__ void __launch_bounds__(64) fused_sweep_kernel(
+__global__ void __launch_bounds__(64, 1) fused_sweep_kernel(
     int E, const double* __restrict__ qin, double* __restrict__ qout, const double* __restrict__ met,
     const double* __restrict__ face, const int* __restrict__ nbr, OpTab op, Phys ph, PhysW phw, double inv_odt,
     const double* __restrict__ src, const double* __restrict__ S, const double* __restrict__ qref,
-    const W* __restrict__ Dinv, const double* __restrict__ rs, const double* __restrict__ cs) {
+    const W* __restrict__ Dinv, const double* __restrict__ rs, const double* __restrict__ cs,
+    double* __restrict__ werr) {
   constexpr int n1 = P + 1, N = n1 * n1, n = 4 * N, EPB = FusedEPB<P>::value, FP = 4 * n1;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ __align__(8) unsigned long long mbar;
+  W* sDinv = reinterpret_cast<W*>(dsm);
+  double* srs = reinterpret_cast<double*>(dsm + (size_t)EPB * n * n * sizeof(W));
+  double* scs = srs + EPB * n;
   __shared__ double sq[EPB][4][N];
   __shared__ double sFt[EPB][4][N];
   __shared__ double sGt[EPB][4][N];
@@ -38,6 +57,42 @@ __global__ void __launch_bounds__(64) fused_sweep_kernel(
   __shared__ W sr[EPB][n];
   __shared__ double sD[n1][n1], sgL[n1], sgR[n1], slm[n1], slp[n1];
   const size_t plane = (size_t)E * N;
+  if (threadIdx.x == 0) {
+    const int e0 = blockIdx.x * EPB, ne = min(EPB, E - e0);
+    const unsigned bD = (unsigned)((size_t)ne * n * n * sizeof(W)), bS = (unsigned)(ne * n * sizeof(double));
+    mbar_init(&mbar);
+    mbar_arrive_expect(&mbar, bD + 2 * bS);
+    bulk_g2s(sDinv, Dinv + (size_t)e0 * n * n, bD, &mbar);
+    bulk_g2s(srs, rs + (size_t)e0 * n, bS, &mbar);
+    bulk_g2s(scs, cs + (size_t)e0 * n, bS, &mbar);
+  }
+  // thread (le, t): face point t = f n1 + k of element e; phase 1 and 3 point t < N
+  const int le0 = threadIdx.x / FP, t0 = threadIdx.x - le0 * FP;
+  const int e_0 = blockIdx.x * EPB + le0;
+  const bool act = le0 < EPB && e_0 < E;
+  double nq[4][n1], gx = 0.0, gy = 0.0, gS = 0.0, qo[4] = {0.0, 0.0, 0.0, 0.0};
+  int fn = 0;   // neighbour's face
+  if (act) {
+    const int f = t0 / n1, k = t0 - f * n1;
+    const int en = __ldg(nbr + (e_0 * 4 + f) * 3 + 0);
+    fn = __ldg(nbr + (e_0 * 4 + f) * 3 + 1);
+    const int kn = __ldg(nbr + (e_0 * 4 + f) * 3 + 2) ? P - k : k;
+    const bool etan = (fn == 0 || fn == 2);
+    const double* base = qin + (size_t)en * N + (etan ? kn : kn * n1);
+    const int stride = etan ? n1 : 1;
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+      for (int m = 0; m < n1; ++m) nq[v][m] = __ldg(base + v * plane + m * stride);
+    const double* g = face + (((size_t)e_0 * 4 + f) * n1 + k) * 3;
+    gx = __ldg(g);
+    gy = __ldg(g + 1);
+    gS = __ldg(g + 2);
+    if (qref && t0 < N) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) qo[v] = __ldg(qref + v * plane + (size_t)e_0 * N + t0);
+    }
+  }
   if (threadIdx.x < n1 * n1) sD[threadIdx.x / n1][threadIdx.x % n1] = op.D[threadIdx.x / n1][threadIdx.x % n1];
   if (threadIdx.x < n1) {
     sgL[threadIdx.x] = op.gL[threadIdx.x];
@@ -83,18 +138,13 @@ __global__ void __launch_bounds__(64) fused_sweep_kernel(
         for (int m = 0; m < n1; ++m) s = fma(plus ? slp[m] : slm[m], sq[le][v][eta ? m * n1 + k : k * n1 + m] - ref[v], s);
         sm[v] = s;
       }
-      const int en = __ldg(nbr + (e * 4 + f) * 3 + 0), fn = __ldg(nbr + (e * 4 + f) * 3 + 1);
-      const int rev = __ldg(nbr + (e * 4 + f) * 3 + 2);
-      const int kn = rev ? P - k : k;
       {
-        const bool pn = (fn == 1 || fn == 2), etan = (fn == 0 || fn == 2);
-        const double* base = qin + (size_t)en * N + (etan ? kn : kn * n1);
-        const int stride = etan ? n1 : 1;
+        const bool pn = (fn == 1 || fn == 2);
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           double s = 0.0;
 #pragma unroll
-          for (int m = 0; m < n1; ++m) s = fma(pn ? slp[m] : slm[m], __ldg(base + v * plane + m * stride) - ref[v], s);
+          for (int m = 0; m < n1; ++m) s = fma(pn ? slp[m] : slm[m], nq[v][m] - ref[v], s);
           sp[v] = s;
         }
       }
@@ -104,9 +154,8 @@ __global__ void __launch_bounds__(64) fused_sweep_kernel(
       const double pgm = qm[0], pgp = qp[0];
       qm[0] += ph.p_ref;
       qp[0] += ph.p_ref;
-      const double* g = face + (((size_t)e * 4 + f) * n1 + k) * 3;
       double out[4];
-      face_roe<DWF>(qm, qp, dq, pgm, pgp, __ldg(g), __ldg(g + 1), __ldg(g + 2), ph, phw, out);
+      face_roe<DWF>(qm, qp, dq, pgm, pgp, gx, gy, gS, ph, phw, out);
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         double loc = 0.0;
@@ -118,6 +167,8 @@ __global__ void __launch_bounds__(64) fused_sweep_kernel(
     }
   }
   __syncthreads();
+  const bool ok = mbar_wait0(&mbar);
+  if (!ok) *werr = 1.0;
   // phase 3: residual and level-system epilogue, thread (le, pt)
   {
     const int le = threadIdx.x / FP, t = threadIdx.x - le * FP;
@@ -128,8 +179,6 @@ __global__ void __launch_bounds__(64) fused_sweep_kernel(
       double qq[4] = {sq[le][0][t], sq[le][1][t], sq[le][2][t], sq[le][3][t]};
       double qc[4];
       if (qref) {
-        double qo[4] = {__ldg(qref + gi), __ldg(qref + plane + gi), __ldg(qref + 2 * plane + gi),
-                        __ldg(qref + 3 * plane + gi)};
         double rho = (qq[0] + ph.p_ref) / qq[3], rhoo = (qo[0] + ph.p_ref) / qo[3];
         qc[0] = rho - rhoo;
         qc[1] = rho * qq[1] - rhoo * qo[1];
@@ -159,7 +208,7 @@ __global__ void __launch_bounds__(64) fused_sweep_kernel(
         if (src) F += src[o];
         if (S) F -= S[o];
         int row = v * N + t;
-        sr[le][row] = scaled_in<W>(F, rs[(size_t)e * n + row]);
+        sr[le][row] = scaled_in<W>(F, ok ? srs[le * n + row] : rs[(size_t)e * n + row]);
       }
     }
   }
@@ -170,18 +219,18 @@ __global__ void __launch_bounds__(64) fused_sweep_kernel(
     const int e = blockIdx.x * EPB + le;
     if (le < EPB && e < E && t < N) {
       W acc[4] = {0, 0, 0, 0};
-      const W* Dm = Dinv + (size_t)e * n * n + 4 * t;
+      const W* Dm = ok ? sDinv + (size_t)le * n * n + 4 * t : Dinv + (size_t)e * n * n + 4 * t;
 #pragma unroll 4
       for (int kk = 0; kk < n; ++kk) {
         W rk = sr[le][kk];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) acc[m] = fma(__ldg(Dm + (size_t)kk * n + m), rk, acc[m]);
+        for (int m = 0; m < 4; ++m) acc[m] = fma(Dm[(size_t)kk * n + m], rk, acc[m]);
       }
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         int row = 4 * t + m;
         int v = row / N, pt = row - v * N;
-        double xv = scaled_out<W>(acc[m], cs[(size_t)e * n + row]);
+        double xv = scaled_out<W>(acc[m], ok ? scs[le * n + row] : cs[(size_t)e * n + row]);
         size_t o = v * plane + (size_t)e * N + pt;
         qout[o] = sq[le][v][pt] + xv;
       }
@@ -196,9 +245,10 @@ static void fused_launch(const Ctx& c, const LevelDev& L, const double* qin, dou
   int threads = (EPB * FP + 31) / 32 * 32;
   int blocks = (c.E + EPB - 1) / EPB;
   const int* nbr = c.d_faces + 5 * c.n_faces;
-#define PMG_FUSED(WT, D)                                                                                       \
-  fused_sweep_kernel<P, WT, D><<<blocks, threads, 0, s>>>(c.E, qin, qout, L.met, L.face, nbr, L.op, c.ph, c.phw, \
-                                                          inv_odt, src, S, qref, (const WT*)L.Dinv, L.rs, L.cs)
+#define PMG_FUSED(WT, D)                                                                                    \
+  fused_sweep_kernel<P, WT, D><<<blocks, threads, fused_smem<P, WT>(), s>>>(                                 \
+      c.E, qin, qout, L.met, L.face, nbr, L.op, c.ph, c.phw, inv_odt, src, S, qref, (const WT*)L.Dinv, L.rs, \
+      L.cs, c.d_scal + 1)
   const bool dwf = flux_dw(c, L);
   if (prec == PMG_PREC_FP64) {
     if (dwf) PMG_FUSED(double, true);

@@ -183,8 +183,42 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const int* __restrict__ 
 // place (eq. smoothing_element_jacobi).  That is safe within one launch: the
 // face fluxes were formed from the old state by the preceding face launch,
 // and a CTA reads and writes only its own elements' states.
+//
+// With APPLY the CTA's common face fluxes, block scales and (where they fit,
+// VolPrefetch::blocks) block inverses are copied to shared memory by bulk
+// asynchronous copies issued at entry, and the reference and forcing states
+// are loaded into registers there too: the latency of these reads then
+// overlaps the flux arithmetic instead of adding one L2 round trip per phase.
+template <int P, class W>
+struct VolPrefetch {
+  static constexpr int n1 = P + 1, N = n1 * n1, EPB = ElemsPerBlock<P>::value, n = 4 * N;
+  static constexpr bool blocks = (size_t)EPB * n * n * sizeof(W) <= 40 * 1024;
+  static constexpr size_t dinv_bytes = blocks ? (size_t)EPB * n * n * sizeof(W) : 0;
+  static constexpr size_t scale_bytes = (size_t)EPB * n * sizeof(double);   // rs, then cs
+  static constexpr size_t flux_bytes = (size_t)EPB * 4 * n1 * sizeof(double);   // per equation
+  static constexpr size_t smem = dinv_bytes + 2 * scale_bytes + 4 * flux_bytes;
+};
+
+// Loads four consecutive block entries (16-byte aligned for float, 32 for double).
+__device__ __forceinline__ void ld4(const float* p, float a[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  a[0] = t.x; a[1] = t.y; a[2] = t.z; a[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double a[4]) {
+  const double2 t0 = reinterpret_cast<const double2*>(p)[0], t1 = reinterpret_cast<const double2*>(p)[1];
+  a[0] = t0.x; a[1] = t0.y; a[2] = t1.x; a[3] = t1.y;
+}
+__device__ __forceinline__ void ldg4(const float* p, float a[4]) {
+  const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  a[0] = t.x; a[1] = t.y; a[2] = t.z; a[3] = t.w;
+}
+__device__ __forceinline__ void ldg4(const double* p, double a[4]) {
+  const double2 t0 = __ldg(reinterpret_cast<const double2*>(p)), t1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  a[0] = t0.x; a[1] = t0.y; a[2] = t1.x; a[3] = t1.y;
+}
+
 template <int P, class W, bool APPLY, bool VISC>
-__global__ void __launch_bounds__(256) volume_kernel(int E, const double* q,
+__global__ void __launch_bounds__(256, 1) volume_kernel(int E, const double* q,
                                                      const double* __restrict__ met,
                                                      const double* __restrict__ Fcom, OpTab op, Phys ph,
                                                      double* __restrict__ out, int mode, double inv_odt,
@@ -195,8 +229,12 @@ __global__ void __launch_bounds__(256) volume_kernel(int E, const double* q,
                                                      double* __restrict__ partial, double* qw,
                                                      const W* __restrict__ Dinv, const double* __restrict__ rs,
                                                      const double* __restrict__ cs,
-                                                     const double* __restrict__ Qj) {
+                                                     const double* __restrict__ Qj,
+                                                     double* __restrict__ werr) {
   constexpr int n1 = P + 1, N = n1 * n1, EPB = ElemsPerBlock<P>::value, n = 4 * N;
+  using PF = VolPrefetch<P, W>;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  __shared__ __align__(8) unsigned long long mbar[2];   // 0: face fluxes, 1: blocks and scales
   __shared__ W sr[APPLY ? EPB : 1][APPLY ? n : 1];
   __shared__ double sV[VISC ? EPB : 1][3][VISC ? N : 1];   // (u, v, T) for the gradients
   __shared__ double sFt[EPB][4][N];
@@ -209,6 +247,38 @@ __global__ void __launch_bounds__(256) volume_kernel(int E, const double* q,
   const int e = blockIdx.x * EPB + le;
   const bool active = (le < EPB) && (e < E);
   const size_t plane = (size_t)E * N;
+  const size_t fplane = (size_t)E * 4 * n1;
+  W* sDinv = reinterpret_cast<W*>(dsm);
+  double* srs = reinterpret_cast<double*>(dsm + PF::dinv_bytes);
+  double* scs = srs + EPB * n;
+  double* sFc = scs + EPB * n;   // [v][local element][face][k]
+  if (APPLY && threadIdx.x == 0) {
+    const int e0 = blockIdx.x * EPB, ne = min(EPB, E - e0);
+    const unsigned bF = (unsigned)(ne * 4 * n1 * sizeof(double));
+    const unsigned bS = (unsigned)(ne * n * sizeof(double));
+    const unsigned bD = PF::blocks ? (unsigned)((size_t)ne * n * n * sizeof(W)) : 0u;
+    mbar_init(&mbar[0]);
+    mbar_init(&mbar[1]);
+    mbar_arrive_expect(&mbar[0], 4 * bF);
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+      bulk_g2s(sFc + v * EPB * 4 * n1, Fcom + v * fplane + (size_t)e0 * 4 * n1, bF, &mbar[0]);
+    mbar_arrive_expect(&mbar[1], 2 * bS + bD);
+    bulk_g2s(srs, rs + (size_t)e0 * n, bS, &mbar[1]);
+    bulk_g2s(scs, cs + (size_t)e0 * n, bS, &mbar[1]);
+    if (PF::blocks) bulk_g2s(sDinv, Dinv + (size_t)e0 * n * n, bD, &mbar[1]);
+  }
+  // reference and forcing states of the epilogue, loaded up front
+  double qo[4] = {0, 0, 0, 0}, srcv[4] = {0, 0, 0, 0}, Sv[4] = {0, 0, 0, 0};
+  if (APPLY && active) {
+    const size_t g0 = (size_t)e * N + pt;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      if (qn) qo[v] = __ldg(qn + v * plane + g0);
+      if (src) srcv[v] = __ldg(src + v * plane + g0);
+      if (S) Sv[v] = __ldg(S + v * plane + g0);
+    }
+  }
   if (threadIdx.x < n1 * n1) sD[threadIdx.x / n1][threadIdx.x % n1] = op.D[threadIdx.x / n1][threadIdx.x % n1];
   if (threadIdx.x < n1) {
     sgL[threadIdx.x] = op.gL[threadIdx.x];
@@ -240,7 +310,6 @@ __global__ void __launch_bounds__(256) volume_kernel(int E, const double* q,
       // corrected gradient: reference derivatives plus the DG correction of
       // the jumps q_com - q_own at the four faces' points on this point's lines
       const int i = pt % n1, j = pt / n1;
-      const size_t fplane = (size_t)E * 4 * n1;
       const double* Qe = Qj + (size_t)e * 4 * n1;
       double gr[6], fv[4], gv[4];
 #pragma unroll
@@ -270,9 +339,10 @@ __global__ void __launch_bounds__(256) volume_kernel(int E, const double* q,
     }
   }
   __syncthreads();
+  const bool okF = APPLY ? mbar_wait0(&mbar[0]) : true;
+  if (!okF) *werr = 1.0;
   if (active) {
     // face jumps: common (reference-direction) minus extrapolated flux polynomial
-    const size_t fplane = (size_t)E * 4 * n1;
     for (int it = pt; it < 16 * n1; it += N) {
       int f = it / (4 * n1), r = it - f * 4 * n1, v = r / n1, k = r - v * n1;
       const bool xi = (f == 1 || f == 3);
@@ -283,11 +353,14 @@ __global__ void __launch_bounds__(256) volume_kernel(int E, const double* q,
         double fv = xi ? sFt[le][v][k * n1 + m] : sGt[le][v][m * n1 + k];
         loc = fma(plus ? slp[m] : slm[m], fv, loc);
       }
-      double com = __ldg(Fcom + v * fplane + ((size_t)e * 4 + f) * n1 + k);
+      double com = (APPLY && okF) ? sFc[((v * EPB + le) * 4 + f) * n1 + k]
+                                  : __ldg(Fcom + v * fplane + ((size_t)e * 4 + f) * n1 + k);
       sJ[le][f][v][k] = (plus ? com : -com) - loc;
     }
   }
   __syncthreads();
+  const bool okS = APPLY ? mbar_wait0(&mbar[1]) : true;
+  if (!okS) *werr = 1.0;
   double ssq = 0.0;
   if (active) {
     const int i = pt % n1, j = pt / n1;
@@ -297,7 +370,10 @@ __global__ void __launch_bounds__(256) volume_kernel(int E, const double* q,
       // rho E = p/(gamma-1) + rho|v|^2/2 and the gauge pressures, so that no
       // p ~ rho E ~ 1/Ma^2 is rounded (q_ref = q^n on the finest level, q^b on
       // coarser levels, where the constant q_c(q^b)/(omega dt) cancels in F - S)
-      double qo[4] = {__ldg(qn + gi), __ldg(qn + plane + gi), __ldg(qn + 2 * plane + gi), __ldg(qn + 3 * plane + gi)};
+      if (!APPLY) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) qo[v] = __ldg(qn + v * plane + gi);
+      }
       double rho = rho_pt, rhoo = (qo[0] + ph.p_ref) * s_rcp(qo[3]);
       qc[0] = rho - rhoo;
       qc[1] = rho * qq[1] - rhoo * qo[1];
@@ -334,11 +410,12 @@ __global__ void __launch_bounds__(256) volume_kernel(int E, const double* q,
         ssq = fma(pd, pd, ssq);
       } else {
         double F = fma(-qc[v], inv_odt, R);
-        if (src) F += src[o];
-        if (mode == RES_SYSTEM && S) F -= S[o];
+        if (src) F += APPLY ? srcv[v] : src[o];
+        if (mode == RES_SYSTEM && S) F -= APPLY ? Sv[v] : S[o];
         if (APPLY) {
           const int row = v * N + pt;
-          sr[APPLY ? le : 0][APPLY ? row : 0] = scaled_in<W>(F, rs[(size_t)e * n + row]);
+          const double rsc = okS ? srs[le * n + row] : rs[(size_t)e * n + row];
+          sr[APPLY ? le : 0][APPLY ? row : 0] = scaled_in<W>(F, rsc);
         } else {
           out[o] = F;
         }
@@ -353,20 +430,36 @@ __global__ void __launch_bounds__(256) volume_kernel(int E, const double* q,
     __syncthreads();
     if (active) {
       // thread (le, pt) owns rows 4 pt .. 4 pt + 3 of its element's block
+      // (column-major: the four rows of a column are one 16/32-byte vector)
       W acc[4] = {0, 0, 0, 0};
-      const W* Dm = Dinv + (size_t)e * n * n + 4 * pt;
+      if (PF::blocks && okS) {
+        const W* Dm = sDinv + (size_t)le * n * n + 4 * pt;
 #pragma unroll 8
-      for (int kk = 0; kk < n; ++kk) {
-        W rk = sr[APPLY ? le : 0][APPLY ? kk : 0];
+        for (int kk = 0; kk < n; ++kk) {
+          const W rk = sr[APPLY ? le : 0][APPLY ? kk : 0];
+          W d[4];
+          ld4(Dm + (size_t)kk * n, d);
 #pragma unroll
-        for (int m = 0; m < 4; ++m) acc[m] = fma(__ldg(Dm + (size_t)kk * n + m), rk, acc[m]);
+          for (int m = 0; m < 4; ++m) acc[m] = fma(d[m], rk, acc[m]);
+        }
+      } else {
+        const W* Dm = Dinv + (size_t)e * n * n + 4 * pt;
+#pragma unroll 8
+        for (int kk = 0; kk < n; ++kk) {
+          const W rk = sr[APPLY ? le : 0][APPLY ? kk : 0];
+          W d[4];
+          ldg4(Dm + (size_t)kk * n, d);
+#pragma unroll
+          for (int m = 0; m < 4; ++m) acc[m] = fma(d[m], rk, acc[m]);
+        }
       }
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const int row = 4 * pt + m;
         const int v = row / N, p2 = row - v * N;
         const size_t o = v * plane + (size_t)e * N + p2;
-        qw[o] = q[o] + scaled_out<W>(acc[m], cs[(size_t)e * n + row]);
+        const double csc = okS ? scs[le * n + row] : cs[(size_t)e * n + row];
+        qw[o] = q[o] + scaled_out<W>(acc[m], csc);
       }
     }
   }
@@ -468,11 +561,11 @@ void launch_volume(const Ctx& c, const LevelDev& L, int level, const double* q, 
     if (c.ph.mu > 0.0)                                                                                       \
       volume_kernel<PP, double, false, true><<<blocks, threads, 0, s>>>(                                     \
           c.E, q, L.met, L.Fcom, L.op, c.ph, out, (int)mode, inv_odt, src, S, Sout, Pd, qn, partial, nullptr, \
-          nullptr, nullptr, nullptr, L.Qj);                                                                  \
+          nullptr, nullptr, nullptr, L.Qj, nullptr);                                                         \
     else                                                                                                     \
       volume_kernel<PP, double, false, false><<<blocks, threads, 0, s>>>(                                    \
           c.E, q, L.met, L.Fcom, L.op, c.ph, out, (int)mode, inv_odt, src, S, Sout, Pd, qn, partial, nullptr, \
-          nullptr, nullptr, nullptr, nullptr);                                                               \
+          nullptr, nullptr, nullptr, nullptr, nullptr);                                                      \
   } while (0)
   switch (L.P) {
     case 0: PMG_VOL(0); break;
@@ -491,18 +584,20 @@ static void volume_apply_dispatch(const Ctx& c, const LevelDev& L, double* q, do
   int threads = residual_threads_per_block(L.P);
   int blocks = residual_blocks_for(L.P, c.E);
   const W* Dinv = (const W*)L.Dinv;
-#define PMG_VA(PP)                                                                                          \
-  do {                                                                                                        \
-    if (c.ph.mu > 0.0)                                                                                        \
-      volume_kernel<PP, W, true, true><<<blocks, threads, 0, s>>>(c.E, q, L.met, L.Fcom, L.op, c.ph, nullptr,  \
-                                                                  (int)RES_SYSTEM, inv_odt, src, S, nullptr,   \
-                                                                  nullptr, qn, nullptr, q, Dinv, L.rs, L.cs,   \
-                                                                  L.Qj);                                       \
-    else                                                                                                      \
-      volume_kernel<PP, W, true, false><<<blocks, threads, 0, s>>>(c.E, q, L.met, L.Fcom, L.op, c.ph, nullptr, \
-                                                                   (int)RES_SYSTEM, inv_odt, src, S, nullptr,  \
-                                                                   nullptr, qn, nullptr, q, Dinv, L.rs, L.cs,  \
-                                                                   nullptr);                                   \
+  double* werr = c.d_scal + 1;
+#define PMG_VA(PP)                                                                                             \
+  do {                                                                                                         \
+    const size_t sm = VolPrefetch<PP, W>::smem;                                                                \
+    if (c.ph.mu > 0.0)                                                                                         \
+      volume_kernel<PP, W, true, true><<<blocks, threads, sm, s>>>(c.E, q, L.met, L.Fcom, L.op, c.ph, nullptr,  \
+                                                                   (int)RES_SYSTEM, inv_odt, src, S, nullptr,   \
+                                                                   nullptr, qn, nullptr, q, Dinv, L.rs, L.cs,   \
+                                                                   L.Qj, werr);                                 \
+    else                                                                                                       \
+      volume_kernel<PP, W, true, false><<<blocks, threads, sm, s>>>(c.E, q, L.met, L.Fcom, L.op, c.ph, nullptr, \
+                                                                    (int)RES_SYSTEM, inv_odt, src, S, nullptr,  \
+                                                                    nullptr, qn, nullptr, q, Dinv, L.rs, L.cs,  \
+                                                                    nullptr, werr);                             \
   } while (0)
   switch (L.P) {
     case 0: PMG_VA(0); break;
@@ -521,6 +616,36 @@ void launch_volume_apply(const Ctx& c, const LevelDev& L, double* q, double inv_
                          const double* S, const double* qn, int prec, cudaStream_t s) {
   if (prec == PMG_PREC_FP64) volume_apply_dispatch<double>(c, L, q, inv_odt, src, S, qn, s);
   else volume_apply_dispatch<float>(c, L, q, inv_odt, src, S, qn, s);
+}
+
+// Dynamic shared memory limits of the fused residual-and-update kernels of
+// every level (their prefetch buffers can exceed the 48 KB default).
+template <class W>
+static cudaError_t prepare_apply(int P, bool visc) {
+#define PMG_PREP(PP)                                                                                          \
+  return visc ? cudaFuncSetAttribute(volume_kernel<PP, W, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                     (int)VolPrefetch<PP, W>::smem)                                            \
+              : cudaFuncSetAttribute(volume_kernel<PP, W, true, false>,                                        \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)VolPrefetch<PP, W>::smem)
+  switch (P) {
+    case 0: PMG_PREP(0);
+    case 1: PMG_PREP(1);
+    case 2: PMG_PREP(2);
+    case 3: PMG_PREP(3);
+    case 4: PMG_PREP(4);
+    default: PMG_PREP(5);
+  }
+#undef PMG_PREP
+}
+
+cudaError_t prepare_residual_kernels(const Ctx& c) {
+  for (int l = 0; l < c.cfg.n_levels; ++l) {
+    const bool visc = c.ph.mu > 0.0;
+    cudaError_t e = c.cfg.block_prec == PMG_PREC_FP64 ? prepare_apply<double>(c.lev[l].P, visc)
+                                                      : prepare_apply<float>(c.lev[l].P, visc);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 void launch_norm_final(const double* partial, int n, double* out, cudaStream_t s) {

@@ -7,6 +7,7 @@
 
 #include "../../include/pmgfr.h"
 #include "physics_dw.cuh"
+#include "tma.cuh"
 
 namespace pmg {
 
@@ -166,6 +167,7 @@ inline bool flux_dw(const Ctx& c, const LevelDev& L) {
 
 // ---------------------------------------------------------- kernel launchers
 void launch_face_flux(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s);
+cudaError_t prepare_residual_kernels(const Ctx& c);   // once per mesh upload
 void launch_volume(const Ctx& c, const LevelDev& L, int level, const double* q, double* out, ResMode mode,
                    double inv_odt, const double* src, const double* S, double* Sout, const double* Pd,
                    double* partial, cudaStream_t s, const double* qn = nullptr);

@@ -1,0 +1,57 @@
+// tma.cuh -- bulk asynchronous copies from global to shared memory
+// (cp.async.bulk: the TMA engine's untiled form) completed on an mbarrier,
+// and a bounded wait for them.
+//
+// A kernel issues its copies from one thread at entry and waits for them
+// where it first reads the data, so that the copies overlap the arithmetic
+// before that point.  Sizes and both addresses must be multiples of 16 bytes.
+// The wait gives up after kWaitTries polls (each poll may itself suspend the
+// thread for a while, so the total stays within about a second); the caller
+// then records the failure in an error slot the host reads and uses the
+// global-memory copy of the data instead, so no thread hangs.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace pmg {
+
+#ifdef __CUDACC__
+constexpr int kWaitTries = 1 << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// One-arrival barrier; the initialisation is made visible to the async proxy.
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// The single arrival, announcing the bytes the copies will deliver.
+__device__ __forceinline__ void mbar_arrive_expect(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Wait for phase 0 of the barrier; false after kWaitTries unsuccessful polls.
+__device__ __forceinline__ bool mbar_wait0(unsigned long long* bar) {
+  const unsigned a = smem_u32(bar);
+  for (int i = 0; i < kWaitTries; ++i) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+#endif
+
+}  // namespace pmg
