@@ -259,6 +259,14 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
     // BR2 lifting factor: penalty eta_f = 4 (faces of a quadrilateral) times
     // the DG correction's g_R'(1) = (P+1)^2 / 2
     L.op.pen = 4.0 * 0.5 * L.n1 * L.n1;
+    memset(&L.opw, 0, sizeof(L.opw));
+    for (int i = 0; i < L.n1; ++i) {
+      for (int k = 0; k < L.n1; ++k) L.opw.D[i][k] = dw_const(L.op.D[i][k]);
+      L.opw.lm[i] = dw_const(L.op.lm[i]);
+      L.opw.lp[i] = dw_const(L.op.lp[i]);
+      L.opw.gL[i] = dw_const(L.op.gL[i]);
+      L.opw.gR[i] = dw_const(L.op.gR[i]);
+    }
     size_t nn2 = (size_t)c.E * L.n * L.n;
     if (dalloc(&L.q, L.tot) || dalloc(&L.qb, L.tot) || dalloc(&L.S, L.tot) || dalloc(&L.F, L.tot) ||
         dalloc(&L.Pd, L.tot) || dalloc(&L.met, geo[l].met.size()) || dalloc(&L.face, geo[l].face.size()) ||
@@ -310,6 +318,7 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
   c.n_partial = maxblocks;
   PMG_CK(prepare_kernels(c));
   PMG_CK(prepare_residual_kernels(c));
+  PMG_CK(prepare_volume_dw_kernels(c));
   c.mesh_ready = true;
   return PMG_OK;
 }
@@ -441,8 +450,11 @@ static int sweeps(Ctx& c, int l, int n, bool F_valid, bool final_residual, bool 
     }
     {
       ProfScope ps(c, K_VOLUME, l);
-      launch_volume_apply(c, L, L.q, 1.0 / c.omega_dt, l == 0 ? c.src : nullptr, l > 0 ? L.S : nullptr, qref,
-                          c.cfg.block_prec, c.stream);
+      if (volume_dw_applies(c, L))
+        launch_volume_apply_dw(c, L, L.q, 1.0 / c.omega_dt, L.S, L.qb, c.cfg.block_prec, c.stream);
+      else
+        launch_volume_apply(c, L, L.q, 1.0 / c.omega_dt, l == 0 ? c.src : nullptr, l > 0 ? L.S : nullptr, qref,
+                            c.cfg.block_prec, c.stream);
     }
   }
   if (final_residual) system_residual(c, l, final_norm);

@@ -25,18 +25,9 @@
 // elements.  The volume launch forms the corrected gradient at each solution
 // point (derivative plus DG correction of those jumps) and subtracts the
 // viscous flux from the inviscid one before the divergence.
-#include "pmg_internal.h"
+#include "sweep_common.cuh"
 
 namespace pmg {
-
-// Elements per CTA of the volume kernel.  The kernel is bound by FP64 issue
-// (2 DFMA per clock per SM), so small CTAs of one or two warps spread even the
-// coarse levels (4096 elements) over all 152 SMs.
-template <int P>
-struct ElemsPerBlock {
-  static constexpr int N = (P + 1) * (P + 1);
-  static constexpr int value = P == 0 ? 32 : P == 1 ? 8 : P == 2 ? 7 : P == 3 ? 4 : P == 4 ? 2 : 1;
-};
 
 // Trace of the solution polynomial along the line through face point k of
 // face f, extrapolated from the line's solution points minus a reference
@@ -182,41 +173,8 @@ __global__ void __launch_bounds__(256) face_flux_kernel(const int* __restrict__ 
 // also performs the element-Jacobi update q += cs .* (D^-1 (rs .* F)) in
 // place (eq. smoothing_element_jacobi).  That is safe within one launch: the
 // face fluxes were formed from the old state by the preceding face launch,
-// and a CTA reads and writes only its own elements' states.
-//
-// With APPLY the CTA's common face fluxes, block scales and (where they fit,
-// VolPrefetch::blocks) block inverses are copied to shared memory by bulk
-// asynchronous copies issued at entry, and the reference and forcing states
-// are loaded into registers there too: the latency of these reads then
-// overlaps the flux arithmetic instead of adding one L2 round trip per phase.
-template <int P, class W>
-struct VolPrefetch {
-  static constexpr int n1 = P + 1, N = n1 * n1, EPB = ElemsPerBlock<P>::value, n = 4 * N;
-  static constexpr bool blocks = (size_t)EPB * n * n * sizeof(W) <= 40 * 1024;
-  static constexpr size_t dinv_bytes = blocks ? (size_t)EPB * n * n * sizeof(W) : 0;
-  static constexpr size_t scale_bytes = (size_t)EPB * n * sizeof(double);   // rs, then cs
-  static constexpr size_t flux_bytes = (size_t)EPB * 4 * n1 * sizeof(double);   // per equation
-  static constexpr size_t smem = dinv_bytes + 2 * scale_bytes + 4 * flux_bytes;
-};
-
-// Loads four consecutive block entries (16-byte aligned for float, 32 for double).
-__device__ __forceinline__ void ld4(const float* p, float a[4]) {
-  const float4 t = *reinterpret_cast<const float4*>(p);
-  a[0] = t.x; a[1] = t.y; a[2] = t.z; a[3] = t.w;
-}
-__device__ __forceinline__ void ld4(const double* p, double a[4]) {
-  const double2 t0 = reinterpret_cast<const double2*>(p)[0], t1 = reinterpret_cast<const double2*>(p)[1];
-  a[0] = t0.x; a[1] = t0.y; a[2] = t1.x; a[3] = t1.y;
-}
-__device__ __forceinline__ void ldg4(const float* p, float a[4]) {
-  const float4 t = __ldg(reinterpret_cast<const float4*>(p));
-  a[0] = t.x; a[1] = t.y; a[2] = t.z; a[3] = t.w;
-}
-__device__ __forceinline__ void ldg4(const double* p, double a[4]) {
-  const double2 t0 = __ldg(reinterpret_cast<const double2*>(p)), t1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
-  a[0] = t0.x; a[1] = t0.y; a[2] = t1.x; a[3] = t1.y;
-}
-
+// and a CTA reads and writes only its own elements' states.  The update's
+// inputs are prefetched at entry (VolPrefetch, sweep_common.cuh).
 template <int P, class W, bool APPLY, bool VISC>
 __global__ void __launch_bounds__(256, 1) volume_kernel(int E, const double* q,
                                                      const double* __restrict__ met,

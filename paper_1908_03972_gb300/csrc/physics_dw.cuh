@@ -16,6 +16,14 @@ namespace pmg {
 // Double-word copies of the gas constants (filled on the host).
 struct PhysW {
   dw gamma, Cp, gm1, inv_gamma, inv_Cp, eps_min2;
+  dw p_ref;     // gauge reference pressure of the device states
+  dw inv_gm1;   // 1 / (gamma - 1)
+};
+
+// Double-word copies of a level's 1D operators (see OpTab).
+struct OpTabW {
+  dw D[6][6];
+  dw lm[6], lp[6], gL[6], gR[6];
 };
 
 inline PhysW make_physw(const Phys& ph) {
@@ -26,6 +34,8 @@ inline PhysW make_physw(const Phys& ph) {
   k.inv_gamma = dw_const(ph.inv_gamma);
   k.inv_Cp = dw_const(1.0 / ph.Cp);
   k.eps_min2 = dw_const(ph.eps_min * ph.eps_min);
+  k.p_ref = dw_const(ph.p_ref);
+  k.inv_gm1 = dw_const(ph.inv_gm1);
   return k;
 }
 

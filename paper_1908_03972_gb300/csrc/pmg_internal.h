@@ -71,6 +71,7 @@ struct LevelDev {
   int P = 0, n1 = 0, N = 0, n = 0;
   size_t tot = 0;              // 4 * E * N
   OpTab op;
+  OpTabW opw;                  // the same operators in double-word
   double* q = nullptr;         // state
   double* q2 = nullptr;        // second state buffer of fused (ping-pong) sweeps
   bool fused = false;          // coarse level smoothed by the fused one-launch sweep
@@ -168,6 +169,12 @@ inline bool flux_dw(const Ctx& c, const LevelDev& L) {
 // ---------------------------------------------------------- kernel launchers
 void launch_face_flux(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s);
 cudaError_t prepare_residual_kernels(const Ctx& c);   // once per mesh upload
+// Coarse-level residual-and-update sweep in double-word arithmetic
+// (k_volume_dw.cu): used where volume_dw_applies().
+bool volume_dw_applies(const Ctx& c, const LevelDev& L);
+void launch_volume_apply_dw(const Ctx& c, const LevelDev& L, double* q, double inv_odt, const double* S,
+                            const double* qb, int prec, cudaStream_t s);
+cudaError_t prepare_volume_dw_kernels(const Ctx& c);
 void launch_volume(const Ctx& c, const LevelDev& L, int level, const double* q, double* out, ResMode mode,
                    double inv_odt, const double* src, const double* S, double* Sout, const double* Pd,
                    double* partial, cudaStream_t s, const double* qn = nullptr);
