@@ -272,7 +272,7 @@ def run_ours(args, wl, world, rank, local):
 
     def make(prec):
         # mixed: FP32 blocks and double-word coarse-level face fluxes; fp64: binary64 throughout
-        flux = pmgfr.PMG_FLUX_DW_COARSE if prec == pmgfr.PMG_PREC_FP32 else pmgfr.PMG_FLUX_FP64
+        flux = pmgfr.PMG_FLUX_DW_SMOOTH if prec == pmgfr.PMG_PREC_FP32 else pmgfr.PMG_FLUX_FP64
         return pmgfr.Solver(nodes, nbr, wl["levels"], wl["smooth"], stream=stream.cuda_stream, block_prec=prec,
                             flux_prec=flux, **kw)
 

@@ -50,18 +50,22 @@ typedef enum {
   PMG_PREC_FP32 = 1  /* blocks equilibrated, factored and applied in FP32 */
 } pmg_prec;
 
-/* Arithmetic of the common Roe flux (eq. invis_com) at the face points.
- * Double-word (float-float) arithmetic runs the same closed form on the FP32
- * pipes at ~2^-46 relative rounding; the face traces and jumps it takes and
- * the central pressure term stay binary64.  On the coarse levels the flux
- * only shapes the FAS corrections; the finest level's residual defines the
- * converged solution and the stopping norm. */
+/* Arithmetic of the residual.  Double-word (float-float) arithmetic runs the
+ * common Roe flux (eq. invis_com) on the FP32 pipes at ~2^-46 relative
+ * rounding, with the face traces, the jumps it takes and the central pressure
+ * term in binary64; with gauge storage (p_gauge != 0) and mu = 0 the
+ * residual-and-update of the element-Jacobi sweeps (the volume terms, the
+ * level-system epilogue) is double-word too.  The sweeps are the smoother
+ * and the coarse levels only shape the FAS corrections of Section 3; the
+ * finest level's residual defines the converged solution: the stopping
+ * norm, the defect restricted to the coarse levels and pmg_residual. */
 typedef enum {
-  PMG_FLUX_FP64 = 0,      /* binary64 on every level */
-  PMG_FLUX_DW_COARSE = 1, /* double-word on the coarse levels, binary64 on
-                             the finest: the converged state solves the
-                             binary64 residual equations */
-  PMG_FLUX_DW = 2         /* double-word on every level */
+  PMG_FLUX_FP64 = 0,      /* binary64 everywhere */
+  PMG_FLUX_DW_SMOOTH = 1, /* double-word in every sweep and in the coarse
+                             levels' residuals, binary64 in the finest
+                             level's residual: the converged state solves
+                             the binary64 residual equations */
+  PMG_FLUX_DW = 2         /* double-word in every residual */
 } pmg_flux_prec;
 
 /* Solver configuration (Sections 2.2-3, 4.1).
@@ -131,8 +135,8 @@ typedef struct {
                      one rebuild used dtau_max (the rule of Section 4.4);
                      1: every refresh_every iterations throughout the stage
                      (Section 4.1 states only the period) */
-  int flux_prec;  /* pmg_flux_prec of the residual's face fluxes (the
-                     element blocks are always differentiated in binary64) */
+  int flux_prec;  /* pmg_flux_prec (the element blocks are always
+                     differentiated in binary64) */
 } pmg_config;
 
 /* Boundary types, in the second slot of a boundary face's neighbour entry

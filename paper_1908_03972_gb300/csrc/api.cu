@@ -117,7 +117,7 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   }
   if (cfg->block_prec != PMG_PREC_FP64 && cfg->block_prec != PMG_PREC_FP32)
     return fail(PMG_EINVAL, "unknown block precision");
-  if (cfg->flux_prec != PMG_FLUX_FP64 && cfg->flux_prec != PMG_FLUX_DW_COARSE && cfg->flux_prec != PMG_FLUX_DW)
+  if (cfg->flux_prec != PMG_FLUX_FP64 && cfg->flux_prec != PMG_FLUX_DW_SMOOTH && cfg->flux_prec != PMG_FLUX_DW)
     return fail(PMG_EINVAL, "unknown flux precision");
   if (!(cfg->gamma > 1.0)) return fail(PMG_EINVAL, "gamma must exceed 1");
   if (cfg->esdirk_order != 0 && (cfg->esdirk_order < 2 || cfg->esdirk_order > 4))
@@ -446,12 +446,13 @@ static int sweeps(Ctx& c, int l, int n, bool F_valid, bool final_residual, bool 
   for (; s < n; ++s) {
     {
       ProfScope ps(c, K_FACE, l);
-      launch_face_flux(c, L, L.q, c.stream);
+      launch_face_flux(c, L, L.q, c.stream, true);
     }
     {
       ProfScope ps(c, K_VOLUME, l);
-      if (volume_dw_applies(c, L))
-        launch_volume_apply_dw(c, L, L.q, 1.0 / c.omega_dt, L.S, L.qb, c.cfg.block_prec, c.stream);
+      if (volume_dw_applies(c))
+        launch_volume_apply_dw(c, L, L.q, 1.0 / c.omega_dt, l == 0 ? c.src : nullptr, l > 0 ? L.S : nullptr, qref,
+                               c.cfg.block_prec, c.stream);
       else
         launch_volume_apply(c, L, L.q, 1.0 / c.omega_dt, l == 0 ? c.src : nullptr, l > 0 ? L.S : nullptr, qref,
                             c.cfg.block_prec, c.stream);

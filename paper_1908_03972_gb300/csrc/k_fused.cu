@@ -249,7 +249,7 @@ static void fused_launch(const Ctx& c, const LevelDev& L, const double* qin, dou
   fused_sweep_kernel<P, WT, D><<<blocks, threads, fused_smem<P, WT>(), s>>>(                                 \
       c.E, qin, qout, L.met, L.face, nbr, L.op, c.ph, c.phw, inv_odt, src, S, qref, (const WT*)L.Dinv, L.rs, \
       L.cs, c.d_scal + 1)
-  const bool dwf = flux_dw(c, L);
+  const bool dwf = flux_dw_sweep(c);
   if (prec == PMG_PREC_FP64) {
     if (dwf) PMG_FUSED(double, true);
     else PMG_FUSED(double, false);

@@ -476,11 +476,11 @@ static int elems_per_block(int P) {
 
 int residual_blocks_for(int P, int E) { int epb = elems_per_block(P); return (E + epb - 1) / epb; }
 
-void launch_face_flux(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s) {
+void launch_face_flux(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s, bool sweep) {
   int total = c.n_faces * L.n1;
   // one warp per CTA: FP64-bound threads, spread over every SM
   int threads = 32, blocks = (total + threads - 1) / threads;
-  const bool visc = c.ph.mu > 0.0, dwf = flux_dw(c, L);
+  const bool visc = c.ph.mu > 0.0, dwf = sweep ? flux_dw_sweep(c) : flux_dw(c, L);
   if (visc) launch_grad(c, L, q, s);
 #define PMG_FACE_V(PP, V, D)                                                                                 \
   face_flux_kernel<PP, V, D><<<blocks, threads, 0, s>>>(c.d_faces, c.n_faces, c.E, q, L.face, L.Fcom, L.op, \

@@ -1,19 +1,21 @@
-// k_volume_dw.cu -- the residual-and-update sweep of a coarse level
+// k_volume_dw.cu -- the residual-and-update of an element-Jacobi sweep
 // (volume_kernel with APPLY, k_residual.cu) in double-word arithmetic.
 //
-// On the coarse levels the update q += cs .* (D^-1 (rs .* F)) only has to
-// drive the FAS corrections of Section 3; the finest level's binary64
-// residual defines the converged state.  Forming F there on the FP32 pipes
-// (dword.cuh, ~2^-46 relative rounding) instead of in binary64 takes the
-// kernel's longest chain, ~130 FP64 instructions per thread at one FP64
-// warp-instruction per ~64 cycles per SM sub-partition, off the FP64 pipe.
+// The sweep q += cs .* (D^-1 (rs .* F)) is the smoother, and on the coarse
+// levels it only drives the FAS corrections of Section 3; the binary64
+// residual of the finest level (a separate evaluation) defines the converged
+// state.  Forming F on the FP32 pipes (dword.cuh, ~2^-46 relative rounding)
+// instead of in binary64 takes the kernel's longest chain, ~130 FP64
+// instructions per thread at one FP64 warp-instruction per ~64 cycles per SM
+// sub-partition, off the FP64 pipe.
 //
 // Same steps and CTA shape as the binary64 kernel: contravariant fluxes of
 // the element's points, the face jumps (common flux minus the extrapolated
 // flux polynomial), the divergence with the DG correction, the level-system
-// epilogue F = R - (q_c(q) - q_c(q^b)) / (omega dt) - S, then the block
-// update.  The states hold gauge pressure; with p_ref = 0 (absolute pressure,
-// p ~ 1/(gamma Ma^2) in the momentum flux) the binary64 kernel is used.
+// epilogue F = R - (q_c(q) - q_c(q_ref)) / (omega dt) + src - S (q_c(q)
+// itself without q_ref), then the block update.  The states hold gauge
+// pressure; with p_ref = 0 (absolute pressure, p ~ 1/(gamma Ma^2) in the
+// momentum flux) the binary64 kernel is used.
 #include "sweep_common.cuh"
 
 namespace pmg {
@@ -32,8 +34,9 @@ __device__ __forceinline__ double scaled_in_dw<double>(dw F, double s) {
 template <int P, class W>
 __global__ void __launch_bounds__(256, 1) volume_apply_dw_kernel(
     int E, double* q, const double* __restrict__ met, const double* __restrict__ Fcom, OpTabW opw, PhysW k,
-    double inv_odt, const double* __restrict__ S, const double* __restrict__ qb, const W* __restrict__ Dinv,
-    const double* __restrict__ rs, const double* __restrict__ cs, double* __restrict__ werr) {
+    double inv_odt, const double* __restrict__ src, const double* __restrict__ S, const double* __restrict__ qref,
+    const W* __restrict__ Dinv, const double* __restrict__ rs, const double* __restrict__ cs,
+    double* __restrict__ werr) {
   constexpr int n1 = P + 1, N = n1 * n1, EPB = ElemsPerBlock<P>::value, n = 4 * N;
   using PF = VolPrefetch<P, W>;
   extern __shared__ __align__(128) unsigned char dsm[];
@@ -70,13 +73,15 @@ __global__ void __launch_bounds__(256, 1) volume_apply_dw_kernel(
     if (PF::blocks) bulk_g2s(sDinv, Dinv + (size_t)e0 * n * n, bD, &mbar[1]);
   }
   const size_t gi = (size_t)e * N + pt;
+  // Sv: src - S of the epilogue
   double qq[4] = {0, 0, 0, 0}, qo[4] = {0, 0, 0, 0}, Sv[4] = {0, 0, 0, 0}, mt[5] = {0, 0, 0, 0, 0};
   if (active) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       qq[v] = q[v * plane + gi];
-      qo[v] = __ldg(qb + v * plane + gi);
-      Sv[v] = __ldg(S + v * plane + gi);
+      if (qref) qo[v] = __ldg(qref + v * plane + gi);
+      if (src) Sv[v] = __ldg(src + v * plane + gi);
+      if (S) Sv[v] -= __ldg(S + v * plane + gi);
     }
 #pragma unroll
     for (int c = 0; c < 5; ++c) mt[c] = __ldg(met + c * plane + gi);
@@ -135,18 +140,25 @@ __global__ void __launch_bounds__(256, 1) volume_apply_dw_kernel(
   if (!okS) *werr = 1.0;
   if (active) {
     const int i = pt % n1, j = pt / n1;
-    // q_c(q) - q_c(q^b), energy through p / (gamma - 1) + rho |v|^2 / 2 with
-    // the gauge-pressure difference (no p ~ 1/Ma^2 is rounded)
-    dw Qo[4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) Qo[v] = dw_from_double(qo[v]);
-    const dw rhoo = (Qo[0] + k.p_ref) * rcp(Qo[3]);
     dw qc[4];
-    qc[0] = rho - rhoo;
-    qc[1] = rho * Q[1] - rhoo * Qo[1];
-    qc[2] = rho * Q[2] - rhoo * Qo[2];
-    qc[3] = (Q[0] - Qo[0]) * k.inv_gm1 +
-            half(rho * (Q[1] * Q[1] + Q[2] * Q[2]) - rhoo * (Qo[1] * Qo[1] + Qo[2] * Qo[2]));
+    if (qref) {
+      // q_c(q) - q_c(q_ref), energy through p / (gamma - 1) + rho |v|^2 / 2
+      // with the gauge-pressure difference (no p ~ 1/Ma^2 is rounded)
+      dw Qo[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) Qo[v] = dw_from_double(qo[v]);
+      const dw rhoo = (Qo[0] + k.p_ref) * rcp(Qo[3]);
+      qc[0] = rho - rhoo;
+      qc[1] = rho * Q[1] - rhoo * Qo[1];
+      qc[2] = rho * Q[2] - rhoo * Qo[2];
+      qc[3] = (Q[0] - Qo[0]) * k.inv_gm1 +
+              half(rho * (Q[1] * Q[1] + Q[2] * Q[2]) - rhoo * (Qo[1] * Qo[1] + Qo[2] * Qo[2]));
+    } else {
+      qc[0] = rho;
+      qc[1] = rho * Q[1];
+      qc[2] = rho * Q[2];
+      qc[3] = rho * (Q[3] * k.inv_gm1 + half(Q[1] * Q[1] + Q[2] * Q[2]));
+    }
     const dw invJ = dw_from_double(mt[4]);
     const dw nodt = dw_from_double(-inv_odt);
 #pragma unroll
@@ -161,11 +173,11 @@ __global__ void __launch_bounds__(256, 1) volume_apply_dw_kernel(
       acc.add_prod(sgR[i], sJ[le][1][v][j]);
       acc.add_prod(sgL[j], sJ[le][0][v][i]);
       acc.add_prod(sgR[j], sJ[le][2][v][i]);
-      // F = -acc / |J| - qc / (omega dt) - S
+      // F = -acc / |J| - qc / (omega dt) + src - S
       dw_acc F;
       F.add_prod(-acc.value(), invJ);
       F.add_prod(qc[v], nodt);
-      F.add(dw_from_double(-Sv[v]));
+      F.add(dw_from_double(Sv[v]));
       const int row = v * N + pt;
       sr[le][row] = scaled_in_dw<W>(F.value(), okS ? srs[le * n + row] : rs[(size_t)e * n + row]);
     }
@@ -207,13 +219,13 @@ __global__ void __launch_bounds__(256, 1) volume_apply_dw_kernel(
 }
 
 template <class W>
-static void dw_dispatch(const Ctx& c, const LevelDev& L, double* q, double inv_odt, const double* S,
-                        const double* qb, cudaStream_t s) {
+static void dw_dispatch(const Ctx& c, const LevelDev& L, double* q, double inv_odt, const double* src,
+                        const double* S, const double* qref, cudaStream_t s) {
   const int threads = residual_threads_per_block(L.P), blocks = residual_blocks_for(L.P, c.E);
   const W* Dinv = (const W*)L.Dinv;
 #define PMG_VDW(PP)                                                                                         \
   volume_apply_dw_kernel<PP, W><<<blocks, threads, VolPrefetch<PP, W>::smem, s>>>(                          \
-      c.E, q, L.met, L.Fcom, L.opw, c.phw, inv_odt, S, qb, Dinv, L.rs, L.cs, c.d_scal + 1)
+      c.E, q, L.met, L.Fcom, L.opw, c.phw, inv_odt, src, S, qref, Dinv, L.rs, L.cs, c.d_scal + 1)
   switch (L.P) {
     case 0: PMG_VDW(0); break;
     case 1: PMG_VDW(1); break;
@@ -225,14 +237,12 @@ static void dw_dispatch(const Ctx& c, const LevelDev& L, double* q, double inv_o
 #undef PMG_VDW
 }
 
-bool volume_dw_applies(const Ctx& c, const LevelDev& L) {
-  return flux_dw(c, L) && L.level > 0 && c.ph.mu == 0.0 && c.ph.p_ref != 0.0;
-}
+bool volume_dw_applies(const Ctx& c) { return flux_dw_sweep(c) && c.ph.mu == 0.0 && c.ph.p_ref != 0.0; }
 
-void launch_volume_apply_dw(const Ctx& c, const LevelDev& L, double* q, double inv_odt, const double* S,
-                            const double* qb, int prec, cudaStream_t s) {
-  if (prec == PMG_PREC_FP64) dw_dispatch<double>(c, L, q, inv_odt, S, qb, s);
-  else dw_dispatch<float>(c, L, q, inv_odt, S, qb, s);
+void launch_volume_apply_dw(const Ctx& c, const LevelDev& L, double* q, double inv_odt, const double* src,
+                            const double* S, const double* qref, int prec, cudaStream_t s) {
+  if (prec == PMG_PREC_FP64) dw_dispatch<double>(c, L, q, inv_odt, src, S, qref, s);
+  else dw_dispatch<float>(c, L, q, inv_odt, src, S, qref, s);
 }
 
 template <class W>
@@ -252,7 +262,7 @@ static cudaError_t prep_dw(int P) {
 }
 
 cudaError_t prepare_volume_dw_kernels(const Ctx& c) {
-  for (int l = 1; l < c.cfg.n_levels; ++l) {
+  for (int l = 0; l < c.cfg.n_levels; ++l) {
     cudaError_t e = c.cfg.block_prec == PMG_PREC_FP64 ? prep_dw<double>(c.lev[l].P) : prep_dw<float>(c.lev[l].P);
     if (e != cudaSuccess) return e;
   }

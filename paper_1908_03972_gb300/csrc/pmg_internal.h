@@ -160,20 +160,24 @@ struct Ctx {
   int stages = 4;
 };
 
-// Face-flux arithmetic of a level (pmg_config.flux_prec): double-word on the
-// coarse levels for PMG_FLUX_DW_COARSE, on every level for PMG_FLUX_DW.
+// Residual arithmetic (pmg_config.flux_prec): double-word in a residual
+// evaluation of a coarse level (and of the finest for PMG_FLUX_DW) ...
 inline bool flux_dw(const Ctx& c, const LevelDev& L) {
-  return c.cfg.flux_prec == PMG_FLUX_DW || (c.cfg.flux_prec == PMG_FLUX_DW_COARSE && L.level > 0);
+  return c.cfg.flux_prec == PMG_FLUX_DW || (c.cfg.flux_prec == PMG_FLUX_DW_SMOOTH && L.level > 0);
 }
+// ... and in every element-Jacobi sweep unless PMG_FLUX_FP64.
+inline bool flux_dw_sweep(const Ctx& c) { return c.cfg.flux_prec != PMG_FLUX_FP64; }
 
 // ---------------------------------------------------------- kernel launchers
-void launch_face_flux(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s);
+// sweep: the flux of an element-Jacobi sweep (flux_dw_sweep) rather than of
+// a residual evaluation (flux_dw)
+void launch_face_flux(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s, bool sweep = false);
 cudaError_t prepare_residual_kernels(const Ctx& c);   // once per mesh upload
-// Coarse-level residual-and-update sweep in double-word arithmetic
-// (k_volume_dw.cu): used where volume_dw_applies().
-bool volume_dw_applies(const Ctx& c, const LevelDev& L);
-void launch_volume_apply_dw(const Ctx& c, const LevelDev& L, double* q, double inv_odt, const double* S,
-                            const double* qb, int prec, cudaStream_t s);
+// Residual-and-update sweep in double-word arithmetic (k_volume_dw.cu):
+// used where volume_dw_applies().
+bool volume_dw_applies(const Ctx& c);
+void launch_volume_apply_dw(const Ctx& c, const LevelDev& L, double* q, double inv_odt, const double* src,
+                            const double* S, const double* qref, int prec, cudaStream_t s);
 cudaError_t prepare_volume_dw_kernels(const Ctx& c);
 void launch_volume(const Ctx& c, const LevelDev& L, int level, const double* q, double* out, ResMode mode,
                    double inv_odt, const double* src, const double* S, double* Sout, const double* Pd,
