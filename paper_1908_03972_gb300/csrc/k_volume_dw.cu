@@ -20,17 +20,6 @@
 
 namespace pmg {
 
-template <class W>
-__device__ __forceinline__ W scaled_in_dw(dw F, double s);
-template <>
-__device__ __forceinline__ float scaled_in_dw<float>(dw F, double s) {
-  return __fmul_rn(__fadd_rn(F.h, F.l), (float)s);
-}
-template <>
-__device__ __forceinline__ double scaled_in_dw<double>(dw F, double s) {
-  return dw_to_double(F) * s;
-}
-
 template <int P, class W>
 __global__ void __launch_bounds__(256, 1) volume_apply_dw_kernel(
     int E, double* q, const double* __restrict__ met, const double* __restrict__ Fcom, OpTabW opw, PhysW k,

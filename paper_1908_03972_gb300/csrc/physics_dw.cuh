@@ -150,6 +150,25 @@ __device__ __forceinline__ void face_roe(const double qm[4], const double qp[4],
     roe_flux_jump(qm, qp, dq, pgm, pgp, nx, ny, dS, ph, out);
   }
 }
+// The double-word face flux left in double-word, the central pressure term
+// included: for gauge storage, where the momentum-flux pressures pgm, pgp
+// are the small p - p_ref.
+__device__ __forceinline__ void face_roe_dw(const double qm[4], const double qp[4], const double dq[4], double pgm,
+                                            double pgp, double nx, double ny, double dS, const PhysW& phw,
+                                            dw out[4]) {
+  dw Qm[4], Qp[4], DQ[4];
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    Qm[v] = dw_from_double(qm[v]);
+    Qp[v] = dw_from_double(qp[v]);
+    DQ[v] = dw_from_double(dq[v]);
+  }
+  const dw NX = dw_from_double(nx), NY = dw_from_double(ny), DS = dw_from_double(dS);
+  roe_flux_jump_dw(Qm, Qp, DQ, NX, NY, DS, phw, out);
+  const dw pc = half((dw_from_double(pgm) + dw_from_double(pgp)) * DS);
+  out[1] = out[1] + pc * NX;
+  out[2] = out[2] + pc * NY;
+}
 #endif  // __CUDACC__
 
 }  // namespace pmg

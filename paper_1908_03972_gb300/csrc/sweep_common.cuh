@@ -48,4 +48,16 @@ __device__ __forceinline__ void ldg4(const double* p, double a[4]) {
   a[0] = t0.x; a[1] = t0.y; a[2] = t1.x; a[3] = t1.y;
 }
 
+// rs .* F of a double-word F in the block precision W (rs: powers of two).
+template <class W>
+__device__ __forceinline__ W scaled_in_dw(dw F, double s);
+template <>
+__device__ __forceinline__ float scaled_in_dw<float>(dw F, double s) {
+  return __fmul_rn(__fadd_rn(F.h, F.l), (float)s);
+}
+template <>
+__device__ __forceinline__ double scaled_in_dw<double>(dw F, double s) {
+  return dw_to_double(F) * s;
+}
+
 }  // namespace pmg
