@@ -1,5 +1,7 @@
-"""The paper's grid-refinement study (Section 4.1, Table 2) through the GPU
-path, as an accuracy pin of the whole solver.
+"""The paper's order studies (Section 4.1, Tables 1 and 2) through the GPU
+path, as accuracy pins of the whole solver.
+
+Grid refinement (Table 2):
 
 Setup of Section 4.1: the isentropic vortex of eq. VP_Solution (free stream
 rho = u = v = 1, Ma_inf = 0.005, alpha = 5, phi = 1/2, centre at the origin)
@@ -17,6 +19,13 @@ ones (tests/golden/paper_orders.json, from Table 2) to 0.05: the paper prints
 two decimals and does not define its error norm (here the discrete L2 norm
 with the Gauss weights), which can move the third.  Measured: 4.369 / 3.913
 (P^3) and 4.720 / 4.230 (P^4) against 4.37 / 3.91 and 4.72 / 4.23.
+
+Time refinement (Table 1), opt-in (about 15 GPU-minutes; set PMG_RUN_TABLE1=1):
+P^5 on a 50^2 mesh of the same square, P{5-3-1}, I{20-20-40}, one period
+t~ = 20 with ESDIRK2 and ESDIRK3 at dt = t~/100, t~/200, t~/400 and ESDIRK4 at
+t~/40, t~/80, t~/120, stages to a 1e-6 drop of the scaled norm.  The velocity
+orders must reproduce the printed ones to 0.05.  Measured: 1.98 / 2.00,
+2.73 / 2.94 and 3.87 / 3.97 against 1.98 / 2.00, 2.73 / 2.94 and 3.87 / 4.00.
 """
 import json
 import math
@@ -69,5 +78,37 @@ def test_table2_velocity_orders(P, levels, key):
     meshes = (12, 24, 36)
     err = [_velocity_error(P, levels, n) for n in meshes]
     orders = [math.log(err[i] / err[i + 1]) / math.log(meshes[i + 1] / meshes[i]) for i in range(2)]
+    for ours, theirs in zip(orders, paper):
+        assert abs(ours - theirs) <= 0.05, (orders, paper, err)
+
+
+def _time_error(order, n_steps):
+    from paper_1908_03972_gb300 import pmgfr
+    nodes, nbr = W.periodic_box(50, 50, -10.0, 10.0, -10.0, 10.0, Ng=1)
+    gpu = pmgfr.Solver(nodes, nbr, [5, 3, 1], [20, 20, 40], Ma_inf=0.005, tol=1e-6, dtau_init=0.01, dtau_max=10.0,
+                       refresh_every=10, max_pseudo=20000, p_gauge=W.freestream_T(0.005),
+                       res_scale=W.freestream_scales(0.005), esdirk_order=order, block_prec=pmgfr.PMG_PREC_FP32)
+    try:
+        xy = gpu.coords()
+        gpu.set_state(W.isentropic_vortex(xy, center=(0.0, 0.0), period=(20.0, 20.0)))
+        for _ in range(n_steps):
+            pmgfr.pmg_esdirk_step(gpu.h, 20.0 / n_steps)
+        q = gpu.get_state()
+    finally:
+        gpu.close()
+    qe = W.isentropic_vortex(xy, t=20.0, center=(0.0, 0.0), period=(20.0, 20.0))
+    _, w = np.polynomial.legendre.leggauss(6)
+    wJ = np.outer(w, w).reshape(-1) * (10.0 / 50) ** 2
+    return math.sqrt(float((wJ[None, :] * (q[1] - qe[1]) ** 2).sum()))
+
+
+@pytest.mark.skipif(os.environ.get("PMG_RUN_TABLE1") != "1", reason="about 15 GPU-minutes: set PMG_RUN_TABLE1=1")
+@pytest.mark.parametrize("order,steps,key", [(2, (100, 200, 400), "esdirk2_time_orders"),
+                                             (3, (100, 200, 400), "esdirk3_time_orders"),
+                                             (4, (40, 80, 120), "esdirk4_time_orders")])
+def test_table1_velocity_orders(order, steps, key):
+    paper = json.load(open(GOLDEN))[key]["u"]
+    err = [_time_error(order, n) for n in steps]
+    orders = [math.log(err[i] / err[i + 1]) / math.log(steps[i + 1] / steps[i]) for i in range(2)]
     for ours, theirs in zip(orders, paper):
         assert abs(ours - theirs) <= 0.05, (orders, paper, err)
