@@ -88,19 +88,21 @@ def apply_flops(P, E):
 
 
 # ------------------------------------------------------------------ helpers
-def csrc_fingerprint():
+def csrc_fingerprint(src=None):
     """Hash of the kernel sources (the k_*.cu files and the device headers they
-    include); host-only files (api.cu, host_tables.cpp) do not change a
-    kernel's counters."""
+    include) with comments and blank space removed; host-only files (api.cu,
+    host_tables.cpp) and comments do not change a kernel's counters."""
     import hashlib
-    src = os.path.join(ROOT, "paper_1908_03972_gb300", "csrc")
+    import re
+    src = src or os.path.join(ROOT, "paper_1908_03972_gb300", "csrc")
     h = hashlib.sha256()
     for f in sorted(os.listdir(src)):
         if not (f.startswith("k_") or f.endswith(".cuh") or f == "pmg_internal.h"):
             continue
         h.update(f.encode())
-        with open(os.path.join(src, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(src, f)) as fh:
+            text = re.sub(r"/\*.*?\*/", "", re.sub(r"//[^\n]*", "", fh.read()), flags=re.S)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -1,4 +1,4 @@
-// k_residual.cu -- FP64 FR/CPR residual on the GPU (Section 2.3).
+// k_residual.cu -- FR/CPR residual on the GPU (Section 2.3).
 //
 // Two launches per evaluation:
 //  * face_flux: one thread per face flux point.  It extrapolates both
@@ -14,7 +14,10 @@
 //    mode (pure R, level system residual, FAS forcing) and an optional
 //    deterministic per-CTA sum of squares for the residual norm.
 //
-// Both kernels are bound by FP64 arithmetic on GB300 (about 1.2 TFLOP/s).
+// In binary64 both kernels are bound by FP64 issue on GB300 (about 1.2
+// TFLOP/s).  The face kernel's double-word variant (face_roe<true>, the
+// element-Jacobi sweeps) runs the Roe flux on the FP32 pipes; the sweeps'
+// residual-and-update in double-word is k_volume_dw.cu.
 //
 // Viscous terms (mu > 0, Section 2.1 fluxes, Section 2.3 common viscous flux):
 // a gradient launch (k_viscous.cu) first forms the broken gradients of
@@ -478,7 +481,7 @@ int residual_blocks_for(int P, int E) { int epb = elems_per_block(P); return (E 
 
 void launch_face_flux(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s, bool sweep) {
   int total = c.n_faces * L.n1;
-  // one warp per CTA: FP64-bound threads, spread over every SM
+  // one warp per CTA: latency-bound threads, spread over every SM
   int threads = 32, blocks = (total + threads - 1) / threads;
   const bool visc = c.ph.mu > 0.0, dwf = sweep ? flux_dw_sweep(c) : flux_dw(c, L);
   if (visc) launch_grad(c, L, q, s);

@@ -5,9 +5,10 @@
 
 namespace pmg {
 
-// Elements per CTA of the volume kernel.  The kernel is bound by FP64 issue
-// (2 DFMA per clock per SM), so small CTAs of one or two warps spread even the
-// coarse levels (4096 elements) over all 152 SMs.
+// Elements per CTA of the volume kernels.  Their threads are bound by FP64
+// issue (binary64: 2 DFMA per clock per SM) or by the latency of their chain
+// (double-word), so small CTAs of one or two warps spread even the coarse
+// levels (4096 elements) over all 152 SMs.
 template <int P>
 struct ElemsPerBlock {
   static constexpr int N = (P + 1) * (P + 1);
