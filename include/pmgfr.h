@@ -237,7 +237,10 @@ pmg_status pmg_prolong(pmg_ctx* ctx, int lf, const double* qc, double* qf, int o
 /* One FAS V-cycle (Section 3) on the finest-level state with the current
  * stage data and pseudo time step dtau; refresh = 1 rebuilds every level's
  * smoother on the way down.  *res_norm_out (may be NULL) receives ||F_0|| at
- * the start of the cycle. */
+ * the start of the cycle (binary64 whatever flux_prec says).  The sweep
+ * kernels wait for their shared-memory bulk copies with a bound of about a
+ * second; a wait that gives up is reported here (and by the calls below that
+ * run V-cycles) as PMG_ECUDA, after the kernels fell back to global loads. */
 pmg_status pmg_vcycle(pmg_ctx* ctx, double dtau, int refresh, double* res_norm_out);
 
 /* Pseudo-transient continuation of the current stage (Section 2.4) from the
