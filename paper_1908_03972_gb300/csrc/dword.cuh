@@ -137,7 +137,7 @@ struct dw_acc {
 // binary64 -> double-word with integer and FP32 operations only (no FP64
 // instruction): h takes the leading 24 significand bits (truncated), the
 // next 23 bits form l, and a Fast2Sum renormalises the pair.  The dropped
-// six bits give a relative error below 2^-47.
+// six bits (of the 52 fraction bits) give a relative error below 2^-46.
 __device__ __forceinline__ dw dw_from_double(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned int hi32 = (unsigned int)(b >> 32), lo32 = (unsigned int)b;
