@@ -5,9 +5,9 @@
 // A kernel issues its copies from one thread at entry and waits for them
 // where it first reads the data, so that the copies overlap the arithmetic
 // before that point.  Sizes and both addresses must be multiples of 16 bytes.
-// The wait gives up after kWaitTries polls (each poll may itself suspend the
-// thread for a while, so the total stays within about a second); the caller
-// then records the failure in an error slot the host reads and uses the
+// The wait gives up once kWaitNs nanoseconds of the global timer have passed
+// since its first unsuccessful poll (or after 2^30 polls); the caller then
+// records the failure in an error slot the host reads and uses the
 // global-memory copy of the data instead, so no thread hangs.
 #pragma once
 #include <cuda_runtime.h>
@@ -15,7 +15,13 @@
 namespace pmg {
 
 #ifdef __CUDACC__
-constexpr int kWaitTries = 1 << 22;
+constexpr unsigned long long kWaitNs = 1000000000ull;   // one second
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -38,10 +44,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                : "memory");
 }
 
-// Wait for phase 0 of the barrier; false after kWaitTries unsuccessful polls.
+// Wait for phase 0 of the barrier; false once kWaitNs have passed since the
+// first unsuccessful poll.
 __device__ __forceinline__ bool mbar_wait0(unsigned long long* bar) {
   const unsigned a = smem_u32(bar);
-  for (int i = 0; i < kWaitTries; ++i) {
+  unsigned long long t0 = 0;
+  for (unsigned i = 0; i < (1u << 30); ++i) {
     unsigned ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
@@ -49,6 +57,9 @@ __device__ __forceinline__ bool mbar_wait0(unsigned long long* bar) {
         : "r"(a)
         : "memory");
     if (ok) return true;
+    const unsigned long long t = global_ns();
+    if (i == 0) t0 = t;
+    else if (t - t0 > kWaitNs) return false;
   }
   return false;
 }
