@@ -1,4 +1,4 @@
-"""The cylinder configuration (BASELINE config 3): viscous flow past a
+"""The cylinder workload: viscous flow past a
 circular cylinder, O-mesh of quadratic (Q2) quadrilaterals with nodes on
 circles r_k = 0.5 100^(k/n_r), far field at r = 50, no-slip adiabatic wall,
 Ma = 0.001 with the eps cut-off (kappa = 1), Re = 100 (mu = 0.01), Pr = 0.72,
