@@ -67,14 +67,6 @@ __device__ __forceinline__ dw operator*(dw x, dw y) {
   return fast_two_sum(ch, cl);
 }
 
-// x * c for an FP32 number c.
-__device__ __forceinline__ dw mul(dw x, float c) {
-  const float ch = __fmul_rn(x.h, c);
-  float cl = __fmaf_rn(x.h, c, -ch);
-  cl = __fmaf_rn(x.l, c, cl);
-  return fast_two_sum(ch, cl);
-}
-
 // x * 2^k is exact: scale both parts.
 __device__ __forceinline__ dw scale2(dw x, float pow2) { return {__fmul_rn(x.h, pow2), __fmul_rn(x.l, pow2)}; }
 
