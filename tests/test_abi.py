@@ -47,3 +47,35 @@ def test_binding_struct_layout_matches_header():
     # 1 int (+4 padding), 2 doubles, 2 ints (C layout)
     assert ctypes.sizeof(pmgfr.pmg_config) == 4 + 64 + 4 + 24 + 4 + 4 + 24 + 16 + 8 + 16 + 32 + 32 + 8 + 16 + 16
     assert ctypes.sizeof(pmgfr.pmg_mesh) == 24
+
+
+def _cfg(**over):
+    from paper_1908_03972_gb300 import pmgfr
+    cfg = pmgfr.make_config([2, 1, 0], [1, 1, 1])
+    for k, v in over.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+@pytest.mark.parametrize("field,value", [("flux_prec", 3), ("block_prec", 2), ("esdirk_order", 5),
+                                         ("n_levels", 0), ("gamma", 1.0), ("mu", -1.0), ("cfl_mode", 1)])
+def test_create_rejects_invalid_configs_before_touching_the_gpu(lib, field, value):
+    """pmg_create validates its configuration first: these fail with
+    PMG_EINVAL on any machine (cfl_mode = 1 with cfl_init = 0)."""
+    from paper_1908_03972_gb300 import pmgfr
+    cfg = _cfg(**{field: value}, **({"cfl_init": 0.0} if field == "cfl_mode" else {}))
+    with pytest.raises(pmgfr.PmgError) as ei:
+        pmgfr.pmg_create(cfg)
+    assert ei.value.status == pmgfr.PMG_EINVAL
+
+
+def test_create_without_a_gpu_fails_instead_of_falling_back(lib):
+    """No CPU fallback: a valid configuration without a CUDA device is
+    PMG_ECUDA."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_1908_03972_gb300 import pmgfr
+    with pytest.raises(pmgfr.PmgError) as ei:
+        pmgfr.pmg_create(_cfg())
+    assert ei.value.status == pmgfr.PMG_ECUDA
