@@ -110,17 +110,53 @@ def test_gamma_equals_M_when_eps_is_one():
         assert np.allclose(G, M, rtol=1e-13, atol=1e-13 * np.abs(M).max())
 
 
-def test_preconditioned_eigenvalues_match_paper():
+# eps of eq. eps_nonmove, values worked out by hand.  With gamma = 1.4 and
+# R = 1, c^2 = 1.4 T: T = 1/1.4 gives c = 1 and T = 1e4/1.4 gives c = 100; the
+# velocity (3, 4) has |v| = 5 and (0.3, 0.4) has |v| = 0.5.  Each row is
+# (T, u, v, Ma_inf, kappa, cutoff, eps).  A squared Mach number, eps taken from
+# Ma_inf instead of the local Mach number, min and max exchanged, or a missing
+# cap at 1 each fails at least one row.
+EPS_HAND = [
+    (1 / 1.4, 0.3, 0.4, 0.005, 1.0, 0, 0.5),     # Ma = 0.5, no cut-off (Section 4.1)
+    (1 / 1.4, 0.3, 0.4, 0.7, 1.0, 1, 0.7),       # cut-off kappa Ma_inf = 0.7 above Ma = 0.5
+    (1 / 1.4, 0.3, 0.4, 0.1, 2.5, 1, 0.5),       # kappa Ma_inf = 0.25 below Ma = 0.5
+    (1e4 / 1.4, 3.0, 4.0, 0.005, 1.0, 0, 0.05),  # Ma = 5/100
+    (1e4 / 1.4, 3.0, 4.0, 0.005, 1.0, 1, 0.05),  # kappa Ma_inf = 0.005 below Ma = 0.05
+    (1e4 / 1.4, 3.0, 4.0, 0.1, 2.5, 1, 0.25),    # kappa Ma_inf = 0.25 (Section 4.4's kappa) above 0.05
+    (1e4 / 1.4, 0.0, 0.0, 0.001, 1.0, 1, 0.001), # fluid at rest: the cut-off alone
+    (1 / 1.4, 3.0, 4.0, 0.005, 1.0, 0, 1.0),     # Ma = 5: capped at 1
+    (1 / 1.4, 3.0, 4.0, 0.5, 1.0, 1, 1.0),       # capped at 1 with the cut-off on
+]
+
+
+@pytest.mark.parametrize("T,u,v,Ma_inf,kappa,cutoff,eps_ref", EPS_HAND)
+def test_precond_eps_hand_values(T, u, v, Ma_inf, kappa, cutoff, eps_ref):
+    q = np.array([T * 1.0, u, v, T])   # rho = 1
+    _, _, eps = O.point_matrices(q, Ma_inf=Ma_inf, kappa=kappa, cutoff=cutoff)
+    assert abs(eps - eps_ref) <= 1e-14 * eps_ref
+
+
+def _eps_by_hand(q, Ma_inf, kappa, cutoff):
+    """eps = min(1, max(kappa Ma_inf, |v|/c)) of eq. eps_nonmove, |v|/c alone without the cut-off."""
+    Ma = math.hypot(q[1], q[2]) / math.sqrt(1.4 * q[3])
+    return min(1.0, max(kappa * Ma_inf, Ma) if cutoff else Ma)
+
+
+@pytest.mark.parametrize("Ma_inf,kappa,cutoff", [(0.005, 1.0, 0), (0.005, 1.0, 1), (0.1, 2.5, 1)])
+def test_preconditioned_eigenvalues_match_paper(Ma_inf, kappa, cutoff):
     # eq. eigenvalues_para: u_n (x2 in 2D), u_n' +- c' with alpha = (1 - beta U_r^2)/2,
-    # beta = 1/c^2 for an ideal gas.
+    # beta = 1/c^2 for an ideal gas and U_r = eps c.  eps is worked out here,
+    # not taken from the oracle, so a wrong eps in Gamma fails the check.  The
+    # states have |v|/c ~ 0.005, so the (0.1, 2.5) row runs the cut-off branch.
     rng = np.random.default_rng(3)
     for q in _random_states(40, seed=3):
         th = rng.uniform(0, 2 * np.pi)
         n = np.array([np.cos(th), np.sin(th)])
-        M, G, eps = O.point_matrices(q)
+        M, G, _ = O.point_matrices(q, Ma_inf=Ma_inf, kappa=kappa, cutoff=cutoff)
         _, A = O.flux(q, n[0], n[1])
         lam = np.sort(np.linalg.eigvals(np.linalg.solve(G, A)).real)
-        c = math.sqrt(1.4 * q[3]); Ur = eps * c; un = q[1] * n[0] + q[2] * n[1]
+        c = math.sqrt(1.4 * q[3]); Ur = _eps_by_hand(q, Ma_inf, kappa, cutoff) * c
+        un = q[1] * n[0] + q[2] * n[1]
         alpha = (1 - Ur ** 2 / c ** 2) / 2
         cp = math.sqrt(alpha ** 2 * un ** 2 + Ur ** 2)
         ref = np.sort([un, un, un * (1 - alpha) + cp, un * (1 - alpha) - cp])
@@ -148,10 +184,24 @@ def test_roe_consistency_and_conservation():
         assert np.allclose(a, -b, rtol=1e-10, atol=1e-10 * np.abs(a).max())
 
 
+def _gamma_by_hand(q, eps):
+    """Gamma of eq. preconditioning at U_r = eps c, Theta of eq. theta: M with
+    its first column rho_p = 1/T replaced by Theta = 1/U_r^2 + 1/(Cp T)
+    (-rho_T/(rho Cp) = 1/(Cp T) for rho = p/T)."""
+    M, _, _ = O.point_matrices(q, Ma_inf=2.0, kappa=1.0, cutoff=1)   # eps = 1: Gamma = M
+    c2 = 1.4 * q[3]
+    theta = 1.0 / (eps ** 2 * c2) + 1.0 / (3.5 * q[3])
+    G = M.copy()
+    G[:, 0] = M[:, 0] * q[3] * theta   # column 0 of M is rho_p (1, u, v, H) - (0, 0, 0, 1)
+    G[3, 0] = (M[3, 0] + 1.0) * q[3] * theta - 1.0
+    return G
+
+
 def _roe_by_eigendecomposition(qm, qp, n, Ma_inf=0.005, cutoff=0, kappa=1.0):
-    """eq. invis_com literally: Gamma R |Lambda| R^-1 with R from numpy.linalg.eig."""
+    """eq. invis_com literally: Gamma R |Lambda| R^-1 with R from numpy.linalg.eig,
+    Gamma built here at the eps of eq. eps_nonmove worked out here."""
     qa = 0.5 * (qm + qp)
-    M, G, eps = O.point_matrices(qa, Ma_inf=Ma_inf, kappa=kappa, cutoff=cutoff)
+    G = _gamma_by_hand(qa, _eps_by_hand(qa, Ma_inf, kappa, cutoff))
     _, A = O.flux(qa, n[0], n[1])
     lam, R = np.linalg.eig(np.linalg.solve(G, A))
     absM = (R @ np.diag(np.abs(lam)) @ np.linalg.inv(R)).real
@@ -159,14 +209,17 @@ def _roe_by_eigendecomposition(qm, qp, n, Ma_inf=0.005, cutoff=0, kappa=1.0):
     return 0.5 * (fm + fp) - 0.5 * G @ absM @ (qp - qm)
 
 
-def test_roe_matches_eigendecomposition_low_mach():
+@pytest.mark.parametrize("Ma_inf,kappa,cutoff", [(0.005, 1.0, 0), (0.1, 2.5, 1), (0.001, 1.0, 1)])
+def test_roe_matches_eigendecomposition_low_mach(Ma_inf, kappa, cutoff):
+    # (0.1, 2.5): the cut-off kappa Ma_inf = 0.25 sets eps; (0.001, 1): the local
+    # Mach number (~0.005) does, with the cut-off on
     rng = np.random.default_rng(6)
     for qm in _random_states(30, seed=6):
         qp = qm + np.array([rng.standard_normal(), 0.1 * rng.standard_normal(),
                             0.1 * rng.standard_normal(), 1e-3 * rng.standard_normal()])
         th = rng.uniform(0, 2 * np.pi); n = np.array([np.cos(th), np.sin(th)])
-        ref = _roe_by_eigendecomposition(qm, qp, n)
-        got = O.roe(qm, qp, n[0], n[1])
+        ref = _roe_by_eigendecomposition(qm, qp, n, Ma_inf=Ma_inf, cutoff=cutoff, kappa=kappa)
+        got = O.roe(qm, qp, n[0], n[1], Ma_inf=Ma_inf, kappa=kappa, cutoff=cutoff)
         assert np.allclose(got, ref, rtol=1e-9, atol=1e-9 * np.abs(ref).max())
 
 
