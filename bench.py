@@ -1,18 +1,26 @@
 #!/usr/bin/env python
 """Benchmark: wall seconds per ESDIRK3 physical step with every implicit stage
-driven to a 1e-8 relative residual drop, for the mixed-precision V-cycle (FP32
-blocks, double-word smoothing sweeps) and the plain one (FP64 blocks, binary64
-throughout) of the element-Jacobi P-multigrid, plus DOF-sweeps/s.
+driven to a 1e-8 relative residual drop, plus DOF-sweeps/s, in three
+arithmetics of the element-Jacobi P-multigrid V-cycle:
+
+  mixed         FP32 blocks; the smoothing sweeps' residual-and-update in
+                double-word (float-float) arithmetic on every level; the
+                finest level's residual (stopping norm, restricted defect)
+                in binary64.  The headline value.
+  mixed_f64res  FP32 blocks, binary64 residual everywhere.
+  fp64          FP64 blocks, binary64 residual everywhere.
 
 Workload (default "c2"): isentropic vortex, Ma_inf = 0.005, periodic
 [0,10]^2, 64x64 straight quads, P{3-2-1-0}, I{5-10-20-40}, ESDIRK3,
 dt = 0.1, dtau 0.01 -> 10, smoother refresh every 10 pseudo-iterations, the
 residual norm with each equation divided by its free-stream convective flux
 scale.  The vortex is advanced by consecutive physical steps from the
-analytic state: W untimed warm-up steps, then K timed steps (the defaults,
-3 + 2, are the configuration's five steps); both block precisions advance
-the same steps.  Inputs are synthetic and resident in HBM when a timed step
-starts.  L2 is flushed before every timed step by writing a 256 MiB buffer.
+analytic state: W untimed warm-up steps, then K timed steps of the mixed leg;
+the other legs time the first min(K, --other-steps) of the same physical
+steps from the same warmed state, and the line reports how far their states
+are from the mixed leg's after those steps.  Inputs are synthetic and
+resident in HBM when a timed step starts.  L2 is flushed before every timed
+step by writing a 256 MiB buffer.
 
 One JSON line is printed by rank 0.  Under torchrun (N > 1) every rank runs
 an independent replica (weak scaling, no data-path collective).
@@ -46,12 +54,6 @@ WORKLOADS = {
                n=8, levels=[2, 1, 0], smooth=[5, 10, 20], dt=0.1),
 }
 
-# FP64 arithmetic peak of one GB300 from its unit counts: 2 FP64 FMA per clock
-# per SM, 152 SMs, 2.07 GHz maximum clock (a DFMA microbenchmark sustains
-# 1.005 TFLOP/s).
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-
-
 def dof_sweeps_per_vcycle(E, levels, smooth):
     """sum_l DOF_l x sweeps_l: 2 n_l on every level but the coarsest, n_L there."""
     tot = 0
@@ -62,22 +64,6 @@ def dof_sweeps_per_vcycle(E, levels, smooth):
 
 
 # ------------------------------------------------ algorithmic work per launch
-# FLOPs counted from the kernel source (fma = 2, add/mul/div/sqrt = 1).
-ROE_FLOPS = 185
-
-
-def face_flops(P, n_faces):
-    n1 = P + 1
-    return n_faces * n1 * (24 * n1 + 12 + ROE_FLOPS)
-
-
-def volume_flops(P, E, split=True):
-    n1 = P + 1
-    N = n1 * n1
-    per_pt = 17 + 24 + 16 * (2 * n1 + 1) / n1 + (22 if split else 10) + 4 * (4 * n1 + 8) + 4 + 12 + 8
-    return E * N * per_pt
-
-
 def apply_bytes(P, E, wbytes):
     n = 4 * (P + 1) ** 2
     return E * (wbytes * n * n + 16 * n + 24 * n)
@@ -105,21 +91,6 @@ def csrc_fingerprint(src=None):
             text = re.sub(r"/\*.*?\*/", "", re.sub(r"//[^\n]*", "", fh.read()), flags=re.S)
         h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
-
-
-def ncu_traffic(key):
-    """DRAM bytes per launch of a kernel from the committed ncu capture, or
-    None when there is none or the kernel sources changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic_c2.json")
-    if not os.path.exists(path):
-        return None
-    with open(path) as f:
-        rec = json.load(f)
-    if rec.get("csrc_sha256_prefix") != csrc_fingerprint():
-        return None
-    k = rec.get("kernels", {}).get(key)
-    return k["dram_bytes_per_launch"] if k else None
-
 
 
 class ClockSampler:
@@ -195,11 +166,32 @@ def barrier_max(value, world, device):
 
 
 # ------------------------------------------------------------ reference arm
-def oracle_sample(wl, n_ref, n_plain):
+def cpu_model():
+    """CPU model name of the host (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def oracle_sample(wl, n_ref, n_plain, threads=1):
     """Time the FP64 CPU oracle on one V-cycle with smoother rebuild and one
-    without, on the full workload, and scale to one step."""
+    without, on the full workload, with `threads` host threads on its element
+    loops, and scale to one step (n_ref rebuilding and n_plain plain V-cycles)."""
     import oracle as O
     from paper_1908_03972_gb300 import workloads as W
+    used = O.set_threads(threads)
     nodes, nbr = W.periodic_box(wl["n"], wl["n"], Ng=1)
     orc = O.Oracle(nodes, nbr, 1, wl["levels"], wl["smooth"], tol=1e-8, res_scale=W.freestream_scales(0.005))
     q = W.isentropic_vortex(orc.coords())
@@ -215,11 +207,15 @@ def oracle_sample(wl, n_ref, n_plain):
     t1 = time.perf_counter()
     orc.vcycle(q1, 0.01, refresh=False)
     t2 = time.perf_counter()
+    O.set_threads(1)
     t_ref, t_plain = t1 - t0, t2 - t1
-    return dict(t_vcycle_refresh=t_ref, t_vcycle=t_plain, s_per_step=n_ref * t_ref + n_plain * t_plain)
+    return dict(t_vcycle_refresh=t_ref, t_vcycle=t_plain, s_per_step=n_ref * t_ref + n_plain * t_plain,
+                threads=used)
 
 
 def load_vcycle_counts():
+    """V-cycles and smoother rebuilds per step of the timed workload, as
+    measured on the GPU and committed (read only)."""
     if os.path.exists(VCYCLE_FILE):
         with open(VCYCLE_FILE) as f:
             return json.load(f)
@@ -231,27 +227,53 @@ def run_reference(args, wl, world, rank):
         return 0
     counts = load_vcycle_counts() if args.workload == "c2" else None
     n_v, n_r = (counts["vcycles"], counts["refreshes"]) if counts else (1, 1)
+    cores = os.cpu_count() or 1
     if args.warmup > 0:   # one untimed sample (page-in, first-touch), not in the median
-        oracle_sample(wl, n_r, n_v - n_r)
-    samples = [oracle_sample(wl, n_r, n_v - n_r) for _ in range(args.steps)]
+        oracle_sample(wl, n_r, n_v - n_r, threads=cores)
+    samples = [oracle_sample(wl, n_r, n_v - n_r, threads=cores) for _ in range(args.steps)]
     s = float(np.median([x["s_per_step"] for x in samples]))
+    used = samples[-1]["threads"]
     E = wl["n"] ** 2
     dsw = dof_sweeps_per_vcycle(E, wl["levels"], wl["smooth"])
-    sample = ("one FAS V-cycle with smoother rebuild and one without on the full workload, single-threaded "
-              f"FP64 oracle; scaled by {n_r} rebuilding and {n_v - n_r} plain V-cycles per step"
+    sample = (f"extrapolated from sampled V-cycles: one FAS V-cycle with smoother rebuild and one without on the "
+              f"full workload, FP64 oracle on {used} host threads ({cpu_model()}); scaled by {n_r} rebuilding "
+              f"and {n_v - n_r} plain V-cycles per step (the GPU's committed counts)"
               + ("" if counts else " (no measured V-cycle count found: per V-cycle figure)"))
     line = {"impl": "reference", "metric": METRIC, "value": s, "unit": "s/step", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * s, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl["name"], "elements": E, "parallelism": "replicas"},
             "dof_sweeps_per_s": dsw / samples[-1]["t_vcycle"],
-            "cpu_baseline": {"kind": "oracle", "value": s, "unit": "s/step", "cores": 1, "sample": sample},
+            "cpu_baseline": {"kind": "oracle", "value": s, "unit": "s/step", "cores": used, "cpu": cpu_model(),
+                             "sample": sample, "extrapolated": True},
             "e2e": {"value": s, "unit": "s/step", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
 # ------------------------------------------------------------------ our arm
+# Measured FP32 instructions of the double-word sweep kernels (ncu), for the
+# FP32-issue roofline of those kernels; see profiles/.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+
+
+def ncu_record():
+    path = os.path.join(ROOT, "profiles", "ncu_traffic_c2.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f)
+    return rec if rec.get("csrc_sha256_prefix") == csrc_fingerprint() else None
+
+
+def solution_diff(qa, qb, p_inf):
+    """max |qa - qb| of the velocity and of (p - p_inf)/(rho_inf |v_inf|^2)
+    (rho_inf |v_inf|^2 = 2 for the vortex)."""
+    return {"u": float(np.abs(qa[1] - qb[1]).max()), "v": float(np.abs(qa[2] - qb[2]).max()),
+            "p_over_rho_v2": float(np.abs(qa[0] - qb[0]).max() / 2.0),
+            "T_over_T_inf": float(np.abs(qa[3] - qb[3]).max() / p_inf)}
+
+
 def run_ours(args, wl, world, rank, local):
     import torch
     from paper_1908_03972_gb300 import build, pmgfr, workloads as W
@@ -268,18 +290,24 @@ def run_ours(args, wl, world, rank, local):
     nodes, nbr = W.periodic_box(wl["n"], wl["n"], Ng=1)
     E = nodes.shape[0]
     stream = torch.cuda.current_stream(device)
+    p_inf = W.freestream_T(0.005)
     kw = dict(tol=1e-8, dtau_init=0.01, dtau_max=10.0, refresh_every=10, max_pseudo=20000, use_graph=1,
-              p_gauge=W.freestream_T(0.005), res_scale=W.freestream_scales(0.005))
+              p_gauge=p_inf, res_scale=W.freestream_scales(0.005))
     dsw = dof_sweeps_per_vcycle(E, wl["levels"], wl["smooth"])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+    # The three legs: (block precision, residual arithmetic of the sweeps)
+    LEGS = {
+        "mixed": (pmgfr.PMG_PREC_FP32, pmgfr.PMG_FLUX_DW_SMOOTH),
+        "mixed_f64res": (pmgfr.PMG_PREC_FP32, pmgfr.PMG_FLUX_FP64),
+        "fp64": (pmgfr.PMG_PREC_FP64, pmgfr.PMG_FLUX_FP64),
+    }
 
-    def make(prec):
-        # mixed: FP32 blocks and double-word coarse-level face fluxes; fp64: binary64 throughout
-        flux = pmgfr.PMG_FLUX_DW_SMOOTH if prec == pmgfr.PMG_PREC_FP32 else pmgfr.PMG_FLUX_FP64
+    def make(leg):
+        prec, flux = LEGS[leg]
         return pmgfr.Solver(nodes, nbr, wl["levels"], wl["smooth"], stream=stream.cuda_stream, block_prec=prec,
                             flux_prec=flux, **kw)
 
-    solver = make(pmgfr.PMG_PREC_FP32)
+    solver = make("mixed")
     q0 = W.isentropic_vortex(solver.coords())
     q0_dev = torch.from_numpy(np.ascontiguousarray(q0)).to(device)
     state_bytes = q0.nbytes
@@ -315,43 +343,52 @@ def run_ours(args, wl, world, rank, local):
         solver.close()
         return 0
 
-    results = {}
-    q_warm = None   # state after the warm-up steps (host), start of the timed steps
-    for prec, label in ((pmgfr.PMG_PREC_FP32, "mixed"), (pmgfr.PMG_PREC_FP64, "fp64")):
-        if args.skip_fp64 and label == "fp64":
-            continue
-        s = solver if label == "mixed" else make(prec)
-        pmgfr.pmg_set_state(s.h, 0, q0_dev)
-        for _ in range(args.warmup):
-            one_step(s, False)
-        if label == "mixed":
-            q_warm = np.ascontiguousarray(s.get_state())
-        sampler = ClockSampler(local) if label == "mixed" else None
+    def timed_steps(s, n, sampler=None):
         if sampler:
             sampler.start()
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
         torch.cuda.synchronize(device)
-        ms, its, drops, nvs, nrs = [], [], [], [], []
-        for _ in range(args.steps):
+        ms, its, drops, nvs, nrs, states = [], [], [], [], [], []
+        for _ in range(n):
             t, stats = one_step(s, True)
             ms.append(t)
             its.append(list(stats.pseudo_iters)[:3])
             drops.append(max(float(x) for x in list(stats.res_drop)[:3]))
             nvs.append(stats.n_vcycles)
             nrs.append(stats.n_refresh)
+            states.append(s.get_state())   # after the step's events: outside the timed step
         torch.cuda.synchronize(device)
         clocks = sampler.stop() if sampler else None
         mean_ms = barrier_max(float(np.mean(ms)), world, device)
         nv = float(np.mean(nvs))
-        results[label] = dict(s_per_step=mean_ms / 1000.0, ms=ms, vcycles=nv, refreshes=float(np.mean(nrs)),
-                              pseudo_iters=its, max_res_drop=drops,
-                              dof_sweeps_per_s=dsw * nv * world / (mean_ms / 1000.0), clocks=clocks)
-        if label != "mixed":
-            s.close()
+        return dict(s_per_step=mean_ms / 1000.0, steps=n, ms=ms, vcycles=nv, refreshes=float(np.mean(nrs)),
+                    pseudo_iters=its, max_res_drop=drops, dof_sweeps_per_s=dsw * nv * world / (mean_ms / 1000.0),
+                    ms_per_vcycle=mean_ms / nv, clocks=clocks), states
 
+    # Headline leg: W warm-up steps from the analytic state, then K timed steps.
+    pmgfr.pmg_set_state(solver.h, 0, q0_dev)
+    for _ in range(args.warmup):
+        one_step(solver, False)
+    q_warm = np.ascontiguousarray(solver.get_state())
+    results = {}
+    results["mixed"], mixed_states = timed_steps(solver, args.steps, ClockSampler(local))
+    # Other legs: the same physical steps from the same warmed state (one
+    # untimed step first for their own graph captures, then reset), K2 steps.
+    k2 = min(args.steps, args.other_steps)
+    legs = [] if args.skip_fp64 else ["mixed_f64res", "fp64"]
+    diffs = {}
+    for leg in legs:
+        s = make(leg)
+        s.set_state(q_warm)
+        one_step(s, False)
+        s.set_state(q_warm)
+        results[leg], st = timed_steps(s, k2)
+        diffs[f"mixed_vs_{leg}"] = solution_diff(mixed_states[k2 - 1], st[k2 - 1], p_inf)
+        s.close()
     mixed = results["mixed"]
+
     # End to end through the C interface with host buffers: the same K steps
     # from the state after the warm-ups, each step taking its state from pinned
     # host memory and returning the new state there.
@@ -384,77 +421,84 @@ def run_ours(args, wl, world, rank, local):
     top = max(prof.items(), key=lambda kv: kv[1][0])
     (top_name, top_lvl), (top_ms, top_n) = top
     P = wl["levels"][top_lvl]
-    n_faces = 2 * E
-    if top_name == "face_flux":
-        work, bound, unit, peak = face_flops(P, n_faces), "alu", "TFLOP/s", FP64_PEAK_TFLOPS
-    elif top_name == "volume":
-        work, bound, unit, peak = volume_flops(P, E, top_lvl == 0), "alu", "TFLOP/s", FP64_PEAK_TFLOPS
-    elif top_name == "apply":
-        work, bound, unit, peak = apply_bytes(P, E, 4), "hbm", "GB/s", None
-    elif top_name == "fused_sweep":
-        # each face is evaluated by both of its elements inside the fused sweep
-        work = 2 * face_flops(P, n_faces) + volume_flops(P, E, True)
-        bound, unit, peak = "alu", "TFLOP/s", FP64_PEAK_TFLOPS
-    else:
-        work, bound, unit, peak = None, "alu", "TFLOP/s", FP64_PEAK_TFLOPS
     avg_s = top_ms / top_n / 1000.0
+    key = f"{top_name}[level {top_lvl}, P={P}]"
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
         peaks = json.load(open(pk_path))
-    if bound == "hbm":
-        peak = peaks.get("hbm_gbs", 6800.0)
-        achieved = work / avg_s / 1e9
-        peak_note = "measured" if "hbm_gbs" in peaks else "fallback"
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_note = "measured" if "hbm_gbs" in peaks else "fallback"
+    rec = ncu_record()
+    krec = (rec or {}).get("kernels", {}).get(key, {})
+    # Which pipe the dominant kernel runs on: the mixed leg's sweep kernels run
+    # their arithmetic in double-word on the FP32 pipes; their roofline is FP32
+    # issue, from the FP32 operations ncu counted (FFMA = 2, FADD/FMUL = 1).
+    if top_name == "apply":
+        work = apply_bytes(P, E, 4)
+        roofline = {"bound": "hbm", "achieved": work / avg_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "peak_source": hbm_note}
+    elif krec.get("fp32_flops_per_launch"):
+        work = krec["fp32_flops_per_launch"]
+        roofline = {"bound": "alu", "achieved": work / avg_s / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz",
+                    "work": "FP32 flops per launch counted by ncu (double-word arithmetic of the method's binary64 "
+                            "operations)"}
     else:
-        achieved = work / avg_s / 1e12 if work else None
-        peak_note = "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz"
-    key = f"{top_name}[level {top_lvl}, P={P}]"
-    # The sweep kernels of the mixed solver run the method's binary64
-    # operations in double-word arithmetic on the FP32 pipes; their work is
-    # still counted as those binary64 flops, against the FP64 peak they
-    # replace.
-    arith = ("double-word (float-float) on the FP32 pipes; work = the binary64 flops it replaces"
-             if top_name in ("face_flux", "volume", "fused_sweep") else "as counted")
-    roofline = {"kernel": key, "bound": bound, "achieved": achieved,
-                "peak": peak, "unit": unit, "frac": (achieved / peak) if achieved else None,
-                "traffic": ncu_traffic(key), "peak_source": peak_note, "arithmetic": arith,
-                "share_of_step": top_ms / total_ms if total_ms else None,
-                "avg_launch_us": avg_s * 1e6, "launches_per_step": top_n}
+        work = None
+        roofline = {"bound": "alu", "achieved": None, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz",
+                    "work": "no ncu FP32 count for the current kernel sources"}
+    roofline.update({"kernel": key, "frac": (roofline["achieved"] / roofline["peak"]) if roofline["achieved"] else None,
+                     "traffic": krec.get("dram_bytes_per_launch"), "share_of_step": top_ms / total_ms,
+                     "avg_launch_us": avg_s * 1e6, "launches_per_step": top_n})
+    # V-cycle level: the FP32 block inverses the sweeps must read per V-cycle
+    # (n^2 entries per element per sweep on every level) over the V-cycle time.
+    blk = sum(4 * E * (4 * (Pl + 1) ** 2) ** 2 * (n if l == len(wl["levels"]) - 1 else 2 * n)
+              for l, (Pl, n) in enumerate(zip(wl["levels"], wl["smooth"])))
+    vc_s = mixed["s_per_step"] / mixed["vcycles"]
+    vcycle_hbm = {"block_bytes_per_vcycle": blk, "ms_per_vcycle": vc_s * 1e3, "achieved_gbs": blk / vc_s / 1e9,
+                  "peak_gbs": hbm_peak, "frac": blk / vc_s / 1e9 / hbm_peak}
 
-    # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    # CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only), on one
+    # host thread and on all of them
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         try:
-            smp = oracle_sample(wl, mixed["refreshes"], mixed["vcycles"] - mixed["refreshes"])
-            cpu = {"value": smp["s_per_step"], "unit": "s/step", "cores": 1, "kind": "oracle",
-                   "sample": ("one V-cycle with smoother rebuild (%.1f s) and one without (%.1f s) on the full "
-                              "workload, single-threaded FP64 oracle, scaled by this run's %d rebuilding and %d "
-                              "plain V-cycles per step" % (smp["t_vcycle_refresh"], smp["t_vcycle"],
-                                                           round(mixed["refreshes"]),
-                                                           round(mixed["vcycles"] - mixed["refreshes"])))}
+            n_r, n_p = mixed["refreshes"], mixed["vcycles"] - mixed["refreshes"]
+            cores = os.cpu_count() or 1
+            one = oracle_sample(wl, n_r, n_p, threads=1)
+            allc = oracle_sample(wl, n_r, n_p, threads=cores)
+            cpu = {"value": allc["s_per_step"], "unit": "s/step", "cores": allc["threads"], "kind": "oracle",
+                   "cpu": cpu_model(), "extrapolated": True, "single_core_value": one["s_per_step"],
+                   "sample": ("extrapolated from sampled V-cycles: one V-cycle with smoother rebuild and one "
+                              "without on the full workload, FP64 oracle, on %d host threads (%.2f s and %.2f s) "
+                              "and on one (%.1f s and %.1f s), scaled by this run's %d rebuilding and %d plain "
+                              "V-cycles per step" % (allc["threads"], allc["t_vcycle_refresh"], allc["t_vcycle"],
+                                                     one["t_vcycle_refresh"], one["t_vcycle"], round(n_r),
+                                                     round(n_p)))}
         except Exception as exc:  # the product number stands without it
             cpu = {"value": None, "unit": "s/step", "cores": 1, "kind": "oracle", "sample": f"failed: {exc}"}
-        if args.workload == "c2":
-            os.makedirs(os.path.dirname(VCYCLE_FILE), exist_ok=True)
-            with open(VCYCLE_FILE, "w") as f:
-                json.dump({"workload": wl["name"], "vcycles": mixed["vcycles"], "refreshes": mixed["refreshes"],
-                           "pseudo_iters": mixed["pseudo_iters"], "warmup_steps": args.warmup}, f, indent=1)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": mixed["s_per_step"], "unit": "s/step", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mixed["s_per_step"] * 1000.0,
-            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 residual + f32x2 (double-word) sweeps + f32 blocks",
             "data": "synthetic",
             "config": {"workload": wl["name"], "elements": E, "dofs_finest": 4 * E * (wl["levels"][0] + 1) ** 2,
                        "blocks": "FP32 equilibrated Gauss-Jordan inverse",
-                       "residual": "FP64; on the coarse levels the Roe face flux in double-word "
-                                   "(float-float, ~2^-46) arithmetic",
-                       "fp64_leg": "FP64 blocks and binary64 Roe flux",
+                       "residual": ("binary64 for the finest level's residual (stopping norm, restricted defect, "
+                                    "pmg_residual); double-word (float-float, ~2^-48) in every smoothing sweep's "
+                                    "residual-and-update on every level and in the coarse levels' residuals"),
+                       "mixed_f64res_leg": "FP32 blocks, binary64 residual everywhere",
+                       "fp64_leg": "FP64 blocks, binary64 residual everywhere",
                        "l2": "flushed (256 MiB write) before every timed step", "parallelism": "replicas"},
             "mixed": {k: v for k, v in mixed.items() if k not in ("clocks",)},
+            "mixed_f64res": {k: v for k, v in results.get("mixed_f64res", {}).items() if k not in ("clocks",)},
             "fp64": {k: v for k, v in results.get("fp64", {}).items() if k not in ("clocks",)},
+            "solution_diff_after_%d_steps" % k2: diffs,
             "dof_sweeps_per_vcycle": dsw,
             "clocks": mixed["clocks"],
             "e2e": {"value": e2e_s, "unit": "s/step", "h2d_bytes_per_step": state_bytes,
@@ -462,6 +506,7 @@ def run_ours(args, wl, world, rank, local):
             "gpu_launches": launches * args.steps,
             "profile_ms_by_kernel": {k: {"ms": v[0], "launches": v[1]} for k, v in sorted(by_class.items())},
             "roofline": roofline,
+            "vcycle_hbm": vcycle_hbm,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -479,7 +524,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
-    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true", help="time the mixed leg only")
+    ap.add_argument("--other-steps", type=int, default=4,
+                    help="timed steps of the mixed_f64res and fp64 legs (at most --steps)")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--ncu-window", type=int, default=0,
                     help="profiling helper: run N V-cycles of the first stage and exit (no bench line)")

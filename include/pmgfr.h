@@ -4,7 +4,7 @@
  *
  * The library solves the 2D Euler equations with Weiss-Smith/Turkel local
  * preconditioning, discretised by FR/CPR (Gauss-Legendre solution points,
- * DG/Radau correction functions) and advanced by ESDIRK3 with dual time
+ * DG/Radau correction functions) and advanced by ESDIRK2, 3 or 4 with dual time
  * stepping.  Each implicit stage is solved by pseudo-transient continuation
  * whose pseudo-iteration is one FAS V-cycle over polynomial levels with an
  * element-Jacobi smoother (Wang & Yu, arXiv 1908.03972, Sections 2-3).
@@ -39,9 +39,12 @@ typedef enum {
   PMG_EINVAL = -1,     /* bad argument, size or call order */
   PMG_ENOMEM = -2,     /* device allocation failed */
   PMG_ECUDA = -3,      /* CUDA runtime error (message in pmg_last_error) */
-  PMG_ESINGULAR = -4,  /* zero pivot while factoring an element block */
+  PMG_ESINGULAR = -4,  /* an element block is singular to working precision */
   PMG_ENONFINITE = -5, /* non-finite residual norm */
   PMG_ENOTCONV = -6,   /* stage did not reach the tolerance in max_pseudo */
+  PMG_ETIMEOUT = -7,   /* a kernel's bounded wait for a bulk shared-memory
+                          copy gave up (the kernel finished from global memory,
+                          so the results are still those of the method) */
   PMG_ESTATE = -8      /* call needs data that was not set (mesh, stage) */
 } pmg_status;
 
@@ -137,6 +140,14 @@ typedef struct {
                      (Section 4.1 states only the period) */
   int flux_prec;  /* pmg_flux_prec (the element blocks are always
                      differentiated in binary64) */
+  double copy_wait_s; /* bound of each kernel's wait for its bulk
+                     shared-memory copies, in seconds (0: one second).  A wait
+                     that gives up sets a flag, the kernel reads the data from
+                     global memory instead and waits (again bounded) for its
+                     copies to land before it exits; the V-cycle calls then
+                     return PMG_ETIMEOUT.  A negative value makes every such
+                     wait give up at once: a diagnostic that runs the
+                     global-memory path and the PMG_ETIMEOUT report. */
 } pmg_config;
 
 /* Boundary types, in the second slot of a boundary face's neighbour entry
@@ -220,10 +231,18 @@ pmg_status pmg_assemble_blocks(pmg_ctx* ctx, int level, double dtau);
  * n = 4 N, row/column index v * N + pt. */
 pmg_status pmg_get_blocks(pmg_ctx* ctx, int level, double* D, int on_device);
 
+/* Replace the assembled FP64 blocks of a level by caller data (same layout as
+ * pmg_get_blocks), e.g. blocks formed or modified on the host.  The blocks
+ * count as assembled and not factored.  Synchronises the stream. */
+pmg_status pmg_set_blocks(pmg_ctx* ctx, int level, const double* D, int on_device);
+
 /* Factor the assembled blocks of a level (or all, level = -1) in the
  * configured precision: power-of-two row/column equilibration, then
  * Gauss-Jordan elimination with partial pivoting to the explicit inverse.
- * Returns PMG_ESINGULAR if a pivot vanishes. */
+ * Returns PMG_ESINGULAR, naming the element, if a pivot is not finite or not
+ * above eps^2 of the working precision (the equilibrated rows have unit size,
+ * so such a block is singular to working precision); the library's V-cycle
+ * calls report it the same way when they rebuild the smoother. */
 pmg_status pmg_factor_blocks(pmg_ctx* ctx, int level);
 
 /* x = D^-1 r per element with the factored blocks (SoA vectors). */
@@ -238,9 +257,9 @@ pmg_status pmg_prolong(pmg_ctx* ctx, int lf, const double* qc, double* qf, int o
  * stage data and pseudo time step dtau; refresh = 1 rebuilds every level's
  * smoother on the way down.  *res_norm_out (may be NULL) receives ||F_0|| at
  * the start of the cycle (binary64 whatever flux_prec says).  The sweep
- * kernels wait for their shared-memory bulk copies with a bound of about a
- * second; a wait that gives up is reported here (and by the calls below that
- * run V-cycles) as PMG_ECUDA, after the kernels fell back to global loads. */
+ * kernels wait for their shared-memory bulk copies with the bound copy_wait_s;
+ * a wait that gives up is reported here (and by the calls below that run
+ * V-cycles) as PMG_ETIMEOUT, after the kernels fell back to global loads. */
 pmg_status pmg_vcycle(pmg_ctx* ctx, double dtau, int refresh, double* res_norm_out);
 
 /* Pseudo-transient continuation of the current stage (Section 2.4) from the
@@ -249,8 +268,9 @@ pmg_status pmg_vcycle(pmg_ctx* ctx, double dtau, int refresh, double* res_norm_o
  * count and the final relative drop.  PMG_ENOTCONV after max_pseudo. */
 pmg_status pmg_stage_solve(pmg_ctx* ctx, int* iters, double* drop);
 
-/* One ESDIRK3 physical step of size dt (eq. ESDIRK_ns) from the finest-level
- * state; the stage initial guess is the previous stage's solution.  Inside the
+/* One physical step of size dt (eq. ESDIRK_ns) with the ESDIRK scheme that
+ * esdirk_order selects (2, 3 or 4) from the finest-level state; the stage
+ * initial guess is the previous stage's solution.  Inside the
  * step the finest-level system F = -q_c(q)/(omega dt) + R(q) + src is
  * evaluated as -(q_c(q) - q_c(q^n))/(omega dt) + R(q) + sum_j a_ij R^j/omega,
  * identical in exact arithmetic, with the energy difference formed from the
@@ -286,18 +306,22 @@ pmg_status pmg_profile_read(pmg_ctx* ctx, double* ms, long long* counts);
  * Computes R = -div f exactly as pmg_residual does, for a state q and an
  * output R that are both caller-owned DEVICE buffers of the level's SoA size
  * on the context's device, which must be the current device.  The call makes
- * no cudaMalloc, cudaFree or other allocating call.  Its scratch (a copy of
- * q and the common face fluxes: 4 E N + 16 E (P+1) doubles) lives in one
- * static device array of 2^21 doubles (16 MiB) that every GPU loading this
- * library holds until the process exits; a level that needs more returns
- * PMG_EINVAL with the sizes in the message.
+ * no cudaMalloc, cudaFree or other allocating call, on the device or the
+ * host.  Its scratch is a copy of q and the common face fluxes, 4 E N +
+ * 16 E (P+1) doubles, plus with mu > 0 the broken gradients and face jumps of
+ * the viscous terms, 6 E N + 12 E (P+1) more.  It lives in one static device
+ * array of 2^21 doubles (16 MiB) that every GPU loading this library holds
+ * until the process exits; a level that needs more returns PMG_EINVAL with
+ * the sizes in the message.
  *
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) for that device, so make the first call before any
- * stream capture.  All calls share the array and each overwrites all of the
- * scratch it reads, so nothing carries over between calls; but calls whose
- * GPU work overlaps (other streams, other contexts, other host threads) race
- * on it.  The call synchronises the context's stream before returning. */
+ * (cudaGetSymbolAddress) for that device and keeps it for the life of the
+ * process, so make the first call before any stream capture, and do not
+ * reset the device (cudaDeviceReset) between calls.  All calls share the
+ * array and each overwrites all of the scratch it reads, so nothing carries
+ * over between calls; but calls whose GPU work overlaps (other streams, other
+ * contexts, other host threads) race on it.  The call synchronises the
+ * context's stream before returning. */
 pmg_status pmg_residual_static(pmg_ctx* ctx, int level, const double* q, double* R);
 
 /* Checkpoint and restore of the finest-level state (no counterpart in the

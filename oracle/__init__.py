@@ -19,11 +19,16 @@ _LIB = os.path.join(_HERE, f"liboracle.{platform.machine()}.so")
 _lib = None
 
 
-def build(force: bool = False, openmp: bool = False) -> str:
-    """Compile the oracle with g++ (no architecture-specific flags)."""
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (no architecture-specific flags), with
+    OpenMP element loops where the compiler offers it.  The loops run on one
+    thread unless set_threads asks for more; results do not depend on it."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", _LIB + ".tmp", _SRC]
-        subprocess.check_call(cmd)
+        base = ["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", _LIB + ".tmp", _SRC]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(_LIB + ".tmp", _LIB)
     return _LIB
 
@@ -34,7 +39,14 @@ def lib():
         build()
         _lib = ctypes.CDLL(_LIB)
         _declare(_lib)
+        _lib.orc_set_threads(1)
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's element loops; returns the number in use
+    (1 when the library was built without OpenMP)."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 _d = ctypes.POINTER(ctypes.c_double)
@@ -99,6 +111,8 @@ def _declare(L):
     L.orc_stage_solve.argtypes = [vp, _d, _i, _d, _d, ci]
     L.orc_esdirk_step.argtypes = [vp, _d, cd, _i, _d]
     L.orc_ser_schedule.argtypes = [_d, ci, cd, cd, ci, _d, _i]
+    L.orc_set_threads.argtypes = [ci]
+    L.orc_set_threads.restype = ci
 
 
 def _p(a):

@@ -34,6 +34,9 @@
 #include <cmath>
 #include <cstring>
 #include <cstdio>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef std::complex<double> cplx;
 
@@ -802,12 +805,19 @@ static void element_residual(const Oracle* o, const Level& L, int e, const S* qe
     }
 }
 
+// Element loops below may run on several host threads (OpenMP, when the
+// library is built with it and orc_set_threads asks for more than one): each
+// element's result depends only on frozen inputs and is written to its own
+// slots, so the results do not depend on the thread count.
 static void full_residual(const Oracle* o, const Level& L, const double* q, double* R) {
   int N = L.g.N, E = o->E;
   std::vector<double> tr;
   neighbour_traces(o, L, q, tr);
-  std::vector<double> qe(4 * N), Re(4 * N);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
   for (int e = 0; e < E; ++e) {
+    std::vector<double> qe(4 * N), Re(4 * N);
     for (int v = 0; v < 4; ++v)
       for (int p = 0; p < N; ++p) qe[v * N + p] = q[((size_t)v * E + e) * N + p];
     element_residual<double>(o, L, e, qe.data(), tr.data(), Re.data());
@@ -875,23 +885,30 @@ static int refresh_level(Oracle* o, int l) {
   neighbour_traces(o, L, L.q.data(), tr);
   L.lu.assign((size_t)E * n * n, 0.0);
   L.piv.assign((size_t)E * n, 0);
+  int singular = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : singular)
+#endif
   for (int e = 0; e < E; ++e) {
     double* Dm = &L.lu[(size_t)e * n * n];
     element_block(o, L, e, L.q.data(), tr.data(), o->dtau, Dm);
-    if (!lu_factor(n, Dm, &L.piv[(size_t)e * n])) return -4;
+    if (!lu_factor(n, Dm, &L.piv[(size_t)e * n])) singular |= 1;
   }
-  return 0;
+  return singular ? -4 : 0;
 }
 
 // Element-Jacobi sweep, eq. smoothing_element_jacobi with alpha_r = 1.
 static void smooth(Oracle* o, int l, int nsweep) {
   Level& L = o->lev[l];
   int N = L.g.N, n = 4 * N, E = o->E;
-  std::vector<double> x(n);
   L.F.resize((size_t)4 * E * N);
   for (int s = 0; s < nsweep; ++s) {
     level_F(o, l, L.q.data(), l == 0, l > 0, L.F.data());
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
     for (int e = 0; e < E; ++e) {
+      std::vector<double> x(n);
       for (int v = 0; v < 4; ++v)
         for (int p = 0; p < N; ++p) x[v * N + p] = L.F[((size_t)v * E + e) * N + p];
       lu_solve(n, &L.lu[(size_t)e * n * n], &L.piv[(size_t)e * n], x.data());
@@ -1039,6 +1056,18 @@ static int esdirk_tableau(int stages, double A[6][6], double b[6], double c[6]) 
 }
 
 extern "C" {
+
+// Host threads of the element loops (OpenMP builds only; 1 otherwise).
+// Returns the number of threads the loops will use.
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : 1);
+  return n > 0 ? n : 1;
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 int orc_esdirk(int stages, double* A, double* b, double* c) {
   double AA[6][6], bb[6], cc[6];

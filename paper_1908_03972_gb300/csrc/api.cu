@@ -129,6 +129,7 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
     return fail(PMG_EINVAL, "Pr must be finite and > 0 when mu > 0");
   for (int v = 0; v < 4; ++v)
     if (!std::isfinite(cfg->res_scale[v])) return fail(PMG_EINVAL, "res_scale must be finite");
+  if (!std::isfinite(cfg->copy_wait_s)) return fail(PMG_EINVAL, "copy_wait_s must be finite");
   int dev;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(PMG_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
@@ -154,6 +155,7 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   c.ph.kT = cfg->mu > 0.0 ? cfg->mu * c.ph.Cp / cfg->Pr : 0.0;
   for (int v = 0; v < 4; ++v) c.ph.nw[v] = cfg->res_scale[v] > 0.0 ? 1.0 / cfg->res_scale[v] : 1.0;
   for (int v = 0; v < 4; ++v) c.ph.qinf[v] = cfg->q_inf[v];
+  c.ph.wait_ns = cfg->copy_wait_s == 0.0 ? 1e9 : cfg->copy_wait_s < 0.0 ? -1.0 : std::min(cfg->copy_wait_s, 60.0) * 1e9;
   c.phw = make_physw(c.ph);
   esdirk_table(c, cfg->esdirk_order == 0 ? 3 : cfg->esdirk_order);
   if (dalloc(&c.d_scal, 4) != cudaSuccess || dalloc(&c.d_flag, 4) != cudaSuccess ||
@@ -294,7 +296,7 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
     PMG_CK(cudaMemset(L.q, 0, L.tot * 8));
     PMG_CK(cudaMemcpy(L.met, geo[l].met.data(), geo[l].met.size() * 8, cudaMemcpyHostToDevice));
     PMG_CK(cudaMemcpy(L.face, geo[l].face.data(), geo[l].face.size() * 8, cudaMemcpyHostToDevice));
-    L.xy_host = geo[l].xy;
+    c.xy_host[l] = geo[l].xy;
     maxblocks = std::max(maxblocks, residual_blocks_for(L.P, c.E));
   }
   for (int l = 0; l + 1 < c.cfg.n_levels; ++l) {
@@ -533,13 +535,26 @@ static pmg_status launch_vcycle(Ctx& c, bool refresh) {
   return PMG_OK;
 }
 
+static pmg_status wait_flag_status(Ctx& c) {
+  if (c.h_scal[1] == 0.0) return PMG_OK;
+  c.h_scal[1] = 0.0;
+  cudaMemsetAsync(c.d_scal + 1, 0, sizeof(double), c.stream);
+  return fail(PMG_ETIMEOUT, "a kernel's bounded wait for its bulk shared-memory copy gave up (it finished from "
+                            "global memory)");
+}
+
+// Reads the flag of the bounded bulk-copy waits (after the work queued so far).
+static pmg_status check_wait_flag(Ctx& c) {
+  PMG_CK(cudaMemcpyAsync(c.h_scal + 1, c.d_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  PMG_CK(cudaStreamSynchronize(c.stream));
+  return wait_flag_status(c);
+}
+
 static pmg_status read_norm(Ctx& c, double* out) {
   PMG_CK(cudaMemcpyAsync(c.h_scal, c.d_scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
   PMG_CK(cudaStreamSynchronize(c.stream));
-  if (c.h_scal[1] != 0.0) {
-    cudaMemsetAsync(c.d_scal + 1, 0, sizeof(double), c.stream);
-    return fail(PMG_ECUDA, "a kernel's wait for its bulk shared-memory copy timed out");
-  }
+  pmg_status ws = wait_flag_status(c);
+  if (ws) return ws;
   *out = std::sqrt(c.h_scal[0]);
   if (c.prof.on) prof_harvest(c);
   return PMG_OK;
@@ -569,7 +584,7 @@ static pmg_status check_singular(Ctx& c) {
   PMG_CK(cudaStreamSynchronize(c.stream));
   if (flag) {
     cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.stream);
-    return fail(PMG_ESINGULAR, "zero pivot in element block " + std::to_string(flag - 1));
+    return fail(PMG_ESINGULAR, "element block " + std::to_string(flag - 1) + " is singular to working precision (pivot not above eps^2)");
   }
   return PMG_OK;
 }
@@ -639,8 +654,8 @@ pmg_status pmg_point_coords(pmg_ctx* h, int level, double* xy) {
   if (!h || !xy) return fail(PMG_EINVAL, "null argument");
   pmg_status st = check_level(h->c, level);
   if (st) return st;
-  const LevelDev& L = h->c.lev[level];
-  memcpy(xy, L.xy_host.data(), L.xy_host.size() * 8);
+  const std::vector<double>& xyh = h->c.xy_host[level];
+  memcpy(xy, xyh.data(), xyh.size() * 8);
   return PMG_OK;
 }
 
@@ -913,6 +928,19 @@ pmg_status pmg_get_blocks(pmg_ctx* h, int level, double* D, int on_device) {
   return PMG_OK;
 }
 
+pmg_status pmg_set_blocks(pmg_ctx* h, int level, const double* D, int on_device) {
+  if (!h || !D) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  pmg_status st = check_level(c, level);
+  if (st) return st;
+  LevelDev& L = c.lev[level];
+  PMG_CK(copy_in(c, L.Dfull, D, (size_t)c.E * L.n * L.n, on_device));
+  PMG_CK(cudaStreamSynchronize(c.stream));
+  L.assembled = true;
+  L.factored = false;
+  return PMG_OK;
+}
+
 pmg_status pmg_factor_blocks(pmg_ctx* h, int level) {
   if (!h) return fail(PMG_EINVAL, "null argument");
   Ctx& c = h->c;
@@ -1018,8 +1046,7 @@ pmg_status pmg_vcycle(pmg_ctx* h, double dtau, int refresh, double* res_norm_out
     st = check_singular(c);
     if (st) return st;
   }
-  PMG_CK(cudaStreamSynchronize(c.stream));
-  return PMG_OK;
+  return check_wait_flag(c);
 }
 
 pmg_status pmg_stage_solve(pmg_ctx* h, int* iters, double* drop) {

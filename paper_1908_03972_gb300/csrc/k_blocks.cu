@@ -12,7 +12,10 @@
 //    row and column scales (exact in any precision) and inverts it by
 //    Gauss-Jordan elimination with partial pivoting in the working precision
 //    (FP64, or FP32 for the mixed-precision smoother).  The explicit inverse
-//    turns every smoothing sweep into a batched matrix-vector product.
+//    turns every smoothing sweep into a batched matrix-vector product.  The
+//    equilibrated rows have unit size, so a pivot that is not finite or not
+//    above eps^2 of the working precision marks a block that is singular to
+//    that precision: the element is flagged for the host (PMG_ESINGULAR).
 //  * apply: x = cs .* (inv(D^) (rs .* r)); each thread owns four consecutive
 //    rows and streams the column-major inverse with 16-byte (FP32) or
 //    2x16-byte (FP64) loads.  This stream is the smoother's HBM/L2 traffic.
@@ -158,6 +161,11 @@ __device__ __forceinline__ double pow2_inv_scale(double m) {
   return ldexp(1.0, -ex);
 }
 
+// Smallest pivot magnitude accepted: eps^2 of the working precision.
+template <class W> struct PivotFloor;
+template <> struct PivotFloor<float> { static constexpr double value = 1.1920928955078125e-07 * 1.1920928955078125e-07; };
+template <> struct PivotFloor<double> { static constexpr double value = 2.220446049250313e-16 * 2.220446049250313e-16; };
+
 template <class W>
 __global__ void __launch_bounds__(256) factor_kernel(int n, const double* __restrict__ Din, W* __restrict__ Dinv,
                                                      double* __restrict__ rs, double* __restrict__ cs,
@@ -209,7 +217,7 @@ __global__ void __launch_bounds__(256) factor_kernel(int n, const double* __rest
       if (tid == 0) {
         s_piv = bi;
         perm[k] = bi;
-        if (!(best > 0.0)) s_bad = 1;
+        if (!(best > PivotFloor<W>::value) || isinf(best)) s_bad = 1;
       }
     }
     __syncthreads();

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(64, 1) fused_sweep_kernel(
     }
   }
   __syncthreads();
-  const bool ok = mbar_wait0(&mbar);
+  const bool ok = mbar_wait0(&mbar, ph.wait_ns);
   if (!ok) *werr = 1.0;
   // phase 3: residual and level-system epilogue, thread (le, pt)
   {
@@ -236,6 +236,7 @@ __global__ void __launch_bounds__(64, 1) fused_sweep_kernel(
       }
     }
   }
+  if (!ok) mbar_drain0(&mbar);   // copies still in flight land before the CTA exits
 }
 
 // The same sweep in double-word arithmetic (gauge storage, the sweeps of
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(64, 1) fused_sweep_dw_kernel(
     }
   }
   __syncthreads();
-  const bool ok = mbar_wait0(&mbar);
+  const bool ok = mbar_wait0(&mbar, k.wait_ns);
   if (!ok) *werr = 1.0;
   // phase 3: divergence, DG correction and level-system epilogue
   if (own) {
@@ -449,6 +450,7 @@ __global__ void __launch_bounds__(64, 1) fused_sweep_dw_kernel(
       qout[v * plane + (size_t)e * N + pt] = sq[le][v][pt] + xv;
     }
   }
+  if (!ok) mbar_drain0(&mbar);   // copies still in flight land before the CTA exits
 }
 
 template <int P>

@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(256, 1) volume_kernel(int E, const double* q,
     }
   }
   __syncthreads();
-  const bool okF = APPLY ? mbar_wait0(&mbar[0]) : true;
+  const bool okF = APPLY ? mbar_wait0(&mbar[0], ph.wait_ns) : true;
   if (!okF) *werr = 1.0;
   if (active) {
     // face jumps: common (reference-direction) minus extrapolated flux polynomial
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(256, 1) volume_kernel(int E, const double* q,
     }
   }
   __syncthreads();
-  const bool okS = APPLY ? mbar_wait0(&mbar[1]) : true;
+  const bool okS = APPLY ? mbar_wait0(&mbar[1], ph.wait_ns) : true;
   if (!okS) *werr = 1.0;
   double ssq = 0.0;
   if (active) {
@@ -436,6 +436,9 @@ __global__ void __launch_bounds__(256, 1) volume_kernel(int E, const double* q,
       partial[blockIdx.x] = s;
     }
   }
+  // copies still in flight land before the CTA exits
+  if (!okF) mbar_drain0(&mbar[0]);
+  if (!okS) mbar_drain0(&mbar[1]);
 }
 
 __global__ void norm_final_kernel(const double* __restrict__ partial, int n, double* __restrict__ out) {

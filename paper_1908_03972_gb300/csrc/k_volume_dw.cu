@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256, 1) volume_apply_dw_kernel(
     }
   }
   __syncthreads();
-  const bool okF = mbar_wait0(&mbar[0]);
+  const bool okF = mbar_wait0(&mbar[0], k.wait_ns);
   if (!okF) *werr = 1.0;
   if (active) {
     for (int it = pt; it < 16 * n1; it += N) {
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256, 1) volume_apply_dw_kernel(
     }
   }
   __syncthreads();
-  const bool okS = mbar_wait0(&mbar[1]);
+  const bool okS = mbar_wait0(&mbar[1], k.wait_ns);
   if (!okS) *werr = 1.0;
   if (active) {
     const int i = pt % n1, j = pt / n1;
@@ -205,6 +205,9 @@ __global__ void __launch_bounds__(256, 1) volume_apply_dw_kernel(
       q[o] = q[o] + scaled_out<W>(acc[m], csc);
     }
   }
+  // copies still in flight land before the CTA exits
+  if (!okF) mbar_drain0(&mbar[0]);
+  if (!okS) mbar_drain0(&mbar[1]);
 }
 
 template <class W>

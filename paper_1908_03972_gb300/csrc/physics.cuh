@@ -23,6 +23,7 @@ struct Phys {
   double kT;         // heat conductivity mu Cp / Pr
   double nw[4];      // weights 1 / res_scale of the equations in the residual norm
   double qinf[4];    // free stream of far-field faces (p absolute, u, v, T)
+  double wait_ns;    // bound of the bulk-copy waits (< 0: give up at once)
 };
 
 // ---------------------------------------------------------------------------

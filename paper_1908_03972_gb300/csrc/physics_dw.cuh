@@ -18,6 +18,7 @@ struct PhysW {
   dw gamma, Cp, gm1, inv_gamma, inv_Cp, eps_min2;
   dw p_ref;     // gauge reference pressure of the device states
   dw inv_gm1;   // 1 / (gamma - 1)
+  double wait_ns;   // bound of the bulk-copy waits (< 0: give up at once)
 };
 
 // Double-word copies of a level's 1D operators (see OpTab).
@@ -36,6 +37,7 @@ inline PhysW make_physw(const Phys& ph) {
   k.eps_min2 = dw_const(ph.eps_min * ph.eps_min);
   k.p_ref = dw_const(ph.p_ref);
   k.inv_gm1 = dw_const(ph.inv_gm1);
+  k.wait_ns = ph.wait_ns;
   return k;
 }
 

@@ -91,7 +91,6 @@ struct LevelDev {
   double* rs = nullptr;        // E * n row scales
   double* cs = nullptr;        // E * n column scales
   bool assembled = false, factored = false;
-  std::vector<double> xy_host;
 };
 
 // Residual kernel epilogues.
@@ -129,6 +128,7 @@ struct Ctx {
   int* d_faces = nullptr;      // n_faces * 5
   double* d_dx = nullptr;      // E element sizes of the CFL form
   LevelDev lev[kMaxLevels];
+  std::vector<double> xy_host[kMaxLevels];   // solution point coordinates of each level
   XferTab xfer[kMaxLevels];
   // stage data (finest level)
   double* src = nullptr;

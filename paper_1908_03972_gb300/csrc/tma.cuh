@@ -5,10 +5,12 @@
 // A kernel issues its copies from one thread at entry and waits for them
 // where it first reads the data, so that the copies overlap the arithmetic
 // before that point.  Sizes and both addresses must be multiples of 16 bytes.
-// The wait gives up once kWaitNs nanoseconds of the global timer have passed
-// since its first unsuccessful poll (or after 2^30 polls); the caller then
-// records the failure in an error slot the host reads and uses the
-// global-memory copy of the data instead, so no thread hangs.
+// The wait gives up once its bound (wait_ns nanoseconds of the global timer,
+// counted from its first unsuccessful poll, or 2^30 polls) has passed; the
+// caller then records the failure in an error slot the host reads, uses the
+// global-memory copy of the data instead, and before it exits drains the
+// copies still in flight with mbar_drain0 (bounded by kWaitNs), so no thread
+// hangs and no copy lands in the shared memory of a finished CTA.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -44,9 +46,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                : "memory");
 }
 
-// Wait for phase 0 of the barrier; false once kWaitNs have passed since the
-// first unsuccessful poll.
-__device__ __forceinline__ bool mbar_wait0(unsigned long long* bar) {
+// Wait for phase 0 of the barrier; false once wait_ns have passed since the
+// first unsuccessful poll.  A negative wait_ns gives up without polling (a
+// diagnostic of the fallback path).
+__device__ __forceinline__ bool mbar_wait0(unsigned long long* bar, double wait_ns) {
+  if (wait_ns < 0.0) return false;
+  const unsigned long long limit = (unsigned long long)wait_ns;
   const unsigned a = smem_u32(bar);
   unsigned long long t0 = 0;
   for (unsigned i = 0; i < (1u << 30); ++i) {
@@ -59,10 +64,14 @@ __device__ __forceinline__ bool mbar_wait0(unsigned long long* bar) {
     if (ok) return true;
     const unsigned long long t = global_ns();
     if (i == 0) t0 = t;
-    else if (t - t0 > kWaitNs) return false;
+    else if (t - t0 > limit) return false;
   }
   return false;
 }
+
+// After a wait that gave up: wait (bounded by kWaitNs) for the copies still
+// in flight, so that they land before the CTA's shared memory is released.
+__device__ __forceinline__ void mbar_drain0(unsigned long long* bar) { (void)mbar_wait0(bar, (double)kWaitNs); }
 #endif
 
 }  // namespace pmg

@@ -17,8 +17,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libpmgfr.so")
 
 PMG_OK = 0
-PMG_EINVAL, PMG_ENOMEM, PMG_ECUDA, PMG_ESINGULAR, PMG_ENONFINITE, PMG_ENOTCONV, PMG_ESTATE = (
-    -1, -2, -3, -4, -5, -6, -8)
+PMG_EINVAL, PMG_ENOMEM, PMG_ECUDA, PMG_ESINGULAR, PMG_ENONFINITE, PMG_ENOTCONV, PMG_ETIMEOUT, PMG_ESTATE = (
+    -1, -2, -3, -4, -5, -6, -7, -8)
 PMG_PREC_FP64, PMG_PREC_FP32 = 0, 1
 PMG_FLUX_FP64, PMG_FLUX_DW_SMOOTH, PMG_FLUX_DW = 0, 1, 2
 
@@ -56,6 +56,7 @@ class pmg_config(ctypes.Structure):
         ("esdirk_order", ctypes.c_int),
         ("refresh_always", ctypes.c_int),
         ("flux_prec", ctypes.c_int),
+        ("copy_wait_s", ctypes.c_double),
     ]
 
 
@@ -104,6 +105,7 @@ def load():
         "pmg_stage_residual": ([vp, ci, vp, vp, ci], ci),
         "pmg_assemble_blocks": ([vp, ci, cd], ci),
         "pmg_get_blocks": ([vp, ci, vp, ci], ci),
+        "pmg_set_blocks": ([vp, ci, vp, ci], ci),
         "pmg_factor_blocks": ([vp, ci], ci),
         "pmg_apply_blocks": ([vp, ci, vp, vp, ci], ci),
         "pmg_restrict": ([vp, ci, vp, vp, ci], ci),
@@ -152,7 +154,7 @@ def make_config(P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutof
                 dtau_max=10.0, tol=1e-8, refresh_every=10, max_pseudo=2000, block_prec=PMG_PREC_FP64,
                 use_graph=1, p_gauge=0.0, mu=0.0, Pr=0.72, res_scale=(1.0, 1.0, 1.0, 1.0),
                 q_inf=(0.0, 0.0, 0.0, 0.0), cfl_mode=0, cfl_init=1e2, cfl_max=1e5,
-                esdirk_order=3, refresh_always=0, flux_prec=PMG_FLUX_DW_SMOOTH) -> pmg_config:
+                esdirk_order=3, refresh_always=0, flux_prec=PMG_FLUX_DW_SMOOTH, copy_wait_s=0.0) -> pmg_config:
     cfg = pmg_config()
     cfg.n_levels = len(P_levels)
     for l, (P, n) in enumerate(zip(P_levels, n_smooth)):
@@ -171,6 +173,7 @@ def make_config(P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutof
     cfg.esdirk_order = esdirk_order
     cfg.refresh_always = refresh_always
     cfg.flux_prec = flux_prec
+    cfg.copy_wait_s = copy_wait_s
     return cfg
 
 
@@ -244,6 +247,11 @@ def pmg_get_blocks(h, level, out):
     p, dev = _ptr(out, True)
     _check(load().pmg_get_blocks(h, level, p, dev))
     return out
+
+
+def pmg_set_blocks(h, level, D):
+    p, dev = _ptr(D)
+    _check(load().pmg_set_blocks(h, level, p, dev))
 
 
 def pmg_factor_blocks(h, level):

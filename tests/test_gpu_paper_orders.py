@@ -20,7 +20,15 @@ two decimals and does not define its error norm (here the discrete L2 norm
 with the Gauss weights), which can move the third.  Measured: 4.369 / 3.913
 (P^3) and 4.720 / 4.230 (P^4) against 4.37 / 3.91 and 4.72 / 4.23.
 
-Time refinement (Table 1), opt-in (about 15 GPU-minutes; set PMG_RUN_TABLE1=1):
+Time refinement (Table 1), reduced form run by default: ESDIRK3 alone, the
+same P^5 50^2 mesh and P{5-3-1}, I{20-20-40}, stages to a 1e-6 drop, but over
+a tenth of the period (t_end = 2) with dt = t~/100, t~/200, t~/400 (10, 20 and
+40 steps).  Over the shorter interval the temporal error is a tenth of the
+printed one and still far above the spatial error of P^5 on 50^2; the rates
+must reproduce Table 1's ESDIRK3 velocity orders (2.73, 2.94) to 0.15, the
+margin allowing for the shorter accumulation of the error.
+
+Time refinement (Table 1), full form opt-in (about 15 GPU-minutes; set PMG_RUN_TABLE1=1):
 P^5 on a 50^2 mesh of the same square, P{5-3-1}, I{20-20-40}, one period
 t~ = 20 with ESDIRK2 and ESDIRK3 at dt = t~/100, t~/200, t~/400 and ESDIRK4 at
 t~/40, t~/80, t~/120, stages to a 1e-6 drop of the scaled norm.  The velocity
@@ -82,7 +90,7 @@ def test_table2_velocity_orders(P, levels, key):
         assert abs(ours - theirs) <= 0.05, (orders, paper, err)
 
 
-def _time_error(order, n_steps):
+def _time_error(order, n_steps, t_end=20.0):
     from paper_1908_03972_gb300 import pmgfr
     nodes, nbr = W.periodic_box(50, 50, -10.0, 10.0, -10.0, 10.0, Ng=1)
     gpu = pmgfr.Solver(nodes, nbr, [5, 3, 1], [20, 20, 40], Ma_inf=0.005, tol=1e-6, dtau_init=0.01, dtau_max=10.0,
@@ -92,11 +100,11 @@ def _time_error(order, n_steps):
         xy = gpu.coords()
         gpu.set_state(W.isentropic_vortex(xy, center=(0.0, 0.0), period=(20.0, 20.0)))
         for _ in range(n_steps):
-            pmgfr.pmg_esdirk_step(gpu.h, 20.0 / n_steps)
+            pmgfr.pmg_esdirk_step(gpu.h, t_end / n_steps)
         q = gpu.get_state()
     finally:
         gpu.close()
-    qe = W.isentropic_vortex(xy, t=20.0, center=(0.0, 0.0), period=(20.0, 20.0))
+    qe = W.isentropic_vortex(xy, t=t_end, center=(0.0, 0.0), period=(20.0, 20.0))
     _, w = np.polynomial.legendre.leggauss(6)
     wJ = np.outer(w, w).reshape(-1) * (10.0 / 50) ** 2
     return math.sqrt(float((wJ[None, :] * (q[1] - qe[1]) ** 2).sum()))
@@ -112,3 +120,13 @@ def test_table1_velocity_orders(order, steps, key):
     orders = [math.log(err[i] / err[i + 1]) / math.log(steps[i + 1] / steps[i]) for i in range(2)]
     for ours, theirs in zip(orders, paper):
         assert abs(ours - theirs) <= 0.05, (orders, paper, err)
+
+
+def test_table1_esdirk3_orders_reduced():
+    paper = json.load(open(GOLDEN))["esdirk3_time_orders"]["u"]
+    steps = (10, 20, 40)   # dt = 0.2, 0.1, 0.05 = t~/100, t~/200, t~/400 up to t = 2
+    err = [_time_error(3, n, t_end=2.0) for n in steps]
+    orders = [math.log(err[i] / err[i + 1]) / math.log(steps[i + 1] / steps[i]) for i in range(2)]
+    print(f"Table 1 reduced (ESDIRK3, t = 2): errors {err}, orders {orders}, paper {paper}")
+    for ours, theirs in zip(orders, paper):
+        assert abs(ours - theirs) <= 0.15, (orders, paper, err)

@@ -89,10 +89,36 @@ def _mesh(name):
     return W.periodic_box(*m["n"], Ng=m["Ng"], perturb=m["perturb"]), m["Ng"]
 
 
+def _plain_per_var(a, b):
+    """max|a_v - b_v| / max|b_v| per equation (0 where b_v vanishes and a_v = b_v)."""
+    out = []
+    for v in range(4):
+        d, m = np.abs(a[v] - b[v]).max(), np.abs(b[v]).max()
+        out.append(d / m if m > 0 else (0.0 if d == 0 else np.inf))
+    return np.array(out)
+
+
+def _oracle_resummed(nodes, nbr, Ng, P, q):
+    """The oracle's residual with every element's local numbering turned by 180
+    degrees: the same discretisation with each line sum taken in the opposite
+    order, mapped back to the original numbering."""
+    E = nodes.shape[0]
+    fn, fb = W.flip_elements(nodes, nbr, range(E), Ng)
+    orf = O.Oracle(fn, fb, Ng, [P], [1])
+    return orf.residual(np.ascontiguousarray(q[:, :, ::-1]))[:, :, ::-1]
+
+
 @pytest.mark.parametrize("gauge", GAUGES)
 @pytest.mark.parametrize("name", list(MESHES))
 @pytest.mark.parametrize("P", [0, 1, 2, 3, 4, 5])
 def test_residual_parity(name, P, gauge):
+    """Two measures.  (1) The padded bound of the module docstring.  (2) The
+    plain measure max|R_gpu - R_orc|/max|R_orc,v| of the 1e-10 relative residual tolerance: it
+    must hold where the oracle itself resolves 1e-10, and elsewhere stay within
+    four times the oracle's own spread under re-summation (at Ma = 0.005 with
+    p ~ 5.7e4 the momentum residual carries the rounding of the pressure
+    terms, and re-summing the oracle moves it by up to ~9e-10 on this
+    measure)."""
     (nodes, nbr), Ng = _mesh(name)
     if gauge and P < Ng:
         pytest.skip("gauge storage needs P >= geometry order")
@@ -104,6 +130,11 @@ def test_residual_parity(name, P, gauge):
         Ro = orc.residual(q)
         Rg = gpu.residual(q)
         assert _rel_per_var(Rg, Ro, orc) <= 1e-10
+        spread = _plain_per_var(_oracle_resummed(nodes, nbr, Ng, P, q), Ro)
+        plain = _plain_per_var(Rg, Ro)
+        print(f"plain measure {name} P={P} gauge={bool(gauge)}: gpu " +
+              " ".join(f"{x:.2e}" for x in plain) + " | oracle re-summed " + " ".join(f"{x:.2e}" for x in spread))
+        assert (plain <= np.maximum(1e-10, 4.0 * spread)).all(), (plain, spread)
         # coordinates of the solution points agree with the oracle's map
         assert np.abs(gpu.coords() - orc.coords()).max() <= 1e-12
     finally:

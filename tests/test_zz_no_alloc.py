@@ -26,15 +26,21 @@ def setup():
     return torch, pmgfr
 
 
-@pytest.mark.parametrize("gauge", [0.0, W.freestream_T(0.005)])
-def test_static_residual_matches_regular_entry_point(setup, gauge):
+# (p_gauge, mu, Ma_inf): absolute and gauge pressure storage of the Euler
+# residual, and the viscous residual, whose broken gradients and face jumps
+# also live in the static scratch
+CASES = [(0.0, 0.0, 0.005), (W.freestream_T(0.005), 0.0, 0.005), (0.0, 0.02, 0.3)]
+
+
+@pytest.mark.parametrize("gauge,mu,Ma", CASES)
+def test_static_residual_matches_regular_entry_point(setup, gauge, mu, Ma):
     torch, pmgfr = setup
     nodes, nbr = W.periodic_box(24, 20, Ng=1)
-    s = pmgfr.Solver(nodes, nbr, [3, 2, 1, 0], [1, 1, 1, 1], p_gauge=gauge)
+    s = pmgfr.Solver(nodes, nbr, [3, 2, 1, 0], [1, 1, 1, 1], p_gauge=gauge, mu=mu, Ma_inf=Ma)
     try:
         dev = torch.device("cuda", torch.cuda.current_device())
         for level in range(4):
-            q = W.isentropic_vortex(s.coords(level), center=(4.0, 6.0))
+            q = W.isentropic_vortex(s.coords(level), center=(4.0, 6.0), Ma_inf=Ma)
             q_dev = torch.from_numpy(np.ascontiguousarray(q)).to(dev)
             ref = torch.empty_like(q_dev)
             pmgfr.pmg_residual(s.h, level, q_dev, ref)
@@ -60,7 +66,8 @@ def test_static_residual_matches_regular_entry_point(setup, gauge):
 
 def test_static_residual_rejects_oversized_levels(setup):
     torch, pmgfr = setup
-    # 4 E N + 16 E (P+1) doubles must fit in 2^21: E = 36864 at P = 3 needs 2.95e6
+    # 4 E N + 16 E (P+1) doubles must fit in 2^21 = 2.10e6: E = 36864 at P = 3
+    # needs 2,359,296 + 2,359,296 = 4.72e6
     nodes, nbr = W.periodic_box(192, 192, Ng=1)
     s = pmgfr.Solver(nodes, nbr, [3], [1])
     try:
