@@ -7,6 +7,8 @@ arithmetics of the element-Jacobi P-multigrid V-cycle:
                 double-word (float-float) arithmetic on every level; the
                 finest level's residual (stopping norm, restricted defect)
                 in binary64.  The headline value.
+  mixed_bf16    as mixed, with BF16 block inverses applied with FP32
+                accumulation.
   mixed_f64res  FP32 blocks, binary64 residual everywhere.
   fp64          FP64 blocks, binary64 residual everywhere.
 
@@ -298,6 +300,7 @@ def run_ours(args, wl, world, rank, local):
     # The three legs: (block precision, residual arithmetic of the sweeps)
     LEGS = {
         "mixed": (pmgfr.PMG_PREC_FP32, pmgfr.PMG_FLUX_DW_SMOOTH),
+        "mixed_bf16": (pmgfr.PMG_PREC_BF16R, pmgfr.PMG_FLUX_DW_SMOOTH),
         "mixed_f64res": (pmgfr.PMG_PREC_FP32, pmgfr.PMG_FLUX_FP64),
         "fp64": (pmgfr.PMG_PREC_FP64, pmgfr.PMG_FLUX_FP64),
     }
@@ -377,7 +380,7 @@ def run_ours(args, wl, world, rank, local):
     # Other legs: the same physical steps from the same warmed state (one
     # untimed step first for their own graph captures, then reset), K2 steps.
     k2 = min(args.steps, args.other_steps)
-    legs = [] if args.skip_fp64 else ["mixed_f64res", "fp64"]
+    legs = [] if args.skip_fp64 else ["mixed_bf16", "mixed_f64res", "fp64"]
     diffs = {}
     for leg in legs:
         s = make(leg)
@@ -492,10 +495,12 @@ def run_ours(args, wl, world, rank, local):
                        "residual": ("binary64 for the finest level's residual (stopping norm, restricted defect, "
                                     "pmg_residual); double-word (float-float, ~2^-48) in every smoothing sweep's "
                                     "residual-and-update on every level and in the coarse levels' residuals"),
+                       "mixed_bf16_leg": "BF16 block inverses applied with FP32 accumulation, residuals as mixed",
                        "mixed_f64res_leg": "FP32 blocks, binary64 residual everywhere",
                        "fp64_leg": "FP64 blocks, binary64 residual everywhere",
                        "l2": "flushed (256 MiB write) before every timed step", "parallelism": "replicas"},
             "mixed": {k: v for k, v in mixed.items() if k not in ("clocks",)},
+            "mixed_bf16": {k: v for k, v in results.get("mixed_bf16", {}).items() if k not in ("clocks",)},
             "mixed_f64res": {k: v for k, v in results.get("mixed_f64res", {}).items() if k not in ("clocks",)},
             "fp64": {k: v for k, v in results.get("fp64", {}).items() if k not in ("clocks",)},
             "solution_diff_after_%d_steps" % k2: diffs,

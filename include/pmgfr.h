@@ -48,9 +48,19 @@ typedef enum {
   PMG_ESTATE = -8      /* call needs data that was not set (mesh, stage) */
 } pmg_status;
 
+/* Precision of the element-Jacobi smoother's blocks (Section 2.4, eq.
+ * smoothing_element_jacobi: the smoother needs only an approximate inverse).
+ * Every sweep applies the inverse to the level-system residual F - S formed
+ * in the residual arithmetic (flux_prec) and adds the result to the binary64
+ * state, so each sweep is one step of a defect correction whose fixed point
+ * is that of F alone: the block precision changes the contraction, not the
+ * converged state. */
 typedef enum {
   PMG_PREC_FP64 = 0, /* blocks factored and applied in FP64 */
-  PMG_PREC_FP32 = 1  /* blocks equilibrated, factored and applied in FP32 */
+  PMG_PREC_FP32 = 1, /* blocks equilibrated, factored and applied in FP32 */
+  PMG_PREC_BF16R = 2 /* blocks equilibrated and factored in FP32, the inverse
+                        stored in BF16 (half the bytes every sweep reads) and
+                        applied with FP32 accumulation */
 } pmg_prec;
 
 /* Arithmetic of the residual.  Double-word (float-float) arithmetic runs the
@@ -148,6 +158,15 @@ typedef struct {
                      return PMG_ETIMEOUT.  A negative value makes every such
                      wait give up at once: a diagnostic that runs the
                      global-memory path and the PMG_ETIMEOUT report. */
+  int device_loop; /* 1 (with use_graph = 1): pmg_stage_solve and the stages
+                     of pmg_esdirk_step run their pseudo-iterations as one
+                     CUDA graph whose conditional WHILE node repeats {a
+                     one-thread controller applying the SER, refresh and stop
+                     rules; the V-cycle with or without smoother rebuild},
+                     with one host synchronisation per stage instead of one
+                     per V-cycle.  0: the host runs the loop.  Both follow the
+                     same rules; dtau may differ in the last bits (device
+                     pow). */
 } pmg_config;
 
 /* Boundary types, in the second slot of a boundary face's neighbour entry

@@ -19,7 +19,8 @@ LIB = os.path.join(OUT_DIR, "libpmgfr.so")
 BUILD_DIR = os.path.join(HERE, "_build", platform.machine())
 ARCH_STAMP = os.path.join(OUT_DIR, ".arch")
 
-CUDA_SOURCES = ["k_residual.cu", "k_volume_dw.cu", "k_blocks.cu", "k_misc.cu", "k_fused.cu", "k_viscous.cu", "api.cu"]
+CUDA_SOURCES = ["k_residual.cu", "k_volume_dw.cu", "k_blocks.cu", "k_misc.cu", "k_fused.cu", "k_viscous.cu", "k_loop.cu",
+                "api.cu"]
 CXX_SOURCES = ["host_tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

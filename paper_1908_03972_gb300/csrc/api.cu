@@ -115,7 +115,7 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
     if (l > 0 && cfg->P[l] >= cfg->P[l - 1]) return fail(PMG_EINVAL, "P levels must decrease");
     if (cfg->n_smooth[l] < 1) return fail(PMG_EINVAL, "smoothing counts must be >= 1");
   }
-  if (cfg->block_prec != PMG_PREC_FP64 && cfg->block_prec != PMG_PREC_FP32)
+  if (cfg->block_prec != PMG_PREC_FP64 && cfg->block_prec != PMG_PREC_FP32 && cfg->block_prec != PMG_PREC_BF16R)
     return fail(PMG_EINVAL, "unknown block precision");
   if (cfg->flux_prec != PMG_FLUX_FP64 && cfg->flux_prec != PMG_FLUX_DW_SMOOTH && cfg->flux_prec != PMG_FLUX_DW)
     return fail(PMG_EINVAL, "unknown flux precision");
@@ -130,6 +130,9 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   for (int v = 0; v < 4; ++v)
     if (!std::isfinite(cfg->res_scale[v])) return fail(PMG_EINVAL, "res_scale must be finite");
   if (!std::isfinite(cfg->copy_wait_s)) return fail(PMG_EINVAL, "copy_wait_s must be finite");
+  if (cfg->device_loop != 0 && cfg->device_loop != 1) return fail(PMG_EINVAL, "device_loop must be 0 or 1");
+  if (cfg->max_pseudo < 0) return fail(PMG_EINVAL, "max_pseudo must be >= 0");
+  if (cfg->refresh_every < 1) return fail(PMG_EINVAL, "refresh_every must be >= 1");
   int dev;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(PMG_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
@@ -158,9 +161,13 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   c.ph.wait_ns = cfg->copy_wait_s == 0.0 ? 1e9 : cfg->copy_wait_s < 0.0 ? -1.0 : std::min(cfg->copy_wait_s, 60.0) * 1e9;
   c.phw = make_physw(c.ph);
   esdirk_table(c, cfg->esdirk_order == 0 ? 3 : cfg->esdirk_order);
+  const size_t nhist = 2 * ((size_t)cfg->max_pseudo + 1);
   if (dalloc(&c.d_scal, 4) != cudaSuccess || dalloc(&c.d_flag, 4) != cudaSuccess ||
       dalloc(&c.d_dtau, 1) != cudaSuccess || cudaMallocHost((void**)&c.h_scal, 8 * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost((void**)&c.h_dtau, sizeof(double)) != cudaSuccess) {
+      cudaMallocHost((void**)&c.h_dtau, sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&c.d_loop, sizeof(LoopState)) != cudaSuccess ||
+      cudaMallocHost((void**)&c.h_loop, sizeof(LoopState)) != cudaSuccess || dalloc(&c.d_hist, nhist) != cudaSuccess ||
+      cudaMallocHost((void**)&c.h_hist, nhist * sizeof(double)) != cudaSuccess) {
     pmg_destroy(h);
     return fail(PMG_ENOMEM, "device allocation failed");
   }
@@ -179,6 +186,11 @@ void pmg_destroy(pmg_ctx* h) {
   cudaStreamSynchronize(c.stream);
   for (int g = 0; g < 2; ++g)
     if (c.graph[g]) cudaGraphExecDestroy(c.graph[g]);
+  if (c.loop_exec) cudaGraphExecDestroy(c.loop_exec);
+  if (c.d_loop) cudaFree(c.d_loop);
+  if (c.h_loop) cudaFreeHost(c.h_loop);
+  if (c.d_hist) cudaFree(c.d_hist);
+  if (c.h_hist) cudaFreeHost(c.h_hist);
   for (int l = 0; l < kMaxLevels; ++l) free_level(c.lev[l]);
   double** ptrs[] = {&c.src, &c.qn, &c.qcn, &c.d_partial, &c.d_scal, &c.d_tmp0, &c.d_tmp1, &c.d_dtau, &c.d_dx};
   for (double** p : ptrs) { if (*p) cudaFree(*p); *p = nullptr; }
@@ -245,7 +257,7 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
   PMG_CK(cudaMemcpy(c.d_faces, fbuf.data(), sizeof(int) * fbuf.size(), cudaMemcpyHostToDevice));
   size_t maxtot = 0;
   int maxblocks = 1;
-  size_t wbytes = c.cfg.block_prec == PMG_PREC_FP64 ? 8 : 4;
+  size_t wbytes = c.cfg.block_prec == PMG_PREC_FP64 ? 8 : c.cfg.block_prec == PMG_PREC_BF16R ? 2 : 4;
   for (int l = 0; l < c.cfg.n_levels; ++l) {
     LevelDev& L = c.lev[l];
     const Ref1D& r = refs[l];
@@ -517,7 +529,7 @@ static pmg_status launch_vcycle(Ctx& c, bool refresh) {
     return PMG_OK;
   }
   int g = refresh ? 1 : 0;
-  if (!c.graph[g] || c.graph_inv_odt[g] != 1.0 / c.omega_dt) {
+  if (!c.graph[g] || c.graph_inv_odt[g] != 1.0 / c.omega_dt || c.graph_split[g] != (int)c.split_stage) {
     if (c.graph[g]) { cudaGraphExecDestroy(c.graph[g]); c.graph[g] = nullptr; }
     cudaGraph_t graph;
     PMG_CK(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
@@ -530,6 +542,7 @@ static pmg_status launch_vcycle(Ctx& c, bool refresh) {
     cudaGraphDestroy(graph);
     if (ie != cudaSuccess) return fail(PMG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
     c.graph_inv_odt[g] = 1.0 / c.omega_dt;
+    c.graph_split[g] = (int)c.split_stage;
   }
   PMG_CK(cudaGraphLaunch(c.graph[g], c.stream));
   return PMG_OK;
@@ -589,12 +602,150 @@ static pmg_status check_singular(Ctx& c) {
   return PMG_OK;
 }
 
+// ------------------------------------------------------ device-side stage loop
+// The graph: WHILE(h_loop) { controller -> IF(h_refresh) { V-cycle with
+// smoother rebuild } -> IF(h_plain) { V-cycle } }.  The V-cycle bodies are
+// captured from the same launch sequence as the host loop's graphs, for the
+// current omega dt and stage form.
+static pmg_status build_loop_graph(Ctx& c) {
+  if (c.loop_exec) { cudaGraphExecDestroy(c.loop_exec); c.loop_exec = nullptr; }
+  cudaGraph_t g = nullptr;
+  PMG_CK(cudaGraphCreate(&g, 0));
+  struct GraphGuard {
+    cudaGraph_t g;
+    ~GraphGuard() { if (g) cudaGraphDestroy(g); }
+  } guard{g};
+  cudaGraphConditionalHandle h_loop, h_refresh, h_plain;
+  PMG_CK(cudaGraphConditionalHandleCreate(&h_loop, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams wp = {};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = h_loop;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  PMG_CK(cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  PMG_CK(cudaGraphConditionalHandleCreate(&h_refresh, body, 0, cudaGraphCondAssignDefault));
+  PMG_CK(cudaGraphConditionalHandleCreate(&h_plain, body, 0, cudaGraphCondAssignDefault));
+  // controller node, captured alone into the body
+  LoopParams prm;
+  prm.tol = c.cfg.tol;
+  prm.refresh_every = c.cfg.refresh_every;
+  prm.refresh_always = c.cfg.refresh_always;
+  prm.max_pseudo = c.cfg.max_pseudo;
+  const int mp1 = c.cfg.max_pseudo + 1;
+  PMG_CK(cudaStreamBeginCaptureToGraph(c.stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  launch_loop_controller(c.d_loop, c.d_scal, c.d_flag, c.d_dtau, c.d_hist, c.d_hist + mp1, prm, h_loop, h_refresh,
+                         h_plain, c.stream);
+  {
+    cudaError_t le = cudaGetLastError();
+    cudaGraph_t got = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(c.stream, &got);
+    if (le != cudaSuccess) return fail(PMG_ECUDA, std::string("loop capture launch: ") + cudaGetErrorString(le));
+    if (ee != cudaSuccess) return fail(PMG_ECUDA, std::string("loop capture: ") + cudaGetErrorString(ee));
+  }
+  cudaGraphNode_t ctl;
+  size_t nn = 1;
+  PMG_CK(cudaGraphGetNodes(body, &ctl, &nn));
+  if (nn != 1) return fail(PMG_ECUDA, "loop graph: the controller capture did not give one node");
+  cudaGraphNode_t prev = ctl;
+  for (int r = 1; r >= 0; --r) {   // IF refresh, then IF plain
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = r ? h_refresh : h_plain;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t inode;
+    PMG_CK(cudaGraphAddNode(&inode, body, &prev, nullptr, 1, &ip));
+    cudaGraph_t vbody = ip.conditional.phGraph_out[0];
+    PMG_CK(cudaStreamBeginCaptureToGraph(c.stream, vbody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    vcycle_level(c, 0, r == 1);
+    cudaError_t le = cudaGetLastError();
+    cudaGraph_t got = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(c.stream, &got);
+    if (le != cudaSuccess) return fail(PMG_ECUDA, std::string("V-cycle capture launch: ") + cudaGetErrorString(le));
+    if (ee != cudaSuccess) return fail(PMG_ECUDA, std::string("V-cycle capture: ") + cudaGetErrorString(ee));
+    prev = inode;
+  }
+  cudaError_t ie = cudaGraphInstantiate(&c.loop_exec, g, 0);
+  if (ie != cudaSuccess) {
+    c.loop_exec = nullptr;
+    return fail(PMG_ECUDA, std::string("loop graph instantiate: ") + cudaGetErrorString(ie));
+  }
+  c.loop_inv_odt = 1.0 / c.omega_dt;
+  c.loop_split = (int)c.split_stage;
+  return PMG_OK;
+}
+
+// The stage's pseudo-iterations as one graph launch (cfg.device_loop); the
+// initial residual norm is in d_scal[0].  One synchronisation at the end reads
+// the loop state and the norm / dtau history.
+static pmg_status stage_solve_device(Ctx& c, double dtau_init, double dtau_max, int* iters, double* drop,
+                                     int* n_refresh) {
+  if (!c.loop_exec || c.loop_inv_odt != 1.0 / c.omega_dt || c.loop_split != (int)c.split_stage) {
+    pmg_status st = build_loop_graph(c);
+    if (st) return st;
+  }
+  LoopState& h = *c.h_loop;
+  PMG_CK(cudaStreamSynchronize(c.stream));   // the pinned mirror is free to rewrite
+  memset(&h, 0, sizeof(h));
+  h.dtau = dtau_init;
+  h.dtau_max = dtau_max;
+  h.status = LOOP_RUNNING;
+  PMG_CK(cudaMemcpyAsync(c.d_loop, &h, sizeof(LoopState), cudaMemcpyHostToDevice, c.stream));
+  PMG_CK(cudaGraphLaunch(c.loop_exec, c.stream));
+  const size_t mp1 = (size_t)c.cfg.max_pseudo + 1;
+  PMG_CK(cudaMemcpyAsync(&h, c.d_loop, sizeof(LoopState), cudaMemcpyDeviceToHost, c.stream));
+  PMG_CK(cudaMemcpyAsync(c.h_hist, c.d_hist, 2 * mp1 * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  PMG_CK(cudaMemcpyAsync(c.h_scal + 1, c.d_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+  PMG_CK(cudaStreamSynchronize(c.stream));
+  const int nrec = std::min(h.iters, c.cfg.max_pseudo) + 1;
+  for (int k = 0; k < nrec; ++k) {
+    c.hist_norm.push_back(c.h_hist[k]);
+    c.hist_dtau.push_back(c.h_hist[mp1 + k]);
+  }
+  if (n_refresh) *n_refresh += h.n_refresh;
+  if (iters) *iters = h.iters;
+  const double nm = h.final_norm, n0 = h.n0;
+  switch (h.status) {
+    case LOOP_CONVERGED:
+      if (drop) *drop = n0 > 0 ? nm / n0 : 0.0;
+      return PMG_OK;
+    case LOOP_NONFINITE:
+      if (drop) *drop = nm;
+      return fail(PMG_ENONFINITE, "non-finite residual norm");
+    case LOOP_SINGULAR:
+      if (drop) *drop = n0 > 0 ? nm / n0 : nm;
+      return check_singular(c);
+    case LOOP_TIMEOUT:
+      if (drop) *drop = n0 > 0 ? nm / n0 : nm;
+      return wait_flag_status(c);
+    case LOOP_NOTCONV:
+      if (drop) *drop = n0 > 0 ? nm / n0 : nm;
+      return fail(PMG_ENOTCONV, "stage not converged within max_pseudo V-cycles");
+    default:
+      return fail(PMG_ECUDA, "device stage loop ended in an unknown state");
+  }
+}
+
 // Pseudo-transient continuation of the current stage (Section 2.4).
 static pmg_status stage_solve(Ctx& c, int* iters, double* drop, int* n_refresh) {
   if (!c.F0_valid) {
     system_residual(c, 0, true);
     PMG_CK_LAUNCH();
     c.F0_valid = true;
+  }
+  if (c.cfg.device_loop && c.cfg.use_graph && !c.prof.on) {
+    double dtau_init = c.cfg.dtau_init, dtau_max = c.cfg.dtau_max;
+    if (c.cfg.cfl_mode) {
+      double dm;
+      pmg_status st = compute_dtau_min(c, &dm);
+      if (st) return st;
+      if (!(dm > 0.0) || !std::isfinite(dm)) return fail(PMG_ENONFINITE, "dtau_min is not a positive number");
+      dtau_init = c.cfg.cfl_init * dm;
+      dtau_max = c.cfg.cfl_max * dm;
+    }
+    return stage_solve_device(c, dtau_init, dtau_max, iters, drop, n_refresh);
   }
   double nm;
   pmg_status st = read_norm(c, &nm);

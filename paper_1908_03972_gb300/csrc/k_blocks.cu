@@ -170,9 +170,10 @@ template <class W>
 __global__ void __launch_bounds__(256) factor_kernel(int n, const double* __restrict__ Din, W* __restrict__ Dinv,
                                                      double* __restrict__ rs, double* __restrict__ cs,
                                                      int* __restrict__ flag) {
+  using T = typename Blk<W>::acc;   // elimination arithmetic (FP32 for BF16 storage)
   extern __shared__ unsigned char smem_raw[];
-  W* A = reinterpret_cast<W*>(smem_raw);                       // n * n, row-major
-  W* colk = A + n * n;                                          // n
+  T* A = reinterpret_cast<T*>(smem_raw);                       // n * n, row-major
+  T* colk = A + n * n;                                          // n
   int* perm = reinterpret_cast<int*>(colk + n);                 // n
   double* sr = reinterpret_cast<double*>(((uintptr_t)(perm + n) + 7) & ~(uintptr_t)7);   // n
   double* sc = sr + n;                                          // n
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(256) factor_kernel(int n, const double* __rest
   __syncthreads();
   for (int t = tid; t < n * n; t += nt) {
     int i = t / n, j = t - i * n;
-    A[t] = (W)(D[t] * sr[i] * sc[j]);
+    A[t] = (T)(D[t] * sr[i] * sc[j]);
   }
   __syncthreads();
   // Gauss-Jordan with partial pivoting, in place
@@ -217,16 +218,16 @@ __global__ void __launch_bounds__(256) factor_kernel(int n, const double* __rest
       if (tid == 0) {
         s_piv = bi;
         perm[k] = bi;
-        if (!(best > PivotFloor<W>::value) || isinf(best)) s_bad = 1;
+        if (!(best > PivotFloor<T>::value) || isinf(best)) s_bad = 1;
       }
     }
     __syncthreads();
     const int p = s_piv;
     if (p != k)
-      for (int j = tid; j < n; j += nt) { W t = A[k * n + j]; A[k * n + j] = A[p * n + j]; A[p * n + j] = t; }
+      for (int j = tid; j < n; j += nt) { T t = A[k * n + j]; A[k * n + j] = A[p * n + j]; A[p * n + j] = t; }
     __syncthreads();
-    W piv = A[k * n + k];
-    W ipiv = (W)1 / piv;
+    T piv = A[k * n + k];
+    T ipiv = (T)1 / piv;
     __syncthreads();
     for (int j = tid; j < n; j += nt) A[k * n + j] = (j == k) ? ipiv : A[k * n + j] * ipiv;
     for (int i = tid; i < n; i += nt) colk[i] = A[i * n + k];
@@ -234,7 +235,7 @@ __global__ void __launch_bounds__(256) factor_kernel(int n, const double* __rest
     for (int t = tid; t < n * n; t += nt) {
       int i = t / n, j = t - i * n;
       if (i == k) continue;
-      W f = colk[i];
+      T f = colk[i];
       if (j == k) A[t] = -f * A[k * n + k];
       else A[t] -= f * A[k * n + j];
     }
@@ -244,14 +245,14 @@ __global__ void __launch_bounds__(256) factor_kernel(int n, const double* __rest
   for (int k = n - 1; k >= 0; --k) {
     int p = perm[k];
     if (p != k)
-      for (int i = tid; i < n; i += nt) { W t = A[i * n + k]; A[i * n + k] = A[i * n + p]; A[i * n + p] = t; }
+      for (int i = tid; i < n; i += nt) { T t = A[i * n + k]; A[i * n + k] = A[i * n + p]; A[i * n + p] = t; }
     __syncthreads();
   }
   // store column-major: Dinv[e][col][row]
   W* out = Dinv + (size_t)e * n * n;
   for (int t = tid; t < n * n; t += nt) {
     int col = t / n, row = t - col * n;
-    out[t] = A[row * n + col];
+    out[t] = (W)A[row * n + col];
   }
   for (int i = tid; i < n; i += nt) {
     rs[(size_t)e * n + i] = sr[i];
@@ -270,6 +271,9 @@ void launch_factor(const Ctx& c, LevelDev& L, int prec, int* flag, cudaStream_t 
   int n = L.n;
   if (prec == PMG_PREC_FP64)
     factor_kernel<double><<<c.E, 256, factor_smem(n, 8), s>>>(n, L.Dfull, (double*)L.Dinv, L.rs, L.cs, flag);
+  else if (prec == PMG_PREC_BF16R)
+    factor_kernel<__nv_bfloat16><<<c.E, 256, factor_smem(n, 4), s>>>(n, L.Dfull, (__nv_bfloat16*)L.Dinv, L.rs,
+                                                                       L.cs, flag);
   else
     factor_kernel<float><<<c.E, 256, factor_smem(n, 4), s>>>(n, L.Dfull, (float*)L.Dinv, L.rs, L.cs, flag);
 }
@@ -282,6 +286,9 @@ cudaError_t prepare_kernels(const Ctx& c) {
   cudaError_t e = cudaFuncSetAttribute(factor_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)factor_smem(nmax, 8));
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(factor_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)factor_smem(nmax, 4));
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(factor_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)factor_smem(nmax, 4));
 }
@@ -292,6 +299,14 @@ template <> struct Vec4<float> {
   __device__ static inline void load(const float* p, float o[4]) {
     float4 t = __ldg(reinterpret_cast<const float4*>(p));
     o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+  }
+};
+template <> struct Vec4<__nv_bfloat16> {
+  __device__ static inline void load(const __nv_bfloat16* p, float o[4]) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+    const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+    o[0] = lo.x; o[1] = lo.y; o[2] = hi.x; o[3] = hi.y;
   }
 };
 template <> struct Vec4<double> {
@@ -314,7 +329,8 @@ __global__ void __launch_bounds__(64) apply_kernel(int E, const W* __restrict__ 
                                                    double* __restrict__ x, int accumulate) {
   constexpr int n = 4 * N;
   constexpr int EPB = ApplyEPB<N>::value;
-  __shared__ W sr[EPB][n];
+  using Acc = typename Blk<W>::acc;
+  __shared__ Acc sr[EPB][n];
   const int le = threadIdx.x / N, t = threadIdx.x - le * N;
   const int e = blockIdx.x * EPB + le;
   const bool active = (le < EPB) && (e < E);
@@ -328,13 +344,13 @@ __global__ void __launch_bounds__(64) apply_kernel(int E, const W* __restrict__ 
   }
   __syncthreads();
   if (!active) return;
-  W acc[4] = {0, 0, 0, 0};
+  Acc acc[4] = {0, 0, 0, 0};
   const W* Dm = Dinv + (size_t)e * n * n + 4 * t;
 #pragma unroll 8
   for (int k = 0; k < n; ++k) {
-    W d[4];
+    Acc d[4];
     Vec4<W>::load(Dm + (size_t)k * n, d);
-    W rk = sr[le][k];
+    Acc rk = sr[le][k];
     acc[0] = fma(d[0], rk, acc[0]);
     acc[1] = fma(d[1], rk, acc[1]);
     acc[2] = fma(d[2], rk, acc[2]);
@@ -381,6 +397,8 @@ static void apply_dispatch(const Ctx& c, const LevelDev& L, const W* Dinv, const
 void launch_apply(const Ctx& c, const LevelDev& L, int prec, const double* r, double* x, int accumulate,
                   cudaStream_t s) {
   if (prec == PMG_PREC_FP64) apply_dispatch<double>(c, L, (const double*)L.Dinv, r, x, accumulate, s);
+  else if (prec == PMG_PREC_BF16R)
+    apply_dispatch<__nv_bfloat16>(c, L, (const __nv_bfloat16*)L.Dinv, r, x, accumulate, s);
   else apply_dispatch<float>(c, L, (const float*)L.Dinv, r, x, accumulate, s);
 }
 

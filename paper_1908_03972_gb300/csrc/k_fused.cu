@@ -54,7 +54,8 @@ __global__ void __launch_bounds__(64, 1) fused_sweep_kernel(
   __shared__ double sFt[EPB][4][N];
   __shared__ double sGt[EPB][4][N];
   __shared__ double sJ[EPB][4][4][n1];
-  __shared__ W sr[EPB][n];
+  using Acc = typename Blk<W>::acc;
+  __shared__ Acc sr[EPB][n];
   __shared__ double sD[n1][n1], sgL[n1], sgR[n1], slm[n1], slp[n1];
   const size_t plane = (size_t)E * N;
   if (threadIdx.x == 0) {
@@ -218,13 +219,13 @@ __global__ void __launch_bounds__(64, 1) fused_sweep_kernel(
     const int le = threadIdx.x / FP, t = threadIdx.x - le * FP;
     const int e = blockIdx.x * EPB + le;
     if (le < EPB && e < E && t < N) {
-      W acc[4] = {0, 0, 0, 0};
+      Acc acc[4] = {0, 0, 0, 0};
       const W* Dm = ok ? sDinv + (size_t)le * n * n + 4 * t : Dinv + (size_t)e * n * n + 4 * t;
 #pragma unroll 4
       for (int kk = 0; kk < n; ++kk) {
-        W rk = sr[le][kk];
+        Acc rk = sr[le][kk];
 #pragma unroll
-        for (int m = 0; m < 4; ++m) acc[m] = fma(Dm[(size_t)kk * n + m], rk, acc[m]);
+        for (int m = 0; m < 4; ++m) acc[m] = fma(blk_val(Dm[(size_t)kk * n + m]), rk, acc[m]);
       }
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
@@ -260,7 +261,8 @@ __global__ void __launch_bounds__(64, 1) fused_sweep_dw_kernel(
   __shared__ dw sFt[EPB][4][N];
   __shared__ dw sGt[EPB][4][N];
   __shared__ dw sJ[EPB][4][4][n1];
-  __shared__ W sr[EPB][n];
+  using Acc = typename Blk<W>::acc;
+  __shared__ Acc sr[EPB][n];
   __shared__ double slm[n1], slp[n1];
   __shared__ dw sD[n1][n1], sgL[n1], sgR[n1], swm[n1], swp[n1];
   const size_t plane = (size_t)E * N;
@@ -434,13 +436,13 @@ __global__ void __launch_bounds__(64, 1) fused_sweep_dw_kernel(
   __syncthreads();
   // phase 4: block apply, rows 4t..4t+3
   if (own) {
-    W acc[4] = {0, 0, 0, 0};
+    Acc acc[4] = {0, 0, 0, 0};
     const W* Dm = ok ? sDinv + (size_t)le * n * n + 4 * t : Dinv + (size_t)e * n * n + 4 * t;
 #pragma unroll 4
     for (int kk = 0; kk < n; ++kk) {
-      const W rk = sr[le][kk];
+      const Acc rk = sr[le][kk];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) acc[m] = fma(Dm[(size_t)kk * n + m], rk, acc[m]);
+      for (int m = 0; m < 4; ++m) acc[m] = fma(blk_val(Dm[(size_t)kk * n + m]), rk, acc[m]);
     }
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
@@ -466,19 +468,22 @@ static void fused_launch(const Ctx& c, const LevelDev& L, const double* qin, dou
       L.cs, c.d_scal + 1)
   const bool dwf = flux_dw_sweep(c);
   if (dwf && c.ph.p_ref != 0.0 && !src) {   // gauge storage: the double-word sweep
-    if (prec == PMG_PREC_FP64)
-      fused_sweep_dw_kernel<P, double><<<blocks, threads, fused_smem<P, double>(), s>>>(
-          c.E, qin, qout, L.met, L.face, nbr, L.opw, L.op, c.phw, c.ph.p_ref, inv_odt, S, qref,
-          (const double*)L.Dinv, L.rs, L.cs, c.d_scal + 1);
-    else
-      fused_sweep_dw_kernel<P, float><<<blocks, threads, fused_smem<P, float>(), s>>>(
-          c.E, qin, qout, L.met, L.face, nbr, L.opw, L.op, c.phw, c.ph.p_ref, inv_odt, S, qref,
-          (const float*)L.Dinv, L.rs, L.cs, c.d_scal + 1);
+#define PMG_FUSED_DW(WT)                                                                         \
+  fused_sweep_dw_kernel<P, WT><<<blocks, threads, fused_smem<P, WT>(), s>>>(                       \
+      c.E, qin, qout, L.met, L.face, nbr, L.opw, L.op, c.phw, c.ph.p_ref, inv_odt, S, qref,        \
+      (const WT*)L.Dinv, L.rs, L.cs, c.d_scal + 1)
+    if (prec == PMG_PREC_FP64) PMG_FUSED_DW(double);
+    else if (prec == PMG_PREC_BF16R) PMG_FUSED_DW(__nv_bfloat16);
+    else PMG_FUSED_DW(float);
+#undef PMG_FUSED_DW
     return;
   }
   if (prec == PMG_PREC_FP64) {
     if (dwf) PMG_FUSED(double, true);
     else PMG_FUSED(double, false);
+  } else if (prec == PMG_PREC_BF16R) {
+    if (dwf) PMG_FUSED(__nv_bfloat16, true);
+    else PMG_FUSED(__nv_bfloat16, false);
   } else {
     if (dwf) PMG_FUSED(float, true);
     else PMG_FUSED(float, false);

@@ -196,7 +196,8 @@ __global__ void __launch_bounds__(256, 1) volume_kernel(int E, const double* q,
   using PF = VolPrefetch<P, W>;
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ __align__(8) unsigned long long mbar[2];   // 0: face fluxes, 1: blocks and scales
-  __shared__ W sr[APPLY ? EPB : 1][APPLY ? n : 1];
+  using Acc = typename Blk<W>::acc;
+  __shared__ Acc sr[APPLY ? EPB : 1][APPLY ? n : 1];
   __shared__ double sV[VISC ? EPB : 1][3][VISC ? N : 1];   // (u, v, T) for the gradients
   __shared__ double sFt[EPB][4][N];
   __shared__ double sGt[EPB][4][N];
@@ -392,13 +393,13 @@ __global__ void __launch_bounds__(256, 1) volume_kernel(int E, const double* q,
     if (active) {
       // thread (le, pt) owns rows 4 pt .. 4 pt + 3 of its element's block
       // (column-major: the four rows of a column are one 16/32-byte vector)
-      W acc[4] = {0, 0, 0, 0};
+      Acc acc[4] = {0, 0, 0, 0};
       if (PF::blocks && okS) {
         const W* Dm = sDinv + (size_t)le * n * n + 4 * pt;
 #pragma unroll 8
         for (int kk = 0; kk < n; ++kk) {
-          const W rk = sr[APPLY ? le : 0][APPLY ? kk : 0];
-          W d[4];
+          const Acc rk = sr[APPLY ? le : 0][APPLY ? kk : 0];
+          Acc d[4];
           ld4(Dm + (size_t)kk * n, d);
 #pragma unroll
           for (int m = 0; m < 4; ++m) acc[m] = fma(d[m], rk, acc[m]);
@@ -407,8 +408,8 @@ __global__ void __launch_bounds__(256, 1) volume_kernel(int E, const double* q,
         const W* Dm = Dinv + (size_t)e * n * n + 4 * pt;
 #pragma unroll 8
         for (int kk = 0; kk < n; ++kk) {
-          const W rk = sr[APPLY ? le : 0][APPLY ? kk : 0];
-          W d[4];
+          const Acc rk = sr[APPLY ? le : 0][APPLY ? kk : 0];
+          Acc d[4];
           ldg4(Dm + (size_t)kk * n, d);
 #pragma unroll
           for (int m = 0; m < 4; ++m) acc[m] = fma(d[m], rk, acc[m]);
@@ -579,6 +580,7 @@ static void volume_apply_dispatch(const Ctx& c, const LevelDev& L, double* q, do
 void launch_volume_apply(const Ctx& c, const LevelDev& L, double* q, double inv_odt, const double* src,
                          const double* S, const double* qn, int prec, cudaStream_t s) {
   if (prec == PMG_PREC_FP64) volume_apply_dispatch<double>(c, L, q, inv_odt, src, S, qn, s);
+  else if (prec == PMG_PREC_BF16R) volume_apply_dispatch<__nv_bfloat16>(c, L, q, inv_odt, src, S, qn, s);
   else volume_apply_dispatch<float>(c, L, q, inv_odt, src, S, qn, s);
 }
 
@@ -605,8 +607,9 @@ static cudaError_t prepare_apply(int P, bool visc) {
 cudaError_t prepare_residual_kernels(const Ctx& c) {
   for (int l = 0; l < c.cfg.n_levels; ++l) {
     const bool visc = c.ph.mu > 0.0;
-    cudaError_t e = c.cfg.block_prec == PMG_PREC_FP64 ? prepare_apply<double>(c.lev[l].P, visc)
-                                                      : prepare_apply<float>(c.lev[l].P, visc);
+    cudaError_t e = c.cfg.block_prec == PMG_PREC_FP64    ? prepare_apply<double>(c.lev[l].P, visc)
+                    : c.cfg.block_prec == PMG_PREC_BF16R ? prepare_apply<__nv_bfloat16>(c.lev[l].P, visc)
+                                                         : prepare_apply<float>(c.lev[l].P, visc);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -30,7 +30,8 @@ __global__ void __launch_bounds__(256, 1) volume_apply_dw_kernel(
   using PF = VolPrefetch<P, W>;
   extern __shared__ __align__(128) unsigned char dsm[];
   __shared__ __align__(8) unsigned long long mbar[2];   // 0: face fluxes, 1: blocks and scales
-  __shared__ W sr[EPB][n];
+  using Acc = typename Blk<W>::acc;
+  __shared__ Acc sr[EPB][n];
   __shared__ dw sFt[EPB][4][N];
   __shared__ dw sGt[EPB][4][N];
   __shared__ dw sJ[EPB][4][4][n1];   // [face][var][k]
@@ -174,13 +175,13 @@ __global__ void __launch_bounds__(256, 1) volume_apply_dw_kernel(
   __syncthreads();
   if (active) {
     // thread (le, pt) owns rows 4 pt .. 4 pt + 3 of its element's block
-    W acc[4] = {0, 0, 0, 0};
+    Acc acc[4] = {0, 0, 0, 0};
     if (PF::blocks && okS) {
       const W* Dm = sDinv + (size_t)le * n * n + 4 * pt;
 #pragma unroll 8
       for (int kk = 0; kk < n; ++kk) {
-        const W rk = sr[le][kk];
-        W d[4];
+        const Acc rk = sr[le][kk];
+        Acc d[4];
         ld4(Dm + (size_t)kk * n, d);
 #pragma unroll
         for (int m = 0; m < 4; ++m) acc[m] = fma(d[m], rk, acc[m]);
@@ -189,8 +190,8 @@ __global__ void __launch_bounds__(256, 1) volume_apply_dw_kernel(
       const W* Dm = Dinv + (size_t)e * n * n + 4 * pt;
 #pragma unroll 8
       for (int kk = 0; kk < n; ++kk) {
-        const W rk = sr[le][kk];
-        W d[4];
+        const Acc rk = sr[le][kk];
+        Acc d[4];
         ldg4(Dm + (size_t)kk * n, d);
 #pragma unroll
         for (int m = 0; m < 4; ++m) acc[m] = fma(d[m], rk, acc[m]);
@@ -234,6 +235,7 @@ bool volume_dw_applies(const Ctx& c) { return flux_dw_sweep(c) && c.ph.mu == 0.0
 void launch_volume_apply_dw(const Ctx& c, const LevelDev& L, double* q, double inv_odt, const double* src,
                             const double* S, const double* qref, int prec, cudaStream_t s) {
   if (prec == PMG_PREC_FP64) dw_dispatch<double>(c, L, q, inv_odt, src, S, qref, s);
+  else if (prec == PMG_PREC_BF16R) dw_dispatch<__nv_bfloat16>(c, L, q, inv_odt, src, S, qref, s);
   else dw_dispatch<float>(c, L, q, inv_odt, src, S, qref, s);
 }
 
@@ -255,7 +257,9 @@ static cudaError_t prep_dw(int P) {
 
 cudaError_t prepare_volume_dw_kernels(const Ctx& c) {
   for (int l = 0; l < c.cfg.n_levels; ++l) {
-    cudaError_t e = c.cfg.block_prec == PMG_PREC_FP64 ? prep_dw<double>(c.lev[l].P) : prep_dw<float>(c.lev[l].P);
+    cudaError_t e = c.cfg.block_prec == PMG_PREC_FP64    ? prep_dw<double>(c.lev[l].P)
+                    : c.cfg.block_prec == PMG_PREC_BF16R ? prep_dw<__nv_bfloat16>(c.lev[l].P)
+                                                         : prep_dw<float>(c.lev[l].P);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -1,5 +1,6 @@
 // pmg_internal.h -- internal data structures of libpmgfr.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -14,13 +15,30 @@ namespace pmg {
 constexpr int kMaxP = 5;
 constexpr int kMaxLevels = 8;
 
-// Block scales are powers of two, so applying them in the block precision W
-// after the conversion gives the same value (barring under- or overflow of
-// W) and, for W = float, keeps these multiplications off the FP64 pipe.
+// Storage type W of the factored block inverses and the arithmetic type of
+// their application, Blk<W>::acc: FP64 and FP32 blocks are applied in their
+// own precision, BF16 blocks (8-bit significand, FP32 exponent range) with
+// FP32 accumulation.
+template <class W> struct Blk { using acc = W; };
+template <> struct Blk<__nv_bfloat16> { using acc = float; };
+
+// Block scales are powers of two, so applying them in the block arithmetic
+// after the conversion gives the same value (barring under- or overflow) and,
+// for FP32 and BF16 blocks, keeps these multiplications off the FP64 pipe.
 template <class W>
-__device__ __forceinline__ W scaled_in(double x, double s) { return (W)x * (W)s; }
+__device__ __forceinline__ typename Blk<W>::acc scaled_in(double x, double s) {
+  using A = typename Blk<W>::acc;
+  return (A)x * (A)s;
+}
 template <class W>
-__device__ __forceinline__ double scaled_out(W a, double s) { return (double)(a * (W)s); }
+__device__ __forceinline__ double scaled_out(typename Blk<W>::acc a, double s) {
+  using A = typename Blk<W>::acc;
+  return (double)(a * (A)s);
+}
+// One stored block entry in the arithmetic type.
+__device__ __forceinline__ double blk_val(double x) { return x; }
+__device__ __forceinline__ float blk_val(float x) { return x; }
+__device__ __forceinline__ float blk_val(__nv_bfloat16 x) { return __bfloat162float(x); }
 
 // ----------------------------------------------------------------- host side
 struct Ref1D {
@@ -105,6 +123,18 @@ enum ResMode : int {
 enum KClass : int { K_FACE = 0, K_VOLUME, K_APPLY, K_ASSEMBLE, K_FACTOR, K_RESTRICT, K_PROLONG, K_NORM, K_STAGE,
                     K_FUSED, K_COUNT };
 
+// Device-side stage loop (k_loop.cu): its state in device memory and its
+// fixed parameters.
+enum LoopStatus : int { LOOP_RUNNING = 0, LOOP_CONVERGED, LOOP_NONFINITE, LOOP_NOTCONV, LOOP_SINGULAR, LOOP_TIMEOUT };
+struct LoopState {
+  double n0, prev, dtau, built, dtau_max, final_norm;
+  int m, iters, status, n_refresh;
+};
+struct LoopParams {
+  double tol;
+  int refresh_every, refresh_always, max_pseudo;
+};
+
 struct Profiler {
   bool on = false;
   std::vector<cudaEvent_t> ev;       // pairs (start, end)
@@ -150,9 +180,19 @@ struct Ctx {
   double* d_tmp0 = nullptr;
   double* d_tmp1 = nullptr;
   size_t tmp_size = 0;
-  // CUDA graphs of the V-cycle (0: plain, 1: with refresh)
+  // CUDA graphs of the V-cycle (0: plain, 1: with refresh), built for one
+  // omega dt and one stage form (split_stage)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   double graph_inv_odt[2] = {0.0, 0.0};
+  int graph_split[2] = {-1, -1};
+  // device-side stage loop (cfg.device_loop): the WHILE graph, its state
+  cudaGraphExec_t loop_exec = nullptr;
+  double loop_inv_odt = 0.0;
+  int loop_split = -1;
+  LoopState* d_loop = nullptr;
+  LoopState* h_loop = nullptr;      // pinned mirror
+  double* d_hist = nullptr;         // 2 (max_pseudo + 1): norms, then dtau
+  double* h_hist = nullptr;         // pinned mirror
   double* d_dtau = nullptr;    // pseudo time step read by the assembly kernel
   double* h_dtau = nullptr;
   // ESDIRK3 tableau
@@ -207,6 +247,10 @@ void launch_grad(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t 
 void launch_assemble_visc(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s);
 void launch_fused_sweep(const Ctx& c, const LevelDev& L, const double* qin, double* qout, double inv_odt,
                         const double* src, const double* S, const double* qref, int prec, cudaStream_t s);
+void launch_loop_controller(LoopState* st, const double* scal, int* sing_flag, double* d_dtau, double* hist_norm,
+                            double* hist_dtau, const LoopParams& prm, cudaGraphConditionalHandle h_loop,
+                            cudaGraphConditionalHandle h_refresh, cudaGraphConditionalHandle h_plain,
+                            cudaStream_t s);
 int residual_threads_per_block(int P);
 int residual_blocks_for(int P, int E);
 cudaError_t prepare_kernels(const Ctx& c);

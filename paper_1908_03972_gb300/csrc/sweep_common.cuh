@@ -48,10 +48,22 @@ __device__ __forceinline__ void ldg4(const double* p, double a[4]) {
   const double2 t0 = __ldg(reinterpret_cast<const double2*>(p)), t1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
   a[0] = t0.x; a[1] = t0.y; a[2] = t1.x; a[3] = t1.y;
 }
+// BF16 entries (8 bytes, 8-byte aligned), widened to FP32.
+__device__ __forceinline__ void bf4_to_f(uint2 u, float a[4]) {
+  const float2 lo = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+  const float2 hi = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+  a[0] = lo.x; a[1] = lo.y; a[2] = hi.x; a[3] = hi.y;
+}
+__device__ __forceinline__ void ld4(const __nv_bfloat16* p, float a[4]) {
+  bf4_to_f(*reinterpret_cast<const uint2*>(p), a);
+}
+__device__ __forceinline__ void ldg4(const __nv_bfloat16* p, float a[4]) {
+  bf4_to_f(__ldg(reinterpret_cast<const uint2*>(p)), a);
+}
 
 // rs .* F of a double-word F in the block precision W (rs: powers of two).
 template <class W>
-__device__ __forceinline__ W scaled_in_dw(dw F, double s);
+__device__ __forceinline__ typename Blk<W>::acc scaled_in_dw(dw F, double s);
 template <>
 __device__ __forceinline__ float scaled_in_dw<float>(dw F, double s) {
   return __fmul_rn(__fadd_rn(F.h, F.l), (float)s);
@@ -59,6 +71,10 @@ __device__ __forceinline__ float scaled_in_dw<float>(dw F, double s) {
 template <>
 __device__ __forceinline__ double scaled_in_dw<double>(dw F, double s) {
   return dw_to_double(F) * s;
+}
+template <>
+__device__ __forceinline__ float scaled_in_dw<__nv_bfloat16>(dw F, double s) {
+  return __fmul_rn(__fadd_rn(F.h, F.l), (float)s);
 }
 
 }  // namespace pmg

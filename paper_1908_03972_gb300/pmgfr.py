@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libpmgfr.so")
 PMG_OK = 0
 PMG_EINVAL, PMG_ENOMEM, PMG_ECUDA, PMG_ESINGULAR, PMG_ENONFINITE, PMG_ENOTCONV, PMG_ETIMEOUT, PMG_ESTATE = (
     -1, -2, -3, -4, -5, -6, -7, -8)
-PMG_PREC_FP64, PMG_PREC_FP32 = 0, 1
+PMG_PREC_FP64, PMG_PREC_FP32, PMG_PREC_BF16R = 0, 1, 2
 PMG_FLUX_FP64, PMG_FLUX_DW_SMOOTH, PMG_FLUX_DW = 0, 1, 2
 
 
@@ -57,6 +57,7 @@ class pmg_config(ctypes.Structure):
         ("refresh_always", ctypes.c_int),
         ("flux_prec", ctypes.c_int),
         ("copy_wait_s", ctypes.c_double),
+        ("device_loop", ctypes.c_int),
     ]
 
 
@@ -154,7 +155,8 @@ def make_config(P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutof
                 dtau_max=10.0, tol=1e-8, refresh_every=10, max_pseudo=2000, block_prec=PMG_PREC_FP64,
                 use_graph=1, p_gauge=0.0, mu=0.0, Pr=0.72, res_scale=(1.0, 1.0, 1.0, 1.0),
                 q_inf=(0.0, 0.0, 0.0, 0.0), cfl_mode=0, cfl_init=1e2, cfl_max=1e5,
-                esdirk_order=3, refresh_always=0, flux_prec=PMG_FLUX_DW_SMOOTH, copy_wait_s=0.0) -> pmg_config:
+                esdirk_order=3, refresh_always=0, flux_prec=PMG_FLUX_DW_SMOOTH, copy_wait_s=0.0,
+                device_loop=0) -> pmg_config:
     cfg = pmg_config()
     cfg.n_levels = len(P_levels)
     for l, (P, n) in enumerate(zip(P_levels, n_smooth)):
@@ -174,6 +176,7 @@ def make_config(P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutof
     cfg.refresh_always = refresh_always
     cfg.flux_prec = flux_prec
     cfg.copy_wait_s = copy_wait_s
+    cfg.device_loop = device_loop
     return cfg
 
 

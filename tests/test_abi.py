@@ -44,9 +44,10 @@ def test_binding_covers_every_symbol():
 def test_binding_struct_layout_matches_header():
     from paper_1908_03972_gb300 import pmgfr
     # pmg_config: 1 int, 2 x int[8], 3 doubles, 1 int, 3 doubles, 4 ints, 3 doubles, 2 x double[4],
-    # 1 int (+4 padding), 2 doubles, 3 ints (+4 padding), 1 double (C layout)
-    assert ctypes.sizeof(pmgfr.pmg_config) == 4 + 64 + 4 + 24 + 4 + 4 + 24 + 16 + 8 + 16 + 32 + 32 + 8 + 16 + 16 + 8
+    # 1 int (+4 padding), 2 doubles, 3 ints (+4 padding), 1 double, 1 int (+4 padding) (C layout)
+    assert ctypes.sizeof(pmgfr.pmg_config) == 4 + 64 + 4 + 24 + 4 + 4 + 24 + 16 + 8 + 16 + 32 + 32 + 8 + 16 + 16 + 8 + 8
     assert pmgfr.pmg_config.copy_wait_s.offset == 272
+    assert pmgfr.pmg_config.device_loop.offset == 280
     assert ctypes.sizeof(pmgfr.pmg_mesh) == 24
 
 
@@ -58,7 +59,7 @@ def _cfg(**over):
     return cfg
 
 
-@pytest.mark.parametrize("field,value", [("flux_prec", 3), ("block_prec", 2), ("esdirk_order", 5),
+@pytest.mark.parametrize("field,value", [("flux_prec", 3), ("block_prec", 3), ("esdirk_order", 5),
                                          ("n_levels", 0), ("gamma", 1.0), ("mu", -1.0), ("cfl_mode", 1)])
 def test_create_rejects_invalid_configs_before_touching_the_gpu(lib, field, value):
     """pmg_create validates its configuration first: these fail with

@@ -46,9 +46,10 @@ def _solver(**kw):
     return s, q
 
 
-def test_nan_state_gives_enonfinite():
+@pytest.mark.parametrize("device_loop", [0, 1])
+def test_nan_state_gives_enonfinite(device_loop):
     from paper_1908_03972_gb300 import pmgfr
-    s, q = _solver()
+    s, q = _solver(device_loop=device_loop)
     try:
         q = q.copy()
         q[1, 5, 3] = np.nan
@@ -60,7 +61,7 @@ def test_nan_state_gives_enonfinite():
         s.close()
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("kind", ["zero_row", "repeated_row"])
 def test_singular_block_gives_esingular_with_element(prec, kind):
     from paper_1908_03972_gb300 import pmgfr
@@ -104,14 +105,30 @@ def test_set_blocks_round_trip_and_factor_matches_assembled():
         s.close()
 
 
-def test_pseudo_iteration_budget_gives_enotconv():
+@pytest.mark.parametrize("device_loop", [0, 1])
+def test_pseudo_iteration_budget_gives_enotconv(device_loop):
     from paper_1908_03972_gb300 import pmgfr
-    s, q = _solver(max_pseudo=1)
+    s, q = _solver(max_pseudo=1, device_loop=device_loop)
     try:
         s.set_state(q)
         with pytest.raises(pmgfr.PmgError) as ei:
             pmgfr.pmg_stage_solve(s.h)
         assert ei.value.status == pmgfr.PMG_ENOTCONV
+        norms, _ = pmgfr.pmg_stage_history(s.h)
+        assert len(norms) == 2   # the initial norm and the one after the single V-cycle
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("device_loop", [0, 1])
+def test_stage_solve_with_waits_that_give_up_gives_etimeout(device_loop):
+    from paper_1908_03972_gb300 import pmgfr
+    s, q = _solver(copy_wait_s=-1.0, device_loop=device_loop)
+    try:
+        s.set_state(q)
+        with pytest.raises(pmgfr.PmgError) as ei:
+            pmgfr.pmg_stage_solve(s.h)
+        assert ei.value.status == pmgfr.PMG_ETIMEOUT
     finally:
         s.close()
 

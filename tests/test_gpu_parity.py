@@ -214,7 +214,11 @@ def test_block_assembly_parity(P, gauge):
         gpu.close()
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-4)])
+# BF16 inverse (2): emulating the kernel's steps in numpy on the oracle's
+# blocks of this setup (power-of-two equilibration, FP32 inverse rounded to
+# BF16, FP32 products) gives worst relative errors of 1.7e-2 (P = 0) down to
+# 2.0e-3 (P = 5); the bound is three times the worst.
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-4), (2, 5e-2)])
 @pytest.mark.parametrize("P", [0, 1, 2, 3, 5])
 def test_factor_and_apply(P, prec, tol):
     nodes, nbr = W.periodic_box(3, 3, Ng=2, perturb=0.3)
@@ -318,7 +322,7 @@ def test_vcycle_parity_fused_coarse_sweeps(prec, gauge, monkeypatch):
 
 
 @pytest.mark.parametrize("gauge", GAUGES)
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_stage_solve_parity(prec, gauge):
     Ng = 1 if gauge else 2
     nodes, nbr = W.periodic_box(4, 4, Ng=Ng, perturb=0.3 if Ng > 1 else 0.0)
@@ -360,7 +364,7 @@ def _c1_oracle_steps():
 
 
 @pytest.mark.parametrize("gauge", GAUGES)
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_esdirk_c1_parity(prec, gauge):
     """Vortex, 8x8 straight quads on [0,10]^2, P{2-1-0}, I{5-10-20}, ESDIRK3,
     dt = 0.1, tol 1e-8 of the free-stream-scaled norm: three consecutive
