@@ -329,8 +329,9 @@ def run_ours(args, wl, world, rank, local):
 
     if args.ncu_window:
         # Profiling window for ncu: the stage-2 system of the first step and
-        # N V-cycles of it (99.9% of a step's launches are V-cycle launches).
-        s = solver
+        # N V-cycles of it (99.9% of a step's launches are V-cycle launches),
+        # with the blocks of the mixed leg or of the BF16 leg.
+        s = solver if args.ncu_blocks == "fp32" else make("mixed_bf16")
         A = 1767732205903.0 / 4055673282236.0
         odt = A * wl["dt"]
         pmgfr.pmg_set_state(s.h, 0, q0_dev)
@@ -342,7 +343,10 @@ def run_ours(args, wl, world, rank, local):
         norms = [pmgfr.pmg_vcycle(s.h, 0.01 if k == 0 else 1.0, k % 10 == 0) for k in range(args.ncu_window)]
         torch.cuda.synchronize(device)
         if rank == 0:
-            print(json.dumps({"ncu_window_vcycles": args.ncu_window, "first_norm": norms[0], "last_norm": norms[-1]}))
+            print(json.dumps({"ncu_window_vcycles": args.ncu_window, "blocks": args.ncu_blocks,
+                              "first_norm": norms[0], "last_norm": norms[-1]}))
+        if s is not solver:
+            s.close()
         solver.close()
         return 0
 
@@ -535,6 +539,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--ncu-window", type=int, default=0,
                     help="profiling helper: run N V-cycles of the first stage and exit (no bench line)")
+    ap.add_argument("--ncu-blocks", default="fp32", choices=["fp32", "bf16"],
+                    help="block precision of the --ncu-window run")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     wl = WORKLOADS[args.workload]

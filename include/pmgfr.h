@@ -259,9 +259,10 @@ pmg_status pmg_set_blocks(pmg_ctx* ctx, int level, const double* D, int on_devic
  * configured precision: power-of-two row/column equilibration, then
  * Gauss-Jordan elimination with partial pivoting to the explicit inverse.
  * Returns PMG_ESINGULAR, naming the element, if a pivot is not finite or not
- * above eps^2 of the working precision (the equilibrated rows have unit size,
- * so such a block is singular to working precision); the library's V-cycle
- * calls report it the same way when they rebuild the smoother. */
+ * above n eps of the working precision (the equilibrated rows have unit size
+ * and a row that depends on others leaves a pivot of rounding size, so such a
+ * block is singular to working precision); the library's V-cycle calls report
+ * it the same way when they rebuild the smoother. */
 pmg_status pmg_factor_blocks(pmg_ctx* ctx, int level);
 
 /* x = D^-1 r per element with the factored blocks (SoA vectors). */

@@ -319,3 +319,190 @@ def lu_solve(A, b):
     if st:
         raise RuntimeError("singular")
     return x
+
+
+# ---------------------------------------------------------------------------
+# Three dimensions: hexahedra, 5 working variables (p, u, v, w, T).
+# ---------------------------------------------------------------------------
+class OrcConfig3(ctypes.Structure):
+    _fields_ = [
+        ("n_levels", ctypes.c_int),
+        ("P", ctypes.c_int * 8),
+        ("n_smooth", ctypes.c_int * 8),
+        ("gamma", ctypes.c_double),
+        ("Ma_inf", ctypes.c_double),
+        ("kappa", ctypes.c_double),
+        ("cutoff", ctypes.c_int),
+        ("esdirk_stages", ctypes.c_int),
+        ("dtau_init", ctypes.c_double),
+        ("dtau_max", ctypes.c_double),
+        ("tol", ctypes.c_double),
+        ("refresh_every", ctypes.c_int),
+        ("max_pseudo", ctypes.c_int),
+        ("res_scale", ctypes.c_double * 5),
+        ("q_inf", ctypes.c_double * 5),
+        ("refresh_always", ctypes.c_int),
+    ]
+
+
+_declared3 = False
+
+
+def _lib3():
+    global _declared3
+    L = lib()
+    if not _declared3:
+        vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.orc3_gll.argtypes = [ci, _d]
+        L.orc3_point_matrices.argtypes = [_d, cd, cd, cd, ci, _d, _d, _d]
+        L.orc3_flux.argtypes = [_d, _d, cd, _d, _d]
+        L.orc3_roe.argtypes = [_d, _d, _d, cd, cd, cd, ci, _d]
+        L.orc3_cons_from_prim.argtypes = [_d, cd, _d]
+        L.orc3_create.argtypes = [ctypes.POINTER(OrcConfig3), ci, ci, _d, _i]
+        L.orc3_create.restype = vp
+        L.orc3_destroy.argtypes = [vp]
+        L.orc3_geometry.argtypes = [vp, ci, _d, _d, _d, _d]
+        L.orc3_residual.argtypes = [vp, ci, _d, _d]
+        L.orc3_set_stage.argtypes = [vp, _d, cd]
+        L.orc3_stage_F.argtypes = [vp, ci, _d, _d]
+        L.orc3_blocks.argtypes = [vp, ci, _d, cd, _d]
+        L.orc3_restrict.argtypes = [vp, ci, _d, _d]
+        L.orc3_prolong.argtypes = [vp, ci, _d, _d]
+        L.orc3_vcycle.argtypes = [vp, _d, cd, ci]
+        L.orc3_stage_solve.argtypes = [vp, _d, _i, _d]
+        L.orc3_esdirk_step.argtypes = [vp, _d, cd, _i, _d]
+        _declared3 = True
+    return L
+
+
+def gll(n: int):
+    """Gauss-Lobatto points of degree n (n + 1 points)."""
+    x = np.zeros(n + 1)
+    _lib3().orc3_gll(n, _p(x))
+    return x
+
+
+def point_matrices3(q, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutoff=0):
+    q = _f64(q); M = np.zeros((5, 5)); G = np.zeros((5, 5)); eps = ctypes.c_double()
+    _lib3().orc3_point_matrices(_p(q), gamma, Ma_inf, kappa, cutoff, _p(M), _p(G), ctypes.byref(eps))
+    return M, G, eps.value
+
+
+def flux3(q, n, gamma=1.4):
+    q = _f64(q); n = _f64(n); f = np.zeros(5); A = np.zeros((5, 5))
+    _lib3().orc3_flux(_p(q), _p(n), gamma, _p(f), _p(A))
+    return f, A
+
+
+def roe3(qm, qp, S, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutoff=0):
+    qm = _f64(qm); qp = _f64(qp); S = _f64(S); out = np.zeros(5)
+    _lib3().orc3_roe(_p(qm), _p(qp), _p(S), gamma, Ma_inf, kappa, cutoff, _p(out))
+    return out
+
+
+def cons_from_prim3(q, gamma=1.4):
+    q = _f64(q); qc = np.zeros(5)
+    _lib3().orc3_cons_from_prim(_p(q), gamma, _p(qc))
+    return qc
+
+
+class Oracle3:
+    """Stateful 3D oracle solver on one hexahedral mesh."""
+
+    def __init__(self, nodes, nbr, Ng, P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutoff=0,
+                 dtau_init=0.01, dtau_max=10.0, tol=1e-8, refresh_every=10, max_pseudo=2000,
+                 res_scale=(1.0,) * 5, q_inf=(0.0,) * 5, esdirk_order=3, refresh_always=0):
+        cfg = OrcConfig3()
+        cfg.n_levels = len(P_levels)
+        for l, P in enumerate(P_levels):
+            cfg.P[l] = P
+            cfg.n_smooth[l] = n_smooth[l]
+        cfg.gamma, cfg.Ma_inf, cfg.kappa, cfg.cutoff = gamma, Ma_inf, kappa, cutoff
+        cfg.esdirk_stages = {2: 3, 3: 4, 4: 6}[esdirk_order]
+        cfg.dtau_init, cfg.dtau_max, cfg.tol = dtau_init, dtau_max, tol
+        cfg.refresh_every, cfg.max_pseudo = refresh_every, max_pseudo
+        for v in range(5):
+            cfg.res_scale[v] = res_scale[v]
+            cfg.q_inf[v] = q_inf[v]
+        cfg.refresh_always = refresh_always
+        self.cfg = cfg
+        self.nodes = _f64(nodes)
+        self.nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+        self.E = self.nodes.shape[0]
+        self.Ng = Ng
+        self.P = list(P_levels)
+        self.h = _lib3().orc3_create(ctypes.byref(cfg), self.E, Ng, _p(self.nodes), self.nbr.ctypes.data_as(_i))
+
+    def __del__(self):
+        try:
+            if self.h:
+                _lib3().orc3_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def N(self, level=0):
+        return (self.P[level] + 1) ** 3
+
+    def shape(self, level=0):
+        return (5, self.E, self.N(level))
+
+    def geometry(self, level=0):
+        """(Ja (E, N, 3, 3), J (E, N), face normals (E, 6, NF, 3), coordinates (E, N, 3))."""
+        N, NF = self.N(level), (self.P[level] + 1) ** 2
+        Ja = np.zeros((self.E, N, 3, 3)); J = np.zeros((self.E, N))
+        fS = np.zeros((self.E, 6, NF, 3)); xyz = np.zeros((self.E, N, 3))
+        _lib3().orc3_geometry(self.h, level, _p(Ja), _p(J), _p(fS), _p(xyz))
+        return Ja, J, fS, xyz
+
+    def coords(self, level=0):
+        return self.geometry(level)[3]
+
+    def residual(self, q, level=0):
+        q = _f64(q); R = np.zeros(self.shape(level))
+        _lib3().orc3_residual(self.h, level, _p(q), _p(R))
+        return R
+
+    def set_stage(self, src, omega_dt):
+        src = _f64(src)
+        _lib3().orc3_set_stage(self.h, _p(src), omega_dt)
+
+    def stage_F(self, q, level=0):
+        q = _f64(q); F = np.zeros(self.shape(level))
+        _lib3().orc3_stage_F(self.h, level, _p(q), _p(F))
+        return F
+
+    def blocks(self, q, dtau, level=0):
+        q = _f64(q); n = 5 * self.N(level)
+        D = np.zeros((self.E, n, n))
+        _lib3().orc3_blocks(self.h, level, _p(q), dtau, _p(D))
+        return D
+
+    def restrict(self, qf, lf):
+        qf = _f64(qf); qc = np.zeros(self.shape(lf + 1))
+        _lib3().orc3_restrict(self.h, lf, _p(qf), _p(qc))
+        return qc
+
+    def prolong(self, qc, lf):
+        qc = _f64(qc); qf = np.zeros(self.shape(lf))
+        _lib3().orc3_prolong(self.h, lf, _p(qc), _p(qf))
+        return qf
+
+    def vcycle(self, q, dtau, refresh=True):
+        q = _f64(q).copy()
+        st = _lib3().orc3_vcycle(self.h, _p(q), dtau, int(refresh))
+        if st:
+            raise RuntimeError(f"oracle V-cycle failed ({st})")
+        return q
+
+    def stage_solve(self, q):
+        q = _f64(q).copy(); it = ctypes.c_int(); dr = ctypes.c_double()
+        st = _lib3().orc3_stage_solve(self.h, _p(q), ctypes.byref(it), ctypes.byref(dr))
+        return q, it.value, dr.value, st
+
+    def esdirk_step(self, q, dt):
+        q = _f64(q).copy(); its = np.zeros(6, dtype=np.int32); drops = np.zeros(6)
+        st = _lib3().orc3_esdirk_step(self.h, _p(q), dt, its.ctypes.data_as(_i), _p(drops))
+        if st:
+            raise RuntimeError(f"oracle step failed ({st})")
+        return q, its, drops

@@ -1449,3 +1449,886 @@ int orc_esdirk_step(void* h, double* q, double dt, int* iters, double* drops) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Three dimensions: hexahedral elements, 5 working variables
+// q_p = (p, u, v, w, T) (Sections 2.1-2.4 with d = 3; Section 3).
+//
+// Layout conventions (shared with the CUDA library only through its C
+// interface):
+//   solution point (i, j, k) of a degree-P hexahedron has index
+//   (k*(P+1) + j)*(P+1) + i, i along xi, j along eta, k along zeta;
+//   a state array is variable-major: q[(v*E + e)*N + pt], N = (P+1)^3;
+//   faces: f = 2*d + s, d = 0 (xi), 1 (eta), 2 (zeta), s = 0 (-1 side) or 1
+//   (+1 side); a face point (a, b) has index b*(P+1) + a, a along the first
+//   and b along the second of the other two reference directions in
+//   increasing order (xi faces: (eta, zeta); eta faces: (xi, zeta); zeta
+//   faces: (xi, eta));
+//   nbr[(e*6+f)*3 + {0,1,2}] = (neighbour element, neighbour face,
+//   orientation o); the neighbour's face point of (a, b) is (a', b') with
+//   (s, t) = (o & 4) ? (b, a) : (a, b), a' = (o & 1) ? P - s : s,
+//   b' = (o & 2) ? P - t : t; a boundary face has neighbour -1 and the
+//   boundary type in the second slot (2 slip wall, 4 far field);
+//   element geometry: (Ng+1)^3 Lagrange nodes at equispaced reference
+//   positions, node (c*(Ng+1) + b)*(Ng+1) + a, a along xi;
+//   nodes[(e*(Ng+1)^3 + node)*3 + {x, y, z}].
+//
+// Metric terms.  On curved hexahedra the metric terms J grad(xi^i) taken
+// from the mapping at the solution points do not satisfy the discrete
+// metric identity, so uniform flow is not steady.  Reading (the paper is
+// silent): the conservative curl form, J a^i_n = -e_i . curl_xi(I(X_l grad_xi
+// X_m)) with (n, m, l) cyclic, where I interpolates at the Gauss-Lobatto
+// points of degree max(P, 1).  These metric terms are polynomials of degree
+// <= P in every direction (exact at the Gauss solution points), their
+// divergence vanishes identically, and on a face the normal component
+// involves only the face's own Gauss-Lobatto values, so both elements of a
+// face see the same normal.  The surface normal of a face point is the
+// outward J a^d of that polynomial; |J| at the solution points is the
+// determinant of the exact map.
+// ===========================================================================
+
+// Gauss-Lobatto points of degree n (n + 1 points): -1, the roots of L_n', +1.
+static std::vector<double> gll_nodes(int n) {
+  std::vector<double> x(n + 1);
+  x[0] = -1.0; x[n] = 1.0;
+  for (int i = 1; i < n; ++i) {
+    // Newton on L_n' from the Chebyshev-Gauss-Lobatto guess; L_n'' from
+    // the Legendre equation (1 - t^2) L'' = 2 t L' - n (n+1) L.
+    double t = -std::cos(M_PI * i / n);
+    for (int it = 0; it < 100; ++it) {
+      double L, dL;
+      legendre(n, t, &L, &dL);
+      double d2 = (2.0 * t * dL - n * (n + 1.0) * L) / (1.0 - t * t);
+      double dt = dL / d2;
+      t -= dt;
+      if (std::fabs(dt) < 1e-16) break;
+    }
+    x[i] = t;
+  }
+  return x;
+}
+
+// ---- thermodynamics and preconditioning in 3D (Sections 2.1-2.2)
+template <class S> static void cons_from_prim3(const S q[5], const Phys& ph, S qc[5]) {
+  S rho = q[0] / q[4];
+  S E = q[4] / (ph.gamma - 1.0) + 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  qc[0] = rho; qc[1] = rho * q[1]; qc[2] = rho * q[2]; qc[3] = rho * q[3]; qc[4] = rho * E;
+}
+
+static void prim_from_cons3(const double qc[5], const Phys& ph, double q[5]) {
+  double rho = qc[0], u = qc[1] / rho, v = qc[2] / rho, w = qc[3] / rho;
+  double p = (ph.gamma - 1.0) * (qc[4] - 0.5 * rho * (u * u + v * v + w * w));
+  q[0] = p; q[1] = u; q[2] = v; q[3] = w; q[4] = p / rho;
+}
+
+// M = dq_c/dq_p (Section 2.2, d = 3).
+template <class S> static void M_matrix3(const S q[5], const Phys& ph, S M[5][5]) {
+  S p = q[0], T = q[4];
+  S rho = p / T, rp = 1.0 / T, rT = -rho / T;
+  double Cp = ph.gamma / (ph.gamma - 1.0);
+  S H = Cp * T + 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) M[i][j] = 0.0;
+  M[0][0] = rp; M[0][4] = rT;
+  for (int c = 1; c <= 3; ++c) { M[c][0] = rp * q[c]; M[c][c] = rho; M[c][4] = rT * q[c]; }
+  M[4][0] = rp * H - 1.0;
+  for (int c = 1; c <= 3; ++c) M[4][c] = rho * q[c];
+  M[4][4] = rT * H + rho * Cp;
+}
+
+// eps of eq. eps_nonmove with |v| over three components.
+template <class S> static S precond_eps3(const S q[5], const Phys& ph) {
+  S Ma = cs_sqrt((q[1] * q[1] + q[2] * q[2] + q[3] * q[3]) / (ph.gamma * q[4]));
+  S e = ph.cutoff ? cs_max(S(ph.kappa * ph.Ma_inf), Ma) : Ma;
+  return cs_min(S(1.0), e);
+}
+
+// Gamma of eq. preconditioning: M with the first column rho_p replaced by
+// Theta of eq. theta (U_r = eps c).
+template <class S> static void Gamma_matrix3(const S q[5], const S& eps, const Phys& ph, S G[5][5]) {
+  M_matrix3(q, ph, G);
+  S T = q[4], rho = q[0] / T, rT = -rho / T;
+  double Cp = ph.gamma / (ph.gamma - 1.0);
+  S H = Cp * T + 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  S Th = 1.0 / (eps * eps * ph.gamma * T) - rT / (rho * Cp);
+  G[0][0] = Th;
+  for (int c = 1; c <= 3; ++c) G[c][0] = Th * q[c];
+  G[4][0] = Th * H - 1.0;
+}
+
+// Inviscid flux through the (possibly unnormalised) vector n (Section 2.1).
+template <class S> static void euler_flux3(const S q[5], const double n[3], const Phys& ph, S f[5]) {
+  S p = q[0], T = q[4];
+  S rho = p / T;
+  double Cp = ph.gamma / (ph.gamma - 1.0);
+  S H = Cp * T + 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  S un = q[1] * n[0] + q[2] * n[1] + q[3] * n[2];
+  f[0] = rho * un;
+  for (int c = 0; c < 3; ++c) f[1 + c] = rho * un * q[1 + c] + p * n[c];
+  f[4] = rho * un * H;
+}
+
+// A_n = d f_n / d q_p, by hand from euler_flux3.
+template <class S> static void flux_jacobian3(const S q[5], const double n[3], const Phys& ph, S A[5][5]) {
+  S p = q[0], T = q[4];
+  S rho = p / T, rp = 1.0 / T, rT = -rho / T;
+  double Cp = ph.gamma / (ph.gamma - 1.0);
+  S H = Cp * T + 0.5 * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  S un = q[1] * n[0] + q[2] * n[1] + q[3] * n[2];
+  A[0][0] = rp * un;
+  for (int c = 0; c < 3; ++c) A[0][1 + c] = rho * n[c];
+  A[0][4] = rT * un;
+  for (int r = 0; r < 3; ++r) {
+    A[1 + r][0] = rp * un * q[1 + r] + n[r];
+    for (int c = 0; c < 3; ++c) A[1 + r][1 + c] = rho * q[1 + r] * n[c] + (r == c ? rho * un : S(0.0));
+    A[1 + r][4] = rT * un * q[1 + r];
+  }
+  A[4][0] = rp * un * H;
+  for (int c = 0; c < 3; ++c) A[4][1 + c] = rho * n[c] * H + rho * un * q[1 + c];
+  A[4][4] = rT * un * H + rho * un * Cp;
+}
+
+// Solve G X = A (n x n, n <= 5) by elimination with partial pivoting on the real part.
+template <class S> static void solve5(S G[5][5], S A[5][5], S X[5][5]) {
+  S a[5][10];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) { a[i][j] = G[i][j]; a[i][5 + j] = A[i][j]; }
+  for (int k = 0; k < 5; ++k) {
+    int p = k;
+    for (int i = k + 1; i < 5; ++i)
+      if (std::fabs(re(a[i][k])) > std::fabs(re(a[p][k]))) p = i;
+    if (p != k) for (int j = 0; j < 10; ++j) std::swap(a[k][j], a[p][j]);
+    for (int i = k + 1; i < 5; ++i) {
+      S l = a[i][k] / a[k][k];
+      for (int j = k; j < 10; ++j) a[i][j] -= l * a[k][j];
+    }
+  }
+  for (int c = 0; c < 5; ++c)
+    for (int i = 4; i >= 0; --i) {
+      S s = a[i][5 + c];
+      for (int j = i + 1; j < 5; ++j) s -= a[i][j] * X[j][c];
+      X[i][c] = s / a[i][i];
+    }
+}
+
+// Preconditioned Roe flux of eq. invis_com in 3D, through the area-scaled
+// normal Sv from - to +: the same construction as roe_flux (arithmetic mean of
+// the primitive states, no entropy fix, Sylvester's formula over the three
+// distinct eigenvalues u_n (three-fold), u_n' +- c' of eq. eigenvalues_para).
+template <class S>
+static void roe_flux3(const S qm[5], const S qp[5], const double Sv[3], const Phys& ph, S out[5]) {
+  double dS = std::sqrt(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
+  double n[3] = {Sv[0] / dS, Sv[1] / dS, Sv[2] / dS};
+  S qa[5];
+  for (int k = 0; k < 5; ++k) qa[k] = 0.5 * (qm[k] + qp[k]);
+  S eps = precond_eps3(qa, ph);
+  S G[5][5], A[5][5], Mt[5][5];
+  Gamma_matrix3(qa, eps, ph, G);
+  flux_jacobian3(qa, n, ph, A);
+  solve5(G, A, Mt);
+  S p = qa[0], T = qa[4];
+  S rho = p / T, rp = 1.0 / T, rT = -rho / T;
+  double Cp = ph.gamma / (ph.gamma - 1.0);
+  S c = cs_sqrt(ph.gamma * T);
+  S Ur = eps * c;
+  S un = qa[1] * n[0] + qa[2] * n[1] + qa[3] * n[2];
+  S beta = rp + rT / (rho * Cp);
+  S alpha = 0.5 * (1.0 - beta * Ur * Ur);
+  S cpr = cs_sqrt(alpha * alpha * un * un + Ur * Ur);
+  S unp = un * (1.0 - alpha);
+  S lam[3] = {un, unp + cpr, unp - cpr};
+  S absM[5][5];
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) absM[i][j] = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    S Pk[5][5];
+    for (int i = 0; i < 5; ++i)
+      for (int j = 0; j < 5; ++j) Pk[i][j] = (i == j) ? S(1.0) : S(0.0);
+    for (int jj = 0; jj < 3; ++jj) {
+      if (jj == k) continue;
+      S fac[5][5], tmp[5][5];
+      for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j)
+          fac[i][j] = (Mt[i][j] - (i == j ? lam[jj] : S(0.0))) / (lam[k] - lam[jj]);
+      for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) {
+          S s = 0.0;
+          for (int m = 0; m < 5; ++m) s += Pk[i][m] * fac[m][j];
+          tmp[i][j] = s;
+        }
+      for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) Pk[i][j] = tmp[i][j];
+    }
+    S al = cs_abs(lam[k]);
+    for (int i = 0; i < 5; ++i)
+      for (int j = 0; j < 5; ++j) absM[i][j] += al * Pk[i][j];
+  }
+  S dq[5], t1[5], diss[5];
+  for (int k = 0; k < 5; ++k) dq[k] = qp[k] - qm[k];
+  for (int i = 0; i < 5; ++i) {
+    S s = 0.0;
+    for (int j = 0; j < 5; ++j) s += absM[i][j] * dq[j];
+    t1[i] = s;
+  }
+  for (int i = 0; i < 5; ++i) {
+    S s = 0.0;
+    for (int j = 0; j < 5; ++j) s += G[i][j] * t1[j];
+    diss[i] = s;
+  }
+  S fm[5], fp[5];
+  euler_flux3(qm, n, ph, fm);
+  euler_flux3(qp, n, ph, fp);
+  for (int k = 0; k < 5; ++k) out[k] = (0.5 * (fm[k] + fp[k]) - 0.5 * diss[k]) * dS;
+}
+
+// Boundary ghost states in 3D (reading, as in 2D): slip wall (p, u - 2 u_n n, T),
+// far field the free stream.  n is the unit outward normal.
+template <class S>
+static void ghost_state3(int bc, const S qm[5], const double n[3], const double qinf[5], S qg[5]) {
+  if (bc == 4) {
+    for (int v = 0; v < 5; ++v) qg[v] = qinf[v];
+    return;
+  }
+  S un = qm[1] * n[0] + qm[2] * n[1] + qm[3] * n[2];
+  qg[0] = qm[0]; qg[4] = qm[4];
+  for (int c = 0; c < 3; ++c) qg[1 + c] = qm[1 + c] - 2.0 * un * n[c];
+}
+
+// ---- geometry of a hexahedron
+static void map3(int Ng, const double* xn, const double r[3], double X[3], double dX[3][3]) {
+  std::vector<double> g(Ng + 1);
+  for (int a = 0; a <= Ng; ++a) g[a] = -1.0 + 2.0 * a / (Ng > 0 ? Ng : 1);
+  for (int n = 0; n < 3; ++n) { X[n] = 0.0; dX[n][0] = dX[n][1] = dX[n][2] = 0.0; }
+  for (int c = 0; c <= Ng; ++c)
+    for (int b = 0; b <= Ng; ++b)
+      for (int a = 0; a <= Ng; ++a) {
+        double la = lagrange(g, a, r[0]), lb = lagrange(g, b, r[1]), lc = lagrange(g, c, r[2]);
+        double da = lagrange_deriv(g, a, r[0]), db = lagrange_deriv(g, b, r[1]), dc = lagrange_deriv(g, c, r[2]);
+        const double* Xn = xn + ((c * (Ng + 1) + b) * (Ng + 1) + a) * 3;
+        for (int n = 0; n < 3; ++n) {
+          X[n] += la * lb * lc * Xn[n];
+          dX[n][0] += da * lb * lc * Xn[n];
+          dX[n][1] += la * db * lc * Xn[n];
+          dX[n][2] += la * lb * dc * Xn[n];
+        }
+      }
+}
+
+struct LevelGeom3 {
+  int P, n1, N, NF;          // NF = (P+1)^2 points per face
+  Basis1D b;
+  std::vector<double> Ja;    // (e, pt, i, n): J a^i_n at the solution points
+  std::vector<double> J;     // (e, pt)
+  std::vector<double> xyz;   // (e, pt, 3)
+  std::vector<double> fS;    // (e, face, fp, 3): outward area-scaled normal
+};
+
+// Reference coordinates of face point (a, b) of face f.
+static void face_ref(const Basis1D& b, int f, int a, int bb, double r[3]) {
+  int d = f / 2, t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  r[d] = (f & 1) ? 1.0 : -1.0;
+  r[t1] = b.x[a];
+  r[t2] = b.x[bb];
+}
+
+// Solution point on the line normal to face f through face point (a, b), at
+// position m along that line.
+static inline int line_pt3(int P, int f, int a, int bb, int m) {
+  int n1 = P + 1, d = f / 2, idx[3];
+  int t1 = d == 0 ? 1 : 0, t2 = d == 2 ? 1 : 2;
+  idx[d] = m; idx[t1] = a; idx[t2] = bb;
+  return (idx[2] * n1 + idx[1]) * n1 + idx[0];
+}
+
+// Neighbour's face point of (a, b) under orientation o.
+static inline void face_map3(int o, int P, int a, int bb, int* a2, int* b2) {
+  int s = (o & 4) ? bb : a, t = (o & 4) ? a : bb;
+  *a2 = (o & 1) ? P - s : s;
+  *b2 = (o & 2) ? P - t : t;
+}
+
+// Conservative-curl metric terms J a^i_n of one element at reference point r:
+// -(d_j W^n_k - d_k W^n_j), (i, j, k) cyclic, W^n_k = X_l dX_m/dxi_k with
+// (n, m, l) cyclic, interpolated at the Gauss-Lobatto points gl.
+static void curl_metrics(const std::vector<double>& gl, const std::vector<double>& W, const double r[3],
+                         double Ja[3][3]) {
+  const int ng = (int)gl.size();
+  std::vector<double> l[3], dl[3];
+  for (int d = 0; d < 3; ++d) {
+    l[d].resize(ng); dl[d].resize(ng);
+    for (int a = 0; a < ng; ++a) { l[d][a] = lagrange(gl, a, r[d]); dl[d][a] = lagrange_deriv(gl, a, r[d]); }
+  }
+  // dW[n][k][j] = d_j W^n_k at r
+  double dW[3][3][3] = {};
+  for (int c = 0; c < ng; ++c)
+    for (int b = 0; b < ng; ++b)
+      for (int a = 0; a < ng; ++a) {
+        const double* w = &W[(size_t)((c * ng + b) * ng + a) * 9];
+        double g0 = dl[0][a] * l[1][b] * l[2][c], g1 = l[0][a] * dl[1][b] * l[2][c], g2 = l[0][a] * l[1][b] * dl[2][c];
+        for (int n = 0; n < 3; ++n)
+          for (int k = 0; k < 3; ++k) {
+            dW[n][k][0] += g0 * w[n * 3 + k];
+            dW[n][k][1] += g1 * w[n * 3 + k];
+            dW[n][k][2] += g2 * w[n * 3 + k];
+          }
+      }
+  for (int i = 0; i < 3; ++i) {
+    int j = (i + 1) % 3, k = (i + 2) % 3;
+    for (int n = 0; n < 3; ++n) Ja[i][n] = -(dW[n][k][j] - dW[n][j][k]);
+  }
+}
+
+struct OrcConfig3 {
+  int n_levels;
+  int P[8];
+  int n_smooth[8];
+  double gamma, Ma_inf, kappa;
+  int cutoff;
+  int esdirk_stages;
+  double dtau_init, dtau_max, tol;
+  int refresh_every, max_pseudo;
+  double res_scale[5];
+  double q_inf[5];
+  int refresh_always;
+};
+
+struct Level3 {
+  LevelGeom3 g;
+  std::vector<double> q, qb, S, F;
+  std::vector<double> lu;
+  std::vector<int> piv;
+};
+
+struct Oracle3 {
+  OrcConfig3 cfg;
+  Phys ph;
+  int E, Ng;
+  std::vector<double> nodes;
+  std::vector<int> nbr;
+  std::vector<Level3> lev;
+  std::vector<std::vector<double>> Rm, Pm;
+  std::vector<double> src;
+  double omega_dt, dtau;
+  double A[6][6], b[6], c[6];
+  int s;
+};
+
+static void build_level_geom3(Oracle3* o, int P, LevelGeom3* g) {
+  g->P = P; g->n1 = P + 1; g->N = g->n1 * g->n1 * g->n1; g->NF = g->n1 * g->n1;
+  g->b = make_basis(P);
+  const int n1 = g->n1, E = o->E, Ng = o->Ng, nn = (Ng + 1) * (Ng + 1) * (Ng + 1);
+  const std::vector<double> gl = gll_nodes(P > 1 ? P : 1);
+  const int ng = (int)gl.size();
+  g->Ja.assign((size_t)E * g->N * 9, 0.0);
+  g->J.assign((size_t)E * g->N, 0.0);
+  g->xyz.assign((size_t)E * g->N * 3, 0.0);
+  g->fS.assign((size_t)E * 6 * g->NF * 3, 0.0);
+  for (int e = 0; e < E; ++e) {
+    const double* xn = &o->nodes[(size_t)e * nn * 3];
+    // W^n_k = X_l dX_m/dxi_k at the Gauss-Lobatto points, (n, m, l) cyclic
+    std::vector<double> W((size_t)ng * ng * ng * 9);
+    for (int c = 0; c < ng; ++c)
+      for (int b = 0; b < ng; ++b)
+        for (int a = 0; a < ng; ++a) {
+          double r[3] = {gl[a], gl[b], gl[c]}, X[3], dX[3][3];
+          map3(Ng, xn, r, X, dX);
+          double* w = &W[(size_t)((c * ng + b) * ng + a) * 9];
+          for (int n = 0; n < 3; ++n) {
+            int m = (n + 1) % 3, l = (n + 2) % 3;
+            for (int k = 0; k < 3; ++k) w[n * 3 + k] = X[l] * dX[m][k];
+          }
+        }
+    for (int kk = 0; kk < n1; ++kk)
+      for (int j = 0; j < n1; ++j)
+        for (int i = 0; i < n1; ++i) {
+          int pt = (kk * n1 + j) * n1 + i;
+          double r[3] = {g->b.x[i], g->b.x[j], g->b.x[kk]}, X[3], dX[3][3], Ja[3][3];
+          map3(Ng, xn, r, X, dX);
+          curl_metrics(gl, W, r, Ja);
+          for (int ii = 0; ii < 3; ++ii)
+            for (int n = 0; n < 3; ++n) g->Ja[((size_t)e * g->N + pt) * 9 + ii * 3 + n] = Ja[ii][n];
+          g->J[(size_t)e * g->N + pt] = dX[0][0] * (dX[1][1] * dX[2][2] - dX[1][2] * dX[2][1]) -
+                                        dX[0][1] * (dX[1][0] * dX[2][2] - dX[1][2] * dX[2][0]) +
+                                        dX[0][2] * (dX[1][0] * dX[2][1] - dX[1][1] * dX[2][0]);
+          for (int n = 0; n < 3; ++n) g->xyz[((size_t)e * g->N + pt) * 3 + n] = X[n];
+        }
+    for (int f = 0; f < 6; ++f)
+      for (int bb = 0; bb < n1; ++bb)
+        for (int a = 0; a < n1; ++a) {
+          double r[3], Ja[3][3];
+          face_ref(g->b, f, a, bb, r);
+          curl_metrics(gl, W, r, Ja);
+          const double sg = (f & 1) ? 1.0 : -1.0;
+          double* s = &g->fS[(((size_t)e * 6 + f) * g->NF + bb * n1 + a) * 3];
+          for (int n = 0; n < 3; ++n) s[n] = sg * Ja[f / 2][n];
+        }
+  }
+}
+
+template <class S>
+static void trace_state3(const Basis1D& b, const S* qe, int N, int f, int a, int bb, S out[5]) {
+  int n1 = b.P + 1;
+  const std::vector<double>& l = (f & 1) ? b.lp : b.lm;
+  for (int v = 0; v < 5; ++v) {
+    S s = 0.0;
+    for (int m = 0; m < n1; ++m) s += l[m] * qe[v * N + line_pt3(b.P, f, a, bb, m)];
+    out[v] = s;
+  }
+}
+
+// Frozen neighbour traces at every element face point (5 values each).
+static void neighbour_traces3(const Oracle3* o, const Level3& L, const double* q, std::vector<double>& tr) {
+  const int E = o->E, N = L.g.N, n1 = L.g.n1, NF = L.g.NF, P = L.g.P;
+  tr.assign((size_t)E * 6 * NF * 5, 0.0);
+  std::vector<double> qe(5 * N);
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      const int en = o->nbr[(e * 6 + f) * 3], fn = o->nbr[(e * 6 + f) * 3 + 1], or_ = o->nbr[(e * 6 + f) * 3 + 2];
+      if (en < 0) continue;
+      for (int v = 0; v < 5; ++v)
+        for (int p = 0; p < N; ++p) qe[v * N + p] = q[((size_t)v * E + en) * N + p];
+      for (int bb = 0; bb < n1; ++bb)
+        for (int a = 0; a < n1; ++a) {
+          int a2, b2;
+          face_map3(or_, P, a, bb, &a2, &b2);
+          double t[5];
+          trace_state3<double>(L.g.b, qe.data(), N, fn, a2, b2, t);
+          for (int v = 0; v < 5; ++v) tr[(((size_t)e * 6 + f) * NF + bb * n1 + a) * 5 + v] = t[v];
+        }
+    }
+}
+
+// FR/CPR residual of one hexahedron, R = -div f (eq. eqn:FR_diff, d = 3):
+// contravariant fluxes F^i = f . J a^i at the solution points, the Lagrange
+// derivative along each reference direction, and the DG correction of the
+// jumps between the common normal flux (Roe, through the outward J a^d of the
+// face point) and the extrapolated flux polynomial.  Neighbours frozen.
+template <class S>
+static void element_residual3(const Oracle3* o, const Level3& L, int e, const S* qe, const double* ntr, S* Re) {
+  const Basis1D& b = L.g.b;
+  const int P = L.g.P, n1 = L.g.n1, N = L.g.N, NF = L.g.NF;
+  const Phys& ph = o->ph;
+  std::vector<S> Ft(3 * 5 * N);   // [i][v][pt]
+  for (int pt = 0; pt < N; ++pt) {
+    S q[5];
+    for (int v = 0; v < 5; ++v) q[v] = qe[v * N + pt];
+    for (int i = 0; i < 3; ++i) {
+      const double* ja = &L.g.Ja[((size_t)e * N + pt) * 9 + i * 3];
+      S f[5];
+      euler_flux3(q, ja, ph, f);
+      for (int v = 0; v < 5; ++v) Ft[(i * 5 + v) * N + pt] = f[v];
+    }
+  }
+  std::vector<S> acc(5 * N, S(0.0));
+  for (int v = 0; v < 5; ++v)
+    for (int kk = 0; kk < n1; ++kk)
+      for (int j = 0; j < n1; ++j)
+        for (int i = 0; i < n1; ++i) {
+          S s = 0.0;
+          for (int m = 0; m < n1; ++m) {
+            s += b.D[i * n1 + m] * Ft[(0 * 5 + v) * N + (kk * n1 + j) * n1 + m];
+            s += b.D[j * n1 + m] * Ft[(1 * 5 + v) * N + (kk * n1 + m) * n1 + i];
+            s += b.D[kk * n1 + m] * Ft[(2 * 5 + v) * N + (m * n1 + j) * n1 + i];
+          }
+          acc[v * N + (kk * n1 + j) * n1 + i] = s;
+        }
+  for (int f = 0; f < 6; ++f) {
+    const int en = o->nbr[(e * 6 + f) * 3], bc = o->nbr[(e * 6 + f) * 3 + 1];
+    const int d = f / 2;
+    const double sg = (f & 1) ? 1.0 : -1.0;
+    const std::vector<double>& l = (f & 1) ? b.lp : b.lm;
+    const std::vector<double>& gp = (f & 1) ? b.gR : b.gL;
+    for (int bb = 0; bb < n1; ++bb)
+      for (int a = 0; a < n1; ++a) {
+        const int fp = bb * n1 + a;
+        S qm[5], qp[5], fo[5];
+        trace_state3(b, qe, N, f, a, bb, qm);
+        const double* Sv = &L.g.fS[(((size_t)e * 6 + f) * NF + fp) * 3];
+        if (en < 0) {
+          double dS = std::sqrt(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
+          double nu[3] = {Sv[0] / dS, Sv[1] / dS, Sv[2] / dS};
+          ghost_state3(bc, qm, nu, o->cfg.q_inf, qp);
+        } else {
+          const double* t = &ntr[(((size_t)e * 6 + f) * NF + fp) * 5];
+          for (int v = 0; v < 5; ++v) qp[v] = t[v];
+        }
+        roe_flux3(qm, qp, Sv, ph, fo);
+        for (int v = 0; v < 5; ++v) {
+          S loc = 0.0;
+          for (int m = 0; m < n1; ++m) loc += l[m] * Ft[(d * 5 + v) * N + line_pt3(P, f, a, bb, m)];
+          S jump = sg * fo[v] - loc;
+          for (int m = 0; m < n1; ++m) acc[v * N + line_pt3(P, f, a, bb, m)] += gp[m] * jump;
+        }
+      }
+  }
+  for (int v = 0; v < 5; ++v)
+    for (int pt = 0; pt < N; ++pt) Re[v * N + pt] = -acc[v * N + pt] / L.g.J[(size_t)e * N + pt];
+}
+
+static void full_residual3(const Oracle3* o, const Level3& L, const double* q, double* R) {
+  const int N = L.g.N, E = o->E;
+  std::vector<double> tr;
+  neighbour_traces3(o, L, q, tr);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+  for (int e = 0; e < E; ++e) {
+    std::vector<double> qe(5 * N), Re(5 * N);
+    for (int v = 0; v < 5; ++v)
+      for (int p = 0; p < N; ++p) qe[v * N + p] = q[((size_t)v * E + e) * N + p];
+    element_residual3<double>(o, L, e, qe.data(), tr.data(), Re.data());
+    for (int v = 0; v < 5; ++v)
+      for (int p = 0; p < N; ++p) R[((size_t)v * E + e) * N + p] = Re[v * N + p];
+  }
+}
+
+// Level system F_l(q) - S_l, eq. ESDIRK_primitive (coarse levels without the
+// stage source, which cancels against S_l: the 2D reading).
+static void level_F3(const Oracle3* o, int l, const double* q, bool with_src, bool minus_S, double* F) {
+  const Level3& L = o->lev[l];
+  const int N = L.g.N, E = o->E;
+  const size_t tot = (size_t)5 * E * N;
+  full_residual3(o, L, q, F);
+  for (int e = 0; e < E; ++e)
+    for (int p = 0; p < N; ++p) {
+      double qq[5], qc[5];
+      for (int v = 0; v < 5; ++v) qq[v] = q[((size_t)v * E + e) * N + p];
+      cons_from_prim3(qq, o->ph, qc);
+      for (int v = 0; v < 5; ++v) {
+        size_t id = ((size_t)v * E + e) * N + p;
+        F[id] += -qc[v] / o->omega_dt;
+        if (with_src) F[id] += o->src[id];
+      }
+    }
+  if (minus_S)
+    for (size_t i = 0; i < tot; ++i) F[i] -= L.S[i];
+}
+
+// Element block D_e = Gamma/dtau + M/(omega dt) - dR_e/dq_e by complex step.
+static void element_block3(const Oracle3* o, const Level3& L, int e, const double* q, const double* ntr,
+                           double dtau, double* Dm) {
+  const int N = L.g.N, n = 5 * N, E = o->E;
+  const double h = 1e-30;
+  std::vector<cplx> qe(n), Re(n);
+  for (int col = 0; col < n; ++col) {
+    for (int v = 0; v < 5; ++v)
+      for (int p = 0; p < N; ++p) qe[v * N + p] = cplx(q[((size_t)v * E + e) * N + p], 0.0);
+    qe[col] += cplx(0.0, h);
+    element_residual3<cplx>(o, L, e, qe.data(), ntr, Re.data());
+    for (int row = 0; row < n; ++row) Dm[(size_t)row * n + col] = -Re[row].imag() / h;
+  }
+  for (int p = 0; p < N; ++p) {
+    double qq[5];
+    for (int v = 0; v < 5; ++v) qq[v] = q[((size_t)v * E + e) * N + p];
+    double eps = precond_eps3(qq, o->ph);
+    double G[5][5], M[5][5];
+    Gamma_matrix3(qq, eps, o->ph, G);
+    M_matrix3(qq, o->ph, M);
+    for (int a = 0; a < 5; ++a)
+      for (int c = 0; c < 5; ++c)
+        Dm[(size_t)(a * N + p) * n + (c * N + p)] += G[a][c] / dtau + M[a][c] / o->omega_dt;
+  }
+}
+
+static int refresh_level3(Oracle3* o, int l) {
+  Level3& L = o->lev[l];
+  const int N = L.g.N, n = 5 * N, E = o->E;
+  std::vector<double> tr;
+  neighbour_traces3(o, L, L.q.data(), tr);
+  L.lu.assign((size_t)E * n * n, 0.0);
+  L.piv.assign((size_t)E * n, 0);
+  int singular = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 2) reduction(| : singular)
+#endif
+  for (int e = 0; e < E; ++e) {
+    double* Dm = &L.lu[(size_t)e * n * n];
+    element_block3(o, L, e, L.q.data(), tr.data(), o->dtau, Dm);
+    if (!lu_factor(n, Dm, &L.piv[(size_t)e * n])) singular |= 1;
+  }
+  return singular ? -4 : 0;
+}
+
+// Element-Jacobi sweeps, eq. smoothing_element_jacobi.
+static void smooth3(Oracle3* o, int l, int nsweep) {
+  Level3& L = o->lev[l];
+  const int N = L.g.N, n = 5 * N, E = o->E;
+  L.F.resize((size_t)5 * E * N);
+  for (int s = 0; s < nsweep; ++s) {
+    level_F3(o, l, L.q.data(), l == 0, l > 0, L.F.data());
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int e = 0; e < E; ++e) {
+      std::vector<double> x(n);
+      for (int v = 0; v < 5; ++v)
+        for (int p = 0; p < N; ++p) x[v * N + p] = L.F[((size_t)v * E + e) * N + p];
+      lu_solve(n, &L.lu[(size_t)e * n * n], &L.piv[(size_t)e * n], x.data());
+      for (int v = 0; v < 5; ++v)
+        for (int p = 0; p < N; ++p) L.q[((size_t)v * E + e) * N + p] += x[v * N + p];
+    }
+  }
+}
+
+// out[v][e][(k,j,i)] = sum op[i][a] op[j][b] op[k][c] in[v][e][(c,b,a)].
+static void apply_tensor3(const std::vector<double>& op, int nout, int nin, int E, const double* in,
+                          double* out) {
+  const int Nin = nin * nin * nin, Nout = nout * nout * nout;
+  for (int v = 0; v < 5; ++v)
+    for (int e = 0; e < E; ++e)
+      for (int k = 0; k < nout; ++k)
+        for (int j = 0; j < nout; ++j)
+          for (int i = 0; i < nout; ++i) {
+            double s = 0.0;
+            for (int c = 0; c < nin; ++c)
+              for (int bb = 0; bb < nin; ++bb)
+                for (int a = 0; a < nin; ++a)
+                  s += op[i * nin + a] * op[j * nin + bb] * op[k * nin + c] *
+                       in[((size_t)v * E + e) * Nin + (c * nin + bb) * nin + a];
+            out[((size_t)v * E + e) * Nout + (k * nout + j) * nout + i] = s;
+          }
+}
+
+// FAS V-cycle (Section 3), the 2D steps on hexahedra.
+static int vcycle_level3(Oracle3* o, int l, bool refresh) {
+  Level3& L = o->lev[l];
+  const int E = o->E;
+  if (refresh) { int st = refresh_level3(o, l); if (st) return st; }
+  smooth3(o, l, o->cfg.n_smooth[l]);
+  if (l == o->cfg.n_levels - 1) return 0;
+  Level3& C = o->lev[l + 1];
+  const int Nf = L.g.N, Nc = C.g.N;
+  std::vector<double> d((size_t)5 * E * Nf);
+  level_F3(o, l, L.q.data(), l == 0, l > 0, d.data());
+  for (auto& x : d) x = -x;
+  C.q.resize((size_t)5 * E * Nc);
+  apply_tensor3(o->Rm[l], C.g.n1, L.g.n1, E, L.q.data(), C.q.data());
+  C.qb = C.q;
+  std::vector<double> Pd((size_t)5 * E * Nc), Fc((size_t)5 * E * Nc);
+  apply_tensor3(o->Rm[l], C.g.n1, L.g.n1, E, d.data(), Pd.data());
+  level_F3(o, l + 1, C.q.data(), false, false, Fc.data());
+  C.S.resize((size_t)5 * E * Nc);
+  for (size_t i = 0; i < C.S.size(); ++i) C.S[i] = Fc[i] + Pd[i];
+  int st = vcycle_level3(o, l + 1, refresh);
+  if (st) return st;
+  std::vector<double> corr((size_t)5 * E * Nc), pc((size_t)5 * E * Nf);
+  for (size_t i = 0; i < corr.size(); ++i) corr[i] = C.q[i] - C.qb[i];
+  apply_tensor3(o->Pm[l], L.g.n1, C.g.n1, E, corr.data(), pc.data());
+  for (size_t i = 0; i < pc.size(); ++i) L.q[i] += pc[i];
+  smooth3(o, l, o->cfg.n_smooth[l]);
+  return 0;
+}
+
+// ||F|| of eq. ser with each equation divided by its reference scale.
+static double residual_norm3(const Oracle3* o, const std::vector<double>& F) {
+  const size_t plane = F.size() / 5;
+  double s = 0.0;
+  for (int v = 0; v < 5; ++v) {
+    double sc = o->cfg.res_scale[v] > 0.0 ? o->cfg.res_scale[v] : 1.0;
+    double t = 0.0;
+    for (size_t i = 0; i < plane; ++i) t += F[v * plane + i] * F[v * plane + i];
+    s += t / (sc * sc);
+  }
+  return std::sqrt(s);
+}
+
+extern "C" {
+
+int orc3_gll(int n, double* x) {
+  std::vector<double> g = gll_nodes(n);
+  for (int i = 0; i <= n; ++i) x[i] = g[i];
+  return 0;
+}
+
+int orc3_point_matrices(const double* q, double gamma, double Ma_inf, double kappa, int cutoff, double* M,
+                        double* G, double* eps_out) {
+  Phys ph = {gamma, Ma_inf, kappa, cutoff};
+  double MM[5][5], GG[5][5];
+  double e = precond_eps3(q, ph);
+  M_matrix3(q, ph, MM);
+  Gamma_matrix3(q, e, ph, GG);
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) { M[i * 5 + j] = MM[i][j]; G[i * 5 + j] = GG[i][j]; }
+  *eps_out = e;
+  return 0;
+}
+
+int orc3_flux(const double* q, const double* n, double gamma, double* f, double* A) {
+  Phys ph = {gamma, 0.0, 1.0, 0};
+  euler_flux3(q, n, ph, f);
+  double AA[5][5];
+  flux_jacobian3(q, n, ph, AA);
+  for (int i = 0; i < 5; ++i)
+    for (int j = 0; j < 5; ++j) A[i * 5 + j] = AA[i][j];
+  return 0;
+}
+
+int orc3_roe(const double* qm, const double* qp, const double* Sv, double gamma, double Ma_inf, double kappa,
+             int cutoff, double* out) {
+  Phys ph = {gamma, Ma_inf, kappa, cutoff};
+  roe_flux3(qm, qp, Sv, ph, out);
+  return 0;
+}
+
+int orc3_cons_from_prim(const double* q, double gamma, double* qc) {
+  Phys ph = {gamma, 0.0, 1.0, 0};
+  cons_from_prim3(q, ph, qc);
+  return 0;
+}
+
+void* orc3_create(const OrcConfig3* cfg, int E, int Ng, const double* nodes, const int* nbr) {
+  Oracle3* o = new Oracle3();
+  o->cfg = *cfg;
+  o->ph.gamma = cfg->gamma; o->ph.Ma_inf = cfg->Ma_inf; o->ph.kappa = cfg->kappa; o->ph.cutoff = cfg->cutoff;
+  o->E = E; o->Ng = Ng;
+  const int nn = (Ng + 1) * (Ng + 1) * (Ng + 1);
+  o->nodes.assign(nodes, nodes + (size_t)E * nn * 3);
+  o->nbr.assign(nbr, nbr + (size_t)E * 18);
+  o->lev.resize(cfg->n_levels);
+  for (int l = 0; l < cfg->n_levels; ++l) {
+    build_level_geom3(o, cfg->P[l], &o->lev[l].g);
+    const size_t tot = (size_t)5 * E * o->lev[l].g.N;
+    o->lev[l].q.assign(tot, 0.0);
+    o->lev[l].S.assign(tot, 0.0);
+  }
+  for (int l = 0; l + 1 < cfg->n_levels; ++l) {
+    o->Rm.push_back(make_restriction(o->lev[l].g.b, o->lev[l + 1].g.b));
+    o->Pm.push_back(make_prolongation(o->lev[l].g.b, o->lev[l + 1].g.b));
+  }
+  o->src.assign((size_t)5 * E * o->lev[0].g.N, 0.0);
+  o->omega_dt = 1.0;
+  o->dtau = cfg->dtau_init;
+  o->s = esdirk_tableau(cfg->esdirk_stages > 0 ? cfg->esdirk_stages : 4, o->A, o->b, o->c);
+  return o;
+}
+
+void orc3_destroy(void* h) { delete (Oracle3*)h; }
+
+// Metric terms of a level: Ja (E, N, 3, 3), J (E, N), face normals (E, 6, NF, 3), coordinates (E, N, 3).
+int orc3_geometry(void* h, int level, double* Ja, double* J, double* fS, double* xyz) {
+  const LevelGeom3& g = ((Oracle3*)h)->lev[level].g;
+  if (Ja) memcpy(Ja, g.Ja.data(), g.Ja.size() * 8);
+  if (J) memcpy(J, g.J.data(), g.J.size() * 8);
+  if (fS) memcpy(fS, g.fS.data(), g.fS.size() * 8);
+  if (xyz) memcpy(xyz, g.xyz.data(), g.xyz.size() * 8);
+  return 0;
+}
+
+int orc3_residual(void* h, int level, const double* q, double* R) {
+  Oracle3* o = (Oracle3*)h;
+  full_residual3(o, o->lev[level], q, R);
+  return 0;
+}
+
+int orc3_set_stage(void* h, const double* src, double omega_dt) {
+  Oracle3* o = (Oracle3*)h;
+  memcpy(o->src.data(), src, o->src.size() * 8);
+  o->omega_dt = omega_dt;
+  return 0;
+}
+
+int orc3_stage_F(void* h, int level, const double* q, double* F) {
+  level_F3((Oracle3*)h, level, q, level == 0, false, F);
+  return 0;
+}
+
+int orc3_blocks(void* h, int level, const double* q, double dtau, double* D) {
+  Oracle3* o = (Oracle3*)h;
+  const Level3& L = o->lev[level];
+  const int n = 5 * L.g.N;
+  std::vector<double> tr;
+  neighbour_traces3(o, L, q, tr);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 2)
+#endif
+  for (int e = 0; e < o->E; ++e) element_block3(o, L, e, q, tr.data(), dtau, D + (size_t)e * n * n);
+  return 0;
+}
+
+int orc3_restrict(void* h, int lf, const double* qf, double* qc) {
+  Oracle3* o = (Oracle3*)h;
+  apply_tensor3(o->Rm[lf], o->lev[lf + 1].g.n1, o->lev[lf].g.n1, o->E, qf, qc);
+  return 0;
+}
+
+int orc3_prolong(void* h, int lf, const double* qc, double* qf) {
+  Oracle3* o = (Oracle3*)h;
+  apply_tensor3(o->Pm[lf], o->lev[lf].g.n1, o->lev[lf + 1].g.n1, o->E, qc, qf);
+  return 0;
+}
+
+// One V-cycle on the finest-level state q (in/out) with the current stage data.
+int orc3_vcycle(void* h, double* q, double dtau, int refresh) {
+  Oracle3* o = (Oracle3*)h;
+  Level3& L = o->lev[0];
+  memcpy(L.q.data(), q, L.q.size() * 8);
+  o->dtau = dtau;
+  int st = vcycle_level3(o, 0, refresh != 0);
+  memcpy(q, L.q.data(), L.q.size() * 8);
+  return st;
+}
+
+// Pseudo-transient continuation of one stage (Section 2.4), as stage_solve.
+int orc3_stage_solve(void* h, double* q, int* iters, double* drop) {
+  Oracle3* o = (Oracle3*)h;
+  std::vector<double> F(o->lev[0].q.size());
+  double dtau = o->cfg.dtau_init, dtau_max = o->cfg.dtau_max, n0 = 0.0, prev = 0.0, built = 0.0;
+  for (int m = 0;; ++m) {
+    level_F3(o, 0, q, true, false, F.data());
+    double nm = residual_norm3(o, F);
+    if (m == 0) n0 = nm;
+    if (nm <= o->cfg.tol * n0 || n0 == 0.0) { *iters = m; *drop = n0 > 0 ? nm / n0 : 0.0; return 0; }
+    if (!std::isfinite(nm)) { *iters = m; *drop = nm; return -5; }
+    if (m >= o->cfg.max_pseudo) { *iters = m; *drop = nm / n0; return -6; }
+    if (m > 0) dtau = ser_next(dtau, prev, nm, dtau_max);
+    bool refresh = refresh_due(m, o->cfg.refresh_every, built, dtau_max, o->cfg.refresh_always != 0);
+    if (refresh) built = dtau;
+    int st = orc3_vcycle(o, q, dtau, refresh);
+    if (st) return st;
+    prev = nm;
+  }
+}
+
+// One ESDIRK physical step (eq. ESDIRK_ns), as orc_esdirk_step.
+int orc3_esdirk_step(void* h, double* q, double dt, int* iters, double* drops) {
+  Oracle3* o = (Oracle3*)h;
+  Level3& L = o->lev[0];
+  const int E = o->E, N = L.g.N, s = o->s;
+  const size_t tot = (size_t)5 * E * N;
+  std::vector<double> qcn(tot), qi(q, q + tot);
+  std::vector<std::vector<double>> Rs(s, std::vector<double>(tot));
+  for (int e = 0; e < E; ++e)
+    for (int p = 0; p < N; ++p) {
+      double qq[5], qc[5];
+      for (int v = 0; v < 5; ++v) qq[v] = q[((size_t)v * E + e) * N + p];
+      cons_from_prim3(qq, o->ph, qc);
+      for (int v = 0; v < 5; ++v) qcn[((size_t)v * E + e) * N + p] = qc[v];
+    }
+  full_residual3(o, L, qi.data(), Rs[0].data());
+  o->omega_dt = o->A[1][1] * dt;
+  for (int i = 1; i < s; ++i) {
+    for (size_t k = 0; k < tot; ++k) {
+      double acc = qcn[k];
+      for (int j = 0; j < i; ++j) acc += dt * o->A[i][j] * Rs[j][k];
+      o->src[k] = acc / o->omega_dt;
+    }
+    int st = orc3_stage_solve(o, qi.data(), &iters[i - 1], &drops[i - 1]);
+    if (st) return st;
+    full_residual3(o, L, qi.data(), Rs[i].data());
+  }
+  for (int e = 0; e < E; ++e)
+    for (int p = 0; p < N; ++p) {
+      double qc[5], qq[5];
+      for (int v = 0; v < 5; ++v) {
+        size_t k = ((size_t)v * E + e) * N + p;
+        double acc = qcn[k];
+        for (int i = 0; i < s; ++i) acc += dt * o->b[i] * Rs[i][k];
+        qc[v] = acc;
+      }
+      prim_from_cons3(qc, o->ph, qq);
+      for (int v = 0; v < 5; ++v) q[((size_t)v * E + e) * N + p] = qq[v];
+    }
+  return 0;
+}
+
+}  // extern "C"

@@ -597,7 +597,7 @@ static pmg_status check_singular(Ctx& c) {
   PMG_CK(cudaStreamSynchronize(c.stream));
   if (flag) {
     cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.stream);
-    return fail(PMG_ESINGULAR, "element block " + std::to_string(flag - 1) + " is singular to working precision (pivot not above eps^2)");
+    return fail(PMG_ESINGULAR, "element block " + std::to_string(flag - 1) + " is singular to working precision (pivot not above n eps)");
   }
   return PMG_OK;
 }

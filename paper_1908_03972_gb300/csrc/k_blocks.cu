@@ -14,8 +14,9 @@
 //    (FP64, or FP32 for the mixed-precision smoother).  The explicit inverse
 //    turns every smoothing sweep into a batched matrix-vector product.  The
 //    equilibrated rows have unit size, so a pivot that is not finite or not
-//    above eps^2 of the working precision marks a block that is singular to
-//    that precision: the element is flagged for the host (PMG_ESINGULAR).
+//    above n eps of the working precision (the rounding a dependent row leaves
+//    after elimination) marks a block that is singular to that precision: the
+//    element is flagged for the host (PMG_ESINGULAR).
 //  * apply: x = cs .* (inv(D^) (rs .* r)); each thread owns four consecutive
 //    rows and streams the column-major inverse with 16-byte (FP32) or
 //    2x16-byte (FP64) loads.  This stream is the smoother's HBM/L2 traffic.
@@ -161,10 +162,11 @@ __device__ __forceinline__ double pow2_inv_scale(double m) {
   return ldexp(1.0, -ex);
 }
 
-// Smallest pivot magnitude accepted: eps^2 of the working precision.
-template <class W> struct PivotFloor;
-template <> struct PivotFloor<float> { static constexpr double value = 1.1920928955078125e-07 * 1.1920928955078125e-07; };
-template <> struct PivotFloor<double> { static constexpr double value = 2.220446049250313e-16 * 2.220446049250313e-16; };
+// Machine epsilon of the working precision; the smallest pivot magnitude
+// accepted is n eps (the equilibrated rows have unit size).
+template <class W> struct Eps;
+template <> struct Eps<float> { static constexpr double value = 1.1920928955078125e-07; };
+template <> struct Eps<double> { static constexpr double value = 2.220446049250313e-16; };
 
 template <class W>
 __global__ void __launch_bounds__(256) factor_kernel(int n, const double* __restrict__ Din, W* __restrict__ Dinv,
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(256) factor_kernel(int n, const double* __rest
       if (tid == 0) {
         s_piv = bi;
         perm[k] = bi;
-        if (!(best > PivotFloor<T>::value) || isinf(best)) s_bad = 1;
+        if (!(best > n * Eps<T>::value) || isinf(best)) s_bad = 1;
       }
     }
     __syncthreads();

