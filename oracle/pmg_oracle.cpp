@@ -1478,13 +1478,18 @@ int orc_esdirk_step(void* h, double* q, double dt, int* iters, double* drops) {
 // metric identity, so uniform flow is not steady.  Reading (the paper is
 // silent): the conservative curl form, J a^i_n = -e_i . curl_xi(I(X_l grad_xi
 // X_m)) with (n, m, l) cyclic, where I interpolates at the Gauss-Lobatto
-// points of degree max(P, 1).  These metric terms are polynomials of degree
-// <= P in every direction (exact at the Gauss solution points), their
-// divergence vanishes identically, and on a face the normal component
+// points of degree Pg = max(P, Ng, 1).  On a face the normal component
 // involves only the face's own Gauss-Lobatto values, so both elements of a
-// face see the same normal.  The surface normal of a face point is the
-// outward J a^d of that polynomial; |J| at the solution points is the
-// determinant of the exact map.
+// face see the same normal; with Pg >= Ng the interpolated gradient of the
+// map is exact, its curl vanishes, and the normal does not change when an
+// element is translated (periodic images of a face agree).  For P >= Ng
+// these metric terms are polynomials of degree <= P in every direction, their
+// discrete divergence at the Gauss solution points vanishes and uniform flow
+// is exactly steady; below the geometry order (coarse P-levels of curved
+// meshes) the scheme stays conservative and free-stream preservation holds
+// to the interpolation error, as with the analytic metrics of the 2D
+// elements.  The surface normal of a face point is the outward J a^d of the
+// polynomial; |J| at the solution points is the determinant of the exact map.
 // ===========================================================================
 
 // Gauss-Lobatto points of degree n (n + 1 points): -1, the roots of L_n', +1.
@@ -1817,7 +1822,8 @@ static void build_level_geom3(Oracle3* o, int P, LevelGeom3* g) {
   g->P = P; g->n1 = P + 1; g->N = g->n1 * g->n1 * g->n1; g->NF = g->n1 * g->n1;
   g->b = make_basis(P);
   const int n1 = g->n1, E = o->E, Ng = o->Ng, nn = (Ng + 1) * (Ng + 1) * (Ng + 1);
-  const std::vector<double> gl = gll_nodes(P > 1 ? P : 1);
+  const int Pg = std::max(std::max(P, Ng), 1);
+  const std::vector<double> gl = gll_nodes(Pg);
   const int ng = (int)gl.size();
   g->Ja.assign((size_t)E * g->N * 9, 0.0);
   g->J.assign((size_t)E * g->N, 0.0);

@@ -301,38 +301,55 @@ def _orient_map(o: int, P: int, a, b):
     return (P - s if o & 1 else s), (P - t if o & 2 else t)
 
 
-def hex_connectivity(ids: np.ndarray, Ng: int, boundary=None):
-    """Face neighbours and orientation codes of hexahedra from the global ids
-    of their geometry nodes ``ids`` (E, (Ng+1)**3) (periodic copies of a node
-    share its id).  Faces left unmatched get ``boundary(e, f)`` as their type."""
-    E = ids.shape[0]
+def hex_connectivity(nodes: np.ndarray, Ng: int, period=(None, None, None), boundary=None, tol: float = 1e-9):
+    """Face neighbours and orientation codes of hexahedra from their geometry.
+
+    Faces are paired by their centroids (coordinates taken modulo
+    ``period[d]`` in periodic directions); the orientation code of a pair is
+    the one under which every face node of one face lies on the matching node
+    of the other.  Faces left unmatched get ``boundary(e, f)`` as their type."""
+    from scipy.spatial import cKDTree
+    E = nodes.shape[0]
     fl = [_face_local_nodes(f, Ng) for f in range(6)]
-    table = {}
+    ext = np.ptp(nodes.reshape(-1, 3), axis=0).max() + 1.0
+    lo = nodes.reshape(-1, 3).min(axis=0)
+    box = np.array([period[d] if period[d] else 1e6 * ext for d in range(3)])
+    cent = np.zeros((E * 6, 3))
     for e in range(E):
         for f in range(6):
-            key = tuple(sorted(ids[e][fl[f]].reshape(-1).tolist()))
-            table.setdefault(key, []).append((e, f))
-    nbr = np.zeros((E, 6, 3), dtype=np.int32)
+            cent[e * 6 + f] = nodes[e][fl[f].reshape(-1)].mean(axis=0)
+    cw = np.mod(cent - lo, box)
+    tree = cKDTree(cw, boxsize=box)
+    scale = tol * ext
     A, B = np.meshgrid(np.arange(Ng + 1), np.arange(Ng + 1), indexing="xy")
-    for key, lst in table.items():
-        if len(lst) == 1:
-            e, f = lst[0]
-            if boundary is None:
-                raise ValueError(f"unmatched face {f} of element {e}")
-            nbr[e, f] = (-1, boundary(e, f), 0)
-            continue
-        if len(lst) != 2:
-            raise ValueError("a face is shared by more than two elements")
-        for (e, f), (e2, f2) in (lst, lst[::-1]):
-            mine = ids[e][fl[f]]
-            theirs = ids[e2][fl[f2]]
-            for o in range(8):   # the first code under which every face node matches
+
+    def wrapped(d):
+        for k in range(3):
+            if period[k]:
+                d[..., k] -= period[k] * np.round(d[..., k] / period[k])
+        return d
+
+    nbr = np.zeros((E, 6, 3), dtype=np.int32)
+    for e in range(E):
+        for f in range(6):
+            cand = [c for c in tree.query_ball_point(cw[e * 6 + f], scale) if c != e * 6 + f]
+            if not cand:
+                if boundary is None:
+                    raise ValueError(f"unmatched face {f} of element {e}")
+                nbr[e, f] = (-1, boundary(e, f), 0)
+                continue
+            if len(cand) != 1:
+                raise ValueError(f"face {f} of element {e} matches {len(cand)} faces")
+            e2, f2 = divmod(cand[0], 6)
+            mine = nodes[e][fl[f]]
+            theirs = nodes[e2][fl[f2]]
+            for o in range(8):
                 a2, b2 = _orient_map(o, Ng, A, B)
-                if np.array_equal(theirs[b2, a2], mine):
+                if np.abs(wrapped(mine - theirs[b2, a2])).max() <= scale:
                     nbr[e, f] = (e2, f2, o)
                     break
             else:
-                raise ValueError(f"faces ({e},{f}) and ({e2},{f2}) share nodes but no orientation matches")
+                raise ValueError(f"faces ({e},{f}) and ({e2},{f2}) meet but no orientation matches")
     return nbr
 
 
@@ -352,8 +369,6 @@ def _box3d(nx, ny, nz, lo, hi, Ng, perturb, seed, periodic=(True, True, True)):
     E = nx * ny * nz
     n1 = Ng + 1
     nodes = np.zeros((E, n1 ** 3, 3))
-    ids = np.zeros((E, n1 ** 3), dtype=np.int64)
-    M = [nx * Ng, ny * Ng, nz * Ng]
     for kz in range(nz):
         for jy in range(ny):
             for ix in range(nx):
@@ -377,17 +392,7 @@ def _box3d(nx, ny, nz, lo, hi, Ng, perturb, seed, periodic=(True, True, True)):
                 nodes[e, :, 0] = (X + sc * dX).reshape(-1)
                 nodes[e, :, 1] = (Y + sc * dY).reshape(-1)
                 nodes[e, :, 2] = (Z + sc * dZ).reshape(-1)
-                I = ix * Ng + np.rint(A * Ng).astype(np.int64)
-                J = jy * Ng + np.rint(B * Ng).astype(np.int64)
-                K = kz * Ng + np.rint(C * Ng).astype(np.int64)
-                if periodic[0]:
-                    I = I % M[0]
-                if periodic[1]:
-                    J = J % M[1]
-                if periodic[2]:
-                    K = K % M[2]
-                ids[e] = ((K * (M[1] + 1) + J) * (M[0] + 1) + I).reshape(-1)
-    return nodes, ids
+    return nodes
 
 
 # the 24 proper rotations of the reference cube (signed permutation matrices, det +1)
@@ -407,15 +412,14 @@ def _cube_rotations():
 CUBE_ROTATIONS = _cube_rotations()
 
 
-def rotate_hex_elements(nodes, ids, Ng: int, rotations: dict):
+def rotate_hex_elements(nodes, Ng: int, rotations: dict):
     """Renumber the local nodes of the listed elements ({element: rotation
     index into CUBE_ROTATIONS}); the geometry is unchanged."""
     nodes = nodes.copy()
-    ids = ids.copy()
     n1 = Ng + 1
     for e, ri in rotations.items():
         R = CUBE_ROTATIONS[ri]
-        old_n, old_i = nodes[e].copy(), ids[e].copy()
+        old_n = nodes[e].copy()
         for c in range(n1):
             for b in range(n1):
                 for a in range(n1):
@@ -423,8 +427,7 @@ def rotate_hex_elements(nodes, ids, Ng: int, rotations: dict):
                     ro = R.T @ rn
                     ao, bo, co = ((ro + Ng) // 2).tolist()
                     nodes[e, (c * n1 + b) * n1 + a] = old_n[(co * n1 + bo) * n1 + ao]
-                    ids[e, (c * n1 + b) * n1 + a] = old_i[(co * n1 + bo) * n1 + ao]
-    return nodes, ids
+    return nodes
 
 
 def periodic_box3d(nx: int, ny: int, nz: int, lo=(0.0, 0.0, 0.0), hi=(10.0, 10.0, 10.0), Ng: int = 1,
@@ -435,10 +438,11 @@ def periodic_box3d(nx: int, ny: int, nz: int, lo=(0.0, 0.0, 0.0), hi=(10.0, 10.0
     elements for ``Ng >= 2``); ``rotations`` {element: index into
     CUBE_ROTATIONS} renumbers elements' local axes, so that faces meet in
     other orientations."""
-    nodes, ids = _box3d(nx, ny, nz, lo, hi, Ng, perturb, seed)
+    nodes = _box3d(nx, ny, nz, lo, hi, Ng, perturb, seed)
     if rotations:
-        nodes, ids = rotate_hex_elements(nodes, ids, Ng, rotations)
-    return nodes, hex_connectivity(ids, Ng)
+        nodes = rotate_hex_elements(nodes, Ng, rotations)
+    period = tuple(hi[d] - lo[d] for d in range(3))
+    return nodes, hex_connectivity(nodes, Ng, period=period)
 
 
 def extrude(nodes2d, nbr2d, Ng: int, nz: int = 1, z0: float = 0.0, z1: float = 1.0):
