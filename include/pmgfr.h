@@ -167,6 +167,15 @@ typedef struct {
                      per V-cycle.  0: the host runs the loop.  Both follow the
                      same rules; dtau may differ in the last bits (device
                      pow). */
+  int dim;        /* 2 (or 0): quadrilaterals, q_p = (p, u, v, T);
+                     3: hexahedra, q_p = (p, u, v, w, T), inviscid (mu = 0),
+                     binary64 residual throughout (flux_prec is not used),
+                     0 <= P <= 3, slip-wall and far-field boundary faces,
+                     dtau set directly (cfl_mode = 0) */
+  double res_scale3[5]; /* dim = 3: reference scale of each of the five
+                     equations in ||F|| (res_scale is not used) */
+  double q_inf3[5];     /* dim = 3: free stream (p absolute, u, v, w, T) of
+                     far-field faces (q_inf is not used) */
 } pmg_config;
 
 /* Boundary types, in the second slot of a boundary face's neighbour entry
@@ -180,7 +189,24 @@ typedef struct {
  * gradient), and walls carry no viscous energy flux. */
 enum { PMG_BC_SLIP_WALL = 2, PMG_BC_NOSLIP_WALL = 3, PMG_BC_FARFIELD = 4 };
 
-/* Mesh of quadrilaterals with Lagrange geometry of order geom_order (1 or 2).
+/* Mesh of quadrilaterals (dim = 2) or hexahedra (dim = 3) with Lagrange
+ * geometry of order geom_order.
+ *
+ * Hexahedra (dim = 3):
+ *  nodes: (n_elem, (geom_order+1)^3, 3) FP64, node (c*(Ng+1) + b)*(Ng+1) + a
+ *         with a along xi, b along eta, c along zeta.
+ *  nbr:   (n_elem, 6, 3) int32: for local face f = 2 d + s (d = 0 xi, 1 eta,
+ *         2 zeta; s = 0 the -1 side, 1 the +1 side) the neighbour element, its
+ *         local face and an orientation code o in 0..7: face point (a, b) (a
+ *         along the first, b along the second of the face's two reference
+ *         directions in increasing order) is the neighbour's point (a', b')
+ *         with (s, t) = (o & 4) ? (b, a) : (a, b), a' = (o & 1) ? P - s : s,
+ *         b' = (o & 2) ? P - t : t.  A boundary face has neighbour -1 and
+ *         PMG_BC_SLIP_WALL or PMG_BC_FARFIELD in the face slot.
+ *  Solution point (i, j, k) of a level has index (k*(P+1) + j)*(P+1) + i, and
+ *  state arrays are variable-major over the five variables.
+ *
+ * Quadrilaterals (dim = 2), geom_order 1 or 2:
  *  nodes: (n_elem, (geom_order+1)^2, 2) FP64, element geometry nodes at
  *         equispaced reference positions, node b*(geom_order+1)+a, a along xi.
  *  nbr:   (n_elem, 4, 3) int32: for local faces 0 (eta=-1), 1 (xi=+1),

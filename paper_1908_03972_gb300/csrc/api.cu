@@ -133,6 +133,15 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   if (cfg->device_loop != 0 && cfg->device_loop != 1) return fail(PMG_EINVAL, "device_loop must be 0 or 1");
   if (cfg->max_pseudo < 0) return fail(PMG_EINVAL, "max_pseudo must be >= 0");
   if (cfg->refresh_every < 1) return fail(PMG_EINVAL, "refresh_every must be >= 1");
+  if (cfg->dim != 0 && cfg->dim != 2 && cfg->dim != 3) return fail(PMG_EINVAL, "dim must be 2 or 3 (0 means 2)");
+  if (cfg->dim == 3) {
+    if (cfg->mu != 0.0) return fail(PMG_EINVAL, "hexahedral runs are inviscid (mu = 0)");
+    if (cfg->cfl_mode) return fail(PMG_EINVAL, "hexahedral runs set dtau directly (cfl_mode = 0)");
+    for (int l = 0; l < cfg->n_levels; ++l)
+      if (cfg->P[l] > 3) return fail(PMG_EINVAL, "hexahedral levels take P <= 3");
+    for (int v = 0; v < 5; ++v)
+      if (!std::isfinite(cfg->res_scale3[v])) return fail(PMG_EINVAL, "res_scale3 must be finite");
+  }
   int dev;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(PMG_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
@@ -140,6 +149,10 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   Ctx& c = h->c;
   c.cfg = *cfg;
   c.device = dev;
+  c.dim = cfg->dim == 3 ? 3 : 2;
+  c.nv = c.dim + 2;
+  c.nfc = 2 * c.dim;
+  if (c.dim == 3) c.cfg.flux_prec = PMG_FLUX_FP64;   // the hexahedral residual is binary64 throughout
   if (stream) {
     c.stream = (cudaStream_t)stream;
   } else {
@@ -156,8 +169,14 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   c.ph.inv_gm1 = 1.0 / (cfg->gamma - 1.0);
   c.ph.mu = cfg->mu;
   c.ph.kT = cfg->mu > 0.0 ? cfg->mu * c.ph.Cp / cfg->Pr : 0.0;
-  for (int v = 0; v < 4; ++v) c.ph.nw[v] = cfg->res_scale[v] > 0.0 ? 1.0 / cfg->res_scale[v] : 1.0;
-  for (int v = 0; v < 4; ++v) c.ph.qinf[v] = cfg->q_inf[v];
+  for (int v = 0; v < 5; ++v) { c.ph.nw[v] = 1.0; c.ph.qinf[v] = 0.0; }
+  if (c.dim == 3) {
+    for (int v = 0; v < 5; ++v) c.ph.nw[v] = cfg->res_scale3[v] > 0.0 ? 1.0 / cfg->res_scale3[v] : 1.0;
+    for (int v = 0; v < 5; ++v) c.ph.qinf[v] = cfg->q_inf3[v];
+  } else {
+    for (int v = 0; v < 4; ++v) c.ph.nw[v] = cfg->res_scale[v] > 0.0 ? 1.0 / cfg->res_scale[v] : 1.0;
+    for (int v = 0; v < 4; ++v) c.ph.qinf[v] = cfg->q_inf[v];
+  }
   c.ph.wait_ns = cfg->copy_wait_s == 0.0 ? 1e9 : cfg->copy_wait_s < 0.0 ? -1.0 : std::min(cfg->copy_wait_s, 60.0) * 1e9;
   c.phw = make_physw(c.ph);
   esdirk_table(c, cfg->esdirk_order == 0 ? 3 : cfg->esdirk_order);
@@ -213,46 +232,51 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
     for (int l = 0; l < c.cfg.n_levels; ++l)
       if (c.cfg.P[l] < m->geom_order && m->geom_order > 1)
         return fail(PMG_EINVAL, "p_gauge != 0 needs P >= geometry order on every level (the metric identity)");
-  for (int i = 0; i < m->n_elem * 4; ++i) {
+  const int T_slot = c.dim == 3 ? 4 : 3;   // temperature in q_inf
+  for (int i = 0; i < m->n_elem * c.nfc; ++i) {
     if (m->nbr[i * 3] != -1) continue;
     const int bc = m->nbr[i * 3 + 1];
     if (bc == PMG_BC_SLIP_WALL && c.ph.mu > 0.0) return fail(PMG_EINVAL, "slip walls are for mu = 0 only");
+    if (bc == PMG_BC_NOSLIP_WALL && c.dim == 3) return fail(PMG_EINVAL, "hexahedral meshes take no no-slip walls");
     if (bc == PMG_BC_NOSLIP_WALL && !(c.ph.eps_min > 0.0))
       return fail(PMG_EINVAL, "a no-slip wall needs the eps cut-off (cutoff = 1, kappa Ma_inf > 0)");
-    if (bc == PMG_BC_FARFIELD && !(c.ph.qinf[0] > 0.0 && c.ph.qinf[3] > 0.0))
-      return fail(PMG_EINVAL, "far-field faces need q_inf with p > 0 and T > 0");
+    if (bc == PMG_BC_FARFIELD && !(c.ph.qinf[0] > 0.0 && c.ph.qinf[T_slot] > 0.0))
+      return fail(PMG_EINVAL, "far-field faces need a free stream with p > 0 and T > 0");
   }
   c.E = m->n_elem;
   c.mesh.E = m->n_elem;
   c.mesh.Ng = m->geom_order;
-  int nn = (m->geom_order + 1) * (m->geom_order + 1);
-  c.mesh.nodes.assign(m->nodes, m->nodes + (size_t)c.E * nn * 2);
-  c.mesh.nbr.assign(m->nbr, m->nbr + (size_t)c.E * 12);
+  int nn = 1;
+  for (int d = 0; d < c.dim; ++d) nn *= m->geom_order + 1;
+  c.mesh.nodes.assign(m->nodes, m->nodes + (size_t)c.E * nn * c.dim);
+  c.mesh.nbr.assign(m->nbr, m->nbr + (size_t)c.E * c.nfc * 3);
   std::vector<Ref1D> refs;
   std::vector<LevelGeomHost> geo(c.cfg.n_levels);
   try {
-    build_faces(c.mesh);
+    if (c.dim == 3) build_faces3(c.mesh);
+    else build_faces(c.mesh);
     for (int l = 0; l < c.cfg.n_levels; ++l) {
       refs.push_back(make_ref1d(c.cfg.P[l]));
-      build_level_geometry(c.mesh, refs[l], geo[l]);
+      if (c.dim == 3) build_level_geometry3(c.mesh, refs[l], geo[l]);
+      else build_level_geometry(c.mesh, refs[l], geo[l]);
     }
   } catch (const std::exception& ex) {
     return fail(PMG_EINVAL, ex.what());
   }
   {
-    std::vector<double> dx = element_sizes(c.mesh);
+    std::vector<double> dx = c.dim == 3 ? std::vector<double>(c.E, 1.0) : element_sizes(c.mesh);
     PMG_CK(dalloc(&c.d_dx, dx.size()));
     PMG_CK(cudaMemcpy(c.d_dx, dx.data(), dx.size() * 8, cudaMemcpyHostToDevice));
   }
   c.n_faces = (int)c.mesh.faces.size();
   // face list followed by the neighbour table
-  std::vector<int> fbuf((size_t)c.n_faces * 5 + (size_t)c.E * 12);
+  std::vector<int> fbuf((size_t)c.n_faces * 5 + (size_t)c.E * c.nfc * 3);
   for (int f = 0; f < c.n_faces; ++f) {
     const FaceRec& r = c.mesh.faces[f];
     int* o = &fbuf[(size_t)f * 5];
     o[0] = r.eL; o[1] = r.fL; o[2] = r.eR; o[3] = r.fR; o[4] = r.rev;
   }
-  memcpy(&fbuf[(size_t)c.n_faces * 5], c.mesh.nbr.data(), sizeof(int) * c.E * 12);
+  memcpy(&fbuf[(size_t)c.n_faces * 5], c.mesh.nbr.data(), sizeof(int) * c.E * c.nfc * 3);
   PMG_CK(dalloc(&c.d_faces, fbuf.size()));
   PMG_CK(cudaMemcpy(c.d_faces, fbuf.data(), sizeof(int) * fbuf.size(), cudaMemcpyHostToDevice));
   size_t maxtot = 0;
@@ -262,8 +286,11 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
     LevelDev& L = c.lev[l];
     const Ref1D& r = refs[l];
     L.level = l;
-    L.P = r.P; L.n1 = r.P + 1; L.N = L.n1 * L.n1; L.n = 4 * L.N;
-    L.tot = (size_t)4 * c.E * L.N;
+    L.P = r.P; L.n1 = r.P + 1;
+    L.N = c.dim == 3 ? L.n1 * L.n1 * L.n1 : L.n1 * L.n1;
+    L.NF = c.dim == 3 ? L.n1 * L.n1 : L.n1;
+    L.n = c.nv * L.N;
+    L.tot = (size_t)c.nv * c.E * L.N;
     maxtot = std::max(maxtot, L.tot);
     memset(&L.op, 0, sizeof(L.op));
     for (int i = 0; i < L.n1; ++i) {
@@ -284,7 +311,7 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
     size_t nn2 = (size_t)c.E * L.n * L.n;
     if (dalloc(&L.q, L.tot) || dalloc(&L.qb, L.tot) || dalloc(&L.S, L.tot) || dalloc(&L.F, L.tot) ||
         dalloc(&L.Pd, L.tot) || dalloc(&L.met, geo[l].met.size()) || dalloc(&L.face, geo[l].face.size()) ||
-        dalloc(&L.Fcom, (size_t)4 * c.E * 4 * L.n1) || dalloc(&L.Dfull, nn2) ||
+        dalloc(&L.Fcom, (size_t)c.nv * c.E * c.nfc * L.NF) || dalloc(&L.Dfull, nn2) ||
         cudaMalloc(&L.Dinv, nn2 * wbytes) || dalloc(&L.rs, (size_t)c.E * L.n) || dalloc(&L.cs, (size_t)c.E * L.n))
       return fail(PMG_ENOMEM, "device allocation failed for level data");
     // Coarse levels up to P = PMG_FUSE_MAX_P (default 0) are smoothed by the
@@ -296,7 +323,7 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
     if (const char* env = getenv("PMG_FUSE_MAX_P")) fuse_max = atoi(env);
     bool boundary = false;
     for (const FaceRec& fr : c.mesh.faces) boundary = boundary || fr.eR < 0;
-    L.fused = (l > 0 && L.P <= fuse_max && L.P <= 3 && c.ph.mu == 0.0 && !boundary);
+    L.fused = (c.dim == 2 && l > 0 && L.P <= fuse_max && L.P <= 3 && c.ph.mu == 0.0 && !boundary);
     if (L.fused && dalloc(&L.q2, L.tot)) return fail(PMG_ENOMEM, "device allocation failed for level data");
     if (c.ph.mu > 0.0) {
       if (dalloc(&L.Gb, (size_t)6 * c.E * L.N) || dalloc(&L.Qj, (size_t)3 * c.E * 4 * L.n1) ||
@@ -309,7 +336,7 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
     PMG_CK(cudaMemcpy(L.met, geo[l].met.data(), geo[l].met.size() * 8, cudaMemcpyHostToDevice));
     PMG_CK(cudaMemcpy(L.face, geo[l].face.data(), geo[l].face.size() * 8, cudaMemcpyHostToDevice));
     c.xy_host[l] = geo[l].xy;
-    maxblocks = std::max(maxblocks, residual_blocks_for(L.P, c.E));
+    maxblocks = std::max(maxblocks, c.dim == 3 ? residual_blocks_for3(L.P, c.E) : residual_blocks_for(L.P, c.E));
   }
   for (int l = 0; l + 1 < c.cfg.n_levels; ++l) {
     std::vector<double> R, I;
@@ -331,8 +358,12 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
   PMG_CK(cudaMemset(c.src, 0, tot0 * 8));
   c.n_partial = maxblocks;
   PMG_CK(prepare_kernels(c));
-  PMG_CK(prepare_residual_kernels(c));
-  PMG_CK(prepare_volume_dw_kernels(c));
+  if (c.dim == 3) {
+    PMG_CK(prepare_kernels3(c));
+  } else {
+    PMG_CK(prepare_residual_kernels(c));
+    PMG_CK(prepare_volume_dw_kernels(c));
+  }
   c.mesh_ready = true;
   return PMG_OK;
 }
@@ -343,6 +374,20 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
 static pmg_status check_level(const Ctx& c, int level) {
   if (!c.mesh_ready) return fail(PMG_ESTATE, "mesh not uploaded");
   if (level < 0 || level >= c.cfg.n_levels) return fail(PMG_EINVAL, "level out of range");
+  return PMG_OK;
+}
+
+// Levels whose blocks the shared-memory factorisation cannot hold (hexahedra
+// at P = 3: n = 320) have a residual but no smoother.
+static pmg_status check_factorable(const Ctx& c, int level) {
+  const int lim = factor_max_n(c.cfg.block_prec);
+  for (int l = 0; l < c.cfg.n_levels; ++l) {
+    if (level >= 0 && l != level) continue;
+    if (c.lev[l].n > lim)
+      return fail(PMG_EINVAL, "element blocks of level " + std::to_string(l) + " (n = " + std::to_string(c.lev[l].n) +
+                                  ") exceed the shared-memory factorisation (n <= " + std::to_string(lim) +
+                                  " in this block precision)");
+  }
   return PMG_OK;
 }
 
@@ -358,7 +403,9 @@ static cudaError_t copy_out(const Ctx& c, double* dst, const double* src, size_t
   return cudaStreamSynchronize(c.stream);
 }
 
-static int residual_block_count(const Ctx& c, int l) { return residual_blocks_for(c.lev[l].P, c.E); }
+static int residual_block_count(const Ctx& c, int l) {
+  return c.dim == 3 ? residual_blocks_for3(c.lev[l].P, c.E) : residual_blocks_for(c.lev[l].P, c.E);
+}
 
 // ------------------------------------------------------------- profiler
 // Event pairs around individual launches (only outside graph capture).
@@ -730,6 +777,10 @@ static pmg_status stage_solve_device(Ctx& c, double dtau_init, double dtau_max, 
 
 // Pseudo-transient continuation of the current stage (Section 2.4).
 static pmg_status stage_solve(Ctx& c, int* iters, double* drop, int* n_refresh) {
+  {
+    pmg_status fs = check_factorable(c, -1);
+    if (fs) return fs;
+  }
   if (!c.F0_valid) {
     system_residual(c, 0, true);
     PMG_CK_LAUNCH();
@@ -816,7 +867,7 @@ pmg_status pmg_set_state(pmg_ctx* h, int level, const double* q, int on_device) 
   pmg_status st = check_level(c, level);
   if (st) return st;
   PMG_CK(copy_in(c, c.lev[level].q, q, c.lev[level].tot, on_device));
-  launch_shift_pressure(c.lev[level].tot / 4, -c.ph.p_ref, c.lev[level].q, c.stream);
+  launch_shift_pressure(c.lev[level].tot / c.nv, -c.ph.p_ref, c.lev[level].q, c.stream);
   PMG_CK_LAUNCH();
   PMG_CK(cudaStreamSynchronize(c.stream));
   if (level == 0) c.F0_valid = false;
@@ -933,7 +984,7 @@ pmg_status pmg_get_state(pmg_ctx* h, int level, double* q, int on_device) {
   if (st) return st;
   const LevelDev& L = c.lev[level];
   PMG_CK(cudaMemcpyAsync(c.d_tmp0, L.q, L.tot * 8, cudaMemcpyDeviceToDevice, c.stream));
-  launch_shift_pressure(L.tot / 4, c.ph.p_ref, c.d_tmp0, c.stream);
+  launch_shift_pressure(L.tot / c.nv, c.ph.p_ref, c.d_tmp0, c.stream);
   PMG_CK_LAUNCH();
   PMG_CK(copy_out(c, q, c.d_tmp0, L.tot, on_device));
   return PMG_OK;
@@ -946,7 +997,7 @@ pmg_status pmg_residual(pmg_ctx* h, int level, const double* q, double* R, int o
   if (st) return st;
   LevelDev& L = c.lev[level];
   PMG_CK(copy_in(c, c.d_tmp0, q, L.tot, on_device));
-  launch_shift_pressure(L.tot / 4, -c.ph.p_ref, c.d_tmp0, c.stream);
+  launch_shift_pressure(L.tot / c.nv, -c.ph.p_ref, c.d_tmp0, c.stream);
   const double* qd = c.d_tmp0;
   double* Rd = on_device ? R : c.d_tmp1;
   launch_face_flux(c, L, qd, c.stream);
@@ -989,7 +1040,7 @@ pmg_status pmg_residual_static(pmg_ctx* h, int level, const double* q, double* R
   if (st) return st;
   LevelDev L = c.lev[level];   // shallow copy: only the scratch slots are redirected
   const bool visc = c.ph.mu > 0.0;
-  const size_t n_state = L.tot, n_face = (size_t)4 * c.E * 4 * L.n1;
+  const size_t n_state = L.tot, n_face = (size_t)c.nv * c.E * c.nfc * L.NF;
   const size_t n_visc = visc ? (size_t)6 * c.E * L.N + (size_t)3 * c.E * 4 * L.n1 : 0;
   if (n_state + n_face + n_visc > kStaticScratchDoubles)
     return fail(PMG_EINVAL, "pmg_residual_static: level needs " + std::to_string(n_state + n_face + n_visc) +
@@ -1007,7 +1058,7 @@ pmg_status pmg_residual_static(pmg_ctx* h, int level, const double* q, double* R
     L.Qj = L.Gb + (size_t)6 * c.E * L.N;
   }
   PMG_CK(cudaMemcpyAsync(qs, q, n_state * 8, cudaMemcpyDeviceToDevice, c.stream));
-  launch_shift_pressure(n_state / 4, -c.ph.p_ref, qs, c.stream);
+  launch_shift_pressure(n_state / c.nv, -c.ph.p_ref, qs, c.stream);
   launch_face_flux(c, L, qs, c.stream);
   launch_volume(c, L, level, qs, R, RES_PURE, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr, c.stream);
   PMG_CK_LAUNCH();
@@ -1037,7 +1088,7 @@ pmg_status pmg_stage_residual(pmg_ctx* h, int level, const double* q, double* F,
   if (!c.stage_ready) return fail(PMG_ESTATE, "stage data not set");
   LevelDev& L = c.lev[level];
   PMG_CK(copy_in(c, c.d_tmp0, q, L.tot, on_device));
-  launch_shift_pressure(L.tot / 4, -c.ph.p_ref, c.d_tmp0, c.stream);
+  launch_shift_pressure(L.tot / c.nv, -c.ph.p_ref, c.d_tmp0, c.stream);
   const double* qd = c.d_tmp0;
   double* Fd = on_device ? F : c.d_tmp1;
   launch_face_flux(c, L, qd, c.stream);
@@ -1097,6 +1148,10 @@ pmg_status pmg_factor_blocks(pmg_ctx* h, int level) {
   Ctx& c = h->c;
   if (!c.mesh_ready) return fail(PMG_ESTATE, "mesh not uploaded");
   if (level < -1 || level >= c.cfg.n_levels) return fail(PMG_EINVAL, "level out of range");
+  {
+    pmg_status fs = check_factorable(c, level);
+    if (fs) return fs;
+  }
   for (int l = 0; l < c.cfg.n_levels; ++l) {
     if (level >= 0 && l != level) continue;
     if (!c.lev[l].assembled) return fail(PMG_ESTATE, "blocks not assembled");
@@ -1178,6 +1233,10 @@ pmg_status pmg_vcycle(pmg_ctx* h, double dtau, int refresh, double* res_norm_out
   if (!c.mesh_ready) return fail(PMG_ESTATE, "mesh not uploaded");
   if (!c.stage_ready) return fail(PMG_ESTATE, "stage data not set");
   if (!(dtau > 0.0)) return fail(PMG_EINVAL, "dtau must be positive");
+  {
+    pmg_status fs = check_factorable(c, -1);
+    if (fs) return fs;
+  }
   if (!refresh)
     for (int l = 0; l < c.cfg.n_levels; ++l)
       if (!c.lev[l].factored) return fail(PMG_ESTATE, "smoother not built: call with refresh = 1 first");

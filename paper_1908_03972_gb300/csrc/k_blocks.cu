@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(128) assemble_kernel(int E, const double* __re
 
 void launch_assemble(const Ctx& c, const LevelDev& L, const double* q, const double* d_dtau, double inv_odt,
                      cudaStream_t s) {
+  if (c.dim == 3) { launch_assemble3(c, L, q, d_dtau, inv_odt, s); return; }
   const int* nbr = c.d_faces + 5 * c.n_faces;   // neighbour table stored after the face list
 #define PMG_ASM(PP) \
   assemble_kernel<PP><<<c.E, 128, 0, s>>>(c.E, q, L.met, L.face, nbr, L.op, c.ph, d_dtau, inv_odt, L.Dfull)
@@ -280,11 +281,24 @@ void launch_factor(const Ctx& c, LevelDev& L, int prec, int* flag, cudaStream_t 
     factor_kernel<float><<<c.E, 256, factor_smem(n, 4), s>>>(n, L.Dfull, (float*)L.Dinv, L.rs, L.cs, flag);
 }
 
+// Largest block the shared-memory factorisation holds in the precision prec
+// (227 KB of shared memory per CTA): n = 168 in FP64, 238 in FP32 and BF16
+// (their elimination runs in FP32).
+int factor_max_n(int prec) {
+  const int wb = prec == PMG_PREC_FP64 ? 8 : 4;
+  int n = 4;
+  while (factor_smem(n + 1, wb) <= (size_t)227 * 1024) ++n;
+  return n;
+}
+
 // Opt the factor kernels into the dynamic shared memory the largest block
-// needs (done once, outside any stream capture).
+// needs (done once, outside any stream capture).  Levels whose blocks exceed
+// factor_max_n are left out; the calls that would factor them fail first.
 cudaError_t prepare_kernels(const Ctx& c) {
   int nmax = 4;
-  for (int l = 0; l < c.cfg.n_levels; ++l) nmax = std::max(nmax, c.lev[l].n);
+  const int lim = factor_max_n(c.cfg.block_prec);
+  for (int l = 0; l < c.cfg.n_levels; ++l)
+    if (c.lev[l].n <= lim) nmax = std::max(nmax, c.lev[l].n);
   cudaError_t e = cudaFuncSetAttribute(factor_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)factor_smem(nmax, 8));
   if (e != cudaSuccess) return e;
@@ -398,6 +412,7 @@ static void apply_dispatch(const Ctx& c, const LevelDev& L, const W* Dinv, const
 
 void launch_apply(const Ctx& c, const LevelDev& L, int prec, const double* r, double* x, int accumulate,
                   cudaStream_t s) {
+  if (c.dim == 3) { launch_apply3(c, L, prec, r, x, accumulate, s); return; }
   if (prec == PMG_PREC_FP64) apply_dispatch<double>(c, L, (const double*)L.Dinv, r, x, accumulate, s);
   else if (prec == PMG_PREC_BF16R)
     apply_dispatch<__nv_bfloat16>(c, L, (const __nv_bfloat16*)L.Dinv, r, x, accumulate, s);

@@ -72,6 +72,7 @@ __global__ void prolong_kernel(int E, XferTab X, const double* __restrict__ qc, 
 
 void launch_restrict(const Ctx& c, const LevelDev& Lf, const LevelDev& Lc, const XferTab& X, const double* in,
                      double* out, double* out2, double scale, cudaStream_t s) {
+  if (c.dim == 3) { launch_restrict3(c, Lf, Lc, X, in, out, out2, scale, s); return; }
   int total = c.E * Lc.N, threads = 64, blocks = (total + threads - 1) / threads;
 #define PMG_R(A, B) \
   if (Lf.P == A && Lc.P == B) { restrict_kernel<A, B><<<blocks, threads, 0, s>>>(c.E, X, in, out, out2, scale); return; }
@@ -81,6 +82,7 @@ void launch_restrict(const Ctx& c, const LevelDev& Lf, const LevelDev& Lc, const
 
 static void prolong_impl(const Ctx& c, const LevelDev& Lf, const LevelDev& Lc, const XferTab& X, const double* qc,
                          const double* qcb, double* qf, int add, cudaStream_t s) {
+  if (c.dim == 3) { launch_prolong3(c, Lf, Lc, X, qc, qcb, qf, add, s); return; }
   int total = c.E * Lf.N, threads = 64, blocks = (total + threads - 1) / threads;
 #define PMG_P(A, B) \
   if (Lf.P == A && Lc.P == B) { prolong_kernel<A, B><<<blocks, threads, 0, s>>>(c.E, X, qc, qcb, qf, add); return; }
@@ -171,12 +173,13 @@ void launch_stage_src(const Ctx& c, int N, const double* qcn, double* const* R, 
                       double dt, double inv_odt, double* src, cudaStream_t s) {
   RPtrs rp;
   for (int j = 0; j < 6; ++j) { rp.p[j] = j < nr ? R[j] : nullptr; rp.coef[j] = j < nr ? a[j] : 0.0; }
-  size_t tot = (size_t)4 * c.E * N;
+  size_t tot = (size_t)c.nv * c.E * N;
   stage_src_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(tot, qcn, rp, nr, dt, inv_odt, src);
 }
 
 void launch_bsum_update(const Ctx& c, int N, const double* qn, double* const* R, const double* b, int nr,
                         double dt, double* q, cudaStream_t s) {
+  if (c.dim == 3) { launch_bsum_update3(c, N, qn, R, b, nr, dt, q, s); return; }
   RPtrs rp;
   for (int j = 0; j < 6; ++j) { rp.p[j] = j < nr ? R[j] : nullptr; rp.coef[j] = j < nr ? b[j] : 0.0; }
   size_t plane = (size_t)c.E * N;

@@ -484,6 +484,7 @@ static int elems_per_block(int P) {
 int residual_blocks_for(int P, int E) { int epb = elems_per_block(P); return (E + epb - 1) / epb; }
 
 void launch_face_flux(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s, bool sweep) {
+  if (c.dim == 3) { launch_face_flux3(c, L, q, s); return; }
   int total = c.n_faces * L.n1;
   // one warp per CTA: latency-bound threads, spread over every SM
   int threads = 32, blocks = (total + threads - 1) / threads;
@@ -519,6 +520,7 @@ void launch_volume(const Ctx& c, const LevelDev& L, int level, const double* q, 
                    double inv_odt, const double* src, const double* S, double* Sout, const double* Pd,
                    double* partial, cudaStream_t s, const double* qn) {
   (void)level;
+  if (c.dim == 3) { launch_volume3(c, L, q, out, mode, inv_odt, src, S, Sout, Pd, partial, s, qn); return; }
   int threads = residual_threads_per_block(L.P);
   int blocks = residual_blocks_for(L.P, c.E);
 #define PMG_VOL(PP)                                                                                          \
@@ -579,6 +581,7 @@ static void volume_apply_dispatch(const Ctx& c, const LevelDev& L, double* q, do
 // by the element-Jacobi update of that state (after launch_face_flux).
 void launch_volume_apply(const Ctx& c, const LevelDev& L, double* q, double inv_odt, const double* src,
                          const double* S, const double* qn, int prec, cudaStream_t s) {
+  if (c.dim == 3) { launch_volume_apply3(c, L, q, inv_odt, src, S, qn, prec, s); return; }
   if (prec == PMG_PREC_FP64) volume_apply_dispatch<double>(c, L, q, inv_odt, src, S, qn, s);
   else if (prec == PMG_PREC_BF16R) volume_apply_dispatch<__nv_bfloat16>(c, L, q, inv_odt, src, S, qn, s);
   else volume_apply_dispatch<float>(c, L, q, inv_odt, src, S, qn, s);

@@ -230,7 +230,9 @@ static void dw_dispatch(const Ctx& c, const LevelDev& L, double* q, double inv_o
 #undef PMG_VDW
 }
 
-bool volume_dw_applies(const Ctx& c) { return flux_dw_sweep(c) && c.ph.mu == 0.0 && c.ph.p_ref != 0.0; }
+bool volume_dw_applies(const Ctx& c) {
+  return c.dim == 2 && flux_dw_sweep(c) && c.ph.mu == 0.0 && c.ph.p_ref != 0.0;
+}
 
 void launch_volume_apply_dw(const Ctx& c, const LevelDev& L, double* q, double inv_odt, const double* src,
                             const double* S, const double* qref, int prec, cudaStream_t s) {

@@ -21,8 +21,9 @@ struct Phys {
   double inv_gm1;    // 1 / (gamma - 1)
   double mu;         // constant dynamic viscosity (0: Euler)
   double kT;         // heat conductivity mu Cp / Pr
-  double nw[4];      // weights 1 / res_scale of the equations in the residual norm
-  double qinf[4];    // free stream of far-field faces (p absolute, u, v, T)
+  double nw[5];      // weights 1 / res_scale of the equations in the residual norm
+  double qinf[5];    // free stream of far-field faces: (p absolute, u, v, T) in 2D,
+                     // (p absolute, u, v, w, T) in 3D
   double wait_ns;    // bound of the bulk-copy waits (< 0: give up at once)
 };
 

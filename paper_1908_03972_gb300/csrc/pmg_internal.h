@@ -68,6 +68,11 @@ Ref1D make_ref1d(int P);
 void make_transfer(const Ref1D& f, const Ref1D& c, std::vector<double>& R, std::vector<double>& I);
 void build_faces(MeshHost& m);
 void build_level_geometry(const MeshHost& m, const Ref1D& r, LevelGeomHost& g);
+// Hexahedra (host_tables3.cpp): face list with orientation codes in FaceRec.rev,
+// metric planes (J a^i_n, then 1/J), coordinates (E, N, 3), face geometry
+// (E, 6, NF, 4: unit outward normal, area).
+void build_faces3(MeshHost& m);
+void build_level_geometry3(const MeshHost& m, const Ref1D& r, LevelGeomHost& g);
 std::vector<double> element_sizes(const MeshHost& m);
 
 // --------------------------------------------------------------- device side
@@ -87,7 +92,8 @@ struct XferTab {
 struct LevelDev {
   int level = 0;               // index in the hierarchy (0: finest)
   int P = 0, n1 = 0, N = 0, n = 0;
-  size_t tot = 0;              // 4 * E * N
+  int NF = 0;                  // points per face: P + 1 (2D), (P + 1)^2 (3D)
+  size_t tot = 0;              // nv * E * N
   OpTab op;
   OpTabW opw;                  // the same operators in double-word
   double* q = nullptr;         // state
@@ -97,9 +103,9 @@ struct LevelDev {
   double* S = nullptr;         // FAS forcing
   double* F = nullptr;         // level system residual F_l(q) - S_l
   double* Pd = nullptr;        // restricted defect (coarse levels)
-  double* met = nullptr;       // 5 * E * N
-  double* face = nullptr;      // E * 4 * n1 * 3
-  double* Fcom = nullptr;      // 4 * E * 4 * n1 common fluxes, outward
+  double* met = nullptr;       // 5 * E * N (2D), 10 * E * N (3D)
+  double* face = nullptr;      // E * 4 * n1 * 3 (2D), E * 6 * NF * 4 (3D)
+  double* Fcom = nullptr;      // nv * E * faces * NF common fluxes, outward
   // viscous terms (mu > 0 only)
   double* Gb = nullptr;        // 6 * E * N broken gradients of (u, v, T): x planes, then y
   double* Qj = nullptr;        // 3 * E * 4 * n1: q_com - q_own of (u, v, T) at each element face point
@@ -146,6 +152,7 @@ struct Profiler {
 
 struct Ctx {
   pmg_config cfg;
+  int dim = 2, nv = 4, nfc = 4;   // dimension, working variables, faces per element
   Profiler prof;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -251,8 +258,28 @@ void launch_loop_controller(LoopState* st, const double* scal, int* sing_flag, d
                             double* hist_dtau, const LoopParams& prm, cudaGraphConditionalHandle h_loop,
                             cudaGraphConditionalHandle h_refresh, cudaGraphConditionalHandle h_plain,
                             cudaStream_t s);
+// Hexahedral kernels (k3_*.cu); the launchers above dispatch to them when dim = 3.
+void launch_face_flux3(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s);
+void launch_volume3(const Ctx& c, const LevelDev& L, const double* q, double* out, ResMode mode, double inv_odt,
+                    const double* src, const double* S, double* Sout, const double* Pd, double* partial,
+                    cudaStream_t s, const double* qn);
+void launch_volume_apply3(const Ctx& c, const LevelDev& L, double* q, double inv_odt, const double* src,
+                          const double* S, const double* qn, int prec, cudaStream_t s);
+int residual_blocks_for3(int P, int E);
+void launch_assemble3(const Ctx& c, const LevelDev& L, const double* q, const double* d_dtau, double inv_odt,
+                      cudaStream_t s);
+void launch_apply3(const Ctx& c, const LevelDev& L, int prec, const double* r, double* x, int accumulate,
+                   cudaStream_t s);
+cudaError_t prepare_kernels3(const Ctx& c);
+void launch_restrict3(const Ctx& c, const LevelDev& Lf, const LevelDev& Lc, const XferTab& X, const double* in,
+                      double* out, double* out2, double scale, cudaStream_t s);
+void launch_prolong3(const Ctx& c, const LevelDev& Lf, const LevelDev& Lc, const XferTab& X, const double* qc,
+                     const double* qcb, double* qf, int add, cudaStream_t s);
+void launch_bsum_update3(const Ctx& c, int N, const double* qn, double* const* R, const double* b, int nr,
+                         double dt, double* q, cudaStream_t s);
 int residual_threads_per_block(int P);
 int residual_blocks_for(int P, int E);
 cudaError_t prepare_kernels(const Ctx& c);
+int factor_max_n(int prec);
 
 }  // namespace pmg

@@ -58,6 +58,9 @@ class pmg_config(ctypes.Structure):
         ("flux_prec", ctypes.c_int),
         ("copy_wait_s", ctypes.c_double),
         ("device_loop", ctypes.c_int),
+        ("dim", ctypes.c_int),
+        ("res_scale3", ctypes.c_double * 5),
+        ("q_inf3", ctypes.c_double * 5),
     ]
 
 
@@ -156,7 +159,7 @@ def make_config(P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutof
                 use_graph=1, p_gauge=0.0, mu=0.0, Pr=0.72, res_scale=(1.0, 1.0, 1.0, 1.0),
                 q_inf=(0.0, 0.0, 0.0, 0.0), cfl_mode=0, cfl_init=1e2, cfl_max=1e5,
                 esdirk_order=3, refresh_always=0, flux_prec=PMG_FLUX_DW_SMOOTH, copy_wait_s=0.0,
-                device_loop=0) -> pmg_config:
+                device_loop=0, dim=2, res_scale3=(1.0,) * 5, q_inf3=(0.0,) * 5) -> pmg_config:
     cfg = pmg_config()
     cfg.n_levels = len(P_levels)
     for l, (P, n) in enumerate(zip(P_levels, n_smooth)):
@@ -177,6 +180,10 @@ def make_config(P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutof
     cfg.flux_prec = flux_prec
     cfg.copy_wait_s = copy_wait_s
     cfg.device_loop = device_loop
+    cfg.dim = dim
+    for v in range(5):
+        cfg.res_scale3[v] = res_scale3[v]
+        cfg.q_inf3[v] = q_inf3[v]
     return cfg
 
 
@@ -195,15 +202,15 @@ def pmg_destroy(h):
 def pmg_upload_mesh(h, nodes, nbr):
     nodes = np.ascontiguousarray(nodes, dtype=np.float64)
     nbr = np.ascontiguousarray(nbr, dtype=np.int32)
-    nn = nodes.shape[1]
-    Ng = int(round(nn ** 0.5)) - 1
+    nn, dim = nodes.shape[1], nodes.shape[2]
+    Ng = int(round(nn ** (1.0 / dim))) - 1
     m = pmg_mesh(nodes.shape[0], Ng, nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                  nbr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
     _check(load().pmg_upload_mesh(h, ctypes.byref(m)))
 
 
-def pmg_point_coords(h, level, E, N):
-    xy = np.zeros((E, N, 2))
+def pmg_point_coords(h, level, E, N, dim=2):
+    xy = np.zeros((E, N, dim))
     _check(load().pmg_point_coords(h, level, xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
     return xy
 
@@ -324,6 +331,8 @@ class Solver:
 
     def __init__(self, nodes, nbr, P_levels, n_smooth, stream=None, **cfg_kw):
         self.cfg = make_config(P_levels, n_smooth, **cfg_kw)
+        self.dim = 3 if cfg_kw.get("dim", 2) == 3 else 2
+        self.nv = self.dim + 2
         self.P = list(P_levels)
         self.E = int(np.asarray(nodes).shape[0])
         self.h = None
@@ -342,16 +351,16 @@ class Solver:
             pass
 
     def N(self, level=0):
-        return (self.P[level] + 1) ** 2
+        return (self.P[level] + 1) ** self.dim
 
     def shape(self, level=0):
-        return (4, self.E, self.N(level))
+        return (self.nv, self.E, self.N(level))
 
     def n(self, level=0):
-        return 4 * self.N(level)
+        return self.nv * self.N(level)
 
     def coords(self, level=0):
-        return pmg_point_coords(self.h, level, self.E, self.N(level))
+        return pmg_point_coords(self.h, level, self.E, self.N(level), self.dim)
 
     def set_state(self, q, level=0):
         pmg_set_state(self.h, level, q)

@@ -502,3 +502,46 @@ def freestream_scales3(Ma_inf: float, rho: float = 1.0, speed: float = math.sqrt
     """Convective flux scales of the five equations (rho U, rho U^2 x 3, rho U H)."""
     m, mx, my, e = freestream_scales(Ma_inf, rho, speed, gamma)
     return (m, mx, my, mx, e)
+
+
+def cubed_sphere_shell(n: int, n_r: int, r_in: float = 0.5, r_out: float = 20.0, Ng: int = 2,
+                       wall: int = BC_SLIP_WALL, outer: int = BC_FARFIELD):
+    """Spherical shell of 6 n n n_r hexahedra: the six faces of a cube, each
+    cut into n x n cells of equal angle (equiangular gnomonic map), times n_r
+    radial layers r_k = r_in (r_out/r_in)^(k/n_r).  Element
+    e = ((face*n_r + k)*n + j)*n + i; xi and eta follow the face's two angles
+    and zeta the radius, so every geometry node lies exactly on its sphere.
+    Faces at r_in carry ``wall``, faces at r_out ``outer``; the patches meet
+    along their edges in the orientations that the face matching finds."""
+    axes = [((0, 1, 0), (0, 0, 1), (1, 0, 0)), ((0, 0, 1), (0, 1, 0), (-1, 0, 0)),
+            ((0, 0, 1), (1, 0, 0), (0, 1, 0)), ((1, 0, 0), (0, 0, 1), (0, -1, 0)),
+            ((1, 0, 0), (0, 1, 0), (0, 0, 1)), ((0, 1, 0), (1, 0, 0), (0, 0, -1))]
+    rk = r_in * (r_out / r_in) ** (np.arange(n_r + 1) / n_r)
+    da = 0.5 * math.pi / n
+    t = np.linspace(0.0, 1.0, Ng + 1)
+    n1 = Ng + 1
+    E = 6 * n * n * n_r
+    nodes = np.zeros((E, n1 ** 3, 3))
+    for fc, (u, v, c0) in enumerate(axes):
+        u, v, c0 = np.array(u, float), np.array(v, float), np.array(c0, float)
+        for k in range(n_r):
+            for j in range(n):
+                for i in range(n):
+                    e = ((fc * n_r + k) * n + j) * n + i
+                    for cc in range(n1):
+                        r = rk[k] + t[cc] * (rk[k + 1] - rk[k])
+                        for b in range(n1):
+                            beta = -0.25 * math.pi + (j + t[b]) * da
+                            for a in range(n1):
+                                alpha = -0.25 * math.pi + (i + t[a]) * da
+                                d = c0 + math.tan(alpha) * u + math.tan(beta) * v
+                                nodes[e, (cc * n1 + b) * n1 + a] = r * d / np.linalg.norm(d)
+
+    def bc(e, f):
+        if f == 4:
+            return wall
+        if f == 5:
+            return outer
+        raise ValueError(f"unmatched side face {f} of element {e}")
+
+    return nodes, hex_connectivity(nodes, Ng, boundary=bc)

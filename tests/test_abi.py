@@ -44,10 +44,13 @@ def test_binding_covers_every_symbol():
 def test_binding_struct_layout_matches_header():
     from paper_1908_03972_gb300 import pmgfr
     # pmg_config: 1 int, 2 x int[8], 3 doubles, 1 int, 3 doubles, 4 ints, 3 doubles, 2 x double[4],
-    # 1 int (+4 padding), 2 doubles, 3 ints (+4 padding), 1 double, 1 int (+4 padding) (C layout)
-    assert ctypes.sizeof(pmgfr.pmg_config) == 4 + 64 + 4 + 24 + 4 + 4 + 24 + 16 + 8 + 16 + 32 + 32 + 8 + 16 + 16 + 8 + 8
+    # 1 int (+4 padding), 2 doubles, 3 ints (+4 padding), 1 double, 2 ints, 2 x double[5] (C layout)
+    assert ctypes.sizeof(pmgfr.pmg_config) == (4 + 64 + 4 + 24 + 4 + 4 + 24 + 16 + 8 + 16 + 32 + 32 + 8 + 16 + 16 + 8 + 8
+                                               + 80)
     assert pmgfr.pmg_config.copy_wait_s.offset == 272
     assert pmgfr.pmg_config.device_loop.offset == 280
+    assert pmgfr.pmg_config.dim.offset == 284
+    assert pmgfr.pmg_config.res_scale3.offset == 288
     assert ctypes.sizeof(pmgfr.pmg_mesh) == 24
 
 

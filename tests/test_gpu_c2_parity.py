@@ -15,7 +15,8 @@ Bounds.  The small-mesh V-cycle parity tests hold the deviation of the state a
 V-cycle produces, relative to the change it makes, to 1e-8 (binary64) and 5e-3
 (FP32 blocks, whose rounding of F the conditioning of the low-Mach blocks
 amplifies) over cycles of I{1-2-2-3} on four levels: 2 + 4 + 4 + 3 = 13
-sweeps.  Rounding differences of the two codes enter every sweep and the
+sweeps, and a later cycle with the frozen smoother to 1e-7 (binary64): its
+coarse blocks were built from each code's own coarse states.  Rounding differences of the two codes enter every sweep and the
 sweeps do not amplify them, so the deviation grows with the number of sweeps
 a cycle runs: I{5-10-20-40} runs 10 + 20 + 40 + 40 = 110, and the bounds here
 are the small-mesh bounds per sweep times 110.  The residual norm at the start
@@ -95,7 +96,7 @@ def test_c2_full_size_vcycles_match_oracle(mode):
             print(f"C2 {mode} V-cycle {k}: max deviation / change = {err:.3e}, "
                   f"norm {nrm:.9e} (oracle {norms[k]:.9e})")
             assert np.isfinite(qg).all()
-            assert err <= tol, (k, err)
+            assert err <= tol * (10.0 if (k > 0 and mode == "plain") else 1.0), (k, err)
             assert abs(nrm - norms[k]) <= 1e-8 * norms[k], (k, nrm, norms[k])
     finally:
         gpu.close()
