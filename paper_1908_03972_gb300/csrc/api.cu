@@ -99,6 +99,8 @@ static void free_level(LevelDev& L) {
   double** ptrs[] = {&L.q,     &L.q2, &L.qb, &L.S,  &L.F,  &L.Pd, &L.met,  &L.face,
                      &L.Fcom,  &L.Dfull, &L.rs, &L.cs, &L.Gb, &L.Qj, &L.fJinv};
   for (double** p : ptrs) { if (*p) cudaFree(*p); *p = nullptr; }
+  int** iptrs[] = {&L.d_toff, &L.d_tlayer, &L.d_telems, &L.d_tlnbr};
+  for (int** p : iptrs) { if (*p) cudaFree(*p); *p = nullptr; }
   if (L.Dinv) cudaFree(L.Dinv);
   L.Dinv = nullptr;
 }
@@ -325,6 +327,42 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
     for (const FaceRec& fr : c.mesh.faces) boundary = boundary || fr.eR < 0;
     L.fused = (c.dim == 2 && l > 0 && L.P <= fuse_max && L.P <= 3 && c.ph.mu == 0.0 && !boundary);
     if (L.fused && dalloc(&L.q2, L.tot)) return fail(PMG_ENOMEM, "device allocation failed for level data");
+    // Fused levels with P <= 1 in the double-word sweep arithmetic may run
+    // several sweeps per launch on tiles with a halo (k_tile.cu): up to
+    // PMG_TILE_DEPTH (P = 0) or PMG_TILE_DEPTH1 (P = 1) sweeps per launch
+    // (0: one sweep per launch), cores of PMG_TILE_CORE (P = 0, default 32)
+    // or PMG_TILE_CORE1 (P = 1, default 16) elements; a tile is at most 512
+    // threads (one per element face point).
+    if (L.fused && L.P <= 1 && c.ph.p_ref != 0.0 && flux_dw_sweep(c)) {
+      int depth = 0, core = L.P == 0 ? 32 : 16;
+      if (const char* env = getenv(L.P == 0 ? "PMG_TILE_DEPTH" : "PMG_TILE_DEPTH1")) depth = atoi(env);
+      if (const char* env = getenv(L.P == 0 ? "PMG_TILE_CORE" : "PMG_TILE_CORE1")) core = atoi(env);
+      if (depth > 0 && core > 0) {
+        TileSet ts;
+        try {
+          ts = build_tiles(c.mesh, core, depth);
+        } catch (const std::exception& ex) {
+          return fail(PMG_EINVAL, ex.what());
+        }
+        const size_t bytes = tile_smem_bytes(L.P, c.cfg.block_prec, ts.max_elems);
+        const int threads = ts.max_elems * tile_face_points(L.P);
+        if (bytes > 0 && bytes <= (size_t)227 * 1024 && threads <= 512) {
+          if (dalloc(&L.d_toff, ts.off.size()) || dalloc(&L.d_tlayer, ts.layer_end.size()) ||
+              dalloc(&L.d_telems, ts.elems.size()) || dalloc(&L.d_tlnbr, ts.lnbr.size()))
+            return fail(PMG_ENOMEM, "device allocation failed for tile data");
+          PMG_CK(cudaMemcpy(L.d_toff, ts.off.data(), ts.off.size() * sizeof(int), cudaMemcpyHostToDevice));
+          PMG_CK(cudaMemcpy(L.d_tlayer, ts.layer_end.data(), ts.layer_end.size() * sizeof(int),
+                            cudaMemcpyHostToDevice));
+          PMG_CK(cudaMemcpy(L.d_telems, ts.elems.data(), ts.elems.size() * sizeof(int), cudaMemcpyHostToDevice));
+          PMG_CK(cudaMemcpy(L.d_tlnbr, ts.lnbr.data(), ts.lnbr.size() * sizeof(int), cudaMemcpyHostToDevice));
+          PMG_CK(prepare_tile_kernel(L.P, c.cfg.block_prec, bytes));
+          L.tiled = true;
+          L.n_tiles = ts.n_tiles;
+          L.tile_M = ts.max_elems;
+          L.tile_depth = depth;
+        }
+      }
+    }
     if (c.ph.mu > 0.0) {
       if (dalloc(&L.Gb, (size_t)6 * c.E * L.N) || dalloc(&L.Qj, (size_t)3 * c.E * 4 * L.n1) ||
           dalloc(&L.fJinv, geo[l].fJinv.size()))
@@ -486,6 +524,20 @@ static void refresh_level(Ctx& c, int l) {
 // Fused levels return the number of state-buffer swaps.
 static int sweeps(Ctx& c, int l, int n, bool F_valid, bool final_residual, bool final_norm) {
   LevelDev& L = c.lev[l];
+  if (L.tiled) {
+    int swaps = 0;
+    for (int done = 0; done < n; done += L.tile_depth) {
+      const int ns = std::min(L.tile_depth, n - done);
+      {
+        ProfScope ps(c, K_FUSED, l);
+        launch_tile_sweeps(c, L, L.q, L.q2, ns, 1.0 / c.omega_dt, L.S, L.qb, c.cfg.block_prec, c.stream);
+      }
+      std::swap(L.q, L.q2);
+      ++swaps;
+    }
+    if (final_residual) system_residual(c, l, final_norm);
+    return swaps;
+  }
   if (L.fused) {
     for (int s = 0; s < n; ++s) {
       {

@@ -312,3 +312,93 @@ void build_faces(MeshHost& m) {
 }
 
 }  // namespace pmg
+
+namespace pmg {
+
+// Tiles of the multi-sweep coarse-level smoother (k_tile.cu).  Every element
+// belongs to the core of exactly one tile.  The cores come from recursive
+// coordinate bisection of the element centroids (split the longer extent at
+// the median until a part holds at most `core` elements), so they are compact
+// on any mesh; the halo of a core is `depth` layers of face neighbours.
+// Elements are listed core first, then halo layer by layer, so that the first
+// layer_end[d] elements of a tile are its core and halo layers 1..d.  Sweep s
+// of a launch of n sweeps updates the elements up to layer n - s, whose
+// neighbours all lie within layer n - s + 1, so the core ends the launch with
+// the values of n plain sweeps.
+static void bisect(std::vector<int>& ids, size_t lo, size_t hi, const std::vector<double>& cx,
+                   const std::vector<double>& cy, int core, std::vector<std::vector<int>>& out) {
+  if (hi - lo <= (size_t)core) {
+    out.emplace_back(ids.begin() + lo, ids.begin() + hi);
+    return;
+  }
+  double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+  for (size_t i = lo; i < hi; ++i) {
+    x0 = std::min(x0, cx[ids[i]]); x1 = std::max(x1, cx[ids[i]]);
+    y0 = std::min(y0, cy[ids[i]]); y1 = std::max(y1, cy[ids[i]]);
+  }
+  const std::vector<double>& key = (x1 - x0 >= y1 - y0) ? cx : cy;
+  const size_t mid = lo + (hi - lo) / 2;
+  std::nth_element(ids.begin() + lo, ids.begin() + mid, ids.begin() + hi,
+                   [&](int a, int b) { return key[a] < key[b] || (key[a] == key[b] && a < b); });
+  bisect(ids, lo, mid, cx, cy, core, out);
+  bisect(ids, mid, hi, cx, cy, core, out);
+}
+
+TileSet build_tiles(const MeshHost& m, int core, int depth) {
+  const int E = m.E, nn = (m.Ng + 1) * (m.Ng + 1);
+  TileSet ts;
+  ts.depth = depth;
+  std::vector<double> cx(E, 0.0), cy(E, 0.0);
+  for (int e = 0; e < E; ++e) {
+    for (int a = 0; a < nn; ++a) {
+      cx[e] += m.nodes[((size_t)e * nn + a) * 2];
+      cy[e] += m.nodes[((size_t)e * nn + a) * 2 + 1];
+    }
+    cx[e] /= nn;
+    cy[e] /= nn;
+  }
+  std::vector<int> ids(E);
+  for (int e = 0; e < E; ++e) ids[e] = e;
+  std::vector<std::vector<int>> cores;
+  bisect(ids, 0, ids.size(), cx, cy, core, cores);
+  std::vector<int> mark(E, -1);
+  ts.n_tiles = (int)cores.size();
+  ts.off.push_back(0);
+  for (int t = 0; t < ts.n_tiles; ++t) {
+    std::vector<int> list = cores[t];
+    std::sort(list.begin(), list.end());
+    for (int e : list) mark[e] = t;
+    std::vector<int> ends{(int)list.size()};
+    size_t lo = 0;
+    for (int d = 1; d <= depth; ++d) {
+      const size_t hi = list.size();
+      for (size_t h = lo; h < hi; ++h)
+        for (int f = 0; f < 4; ++f) {
+          const int en = m.nbr[(size_t)(list[h] * 4 + f) * 3];
+          if (en >= 0 && mark[en] != t) {
+            mark[en] = t;
+            list.push_back(en);
+          }
+        }
+      lo = hi;
+      ends.push_back((int)list.size());
+    }
+    for (int i = 0; i < (int)list.size(); ++i)
+      for (int f = 0; f < 4; ++f) {
+        const int en = m.nbr[(size_t)(list[i] * 4 + f) * 3];
+        int ls = -1;
+        for (int j = 0; j < (int)list.size() && en >= 0; ++j)
+          if (list[j] == en) { ls = j; break; }
+        if (ls < 0 && en >= 0 && i < ends[depth > 0 ? depth - 1 : 0] && depth > 0)
+          throw std::runtime_error("tile halo does not close");
+        ts.lnbr.push_back(ls);
+      }
+    for (int e : list) ts.elems.push_back(e);
+    for (int d = 0; d <= depth; ++d) ts.layer_end.push_back(ends[d]);
+    ts.off.push_back((int)ts.elems.size());
+    ts.max_elems = std::max(ts.max_elems, (int)list.size());
+  }
+  return ts;
+}
+
+}  // namespace pmg

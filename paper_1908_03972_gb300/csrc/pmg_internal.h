@@ -57,6 +57,16 @@ struct MeshHost {
   std::vector<FaceRec> faces;
 };
 
+// Tiles of the multi-sweep smoother (host_tables.cpp build_tiles).
+struct TileSet {
+  int depth = 0, n_tiles = 0, max_elems = 0;
+  std::vector<int> off;        // n_tiles + 1 offsets into elems
+  std::vector<int> layer_end;  // n_tiles x (depth + 1): end of the core, then of halo layers 1..depth
+  std::vector<int> elems;      // element ids, per tile core first, then halo layers
+  std::vector<int> lnbr;       // per listed element and face: slot of the neighbour in the tile (-1: outside)
+};
+TileSet build_tiles(const struct MeshHost& m, int core, int depth);
+
 struct LevelGeomHost {
   std::vector<double> met;   // 5 planes of E*N: a, b, c, d, 1/|J|
   std::vector<double> xy;    // (E, N, 2)
@@ -115,6 +125,13 @@ struct LevelDev {
   double* rs = nullptr;        // E * n row scales
   double* cs = nullptr;        // E * n column scales
   bool assembled = false, factored = false;
+  // multi-sweep tiles (k_tile.cu), when the level is tiled
+  bool tiled = false;
+  int n_tiles = 0, tile_M = 0, tile_depth = 0;
+  int* d_toff = nullptr;       // n_tiles + 1
+  int* d_tlayer = nullptr;     // n_tiles * (tile_depth + 1)
+  int* d_telems = nullptr;     // listed elements of all tiles
+  int* d_tlnbr = nullptr;      // 4 per listed element
 };
 
 // Residual kernel epilogues.
@@ -277,6 +294,11 @@ void launch_prolong3(const Ctx& c, const LevelDev& Lf, const LevelDev& Lc, const
                      const double* qcb, double* qf, int add, cudaStream_t s);
 void launch_bsum_update3(const Ctx& c, int N, const double* qn, double* const* R, const double* b, int nr,
                          double dt, double* q, cudaStream_t s);
+void launch_tile_sweeps(const Ctx& c, const LevelDev& L, const double* qin, double* qout, int nsweep,
+                        double inv_odt, const double* S, const double* qref, int prec, cudaStream_t s);
+size_t tile_smem_bytes(int P, int prec, int M);
+int tile_face_points(int P);
+cudaError_t prepare_tile_kernel(int P, int prec, size_t bytes);
 int residual_threads_per_block(int P);
 int residual_blocks_for(int P, int E);
 cudaError_t prepare_kernels(const Ctx& c);

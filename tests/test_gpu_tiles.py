@@ -1,0 +1,76 @@
+"""The multi-sweep coarse-level smoother (k_tile.cu): several element-Jacobi
+sweeps per launch on tiles that carry a halo of face neighbours.  Per element
+and sweep it repeats the arithmetic of the one-sweep fused kernel operation for
+operation, so V-cycles and stage solves with tiles must give the states of the
+per-sweep path bit for bit, for any number of sweeps per launch (including a
+last launch with fewer sweeps than the tile depth)."""
+import numpy as np
+import pytest
+
+from paper_1908_03972_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TINF = W.freestream_T(0.005)
+KW = dict(p_gauge=TINF, tol=1e-8, res_scale=W.freestream_scales(0.005), max_pseudo=4000)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1908_03972_gb300 import build, pmgfr
+    build.build()
+    pmgfr.load()
+
+
+def _qc(q):
+    rho = q[0] / q[3]
+    return np.stack([rho, rho * q[1], rho * q[2], rho * (q[3] / 0.4 + 0.5 * (q[1] ** 2 + q[2] ** 2))])
+
+
+def _run(monkeypatch, env, prec, n=16, levels=(3, 2, 1, 0), smooth=(1, 2, 5, 9), stage=False):
+    from paper_1908_03972_gb300 import pmgfr
+    for k in ("PMG_TILE_DEPTH", "PMG_TILE_DEPTH1", "PMG_FUSE_MAX_P", "PMG_TILE_CORE", "PMG_TILE_CORE1"):
+        monkeypatch.delenv(k, raising=False)
+    for k, v in env.items():
+        monkeypatch.setenv(k, str(v))
+    nodes, nbr = W.periodic_box(n, n, Ng=1)
+    s = pmgfr.Solver(nodes, nbr, list(levels), list(smooth), block_prec=prec, **KW)
+    try:
+        q = W.isentropic_vortex(s.coords(), center=(4.0, 6.0))
+        odt = 0.0436
+        s.set_stage(_qc(q) / odt + 0.5 * s.residual(q), odt)
+        if stage:
+            qs, it, drop = s.stage_solve(q)
+            return qs, it, drop
+        q1, _ = s.vcycle(q, 0.01, refresh=True)
+        q2, _ = s.vcycle(q1, 1.0, refresh=False)
+        return q1, q2
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("depth", [2, 3, 4])
+def test_tiled_p0_sweeps_are_bit_identical(monkeypatch, prec, depth):
+    ref = _run(monkeypatch, {}, prec)
+    til = _run(monkeypatch, {"PMG_TILE_DEPTH": depth}, prec)
+    for a, b in zip(ref, til):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_tiled_p1_sweeps_are_bit_identical_to_fused(monkeypatch, prec):
+    ref = _run(monkeypatch, {"PMG_FUSE_MAX_P": 1}, prec)
+    til = _run(monkeypatch, {"PMG_FUSE_MAX_P": 1, "PMG_TILE_DEPTH": 4, "PMG_TILE_DEPTH1": 2}, prec)
+    for a, b in zip(ref, til):
+        assert np.array_equal(a, b)
+
+
+def test_tiled_stage_solve_is_bit_identical(monkeypatch):
+    ref = _run(monkeypatch, {}, 1, n=12, levels=(2, 1, 0), smooth=(3, 5, 10), stage=True)
+    til = _run(monkeypatch, {"PMG_TILE_DEPTH": 4}, 1, n=12, levels=(2, 1, 0), smooth=(3, 5, 10), stage=True)
+    assert ref[1] == til[1] and ref[2] == til[2] and ref[2] <= 1e-8
+    assert np.array_equal(ref[0], til[0])
