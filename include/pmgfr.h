@@ -343,6 +343,33 @@ pmg_status pmg_profile(pmg_ctx* ctx, int enable);
 #define PMG_PROF_CLASSES 10
 pmg_status pmg_profile_read(pmg_ctx* ctx, double* ms, long long* counts);
 
+/* Autotuner of the coarse-level smoothing schedule (no counterpart in the
+ * paper; the choice changes launch shapes, not the arithmetic).  For every
+ * level that the double-word coarse-level kernels can serve (2D, a coarse
+ * level with P <= 1, gauge storage, mu = 0, no boundary faces, flux_prec not
+ * PMG_FLUX_FP64) it times the level's n_smooth sweeps, once untimed and
+ * `reps` times between CUDA events on the context's stream, under each
+ * candidate: the split face and volume launches (P = 1 only), one fused
+ * launch per sweep, and tiles of 16, 32 or 64 core elements with 2, 3 or 4
+ * sweeps per launch (k_tile.cu; every choice gives the same states bit for
+ * bit on the fused path).  It keeps the fastest per level.  With cache_path
+ * (a host string, may be NULL) a choice found there for the same (P, elements,
+ * n_smooth, block_prec, SM count) is applied without timing, and new choices
+ * are appended.  Needs the stage data and a smoother built by a V-cycle with
+ * refresh = 1; the levels' data is left as the sweeps leave it, so the next
+ * V-cycle recomputes what it uses.  report (may be NULL) receives the choice
+ * and the timings per level. */
+typedef struct {
+  int n_levels;
+  int fused[8];        /* 1: one launch per sweep or tiles; 0: split launches */
+  int tile_core[8];    /* core elements per tile (0: no tiles) */
+  int tile_depth[8];   /* sweeps per launch (0: no tiles) */
+  int candidates[8];   /* schedules timed (0: level not tunable) */
+  double us_per_sweep[8];        /* time per sweep of the choice, microseconds */
+  double us_per_sweep_before[8]; /* time per sweep of the schedule in place before the call */
+} pmg_tune_report;
+pmg_status pmg_autotune(pmg_ctx* ctx, int reps, const char* cache_path, pmg_tune_report* report);
+
 /* Allocation-free variant of pmg_residual, for callers that must not
  * allocate device memory once they are running: for example an application
  * that has handed all spare device memory to its own pool, or that runs under

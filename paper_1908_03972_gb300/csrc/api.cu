@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <array>
 #include <utility>
 
 #include "pmg_internal.h"
@@ -103,6 +104,42 @@ static void free_level(LevelDev& L) {
   for (int** p : iptrs) { if (*p) cudaFree(*p); *p = nullptr; }
   if (L.Dinv) cudaFree(L.Dinv);
   L.Dinv = nullptr;
+}
+
+// Multi-sweep tiles of a coarse level (k_tile.cu): build and upload them, or
+// drop them (depth 0).  Returns PMG_EINVAL when the tile does not fit (512
+// threads, 227 KB of shared memory per CTA).
+static pmg_status set_level_tiles(Ctx& c, LevelDev& L, int core, int depth) {
+  int** iptrs[] = {&L.d_toff, &L.d_tlayer, &L.d_telems, &L.d_tlnbr};
+  for (int** p : iptrs) { if (*p) cudaFree(*p); *p = nullptr; }
+  L.tiled = false;
+  L.n_tiles = L.tile_M = L.tile_depth = 0;
+  L.tile_core = 0;
+  if (depth <= 0) return PMG_OK;
+  TileSet ts;
+  try {
+    ts = build_tiles(c.mesh, core, depth);
+  } catch (const std::exception& ex) {
+    return fail(PMG_EINVAL, ex.what());
+  }
+  const size_t bytes = tile_smem_bytes(L.P, c.cfg.block_prec, ts.max_elems);
+  const int threads = ts.max_elems * tile_face_points(L.P);
+  if (!(bytes > 0 && bytes <= (size_t)227 * 1024 && threads <= 512))
+    return fail(PMG_EINVAL, "tile of " + std::to_string(ts.max_elems) + " elements does not fit a CTA");
+  if (dalloc(&L.d_toff, ts.off.size()) || dalloc(&L.d_tlayer, ts.layer_end.size()) ||
+      dalloc(&L.d_telems, ts.elems.size()) || dalloc(&L.d_tlnbr, ts.lnbr.size()))
+    return fail(PMG_ENOMEM, "device allocation failed for tile data");
+  PMG_CK(cudaMemcpy(L.d_toff, ts.off.data(), ts.off.size() * sizeof(int), cudaMemcpyHostToDevice));
+  PMG_CK(cudaMemcpy(L.d_tlayer, ts.layer_end.data(), ts.layer_end.size() * sizeof(int), cudaMemcpyHostToDevice));
+  PMG_CK(cudaMemcpy(L.d_telems, ts.elems.data(), ts.elems.size() * sizeof(int), cudaMemcpyHostToDevice));
+  PMG_CK(cudaMemcpy(L.d_tlnbr, ts.lnbr.data(), ts.lnbr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  PMG_CK(prepare_tile_kernel(L.P, c.cfg.block_prec, bytes));
+  L.tiled = true;
+  L.n_tiles = ts.n_tiles;
+  L.tile_M = ts.max_elems;
+  L.tile_depth = depth;
+  L.tile_core = core;
+  return PMG_OK;
 }
 
 extern "C" {
@@ -326,41 +363,23 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
     bool boundary = false;
     for (const FaceRec& fr : c.mesh.faces) boundary = boundary || fr.eR < 0;
     L.fused = (c.dim == 2 && l > 0 && L.P <= fuse_max && L.P <= 3 && c.ph.mu == 0.0 && !boundary);
-    if (L.fused && dalloc(&L.q2, L.tot)) return fail(PMG_ENOMEM, "device allocation failed for level data");
-    // Fused levels with P <= 1 in the double-word sweep arithmetic may run
-    // several sweeps per launch on tiles with a halo (k_tile.cu): up to
-    // PMG_TILE_DEPTH (P = 0) or PMG_TILE_DEPTH1 (P = 1) sweeps per launch
-    // (0: one sweep per launch), cores of PMG_TILE_CORE (P = 0, default 32)
-    // or PMG_TILE_CORE1 (P = 1, default 16) elements; a tile is at most 512
-    // threads (one per element face point).
-    if (L.fused && L.P <= 1 && c.ph.p_ref != 0.0 && flux_dw_sweep(c)) {
+    // Coarse levels with P <= 1 that the double-word sweep arithmetic serves
+    // (gauge storage, mu = 0, no boundary faces) may be smoothed by the fused
+    // one-sweep kernel or by the multi-sweep tiles (k_tile.cu); pmg_autotune
+    // chooses between them.  Without it: up to PMG_TILE_DEPTH (P = 0) or
+    // PMG_TILE_DEPTH1 (P = 1) sweeps per launch on cores of PMG_TILE_CORE
+    // (default 32) or PMG_TILE_CORE1 (default 16) elements.
+    L.tileable = c.dim == 2 && l > 0 && L.P <= 1 && c.ph.mu == 0.0 && !boundary && c.ph.p_ref != 0.0 &&
+                 flux_dw_sweep(c);
+    if ((L.fused || L.tileable) && dalloc(&L.q2, L.tot))
+      return fail(PMG_ENOMEM, "device allocation failed for level data");
+    if (L.fused && L.tileable) {
       int depth = 0, core = L.P == 0 ? 32 : 16;
       if (const char* env = getenv(L.P == 0 ? "PMG_TILE_DEPTH" : "PMG_TILE_DEPTH1")) depth = atoi(env);
       if (const char* env = getenv(L.P == 0 ? "PMG_TILE_CORE" : "PMG_TILE_CORE1")) core = atoi(env);
       if (depth > 0 && core > 0) {
-        TileSet ts;
-        try {
-          ts = build_tiles(c.mesh, core, depth);
-        } catch (const std::exception& ex) {
-          return fail(PMG_EINVAL, ex.what());
-        }
-        const size_t bytes = tile_smem_bytes(L.P, c.cfg.block_prec, ts.max_elems);
-        const int threads = ts.max_elems * tile_face_points(L.P);
-        if (bytes > 0 && bytes <= (size_t)227 * 1024 && threads <= 512) {
-          if (dalloc(&L.d_toff, ts.off.size()) || dalloc(&L.d_tlayer, ts.layer_end.size()) ||
-              dalloc(&L.d_telems, ts.elems.size()) || dalloc(&L.d_tlnbr, ts.lnbr.size()))
-            return fail(PMG_ENOMEM, "device allocation failed for tile data");
-          PMG_CK(cudaMemcpy(L.d_toff, ts.off.data(), ts.off.size() * sizeof(int), cudaMemcpyHostToDevice));
-          PMG_CK(cudaMemcpy(L.d_tlayer, ts.layer_end.data(), ts.layer_end.size() * sizeof(int),
-                            cudaMemcpyHostToDevice));
-          PMG_CK(cudaMemcpy(L.d_telems, ts.elems.data(), ts.elems.size() * sizeof(int), cudaMemcpyHostToDevice));
-          PMG_CK(cudaMemcpy(L.d_tlnbr, ts.lnbr.data(), ts.lnbr.size() * sizeof(int), cudaMemcpyHostToDevice));
-          PMG_CK(prepare_tile_kernel(L.P, c.cfg.block_prec, bytes));
-          L.tiled = true;
-          L.n_tiles = ts.n_tiles;
-          L.tile_M = ts.max_elems;
-          L.tile_depth = depth;
-        }
+        pmg_status ts = set_level_tiles(c, L, core, depth);
+        if (ts) return ts;
       }
     }
     if (c.ph.mu > 0.0) {
@@ -1319,6 +1338,110 @@ pmg_status pmg_stage_solve(pmg_ctx* h, int* iters, double* drop) {
   c.hist_norm.clear();
   c.hist_dtau.clear();
   return stage_solve(c, iters, drop, nullptr);
+}
+
+// ------------------------------------------------------------- autotuner
+// Times the smoothing of every level the fused and tiled coarse-level kernels
+// can serve under each candidate schedule and keeps the fastest: the split
+// face and volume launches (P = 1), one fused launch per sweep, or tiles of
+// 16, 32 or 64 core elements with 2, 3 or 4 sweeps per launch.  Each
+// candidate runs the level's n_smooth sweeps once untimed and `reps` times
+// between events on the context's stream, on the level's current data.
+pmg_status pmg_autotune(pmg_ctx* h, int reps, const char* cache_path, pmg_tune_report* rep) {
+  if (!h) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  if (!c.mesh_ready) return fail(PMG_ESTATE, "mesh not uploaded");
+  if (!c.stage_ready) return fail(PMG_ESTATE, "stage data not set");
+  for (int l = 0; l < c.cfg.n_levels; ++l)
+    if (!c.lev[l].factored) return fail(PMG_ESTATE, "smoother not built: run a V-cycle with refresh = 1 first");
+  if (reps < 1) reps = 1;
+  pmg_tune_report local;
+  memset(&local, 0, sizeof(local));
+  local.n_levels = c.cfg.n_levels;
+  int dev_sms = 0;
+  cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c.device);
+  // cache: lines "P E n_smooth block_prec sms fused core depth"
+  std::vector<std::array<int, 8>> cache;
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "r")) {
+      std::array<int, 8> r;
+      while (fscanf(f, "%d %d %d %d %d %d %d %d", &r[0], &r[1], &r[2], &r[3], &r[4], &r[5], &r[6], &r[7]) == 8)
+        cache.push_back(r);
+      fclose(f);
+    }
+  }
+  cudaEvent_t e0, e1;
+  PMG_CK(cudaEventCreate(&e0));
+  PMG_CK(cudaEventCreate(&e1));
+  struct Cand { int fused, core, depth; };
+  pmg_status result = PMG_OK;
+  for (int l = 0; l < c.cfg.n_levels && result == PMG_OK; ++l) {
+    LevelDev& L = c.lev[l];
+    local.fused[l] = L.fused ? 1 : 0;
+    local.tile_core[l] = L.tiled ? L.tile_core : 0;
+    local.tile_depth[l] = L.tiled ? L.tile_depth : 0;
+    if (!L.tileable) continue;
+    const int n = c.cfg.n_smooth[l];
+    const std::array<int, 5> key{L.P, c.E, n, c.cfg.block_prec, dev_sms};
+    const int was_fused = L.fused, was_core = L.tiled ? L.tile_core : 0, was_depth = L.tiled ? L.tile_depth : 0;
+    std::vector<Cand> cands;
+    bool cached = false;
+    for (const auto& r : cache)
+      if (r[0] == key[0] && r[1] == key[1] && r[2] == key[2] && r[3] == key[3] && r[4] == key[4]) {
+        cands = {{r[5], r[6], r[7]}};
+        cached = true;
+      }
+    if (!cached) {
+      if (L.P >= 1) cands.push_back({0, 0, 0});
+      cands.push_back({1, 0, 0});
+      for (int core : {16, 32, 64})
+        for (int depth : {2, 3, 4}) cands.push_back({1, core, depth});
+    }
+    double best = 1e300, before = 0.0;
+    Cand pick{was_fused, was_core, was_depth};
+    for (const Cand& cd : cands) {
+      L.fused = cd.fused != 0;
+      if (set_level_tiles(c, L, cd.core, cd.fused ? cd.depth : 0) != PMG_OK) continue;   // does not fit
+      restore_buffer(c, l, sweeps(c, l, n, false, false, false));
+      PMG_CK(cudaEventRecord(e0, c.stream));
+      for (int r = 0; r < reps; ++r) restore_buffer(c, l, sweeps(c, l, n, false, false, false));
+      PMG_CK(cudaEventRecord(e1, c.stream));
+      cudaError_t le = cudaGetLastError();
+      if (le != cudaSuccess) { result = fail(PMG_ECUDA, std::string("autotune: ") + cudaGetErrorString(le)); break; }
+      PMG_CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      PMG_CK(cudaEventElapsedTime(&ms, e0, e1));
+      const double us = 1000.0 * ms / (reps * n);
+      if (cd.fused == was_fused && cd.core == was_core && (cd.fused ? cd.depth : 0) == was_depth) before = us;
+      if (us < best) { best = us; pick = cd; }
+      ++local.candidates[l];
+    }
+    if (result != PMG_OK) break;
+    L.fused = pick.fused != 0;
+    pmg_status st = set_level_tiles(c, L, pick.core, pick.fused ? pick.depth : 0);
+    if (st) { result = st; break; }
+    local.fused[l] = pick.fused;
+    local.tile_core[l] = L.tiled ? pick.core : 0;
+    local.tile_depth[l] = L.tiled ? pick.depth : 0;
+    local.us_per_sweep[l] = best;
+    local.us_per_sweep_before[l] = before;
+    if (cache_path && !cached) {
+      if (FILE* f = fopen(cache_path, "a")) {
+        fprintf(f, "%d %d %d %d %d %d %d %d\n", key[0], key[1], key[2], key[3], key[4], pick.fused, local.tile_core[l],
+                local.tile_depth[l]);
+        fclose(f);
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // the V-cycle launch sequence changed: captured graphs are rebuilt on demand
+  for (int g = 0; g < 2; ++g)
+    if (c.graph[g]) { cudaGraphExecDestroy(c.graph[g]); c.graph[g] = nullptr; }
+  if (c.loop_exec) { cudaGraphExecDestroy(c.loop_exec); c.loop_exec = nullptr; }
+  c.F0_valid = false;
+  if (rep) *rep = local;
+  return result;
 }
 
 pmg_status pmg_profile(pmg_ctx* h, int enable) {

@@ -126,8 +126,9 @@ struct LevelDev {
   double* cs = nullptr;        // E * n column scales
   bool assembled = false, factored = false;
   // multi-sweep tiles (k_tile.cu), when the level is tiled
+  bool tileable = false;       // the double-word fused sweep and tiles may serve this level
   bool tiled = false;
-  int n_tiles = 0, tile_M = 0, tile_depth = 0;
+  int n_tiles = 0, tile_M = 0, tile_depth = 0, tile_core = 0;
   int* d_toff = nullptr;       // n_tiles + 1
   int* d_tlayer = nullptr;     // n_tiles * (tile_depth + 1)
   int* d_telems = nullptr;     // listed elements of all tiles

@@ -83,6 +83,18 @@ class pmg_step_stats(ctypes.Structure):
     ]
 
 
+class pmg_tune_report(ctypes.Structure):
+    _fields_ = [
+        ("n_levels", ctypes.c_int),
+        ("fused", ctypes.c_int * 8),
+        ("tile_core", ctypes.c_int * 8),
+        ("tile_depth", ctypes.c_int * 8),
+        ("candidates", ctypes.c_int * 8),
+        ("us_per_sweep", ctypes.c_double * 8),
+        ("us_per_sweep_before", ctypes.c_double * 8),
+    ]
+
+
 _lib = None
 
 
@@ -120,6 +132,7 @@ def load():
         "pmg_stage_history": ([vp, pd, pd, ci, ctypes.POINTER(ci)], ci),
         "pmg_profile": ([vp, ci], ci),
         "pmg_residual_static": ([vp, ci, vp, vp], ci),
+        "pmg_autotune": ([vp, ci, ctypes.c_char_p, ctypes.POINTER(pmg_tune_report)], ci),
         "pmg_checkpoint": ([vp, ctypes.c_char_p], ci),
         "pmg_dtau_min": ([vp, ctypes.POINTER(ctypes.c_double)], ci),
         "pmg_restore": ([vp, ctypes.c_char_p], ci),
@@ -446,6 +459,19 @@ def pmg_residual_static(h, level, q, out):
     if not (d1 and d2):
         raise TypeError("pmg_residual_static takes device tensors only")
     _check(load().pmg_residual_static(h, level, pq, pr))
+    return out
+
+
+def pmg_autotune(h, reps=3, cache_path=None):
+    """Tune the coarse-level smoothing schedule; returns a dict per tuned level."""
+    rep = pmg_tune_report()
+    _check(load().pmg_autotune(h, int(reps), os.fsencode(cache_path) if cache_path else None, ctypes.byref(rep)))
+    out = {}
+    for l in range(rep.n_levels):
+        if rep.candidates[l]:
+            out[l] = dict(fused=rep.fused[l], tile_core=rep.tile_core[l], tile_depth=rep.tile_depth[l],
+                          candidates=rep.candidates[l], us_per_sweep=rep.us_per_sweep[l],
+                          us_per_sweep_before=rep.us_per_sweep_before[l])
     return out
 
 
