@@ -294,7 +294,7 @@ def run_ours(args, wl, world, rank, local):
     stream = torch.cuda.current_stream(device)
     p_inf = W.freestream_T(0.005)
     kw = dict(tol=1e-8, dtau_init=0.01, dtau_max=10.0, refresh_every=10, max_pseudo=20000, use_graph=1,
-              p_gauge=p_inf, res_scale=W.freestream_scales(0.005))
+              p_gauge=p_inf, res_scale=W.freestream_scales(0.005), device_loop=args.device_loop)
     dsw = dof_sweeps_per_vcycle(E, wl["levels"], wl["smooth"])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
     # The three legs: (block precision, residual arithmetic of the sweeps)
@@ -375,10 +375,15 @@ def run_ours(args, wl, world, rank, local):
                     pseudo_iters=its, max_res_drop=drops, dof_sweeps_per_s=dsw * nv * world / (mean_ms / 1000.0),
                     ms_per_vcycle=mean_ms / nv, clocks=clocks), states
 
-    # Headline leg: W warm-up steps from the analytic state, then K timed steps.
+    # Headline leg: W warm-up steps from the analytic state, then K timed
+    # steps.  After the first warm-up step (which leaves stage data and a built
+    # smoother) the autotuner picks each coarse level's smoothing schedule.
+    pmg_tune = {}
     pmgfr.pmg_set_state(solver.h, 0, q0_dev)
-    for _ in range(args.warmup):
+    for w in range(args.warmup):
         one_step(solver, False)
+        if w == 0 and not args.no_autotune:
+            pmg_tune = pmgfr.pmg_autotune(solver.h, reps=3)
     q_warm = np.ascontiguousarray(solver.get_state())
     results = {}
     results["mixed"], mixed_states = timed_steps(solver, args.steps, ClockSampler(local))
@@ -391,6 +396,8 @@ def run_ours(args, wl, world, rank, local):
         s = make(leg)
         s.set_state(q_warm)
         one_step(s, False)
+        if not args.no_autotune:
+            pmgfr.pmg_autotune(s.h, reps=3)
         s.set_state(q_warm)
         results[leg], st = timed_steps(s, k2)
         diffs[f"mixed_vs_{leg}"] = solution_diff(mixed_states[k2 - 1], st[k2 - 1], p_inf)
@@ -510,6 +517,8 @@ def run_ours(args, wl, world, rank, local):
             "fp64": {k: v for k, v in results.get("fp64", {}).items() if k not in ("clocks",)},
             "solution_diff_after_%d_steps" % k2: diffs,
             "dof_sweeps_per_vcycle": dsw,
+            "autotune": {f"level {l}": v for l, v in pmg_tune.items()},
+            "device_loop": args.device_loop,
             "clocks": mixed["clocks"],
             "e2e": {"value": e2e_s, "unit": "s/step", "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes},
@@ -535,6 +544,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--skip-fp64", action="store_true", help="time the mixed leg only")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default coarse-level schedule")
+    ap.add_argument("--device-loop", type=int, default=0, choices=[0, 1],
+                    help="1: each stage's pseudo-iterations as one CUDA graph with a conditional WHILE node")
     ap.add_argument("--other-steps", type=int, default=4,
                     help="timed steps of the mixed_f64res and fp64 legs (at most --steps)")
     ap.add_argument("--skip-cpu", action="store_true")

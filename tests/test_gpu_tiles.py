@@ -74,3 +74,39 @@ def test_tiled_stage_solve_is_bit_identical(monkeypatch):
     til = _run(monkeypatch, {"PMG_TILE_DEPTH": 4}, 1, n=12, levels=(2, 1, 0), smooth=(3, 5, 10), stage=True)
     assert ref[1] == til[1] and ref[2] == til[2] and ref[2] <= 1e-8
     assert np.array_equal(ref[0], til[0])
+
+
+def test_autotune_reports_choices_and_keeps_convergence(monkeypatch, tmp_path):
+    """pmg_autotune times the tunable coarse levels' schedules and keeps the
+    fastest; a stage solve afterwards converges to the state of the untuned
+    solver (within the stopping tolerance), and a second call with the cache
+    file applies the recorded choice without timing the others."""
+    from paper_1908_03972_gb300 import pmgfr
+    for k in ("PMG_TILE_DEPTH", "PMG_TILE_DEPTH1", "PMG_FUSE_MAX_P"):
+        monkeypatch.delenv(k, raising=False)
+    nodes, nbr = W.periodic_box(16, 16, Ng=1)
+    res = {}
+    for tuned in (False, True):
+        s = pmgfr.Solver(nodes, nbr, [3, 2, 1, 0], [1, 2, 5, 9], block_prec=1, **KW)
+        try:
+            q = W.isentropic_vortex(s.coords(), center=(4.0, 6.0))
+            odt = 0.0436
+            s.set_stage(_qc(q) / odt + 0.5 * s.residual(q), odt)
+            s.vcycle(q, 0.01, refresh=True)
+            if tuned:
+                cache = str(tmp_path / "tune.txt")
+                rep = pmgfr.pmg_autotune(s.h, reps=2, cache_path=cache)
+                assert set(rep) == {2, 3}                      # the P = 1 and P = 0 levels
+                assert rep[3]["candidates"] >= 2 and rep[2]["candidates"] >= 3
+                assert all(v["us_per_sweep"] > 0 for v in rep.values())
+                rep2 = pmgfr.pmg_autotune(s.h, reps=1, cache_path=cache)
+                assert all(rep2[l]["candidates"] == 1 for l in rep2)
+                assert all((rep2[l]["fused"], rep2[l]["tile_core"], rep2[l]["tile_depth"]) ==
+                           (rep[l]["fused"], rep[l]["tile_core"], rep[l]["tile_depth"]) for l in rep)
+            qs, it, drop = s.stage_solve(q)
+            assert drop <= 1e-8
+            res[tuned] = qs
+        finally:
+            s.close()
+    assert np.abs(res[True][0] - res[False][0]).max() / 2.0 <= 2e-6
+    assert np.abs(res[True][1:3] - res[False][1:3]).max() <= 1e-7
