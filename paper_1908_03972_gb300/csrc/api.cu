@@ -229,8 +229,11 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
     pmg_destroy(h);
     return fail(PMG_ENOMEM, "device allocation failed");
   }
-  // d_scal[1]: set by kernels whose bounded wait for a bulk copy gave up
-  if (cudaMemset(c.d_scal, 0, 4 * sizeof(double)) != cudaSuccess) {
+  // d_scal[1]: set by kernels whose bounded wait for a bulk copy gave up;
+  // d_flag: 1 + the highest singular element of the last rebuild.  Both start
+  // at zero (cudaMalloc may hand back memory another context left behind).
+  if (cudaMemset(c.d_scal, 0, 4 * sizeof(double)) != cudaSuccess ||
+      cudaMemset(c.d_flag, 0, 4 * sizeof(int)) != cudaSuccess) {
     pmg_destroy(h);
     return fail(PMG_ECUDA, "device memset failed");
   }

@@ -56,7 +56,9 @@ def _run(monkeypatch, env, prec, n=16, levels=(3, 2, 1, 0), smooth=(1, 2, 5, 9),
 @pytest.mark.parametrize("depth", [2, 3, 4])
 def test_tiled_p0_sweeps_are_bit_identical(monkeypatch, prec, depth):
     ref = _run(monkeypatch, {}, prec)
-    til = _run(monkeypatch, {"PMG_TILE_DEPTH": depth}, prec)
+    # a CTA holds (tile elements) x (face points) <= 512 threads: cores of 32
+    # elements take at most 3 halo layers at P = 0, cores of 16 take 4
+    til = _run(monkeypatch, {"PMG_TILE_DEPTH": depth, "PMG_TILE_CORE": 32 if depth < 4 else 16}, prec)
     for a, b in zip(ref, til):
         assert np.array_equal(a, b)
 
@@ -64,16 +66,27 @@ def test_tiled_p0_sweeps_are_bit_identical(monkeypatch, prec, depth):
 @pytest.mark.parametrize("prec", [1, 2])
 def test_tiled_p1_sweeps_are_bit_identical_to_fused(monkeypatch, prec):
     ref = _run(monkeypatch, {"PMG_FUSE_MAX_P": 1}, prec)
-    til = _run(monkeypatch, {"PMG_FUSE_MAX_P": 1, "PMG_TILE_DEPTH": 4, "PMG_TILE_DEPTH1": 2}, prec)
+    til = _run(monkeypatch, {"PMG_FUSE_MAX_P": 1, "PMG_TILE_DEPTH": 4, "PMG_TILE_CORE": 16, "PMG_TILE_DEPTH1": 2,
+                             "PMG_TILE_CORE1": 16}, prec)
     for a, b in zip(ref, til):
         assert np.array_equal(a, b)
 
 
 def test_tiled_stage_solve_is_bit_identical(monkeypatch):
     ref = _run(monkeypatch, {}, 1, n=12, levels=(2, 1, 0), smooth=(3, 5, 10), stage=True)
-    til = _run(monkeypatch, {"PMG_TILE_DEPTH": 4}, 1, n=12, levels=(2, 1, 0), smooth=(3, 5, 10), stage=True)
+    til = _run(monkeypatch, {"PMG_TILE_DEPTH": 4, "PMG_TILE_CORE": 16}, 1, n=12, levels=(2, 1, 0), smooth=(3, 5, 10),
+               stage=True)
     assert ref[1] == til[1] and ref[2] == til[2] and ref[2] <= 1e-8
     assert np.array_equal(ref[0], til[0])
+
+
+def test_oversized_tile_is_refused(monkeypatch):
+    """A tile whose elements x face points exceed one CTA's 512 threads is
+    refused at upload with PMG_EINVAL, before any launch."""
+    from paper_1908_03972_gb300 import pmgfr
+    with pytest.raises(pmgfr.PmgError) as ei:
+        _run(monkeypatch, {"PMG_TILE_DEPTH": 4, "PMG_TILE_CORE": 32}, 1)
+    assert ei.value.status == pmgfr.PMG_EINVAL and "does not fit" in str(ei.value)
 
 
 def test_autotune_reports_choices_and_keeps_convergence(monkeypatch, tmp_path):
