@@ -352,7 +352,8 @@ pmg_status pmg_profile_read(pmg_ctx* ctx, double* ms, long long* counts);
  * candidate: the split face and volume launches (P = 1 only), one fused
  * launch per sweep, and tiles of 16, 32 or 64 core elements with 2, 3 or 4
  * sweeps per launch (k_tile.cu; every choice gives the same states bit for
- * bit on the fused path).  It keeps the fastest per level.  With cache_path
+ * bit on the fused path).  It keeps the fastest per level, unless it beats
+ * the schedule in place by 2% or less, which then stays.  With cache_path
  * (a host string, may be NULL) a choice found there for the same (P, elements,
  * n_smooth, block_prec, SM count) is applied without timing, and new choices
  * are appended.  Needs the stage data and a smoother built by a V-cycle with

@@ -1420,6 +1420,13 @@ pmg_status pmg_autotune(pmg_ctx* h, int reps, const char* cache_path, pmg_tune_r
       ++local.candidates[l];
     }
     if (result != PMG_OK) break;
+    // keep the schedule in place unless another beats it by more than 2%:
+    // timings of equivalent schedules differ by noise, and a change of
+    // schedule changes the launch sequence for nothing
+    if (!cached && before > 0.0 && best > 0.98 * before) {
+      pick = Cand{was_fused, was_core, was_depth};
+      best = before;
+    }
     L.fused = pick.fused != 0;
     pmg_status st = set_level_tiles(c, L, pick.core, pick.fused ? pick.depth : 0);
     if (st) { result = st; break; }
