@@ -77,17 +77,22 @@ def apply_flops(P, E):
 
 
 # ------------------------------------------------------------------ helpers
+# The translation units of the kernels whose ncu counters profiles/ holds (the
+# double-word sweep, face-flux and residual-and-update kernels) and the device
+# headers they include.
+FINGERPRINT_FILES = ("k_fused.cu", "k_residual.cu", "k_volume_dw.cu", "sweep_common.cuh", "dword.cuh",
+                     "physics.cuh", "physics_dw.cuh", "tma.cuh", "pmg_internal.h")
+
+
 def csrc_fingerprint(src=None):
-    """Hash of the kernel sources (the k_*.cu files and the device headers they
-    include) with comments and blank space removed; host-only files (api.cu,
-    host_tables.cpp) and comments do not change a kernel's counters."""
+    """Hash of the recorded kernels' sources (FINGERPRINT_FILES) with comments
+    and blank space removed; other kernels' files, host-only files (api.cu,
+    host_tables.cpp) and comments do not change those kernels' counters."""
     import hashlib
     import re
     src = src or os.path.join(ROOT, "paper_1908_03972_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(src)):
-        if not (f.startswith("k_") or f.endswith(".cuh") or f == "pmg_internal.h"):
-            continue
+    for f in FINGERPRINT_FILES:
         h.update(f.encode())
         with open(os.path.join(src, f)) as fh:
             text = re.sub(r"/\*.*?\*/", "", re.sub(r"//[^\n]*", "", fh.read()), flags=re.S)

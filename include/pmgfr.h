@@ -284,7 +284,8 @@ pmg_status pmg_set_blocks(pmg_ctx* ctx, int level, const double* D, int on_devic
 /* Factor the assembled blocks of a level (or all, level = -1) in the
  * configured precision: power-of-two row/column equilibration, then
  * Gauss-Jordan elimination with partial pivoting to the explicit inverse.
- * Returns PMG_ESINGULAR, naming the element, if a pivot is not finite or not
+ * Returns PMG_ESINGULAR, naming the element and level of the highest such
+ * block (level-major order), if a pivot is not finite or not
  * above n eps of the working precision (the equilibrated rows have unit size
  * and a row that depends on others leaves a pivot of rounding size, so such a
  * block is singular to working precision); the library's V-cycle calls report

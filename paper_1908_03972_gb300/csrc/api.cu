@@ -532,7 +532,7 @@ static void refresh_level(Ctx& c, int l) {
   }
   {
     ProfScope ps(c, K_FACTOR, l);
-    launch_factor(c, L, c.cfg.block_prec, c.d_flag, c.stream);
+    launch_factor(c, L, l, c.cfg.block_prec, c.d_flag, c.stream);
   }
   L.assembled = L.factored = true;
 }
@@ -718,7 +718,9 @@ static pmg_status check_singular(Ctx& c) {
   PMG_CK(cudaStreamSynchronize(c.stream));
   if (flag) {
     cudaMemsetAsync(c.d_flag, 0, sizeof(int), c.stream);
-    return fail(PMG_ESINGULAR, "element block " + std::to_string(flag - 1) + " is singular to working precision (pivot not above n eps)");
+    const int lv = (flag - 1) / c.E, e = (flag - 1) % c.E;
+    return fail(PMG_ESINGULAR, "element block " + std::to_string(e) + " of level " + std::to_string(lv) +
+                                   " is singular to working precision (pivot not above n eps)");
   }
   return PMG_OK;
 }
@@ -1229,7 +1231,7 @@ pmg_status pmg_factor_blocks(pmg_ctx* h, int level) {
   for (int l = 0; l < c.cfg.n_levels; ++l) {
     if (level >= 0 && l != level) continue;
     if (!c.lev[l].assembled) return fail(PMG_ESTATE, "blocks not assembled");
-    launch_factor(c, c.lev[l], c.cfg.block_prec, c.d_flag, c.stream);
+    launch_factor(c, c.lev[l], l, c.cfg.block_prec, c.d_flag, c.stream);
     c.lev[l].factored = true;
   }
   PMG_CK_LAUNCH();

@@ -172,7 +172,7 @@ template <> struct Eps<double> { static constexpr double value = 2.2204460492503
 template <class W>
 __global__ void __launch_bounds__(256) factor_kernel(int n, const double* __restrict__ Din, W* __restrict__ Dinv,
                                                      double* __restrict__ rs, double* __restrict__ cs,
-                                                     int* __restrict__ flag) {
+                                                     int* __restrict__ flag, int flag_base) {
   using T = typename Blk<W>::acc;   // elimination arithmetic (FP32 for BF16 storage)
   extern __shared__ unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);                       // n * n, row-major
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(256) factor_kernel(int n, const double* __rest
     rs[(size_t)e * n + i] = sr[i];
     cs[(size_t)e * n + i] = sc[i];
   }
-  if (tid == 0 && s_bad) atomicMax(flag, e + 1);
+  if (tid == 0 && s_bad) atomicMax(flag, flag_base + e + 1);
 }
 
 static size_t factor_smem(int n, int wbytes) {
@@ -270,15 +270,15 @@ static size_t factor_smem(int n, int wbytes) {
   return b + 2 * (size_t)n * 8;
 }
 
-void launch_factor(const Ctx& c, LevelDev& L, int prec, int* flag, cudaStream_t s) {
-  int n = L.n;
+void launch_factor(const Ctx& c, LevelDev& L, int level, int prec, int* flag, cudaStream_t s) {
+  const int n = L.n, base = level * c.E;   // the flag holds 1 + level E + element of the highest bad block
   if (prec == PMG_PREC_FP64)
-    factor_kernel<double><<<c.E, 256, factor_smem(n, 8), s>>>(n, L.Dfull, (double*)L.Dinv, L.rs, L.cs, flag);
+    factor_kernel<double><<<c.E, 256, factor_smem(n, 8), s>>>(n, L.Dfull, (double*)L.Dinv, L.rs, L.cs, flag, base);
   else if (prec == PMG_PREC_BF16R)
     factor_kernel<__nv_bfloat16><<<c.E, 256, factor_smem(n, 4), s>>>(n, L.Dfull, (__nv_bfloat16*)L.Dinv, L.rs,
-                                                                       L.cs, flag);
+                                                                       L.cs, flag, base);
   else
-    factor_kernel<float><<<c.E, 256, factor_smem(n, 4), s>>>(n, L.Dfull, (float*)L.Dinv, L.rs, L.cs, flag);
+    factor_kernel<float><<<c.E, 256, factor_smem(n, 4), s>>>(n, L.Dfull, (float*)L.Dinv, L.rs, L.cs, flag, base);
 }
 
 // Largest block the shared-memory factorisation holds in the precision prec

@@ -252,7 +252,7 @@ void launch_volume_apply(const Ctx& c, const LevelDev& L, double* q, double inv_
                          const double* S, const double* qn, int prec, cudaStream_t s);
 void launch_assemble(const Ctx& c, const LevelDev& L, const double* q, const double* d_dtau, double inv_odt,
                      cudaStream_t s);
-void launch_factor(const Ctx& c, LevelDev& L, int prec, int* flag, cudaStream_t s);
+void launch_factor(const Ctx& c, LevelDev& L, int level, int prec, int* flag, cudaStream_t s);
 void launch_apply(const Ctx& c, const LevelDev& L, int prec, const double* r, double* x, int accumulate,
                   cudaStream_t s);
 void launch_restrict(const Ctx& c, const LevelDev& Lf, const LevelDev& Lc, const XferTab& X, const double* in,

@@ -69,12 +69,13 @@ def test_fingerprint_ignores_comments_and_blank_space(tmp_path):
     shutil.copytree(src, dst)
     ref = bench.csrc_fingerprint(str(dst))
     assert ref == bench.csrc_fingerprint(src)
-    f = dst / "k_misc.cu"
+    f = dst / "k_fused.cu"
     text = f.read_text()
     f.write_text("// a new comment line\n\n" + text.replace(";\n", ";   /* trailing */\n", 3))
     assert bench.csrc_fingerprint(str(dst)) == ref
     f.write_text(text.replace("namespace pmg {", "namespace pmg {\nconstexpr int kProbe = 1;", 1))
     assert bench.csrc_fingerprint(str(dst)) != ref
     (dst / "api.cu").write_text("host code changes do not count\n")
+    (dst / "k_blocks.cu").write_text("nor do kernels whose counters are not recorded\n")
     f.write_text(text)
     assert bench.csrc_fingerprint(str(dst)) == ref
