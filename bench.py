@@ -11,6 +11,9 @@ arithmetics of the element-Jacobi P-multigrid V-cycle:
                 accumulation.
   mixed_f64res  FP32 blocks, binary64 residual everywhere.
   fp64          FP64 blocks, binary64 residual everywhere.
+  nk_pmg        as mixed, with every stage solved by Newton-Krylov (FGMRES,
+                difference Jacobian, one FAS V-cycle as the preconditioner)
+                instead of pseudo-transient continuation.
 
 Workload (default "c2"): isentropic vortex, Ma_inf = 0.005, periodic
 [0,10]^2, 64x64 straight quads, P{3-2-1-0}, I{5-10-20-40}, ESDIRK3,
@@ -308,12 +311,21 @@ def run_ours(args, wl, world, rank, local):
         "mixed_bf16": (pmgfr.PMG_PREC_BF16R, pmgfr.PMG_FLUX_DW_SMOOTH),
         "mixed_f64res": (pmgfr.PMG_PREC_FP32, pmgfr.PMG_FLUX_FP64),
         "fp64": (pmgfr.PMG_PREC_FP64, pmgfr.PMG_FLUX_FP64),
+        "nk_pmg": (pmgfr.PMG_PREC_FP32, pmgfr.PMG_FLUX_DW_SMOOTH),
     }
+    # Newton-Krylov stages with one V-cycle as the preconditioner (the
+    # variant the paper's conclusions name as future work); the difference
+    # step is taken relative to the absolute pressure and temperature scale.
+    NK_OPTS = dict(precond=pmgfr.PMG_NK_PC_VCYCLE, krylov_dim=30, max_krylov=60, dtau_pc=10.0,
+                   state_scale=(p_inf, 1.0, 1.0, p_inf))
 
     def make(leg):
         prec, flux = LEGS[leg]
-        return pmgfr.Solver(nodes, nbr, wl["levels"], wl["smooth"], stream=stream.cuda_stream, block_prec=prec,
-                            flux_prec=flux, **kw)
+        s = pmgfr.Solver(nodes, nbr, wl["levels"], wl["smooth"], stream=stream.cuda_stream, block_prec=prec,
+                         flux_prec=flux, **kw)
+        if leg == "nk_pmg":
+            pmgfr.pmg_set_stage_solver(s.h, pmgfr.PMG_STAGE_NK, **NK_OPTS)
+        return s
 
     solver = make("mixed")
     q0 = W.isentropic_vortex(solver.coords())
@@ -396,6 +408,9 @@ def run_ours(args, wl, world, rank, local):
     # untimed step first for their own graph captures, then reset), K2 steps.
     k2 = min(args.steps, args.other_steps)
     legs = [] if args.skip_fp64 else ["mixed_bf16", "mixed_f64res", "fp64"]
+    if not args.skip_nk:
+        legs.append("nk_pmg")
+    nk_work = {}
     diffs = {}
     for leg in legs:
         s = make(leg)
@@ -404,7 +419,11 @@ def run_ours(args, wl, world, rank, local):
         if not args.no_autotune:
             pmgfr.pmg_autotune(s.h, reps=3)
         s.set_state(q_warm)
+        if leg == "nk_pmg":
+            pmgfr.pmg_nk_stats_read(s.h, reset=True)
         results[leg], st = timed_steps(s, k2)
+        if leg == "nk_pmg":
+            nk_work = {k: v / k2 for k, v in pmgfr.pmg_nk_stats_read(s.h, reset=True).items()}
         diffs[f"mixed_vs_{leg}"] = solution_diff(mixed_states[k2 - 1], st[k2 - 1], p_inf)
         s.close()
     mixed = results["mixed"]
@@ -515,11 +534,16 @@ def run_ours(args, wl, world, rank, local):
                        "mixed_bf16_leg": "BF16 block inverses applied with FP32 accumulation, residuals as mixed",
                        "mixed_f64res_leg": "FP32 blocks, binary64 residual everywhere",
                        "fp64_leg": "FP64 blocks, binary64 residual everywhere",
+                       "nk_pmg_leg": ("as mixed, each stage solved by Newton-Krylov (restarted FGMRES(30), "
+                                      "difference Jacobian, one FAS V-cycle as the preconditioner, eta 1e-2) "
+                                      "instead of pseudo-transient continuation; pseudo_iters count Newton steps"),
                        "l2": "flushed (256 MiB write) before every timed step", "parallelism": "replicas"},
             "mixed": {k: v for k, v in mixed.items() if k not in ("clocks",)},
             "mixed_bf16": {k: v for k, v in results.get("mixed_bf16", {}).items() if k not in ("clocks",)},
             "mixed_f64res": {k: v for k, v in results.get("mixed_f64res", {}).items() if k not in ("clocks",)},
             "fp64": {k: v for k, v in results.get("fp64", {}).items() if k not in ("clocks",)},
+            "nk_pmg": dict({k: v for k, v in results.get("nk_pmg", {}).items() if k not in ("clocks",)},
+                           **({"per_step": nk_work} if nk_work else {})),
             "solution_diff_after_%d_steps" % k2: diffs,
             "dof_sweeps_per_vcycle": dsw,
             "autotune": {f"level {l}": v for l, v in pmg_tune.items()},
@@ -548,7 +572,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
-    ap.add_argument("--skip-fp64", action="store_true", help="time the mixed leg only")
+    ap.add_argument("--skip-fp64", action="store_true", help="skip the BF16, binary64-residual and FP64 legs")
+    ap.add_argument("--skip-nk", action="store_true", help="skip the Newton-Krylov leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default coarse-level schedule")
     ap.add_argument("--device-loop", type=int, default=0, choices=[0, 1],
                     help="1: each stage's pseudo-iterations as one CUDA graph with a conditional WHILE node")

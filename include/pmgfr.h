@@ -324,6 +324,67 @@ pmg_status pmg_stage_solve(pmg_ctx* ctx, int* iters, double* drop);
  * pressure difference so that rho E ~ 1/Ma^2 is never rounded. */
 pmg_status pmg_esdirk_step(pmg_ctx* ctx, double dt, pmg_step_stats* stats);
 
+/* Newton-Krylov stage solver (no part of the paper's method: its introduction
+ * describes matrix-free Newton-Krylov solvers and its concluding section
+ * names Newton-Krylov with the P-multigrid method as preconditioner as future
+ * work).  Selected with pmg_set_stage_solver, it replaces the pseudo-transient
+ * continuation in pmg_stage_solve and in every stage of pmg_esdirk_step:
+ *
+ *   Newton on F(q) = 0 (the stage system of pmg_set_stage / the ESDIRK
+ *   stage): solve A delta = F(q), A = -dF/dq, to the relative tolerance eta
+ *   by restarted FGMRES(krylov_dim) with right preconditioning, in the space
+ *   where each equation is divided by its res_scale (the stage norm); then
+ *   q += lam delta, lam halved (at most max_backtrack times, the last trial
+ *   kept) until ||F|| falls by the factor (1 - 1e-4 lam).  The stage ends
+ *   when ||F|| <= tol ||F^0|| (PMG_OK), after max_newton steps (PMG_ENOTCONV)
+ *   or on a non-finite norm (PMG_ENONFINITE).
+ *   A z = -(F(q + h z) - F(q)) / h, h = delta0 / rms(z_v / state_scale_v),
+ *   with F in binary64 whatever flux_prec says.
+ *   Preconditioner PMG_NK_PC_BLOCK: z = D^-1 r with the finest level's
+ *   element blocks at the Newton iterate and dtau_pc.  PMG_NK_PC_VCYCLE: one
+ *   FAS V-cycle (the configured levels, smoothing counts and arithmetic) on
+ *   the stage system with source src - F(q) + eps r from q, z = (q' - q)/eps,
+ *   eps = pc_eps ||F(q)||; its blocks are rebuilt (all levels, dtau_pc) in the first
+ *   application of every pc_refresh-th Newton step.
+ *
+ * With the Newton-Krylov solver pmg_step_stats.pseudo_iters counts Newton
+ * steps and n_vcycles the preconditioner's V-cycles; pmg_stage_history holds
+ * ||F|| after every Newton step (dtau entries 0). */
+typedef enum { PMG_STAGE_PTC = 0, PMG_STAGE_NK = 1 } pmg_stage_solver;
+typedef enum { PMG_NK_PC_BLOCK = 0, PMG_NK_PC_VCYCLE = 1 } pmg_nk_precond;
+typedef struct {
+  int max_newton;          /* Newton steps per stage (<= 0: 30) */
+  int krylov_dim;          /* FGMRES restart length m, 1..64 (<= 0: 20) */
+  int max_krylov;          /* Krylov iterations per Newton step (<= 0: 2 m) */
+  double eta;              /* relative tolerance of each linear solve (<= 0: 1e-2) */
+  int precond;             /* pmg_nk_precond */
+  double dtau_pc;          /* dtau in the preconditioner's blocks (<= 0: dtau_max) */
+  int pc_refresh;          /* rebuild its blocks every pc_refresh Newton steps (<= 0: 1) */
+  double delta0;           /* difference step of the Jacobian-vector product (<= 0: 1e-7) */
+  double state_scale[5];   /* scale of each state variable for that step; an entry <= 0
+                              takes the RMS of the variable over the stage's first
+                              iterate (plus |p_gauge| for the pressure) */
+  int max_backtrack;       /* step halvings of the line search (< 0: 6) */
+  double pc_eps;           /* V-cycle preconditioner: eps = pc_eps ||F(q)|| (<= 0: 0.1;
+                              with 1 the V-cycle sees the whole Newton defect and
+                              can leave its linear range) */
+} pmg_nk_options;
+typedef struct {
+  long long newton;        /* Newton steps */
+  long long krylov;        /* FGMRES iterations */
+  long long vcycles;       /* preconditioner V-cycles */
+  long long residuals;     /* binary64 stage-residual evaluations */
+} pmg_nk_stats;
+
+/* Choose the stage solver: PMG_STAGE_PTC (the default) or PMG_STAGE_NK with
+ * options (opts may be NULL for the defaults; copied).  PMG_EINVAL for an
+ * unknown solver or options out of range. */
+pmg_status pmg_set_stage_solver(pmg_ctx* ctx, int solver, const pmg_nk_options* opts);
+
+/* Counts of the Newton-Krylov work since the last reset (reset = 1 zeroes
+ * them after the read).  Host memory. */
+pmg_status pmg_nk_stats_read(pmg_ctx* ctx, pmg_nk_stats* out, int reset);
+
 /* Residual norm ||F^m|| and pseudo time step of every pseudo-iteration of the
  * last pmg_stage_solve or pmg_esdirk_step (all stages, in order).  Up to
  * max_count entries are written to norms / dtau (either may be NULL);

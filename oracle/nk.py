@@ -33,8 +33,9 @@ preconditioner as future work.  This module writes that variant out:
     D at q and dtau_pc (Section 2.4: Gamma/dtau + M/(omega dt) - dR_e/dq_e);
   * "vcycle": one FAS V-cycle (Section 3) on G(q') = F(q') - F(q) + eps r
     from q' = q, i.e. the stage system with source src - F(q) + eps r, and
-    z = (q' - q) / eps with eps = ||F(q)||_W (the V-cycle sees a defect of
-    the size of the Newton defect); the blocks of every level are rebuilt in
+    z = (q' - q) / eps with eps = pc_eps ||F(q)||_W (pc_eps = 0.1: the
+    V-cycle sees a tenth of the Newton defect, within its linear range); the
+    blocks of every level are rebuilt in
     the first application of each Newton step whose index is a multiple of
     pc_refresh.
 """
@@ -92,7 +93,8 @@ def fgmres(apply_A, apply_M, b, m, max_it, rtol):
 
 
 def nk_stage_solve(orc, q, src, odt, W, s, *, tol=1e-8, max_newton=30, m=20, max_krylov=40, eta=1e-2,
-                   precond="vcycle", dtau_pc=10.0, pc_refresh=1, delta0=1e-7, max_backtrack=6, norm0=None):
+                   precond="vcycle", dtau_pc=10.0, pc_refresh=1, delta0=1e-7, max_backtrack=6, norm0=None,
+                   pc_eps=0.1):
     """Newton-Krylov solve of the stage system with source src and omega dt =
     odt on the oracle `orc`, from q.  W: 1 / residual scale per equation; s:
     state scale per variable.  Stops when ||F||_W <= tol * ||F(q_start)||_W
@@ -117,7 +119,7 @@ def nk_stage_solve(orc, q, src, odt, W, s, *, tol=1e-8, max_newton=30, m=20, max
     for k in range(max_newton):
         if nrm <= tol * n0 or n0 == 0.0:
             return dict(q=q, residuals=n_res, norms=norms, status=0, **stats)
-        eps = nrm
+        eps = pc_eps * nrm
         refresh = [k % pc_refresh == 0]
         if precond == "block" and refresh[0]:
             D = orc.blocks(q, dtau_pc)

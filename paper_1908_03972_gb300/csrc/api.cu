@@ -109,6 +109,15 @@ static void free_level(LevelDev& L) {
 // Multi-sweep tiles of a coarse level (k_tile.cu): build and upload them, or
 // drop them (depth 0).  Returns PMG_EINVAL when the tile does not fit (512
 // threads, 227 KB of shared memory per CTA).
+static void nk_free(Ctx& c) {
+  double** ptrs[] = {&c.nk_q, &c.nk_F, &c.nk_src, &c.nk_w, &c.nk_t, &c.nk_x,
+                     &c.nk_V, &c.nk_Z, &c.nk_part, &c.nk_dots, &c.nk_coef};
+  for (double** p : ptrs) { if (*p) cudaFree(*p); *p = nullptr; }
+  if (c.h_nk) cudaFreeHost(c.h_nk);
+  c.h_nk = nullptr;
+  c.nk_m = 0;
+}
+
 static pmg_status set_level_tiles(Ctx& c, LevelDev& L, int core, int depth) {
   int** iptrs[] = {&L.d_toff, &L.d_tlayer, &L.d_telems, &L.d_tlnbr};
   for (int** p : iptrs) { if (*p) cudaFree(*p); *p = nullptr; }
@@ -245,6 +254,7 @@ void pmg_destroy(pmg_ctx* h) {
   if (!h) return;
   Ctx& c = h->c;
   cudaStreamSynchronize(c.stream);
+  nk_free(c);
   for (int g = 0; g < 2; ++g)
     if (c.graph[g]) cudaGraphExecDestroy(c.graph[g]);
   if (c.loop_exec) cudaGraphExecDestroy(c.loop_exec);
@@ -852,11 +862,314 @@ static pmg_status stage_solve_device(Ctx& c, double dtau_init, double dtau_max, 
 }
 
 // Pseudo-transient continuation of the current stage (Section 2.4).
-static pmg_status stage_solve(Ctx& c, int* iters, double* drop, int* n_refresh) {
+// ------------------------------------------------- Newton-Krylov stage solver
+// Newton on the stage system with restarted, right-preconditioned FGMRES
+// (Saad 1993) in the space where each equation is divided by its residual
+// scale; classical Gram-Schmidt done twice, Givens rotations on the host.
+// The Jacobian acts only through differences of binary64 stage residuals
+// (the matrix-free products the paper's introduction describes); the
+// preconditioner is the element-block Jacobi smoother's blocks or one FAS
+// V-cycle (Section 3) -- the P-multigrid preconditioner the paper's
+// concluding section proposes.
+static pmg_nk_options nk_defaults(const Ctx& c, const pmg_nk_options* o) {
+  pmg_nk_options r;
+  memset(&r, 0, sizeof(r));
+  if (o) r = *o;
+  else r.precond = PMG_NK_PC_VCYCLE;
+  if (r.max_newton <= 0) r.max_newton = 30;
+  if (r.krylov_dim <= 0) r.krylov_dim = 20;
+  if (r.max_krylov <= 0) r.max_krylov = 2 * r.krylov_dim;
+  if (!(r.eta > 0.0)) r.eta = 1e-2;
+  if (!(r.dtau_pc > 0.0)) r.dtau_pc = c.cfg.dtau_max;
+  if (r.pc_refresh <= 0) r.pc_refresh = 1;
+  if (!(r.delta0 > 0.0)) r.delta0 = 1e-7;
+  if (r.max_backtrack < 0) r.max_backtrack = 6;
+  if (!(r.pc_eps > 0.0)) r.pc_eps = 0.1;
+  return r;
+}
+
+static pmg_status nk_alloc(Ctx& c, int m) {
+  if (c.nk_V && c.nk_m >= m) return PMG_OK;
+  nk_free(c);
+  const size_t n = c.lev[0].tot;
+  if (dalloc(&c.nk_q, n) || dalloc(&c.nk_F, n) || dalloc(&c.nk_src, n) || dalloc(&c.nk_w, n) ||
+      dalloc(&c.nk_t, n) || dalloc(&c.nk_x, n) || dalloc(&c.nk_V, (size_t)(m + 1) * n) ||
+      dalloc(&c.nk_Z, (size_t)m * n) || dalloc(&c.nk_part, (size_t)kDotBlocks * (m + 2)) ||
+      dalloc(&c.nk_dots, (size_t)3 * m + 3) || dalloc(&c.nk_coef, (size_t)m + 1) ||
+      cudaMallocHost((void**)&c.h_nk, ((size_t)3 * m + 3) * sizeof(double)) != cudaSuccess) {
+    nk_free(c);
+    return fail(PMG_ENOMEM, "device allocation failed for the Newton-Krylov vectors");
+  }
+  c.nk_m = m;
+  return PMG_OK;
+}
+
+// The vectors and the finest level's operators the solver works with.
+struct NkWork {
+  Ctx& c;
+  LevelDev& L;
+  pmg_nk_options o;
+  size_t n, plane;
+  Scale5 one, W, Winv, sinv;
+  int m;
+
+  NkWork(Ctx& cc, const pmg_nk_options& oo) : c(cc), L(cc.lev[0]), o(oo) {
+    n = L.tot;
+    plane = (size_t)c.E * L.N;
+    m = o.krylov_dim;
+    for (int v = 0; v < 5; ++v) {
+      one.s[v] = 1.0;
+      W.s[v] = v < c.nv ? c.ph.nw[v] : 1.0;
+      Winv.s[v] = 1.0 / W.s[v];
+      sinv.s[v] = 1.0;
+    }
+  }
+  void combine(double* out, const double* x0, double a0, const double* x1, double a1, const Scale5& s0,
+               const double* x2, double a2, const Scale5& s2) {
+    launch_plane_combine(out, x0, a0, x1, a1, s0, x2, a2, s2, plane, n, c.stream);
+  }
+  void copy(double* dst, const double* src) { combine(dst, src, 1.0, nullptr, 0.0, one, nullptr, 0.0, one); }
+  // h_nk[0..count) <- nk_dots[0..count)
+  pmg_status fetch(int count) {
+    PMG_CK(cudaMemcpyAsync(c.h_nk, c.nk_dots, count * sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    PMG_CK(cudaStreamSynchronize(c.stream));
+    return PMG_OK;
+  }
+  // ||x||_2 of a vector of the finest size
+  pmg_status norm2(const double* x, double* out) {
+    launch_multi_dot(x, n, 1, x, n, c.nk_part, c.nk_dots, c.stream);
+    pmg_status st = fetch(1);
+    if (st) return st;
+    *out = std::sqrt(std::max(c.h_nk[0], 0.0));
+    return PMG_OK;
+  }
+  // state scales: the option, else the RMS of the variable in q (+ |p_gauge| for p)
+  pmg_status set_state_scales(const double* q) {
+    for (int v = 0; v < c.nv; ++v) {
+      double sv = o.state_scale[v];
+      if (!(sv > 0.0)) {
+        launch_multi_dot(q + v * plane, plane, 1, q + v * plane, plane, c.nk_part, c.nk_dots, c.stream);
+        pmg_status st = fetch(1);
+        if (st) return st;
+        sv = std::sqrt(std::max(c.h_nk[0], 0.0) / (double)plane) + (v == 0 ? std::fabs(c.ph.p_ref) : 0.0);
+        if (!(sv > 0.0) || !std::isfinite(sv)) sv = 1.0;
+      }
+      sinv.s[v] = 1.0 / sv;
+    }
+    return PMG_OK;
+  }
+  // w = W A z = -W (F(q + h z) - F(q)) / h at q = nk_q (F(q) in nk_F)
+  pmg_status apply_A(const double* z, double* w) {
+    combine(c.nk_t, z, 1.0, nullptr, 0.0, sinv, nullptr, 0.0, one);
+    double ss;
+    pmg_status st = norm2(c.nk_t, &ss);
+    if (st) return st;
+    const double rms = ss / std::sqrt((double)n);
+    if (!(rms > 0.0)) {
+      PMG_CK(cudaMemsetAsync(w, 0, n * sizeof(double), c.stream));
+      return PMG_OK;
+    }
+    const double h = o.delta0 / rms;
+    combine(L.q, c.nk_q, 1.0, nullptr, 0.0, one, z, h, one);
+    system_residual(c, 0, false);
+    Scale5 Wh;
+    for (int v = 0; v < 5; ++v) Wh.s[v] = -W.s[v] / h;
+    combine(w, L.F, 1.0, c.nk_F, -1.0, Wh, nullptr, 0.0, one);
+    ++c.nk_count[3];
+    PMG_CK_LAUNCH();
+    return PMG_OK;
+  }
+  // z = M^-1 (v / W): the element blocks, or one V-cycle on the stage system
+  // with source src - F(q) + eps v / W from q, z = (q' - q) / eps
+  pmg_status apply_M(const double* v, double* z, bool* refresh, double eps) {
+    if (o.precond == PMG_NK_PC_BLOCK) {
+      combine(c.nk_t, v, 1.0, nullptr, 0.0, Winv, nullptr, 0.0, one);
+      launch_apply(c, L, c.cfg.block_prec, c.nk_t, z, 0, c.stream);
+      PMG_CK_LAUNCH();
+      return PMG_OK;
+    }
+    combine(c.src, c.nk_src, 1.0, c.nk_F, -1.0, one, v, eps, Winv);
+    copy(L.q, c.nk_q);
+    system_residual(c, 0, false);   // the V-cycle starts from lev[0].F = F(q) - S
+    pmg_status st;
+    if (*refresh) {
+      st = set_dtau(c, o.dtau_pc);
+      if (st) return st;
+    }
+    st = launch_vcycle(c, *refresh);
+    if (st) return st;
+    if (*refresh) {
+      st = check_singular(c);
+      if (st) return st;
+      *refresh = false;
+    }
+    combine(z, L.q, 1.0 / eps, c.nk_q, -1.0 / eps, one, nullptr, 0.0, one);
+    copy(c.src, c.nk_src);
+    ++c.nk_count[2];
+    PMG_CK_LAUNCH();
+    return PMG_OK;
+  }
+
+  // One inexact Newton correction: FGMRES on A x = F(q) into nk_x.
+  pmg_status krylov(double eps, bool refresh) {
+    PMG_CK(cudaMemsetAsync(c.nk_x, 0, n * sizeof(double), c.stream));
+    combine(c.nk_V, c.nk_F, 1.0, nullptr, 0.0, W, nullptr, 0.0, one);   // b = W F
+    double beta0;
+    pmg_status st = norm2(c.nk_V, &beta0);
+    if (st) return st;
+    const double target = o.eta * beta0;
+    double res = beta0;
+    int it = 0;
+    bool first = true;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+    while (it < o.max_krylov && res > target) {
+      double beta = beta0;
+      if (!first) {   // restart from r = b - A x
+        st = apply_A(c.nk_x, c.nk_w);
+        if (st) return st;
+        combine(c.nk_V, c.nk_F, 1.0, nullptr, 0.0, W, c.nk_w, -1.0, one);
+        st = norm2(c.nk_V, &beta);
+        if (st) return st;
+      }
+      first = false;
+      if (!(beta > 0.0)) break;
+      combine(c.nk_V, c.nk_V, 1.0 / beta, nullptr, 0.0, one, nullptr, 0.0, one);
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      int jl = -1;
+      for (int j = 0; j < m; ++j) {
+        double* Vj = c.nk_V + (size_t)j * n;
+        double* Zj = c.nk_Z + (size_t)j * n;
+        st = apply_M(Vj, Zj, &refresh, eps);
+        if (st) return st;
+        st = apply_A(Zj, c.nk_w);
+        if (st) return st;
+        // classical Gram-Schmidt, twice
+        launch_multi_dot(c.nk_V, n, j + 1, c.nk_w, n, c.nk_part, c.nk_dots, c.stream);
+        launch_combination(c.nk_w, c.nk_V, n, j + 1, c.nk_dots, -1.0, n, c.stream);
+        launch_multi_dot(c.nk_V, n, j + 1, c.nk_w, n, c.nk_part, c.nk_dots + m + 1, c.stream);
+        launch_combination(c.nk_w, c.nk_V, n, j + 1, c.nk_dots + m + 1, -1.0, n, c.stream);
+        launch_multi_dot(c.nk_w, n, 1, c.nk_w, n, c.nk_part, c.nk_dots + 2 * m + 2, c.stream);
+        PMG_CK_LAUNCH();
+        st = fetch(2 * m + 3);
+        if (st) return st;
+        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = c.h_nk[i] + c.h_nk[m + 1 + i];
+        const double hn = std::sqrt(std::max(c.h_nk[2 * m + 2], 0.0));
+        for (int i = 0; i < j; ++i) {
+          const double a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
+          H[(size_t)i * m + j] = cs[i] * a + sn[i] * b;
+          H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+        }
+        const double a = H[(size_t)j * m + j], r = std::hypot(a, hn);
+        cs[j] = r > 0.0 ? a / r : 1.0;
+        sn[j] = r > 0.0 ? hn / r : 0.0;
+        H[(size_t)j * m + j] = r;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        res = std::fabs(g[j + 1]);
+        ++it;
+        ++c.nk_count[1];
+        jl = j;
+        if (!(hn > 0.0) || res <= target || it >= o.max_krylov) break;
+        combine(c.nk_V + (size_t)(j + 1) * n, c.nk_w, 1.0 / hn, nullptr, 0.0, one, nullptr, 0.0, one);
+      }
+      if (jl < 0) break;
+      for (int i = jl; i >= 0; --i) {
+        double t = g[i];
+        for (int k = i + 1; k <= jl; ++k) t -= H[(size_t)i * m + k] * y[k];
+        y[i] = H[(size_t)i * m + i] != 0.0 ? t / H[(size_t)i * m + i] : 0.0;
+      }
+      for (int i = 0; i <= jl; ++i) c.h_nk[i] = y[i];
+      PMG_CK(cudaMemcpyAsync(c.nk_coef, c.h_nk, (jl + 1) * sizeof(double), cudaMemcpyHostToDevice, c.stream));
+      launch_combination(c.nk_x, c.nk_Z, n, jl + 1, c.nk_coef, 1.0, n, c.stream);
+      PMG_CK_LAUNCH();
+      PMG_CK(cudaStreamSynchronize(c.stream));   // h_nk is rewritten by the next fetch
+    }
+    return PMG_OK;
+  }
+};
+
+// Newton steps until ||F|| <= tol ||F^0||; iters = Newton steps, *vcycles
+// (may be NULL) = the preconditioner's V-cycles.  Leaves the iterate in
+// lev[0].q with F(q) in lev[0].F.
+static pmg_status nk_stage_solve(Ctx& c, int* iters, double* drop, int* n_refresh, int* vcycles) {
+  NkWork w(c, c.nk);
+  pmg_status st = nk_alloc(c, w.m);
+  if (st) return st;
+  LevelDev& L = c.lev[0];
+  const long long vc0 = c.nk_count[2];
+  auto finish = [&](int k, double nrm, double n0) {
+    if (iters) *iters = k;
+    if (drop) *drop = n0 > 0.0 ? nrm / n0 : nrm;
+    if (vcycles) *vcycles = (int)(c.nk_count[2] - vc0);
+  };
+  PMG_CK(cudaMemcpyAsync(c.nk_src, c.src, w.n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+  system_residual(c, 0, true);
+  PMG_CK_LAUNCH();
+  double nrm;
+  st = read_norm(c, &nrm);
+  if (st) return st;
+  ++c.nk_count[3];
+  w.copy(c.nk_q, L.q);
+  w.copy(c.nk_F, L.F);
+  c.F0_valid = true;
+  st = w.set_state_scales(L.q);
+  if (st) return st;
+  const double n0 = nrm;
+  for (int k = 0;; ++k) {
+    c.hist_norm.push_back(nrm);
+    c.hist_dtau.push_back(0.0);
+    if (nrm <= c.cfg.tol * n0 || n0 == 0.0) {
+      finish(k, nrm, n0);
+      return PMG_OK;
+    }
+    if (!std::isfinite(nrm)) {
+      finish(k, nrm, n0);
+      return fail(PMG_ENONFINITE, "non-finite residual norm");
+    }
+    if (k >= w.o.max_newton) {
+      finish(k, nrm, n0);
+      return fail(PMG_ENOTCONV, "stage not converged within max_newton Newton steps");
+    }
+    const bool refresh = k % w.o.pc_refresh == 0;
+    if (refresh) {
+      if (n_refresh) ++*n_refresh;
+      if (w.o.precond == PMG_NK_PC_BLOCK) {   // blocks at the iterate (lev[0].q holds it here)
+        st = set_dtau(c, w.o.dtau_pc);
+        if (st) return st;
+        refresh_level(c, 0);
+        st = check_singular(c);
+        if (st) return st;
+      }
+    }
+    st = w.krylov(w.o.pc_eps * nrm, refresh && w.o.precond == PMG_NK_PC_VCYCLE);
+    if (st) return st;
+    // backtracking on ||F||
+    double lam = 1.0, nn = 0.0;
+    for (int t = 0; t <= w.o.max_backtrack; ++t) {
+      w.combine(L.q, c.nk_q, 1.0, nullptr, 0.0, w.one, c.nk_x, lam, w.one);
+      system_residual(c, 0, true);
+      PMG_CK_LAUNCH();
+      st = read_norm(c, &nn);
+      if (st) return st;
+      ++c.nk_count[3];
+      if (std::isfinite(nn) && nn <= (1.0 - 1e-4 * lam) * nrm) break;
+      if (t < w.o.max_backtrack) lam *= 0.5;
+    }
+    w.copy(c.nk_q, L.q);
+    w.copy(c.nk_F, L.F);
+    ++c.nk_count[0];
+    nrm = nn;
+  }
+}
+
+static pmg_status stage_solve(Ctx& c, int* iters, double* drop, int* n_refresh, int* vcycles = nullptr) {
   {
     pmg_status fs = check_factorable(c, -1);
     if (fs) return fs;
   }
+  if (c.stage_solver == PMG_STAGE_NK) return nk_stage_solve(c, iters, drop, n_refresh, vcycles);
+  if (vcycles) *vcycles = -1;   // the caller counts pseudo-iterations
   if (!c.F0_valid) {
     system_residual(c, 0, true);
     PMG_CK_LAUNCH();
@@ -1345,6 +1658,38 @@ pmg_status pmg_stage_solve(pmg_ctx* h, int* iters, double* drop) {
   return stage_solve(c, iters, drop, nullptr);
 }
 
+pmg_status pmg_set_stage_solver(pmg_ctx* h, int solver, const pmg_nk_options* opts) {
+  if (!h) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  if (solver != PMG_STAGE_PTC && solver != PMG_STAGE_NK) return fail(PMG_EINVAL, "unknown stage solver");
+  const pmg_nk_options o = nk_defaults(c, opts);
+  if (o.krylov_dim > 64) return fail(PMG_EINVAL, "krylov_dim must be at most 64");
+  if (o.precond != PMG_NK_PC_BLOCK && o.precond != PMG_NK_PC_VCYCLE)
+    return fail(PMG_EINVAL, "unknown Newton-Krylov preconditioner");
+  if (!(o.eta < 1.0) || !std::isfinite(o.dtau_pc) || !std::isfinite(o.delta0) || !(o.delta0 < 1.0) ||
+      !std::isfinite(o.pc_eps))
+    return fail(PMG_EINVAL, "Newton-Krylov options out of range (eta < 1, delta0 < 1, finite dtau_pc)");
+  for (int v = 0; v < 5; ++v)
+    if (!std::isfinite(o.state_scale[v])) return fail(PMG_EINVAL, "state_scale must be finite");
+  c.stage_solver = solver;
+  c.nk = o;
+  return PMG_OK;
+}
+
+pmg_status pmg_nk_stats_read(pmg_ctx* h, pmg_nk_stats* out, int reset) {
+  if (!h) return fail(PMG_EINVAL, "null argument");
+  Ctx& c = h->c;
+  if (out) {
+    out->newton = c.nk_count[0];
+    out->krylov = c.nk_count[1];
+    out->vcycles = c.nk_count[2];
+    out->residuals = c.nk_count[3];
+  }
+  if (reset)
+    for (long long& v : c.nk_count) v = 0;
+  return PMG_OK;
+}
+
 // ------------------------------------------------------------- autotuner
 // Times the smoothing of every level the fused and tiled coarse-level kernels
 // can serve under each candidate schedule and keeps the fastest: the split
@@ -1542,10 +1887,11 @@ pmg_status pmg_esdirk_step(pmg_ctx* h, double dt, pmg_step_stats* stats) {
     c.F0_valid = false;
     int it = 0;
     double dr = 0.0;
-    st = stage_solve(c, &it, &dr, &local.n_refresh);
+    int vc = -1;
+    st = stage_solve(c, &it, &dr, &local.n_refresh, &vc);
     local.pseudo_iters[i - 1] = it;
     local.res_drop[i - 1] = dr;
-    local.n_vcycles += it;
+    local.n_vcycles += vc >= 0 ? vc : it;
     if (st) break;
     {
       ProfScope ps(c, K_FACE, 0);

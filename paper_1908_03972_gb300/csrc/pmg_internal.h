@@ -195,6 +195,23 @@ struct Ctx {
   bool split_stage = false;    // src holds sum_j a_ij R^j / omega and q^n is in qn
   std::vector<double> hist_norm, hist_dtau;   // pseudo-iteration history of the last step
   bool F0_valid = false;       // lev[0].F holds F_0(q) for the current q
+  // Newton-Krylov stage solver (api.cu nk_stage_solve; vectors of the finest size)
+  int stage_solver = PMG_STAGE_PTC;
+  pmg_nk_options nk{};
+  int nk_m = 0;                // Krylov vectors allocated for
+  double* nk_q = nullptr;      // Newton iterate
+  double* nk_F = nullptr;      // F at the iterate
+  double* nk_src = nullptr;    // the stage source (the V-cycle preconditioner changes c.src)
+  double* nk_w = nullptr;      // A z, and the restart residual
+  double* nk_t = nullptr;      // scratch
+  double* nk_x = nullptr;      // Newton correction
+  double* nk_V = nullptr;      // (m + 1) Krylov basis vectors
+  double* nk_Z = nullptr;      // m preconditioned directions
+  double* nk_part = nullptr;   // partial sums of the multi-dot kernel
+  double* nk_dots = nullptr;   // its results (3 m + 3)
+  double* nk_coef = nullptr;   // combination coefficients (m)
+  double* h_nk = nullptr;      // pinned host mirror (3 m + 3)
+  long long nk_count[4] = {0, 0, 0, 0};   // newton, krylov, vcycles, residuals
   // reductions
   double* d_partial = nullptr; // per-block partial sums
   int n_partial = 0;
@@ -295,6 +312,20 @@ void launch_prolong3(const Ctx& c, const LevelDev& Lf, const LevelDev& Lc, const
                      const double* qcb, double* qf, int add, cudaStream_t s);
 void launch_bsum_update3(const Ctx& c, int N, const double* qn, double* const* R, const double* b, int nr,
                          double dt, double* q, cudaStream_t s);
+// Vector kernels of the Newton-Krylov solver (k_krylov.cu).
+constexpr int kDotBlocks = 304;
+struct Scale5 {
+  double s[5];
+};
+// out_j = sum_i X_j[i] y[i] for j < k, X_j = X + j ld (part: kDotBlocks k doubles)
+void launch_multi_dot(const double* X, size_t ld, int k, const double* y, size_t n, double* part, double* out,
+                      cudaStream_t s);
+// y += sign sum_{j<k} coef[j] X_j (coef on the device, k <= 64)
+void launch_combination(double* y, const double* X, size_t ld, int k, const double* coef, double sign, size_t n,
+                        cudaStream_t s);
+// out = (a0 x0 + a1 x1) s0[v] + a2 x2 s2[v], v = i / plane (null inputs count as 0)
+void launch_plane_combine(double* out, const double* x0, double a0, const double* x1, double a1, const Scale5& s0,
+                          const double* x2, double a2, const Scale5& s2, size_t plane, size_t n, cudaStream_t s);
 void launch_tile_sweeps(const Ctx& c, const LevelDev& L, const double* qin, double* qout, int nsweep,
                         double inv_odt, const double* S, const double* qref, int prec, cudaStream_t s);
 size_t tile_smem_bytes(int P, int prec, int M);

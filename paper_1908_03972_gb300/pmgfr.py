@@ -21,6 +21,8 @@ PMG_EINVAL, PMG_ENOMEM, PMG_ECUDA, PMG_ESINGULAR, PMG_ENONFINITE, PMG_ENOTCONV, 
     -1, -2, -3, -4, -5, -6, -7, -8)
 PMG_PREC_FP64, PMG_PREC_FP32, PMG_PREC_BF16R = 0, 1, 2
 PMG_FLUX_FP64, PMG_FLUX_DW_SMOOTH, PMG_FLUX_DW = 0, 1, 2
+PMG_STAGE_PTC, PMG_STAGE_NK = 0, 1
+PMG_NK_PC_BLOCK, PMG_NK_PC_VCYCLE = 0, 1
 
 
 class PmgError(RuntimeError):
@@ -95,6 +97,27 @@ class pmg_tune_report(ctypes.Structure):
     ]
 
 
+class pmg_nk_options(ctypes.Structure):
+    _fields_ = [
+        ("max_newton", ctypes.c_int),
+        ("krylov_dim", ctypes.c_int),
+        ("max_krylov", ctypes.c_int),
+        ("eta", ctypes.c_double),
+        ("precond", ctypes.c_int),
+        ("dtau_pc", ctypes.c_double),
+        ("pc_refresh", ctypes.c_int),
+        ("delta0", ctypes.c_double),
+        ("state_scale", ctypes.c_double * 5),
+        ("max_backtrack", ctypes.c_int),
+        ("pc_eps", ctypes.c_double),
+    ]
+
+
+class pmg_nk_stats(ctypes.Structure):
+    _fields_ = [("newton", ctypes.c_longlong), ("krylov", ctypes.c_longlong), ("vcycles", ctypes.c_longlong),
+                ("residuals", ctypes.c_longlong)]
+
+
 _lib = None
 
 
@@ -137,6 +160,8 @@ def load():
         "pmg_dtau_min": ([vp, ctypes.POINTER(ctypes.c_double)], ci),
         "pmg_restore": ([vp, ctypes.c_char_p], ci),
         "pmg_profile_read": ([vp, pd, ctypes.POINTER(ctypes.c_longlong)], ci),
+        "pmg_set_stage_solver": ([vp, ci, ctypes.POINTER(pmg_nk_options)], ci),
+        "pmg_nk_stats_read": ([vp, ctypes.POINTER(pmg_nk_stats), ci], ci),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -337,6 +362,26 @@ def pmg_stage_history(h):
     pd = ctypes.POINTER(ctypes.c_double)
     _check(load().pmg_stage_history(h, norms.ctypes.data_as(pd), dtau.ctypes.data_as(pd), n.value, ctypes.byref(n)))
     return norms[: n.value], dtau[: n.value]
+
+
+def pmg_set_stage_solver(h, solver, *, max_newton=0, krylov_dim=0, max_krylov=0, eta=0.0,
+                         precond=PMG_NK_PC_VCYCLE, dtau_pc=0.0, pc_refresh=0, delta0=0.0, state_scale=(0.0,) * 5,
+                         max_backtrack=-1, pc_eps=0.0):
+    """PMG_STAGE_PTC, or PMG_STAGE_NK with its options (0 / negative: the defaults)."""
+    o = pmg_nk_options()
+    o.max_newton, o.krylov_dim, o.max_krylov, o.eta = max_newton, krylov_dim, max_krylov, eta
+    o.precond, o.dtau_pc, o.pc_refresh, o.delta0 = precond, dtau_pc, pc_refresh, delta0
+    for v in range(5):
+        o.state_scale[v] = state_scale[v] if v < len(state_scale) else 0.0
+    o.max_backtrack = max_backtrack
+    o.pc_eps = pc_eps
+    _check(load().pmg_set_stage_solver(h, int(solver), ctypes.byref(o)))
+
+
+def pmg_nk_stats_read(h, reset=False):
+    st = pmg_nk_stats()
+    _check(load().pmg_nk_stats_read(h, ctypes.byref(st), int(reset)))
+    return dict(newton=st.newton, krylov=st.krylov, vcycles=st.vcycles, residuals=st.residuals)
 
 
 class Solver:

@@ -84,3 +84,26 @@ def test_create_without_a_gpu_fails_instead_of_falling_back(lib):
     with pytest.raises(pmgfr.PmgError) as ei:
         pmgfr.pmg_create(_cfg())
     assert ei.value.status == pmgfr.PMG_ECUDA
+
+
+def test_nk_structs_match_the_c_compiler(tmp_path):
+    """pmg_nk_options / pmg_nk_stats: sizes and offsets from gcc on the header
+    against the binding's ctypes structures."""
+    import shutil
+    import subprocess
+    from paper_1908_03972_gb300 import pmgfr
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    fields = [f for f, _ in pmgfr.pmg_nk_options._fields_]
+    prog = tmp_path / "lay.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{os.path.join(ROOT, "include", "pmgfr.h")}"',
+             "int main(void) {", 'printf("%zu %zu\\n", sizeof(pmg_nk_options), sizeof(pmg_nk_stats));']
+    lines += [f'printf("%zu\\n", offsetof(pmg_nk_options, {f}));' for f in fields]
+    lines += ["return 0; }"]
+    prog.write_text("\n".join(lines))
+    exe = tmp_path / "lay"
+    subprocess.run(["gcc", "-std=c99", str(prog), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert int(out[0]) == ctypes.sizeof(pmgfr.pmg_nk_options)
+    assert int(out[1]) == ctypes.sizeof(pmgfr.pmg_nk_stats)
+    assert [int(x) for x in out[2:]] == [getattr(pmgfr.pmg_nk_options, f).offset for f in fields]
