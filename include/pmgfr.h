@@ -107,9 +107,13 @@ typedef struct {
                      p_gauge times the discrete metric identity.  At low Mach
                      a value near the free-stream pressure keeps the pressure
                      resolution at the level of its variations.  Curved
-                     (geom_order > 1) meshes need P >= geom_order on every
-                     level (pmg_upload_mesh returns PMG_EINVAL otherwise).  Every call still takes
-                     and returns absolute p. */
+                     (geom_order > 1) meshes need P >= geom_order on the
+                     finest level (pmg_upload_mesh returns PMG_EINVAL
+                     otherwise).  A coarser level with P < geom_order gets
+                     a constant p_gauge times its metric-identity residual
+                     back in the residual calls; the V-cycle's FAS equations
+                     do not depend on it.  Every call still takes and
+                     returns absolute p. */
   double mu;      /* constant dynamic viscosity (Section 2.1); 0: Euler.
                      mu > 0 adds the viscous fluxes with the common
                      solution of eq. com_q and the BR2 common gradient of

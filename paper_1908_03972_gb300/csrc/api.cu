@@ -98,7 +98,7 @@ static void esdirk_table(Ctx& c, int order) {
 
 static void free_level(LevelDev& L) {
   double** ptrs[] = {&L.q,     &L.q2, &L.qb, &L.S,  &L.F,  &L.Pd, &L.met,  &L.face,
-                     &L.Fcom,  &L.Dfull, &L.rs, &L.cs, &L.Gb, &L.Qj, &L.fJinv};
+                     &L.Fcom,  &L.Dfull, &L.rs, &L.cs, &L.Gb, &L.Qj, &L.fJinv, &L.Cgauge};
   for (double** p : ptrs) { if (*p) cudaFree(*p); *p = nullptr; }
   int** iptrs[] = {&L.d_toff, &L.d_tlayer, &L.d_telems, &L.d_tlnbr};
   for (int** p : iptrs) { if (*p) cudaFree(*p); *p = nullptr; }
@@ -106,9 +106,6 @@ static void free_level(LevelDev& L) {
   L.Dinv = nullptr;
 }
 
-// Multi-sweep tiles of a coarse level (k_tile.cu): build and upload them, or
-// drop them (depth 0).  Returns PMG_EINVAL when the tile does not fit (512
-// threads, 227 KB of shared memory per CTA).
 static void nk_free(Ctx& c) {
   double** ptrs[] = {&c.nk_q, &c.nk_F, &c.nk_src, &c.nk_w, &c.nk_t, &c.nk_x,
                      &c.nk_V, &c.nk_Z, &c.nk_part, &c.nk_dots, &c.nk_coef};
@@ -118,6 +115,9 @@ static void nk_free(Ctx& c) {
   c.nk_m = 0;
 }
 
+// Multi-sweep tiles of a coarse level (k_tile.cu): build and upload them, or
+// drop them (depth 0).  Returns PMG_EINVAL when the tile does not fit (512
+// threads, 227 KB of shared memory per CTA).
 static pmg_status set_level_tiles(Ctx& c, LevelDev& L, int core, int depth) {
   int** iptrs[] = {&L.d_toff, &L.d_tlayer, &L.d_telems, &L.d_tlnbr};
   for (int** p : iptrs) { if (*p) cudaFree(*p); *p = nullptr; }
@@ -275,15 +275,68 @@ void pmg_destroy(pmg_ctx* h) {
   delete h;
 }
 
+// Gauge storage on a curved mesh: on a level with P below the geometry order
+// the discrete metric identity holds only to the interpolation error, and the
+// gauge momentum flux (p - p_gauge) leaves out p_gauge times that residual.
+// Cgauge = R(uniform state, absolute pressure) - R(the same state, gauge
+// storage) is that constant, computed once: the convective parts of the two
+// evaluations are the same operations on the same numbers.  The state moves
+// with the free stream (or u = 1) so that the preconditioned flux has eps > 0;
+// far-field faces see the same state.
+static pmg_status compute_gauge_constant(Ctx& c, int l) {
+  LevelDev& L = c.lev[l];
+  if (dalloc(&L.Cgauge, L.tot)) return fail(PMG_ENOMEM, "device allocation failed for level data");
+  const size_t plane = (size_t)c.E * L.N;
+  const int T_slot = c.nv - 1;
+  double qu[5] = {c.ph.p_ref, 1.0, 0.0, 0.0, 0.0};
+  qu[T_slot] = c.ph.p_ref;   // rho = 1
+  if (c.ph.qinf[0] > 0.0 && c.ph.qinf[T_slot] > 0.0)
+    for (int v = 0; v < c.nv; ++v) qu[v] = c.ph.qinf[v];
+  std::vector<double> h(L.tot);
+  for (int v = 0; v < c.nv; ++v) std::fill(h.begin() + v * plane, h.begin() + (v + 1) * plane, qu[v]);
+  const Phys keep = c.ph;
+  const PhysW keepw = c.phw;
+  for (int v = 0; v < c.nv; ++v) c.ph.qinf[v] = qu[v];
+  // gauge form: stored p - p_gauge
+  PMG_CK(cudaMemcpy(c.d_tmp0, h.data(), L.tot * 8, cudaMemcpyHostToDevice));
+  launch_shift_pressure(plane, -keep.p_ref, c.d_tmp0, c.stream);
+  c.phw = make_physw(c.ph);
+  launch_face_flux(c, L, c.d_tmp0, c.stream);
+  launch_volume(c, L, l, c.d_tmp0, c.d_tmp1, RES_PURE, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr, c.stream);
+  // absolute form
+  PMG_CK(cudaMemcpyAsync(c.d_tmp0, h.data(), L.tot * 8, cudaMemcpyHostToDevice, c.stream));
+  c.ph.p_ref = 0.0;
+  c.phw = make_physw(c.ph);
+  launch_face_flux(c, L, c.d_tmp0, c.stream);
+  launch_volume(c, L, l, c.d_tmp0, L.Cgauge, RES_PURE, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr, c.stream);
+  Scale5 one;
+  for (double& x : one.s) x = 1.0;
+  launch_plane_combine(L.Cgauge, L.Cgauge, 1.0, c.d_tmp1, -1.0, one, nullptr, 0.0, one, plane, L.tot, c.stream);
+  const cudaError_t le = cudaGetLastError();
+  const cudaError_t se = cudaStreamSynchronize(c.stream);
+  c.ph = keep;
+  c.phw = keepw;
+  if (le != cudaSuccess || se != cudaSuccess)
+    return fail(PMG_ECUDA, std::string("gauge constant: ") + cudaGetErrorString(le != cudaSuccess ? le : se));
+  return PMG_OK;
+}
+
+// R += Cgauge on the levels that have one (the residual calls' output).
+static void add_gauge_constant(Ctx& c, int l, double* R) {
+  LevelDev& L = c.lev[l];
+  if (!L.Cgauge) return;
+  Scale5 one;
+  for (double& x : one.s) x = 1.0;
+  launch_plane_combine(R, R, 1.0, L.Cgauge, 1.0, one, nullptr, 0.0, one, (size_t)c.E * L.N, L.tot, c.stream);
+}
+
 pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
   if (!h || !m || !m->nodes || !m->nbr) return fail(PMG_EINVAL, "null argument");
   Ctx& c = h->c;
   if (c.mesh_ready) return fail(PMG_EINVAL, "mesh already uploaded");
   if (m->n_elem < 1 || m->geom_order < 1 || m->geom_order > 4) return fail(PMG_EINVAL, "bad mesh sizes");
-  if (c.ph.p_ref != 0.0)
-    for (int l = 0; l < c.cfg.n_levels; ++l)
-      if (c.cfg.P[l] < m->geom_order && m->geom_order > 1)
-        return fail(PMG_EINVAL, "p_gauge != 0 needs P >= geometry order on every level (the metric identity)");
+  if (c.ph.p_ref != 0.0 && c.cfg.P[0] < m->geom_order && m->geom_order > 1)
+    return fail(PMG_EINVAL, "p_gauge != 0 needs P >= geometry order on the finest level (the metric identity)");
   const int T_slot = c.dim == 3 ? 4 : 3;   // temperature in q_inf
   for (int i = 0; i < m->n_elem * c.nfc; ++i) {
     if (m->nbr[i * 3] != -1) continue;
@@ -434,6 +487,12 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
     PMG_CK(prepare_residual_kernels(c));
     PMG_CK(prepare_volume_dw_kernels(c));
   }
+  if (c.ph.p_ref != 0.0 && c.mesh.Ng > 1)
+    for (int l = 1; l < c.cfg.n_levels; ++l)
+      if (c.cfg.P[l] < c.mesh.Ng) {
+        pmg_status gs = compute_gauge_constant(c, l);
+        if (gs) return gs;
+      }
   c.mesh_ready = true;
   return PMG_OK;
 }
@@ -1391,6 +1450,7 @@ pmg_status pmg_residual(pmg_ctx* h, int level, const double* q, double* R, int o
   double* Rd = on_device ? R : c.d_tmp1;
   launch_face_flux(c, L, qd, c.stream);
   launch_volume(c, L, level, qd, Rd, RES_PURE, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr, c.stream);
+  add_gauge_constant(c, level, Rd);
   PMG_CK_LAUNCH();
   if (!on_device) PMG_CK(copy_out(c, R, Rd, L.tot, 0));
   else PMG_CK(cudaStreamSynchronize(c.stream));
@@ -1450,6 +1510,7 @@ pmg_status pmg_residual_static(pmg_ctx* h, int level, const double* q, double* R
   launch_shift_pressure(n_state / c.nv, -c.ph.p_ref, qs, c.stream);
   launch_face_flux(c, L, qs, c.stream);
   launch_volume(c, L, level, qs, R, RES_PURE, 0.0, nullptr, nullptr, nullptr, nullptr, nullptr, c.stream);
+  add_gauge_constant(c, level, R);
   PMG_CK_LAUNCH();
   PMG_CK(cudaStreamSynchronize(c.stream));
   return PMG_OK;
@@ -1483,6 +1544,7 @@ pmg_status pmg_stage_residual(pmg_ctx* h, int level, const double* q, double* F,
   launch_face_flux(c, L, qd, c.stream);
   launch_volume(c, L, level, qd, Fd, RES_STAGEF, 1.0 / c.omega_dt, level == 0 ? c.src : nullptr, nullptr, nullptr,
                 nullptr, nullptr, c.stream);
+  add_gauge_constant(c, level, Fd);
   PMG_CK_LAUNCH();
   if (!on_device) PMG_CK(copy_out(c, F, Fd, L.tot, 0));
   else PMG_CK(cudaStreamSynchronize(c.stream));

@@ -112,6 +112,11 @@ struct LevelDev {
   double* qb = nullptr;        // state at entry of the level in the V-cycle
   double* S = nullptr;         // FAS forcing
   double* F = nullptr;         // level system residual F_l(q) - S_l
+  double* Cgauge = nullptr;    // gauge storage on a level with P < geometry order: p_gauge times the
+                               // level's discrete metric-identity residual (momentum rows), the part of
+                               // R that the gauge momentum flux leaves out; a constant, so the FAS
+                               // coarse-level equations F_c(q) - F_c(q^b) - P d do not see it, and the
+                               // residual calls add it back
   double* Pd = nullptr;        // restricted defect (coarse levels)
   double* met = nullptr;       // 5 * E * N (2D), 10 * E * N (3D)
   double* face = nullptr;      // E * 4 * n1 * 3 (2D), E * 6 * NF * 4 (3D)
