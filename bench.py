@@ -565,6 +565,125 @@ def run_ours(args, wl, world, rank, local):
     return 0
 
 
+
+# ------------------------------------------------------- hierarchy study
+HIERARCHIES = [([4], [10]), ([4, 3], [5, 10]), ([4, 2], [5, 10]), ([4, 1], [5, 10]), ([4, 3, 2], [5, 10, 20]),
+               ([4, 3, 1], [5, 10, 20]), ([4, 2, 1], [5, 10, 20])]
+
+
+def run_hierarchy_study(args):
+    """The P-hierarchies of the paper's P = 4 study (Section 4.2: P{4-3},
+    P{4-2}, P{4-1}, P{4-3-2}, P{4-3-1}, P{4-2-1}, and the single level) on
+    the cylinder workload at 1/16 of its elements (16 x 64 Q2 quads, Re = 100,
+    Ma = 0.001, no-slip wall), the system of the first implicit ESDIRK3 stage
+    from the free stream with 1e-3 noise in v, with gauge storage and BF16
+    blocks.  Each hierarchy solves it to a 1e-8 drop twice: by the paper's
+    pseudo-transient continuation (dtau 0.01 -> 1 by SER, the smoother rebuilt
+    every 10 iterations throughout; dtau_max = 10 diverges, see the
+    findings) and by Newton-Krylov with one V-cycle of the hierarchy as the
+    preconditioner.  One JSON line per hierarchy: V-cycles and GPU seconds."""
+    import torch
+    from paper_1908_03972_gb300 import build, pmgfr, workloads as W
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    build.build()
+    pmgfr.load()
+    MA, MU = 0.001, 0.01
+    T = W.freestream_T(MA, speed=1.0)
+    nodes, nbr = W.cylinder_omesh(16, 64, 0.5, 50.0, Ng=2)
+    stream = torch.cuda.current_stream()
+    for levels, smooth in HIERARCHIES:
+        out = {"study": "hierarchy", "workload": "cylinder 16x64 Q2 quads (1/16 of 64x256), Re 100, Ma 0.001, "
+                                                 "first implicit ESDIRK3 stage (dt 0.05) from the free stream",
+               "hierarchy": "P{" + "-".join(map(str, levels)) + "}", "smoothing": "I{" + "-".join(map(str, smooth)) + "}"}
+        for solver in ("ptc", "nk"):
+            s = pmgfr.Solver(nodes, nbr, levels, smooth, stream=stream.cuda_stream, block_prec=pmgfr.PMG_PREC_BF16R,
+                             Ma_inf=MA, mu=MU, cutoff=1, kappa=1.0, q_inf=(T, 1.0, 0.0, T), p_gauge=T,
+                             res_scale=W.freestream_scales(MA, speed=1.0), tol=1e-8, dtau_init=0.01, dtau_max=1.0,
+                             refresh_every=10, refresh_always=1, max_pseudo=20000)
+            try:
+                if solver == "nk":
+                    pmgfr.pmg_set_stage_solver(s.h, pmgfr.PMG_STAGE_NK, precond=pmgfr.PMG_NK_PC_VCYCLE,
+                                               krylov_dim=30, max_krylov=60, dtau_pc=1.0, max_newton=40,
+                                               state_scale=(T, 1.0, 1.0, T))
+                q = W.freestream_noise_state(s.coords(), MA)
+                rho = q[0] / q[3]
+                qc = np.stack([rho, rho * q[1], rho * q[2], rho * (q[3] / 0.4 + 0.5 * (q[1] ** 2 + q[2] ** 2))])
+                A = 1767732205903.0 / 4055673282236.0
+                odt = A * 0.05
+                s.set_stage((qc + 0.05 * A * s.residual(q)) / odt, odt)
+                s.set_state(q)
+                pmgfr.pmg_nk_stats_read(s.h, reset=True)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                try:
+                    it, drop = pmgfr.pmg_stage_solve(s.h)
+                    status = "converged"
+                except pmgfr.PmgError as ex:
+                    it, drop, status = -1, float("nan"), str(ex)
+                torch.cuda.synchronize()
+                sec = time.perf_counter() - t0
+                rec = {"status": status, "seconds": sec, "drop": drop}
+                if solver == "nk":
+                    st = pmgfr.pmg_nk_stats_read(s.h)
+                    rec.update(newton=it, vcycles=st["vcycles"], residuals=st["residuals"])
+                else:
+                    rec.update(vcycles=it)
+                out[solver] = rec
+            finally:
+                s.close()
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_cylinder_study(args):
+    """The cylinder workload (Re = 100, Ma = 0.001, no-slip wall, P{4-2-1},
+    I{5-10-20}, ESDIRK3 dt = 0.05, from the free stream with 1e-3 noise in v,
+    gauge storage) with Newton-Krylov stages and one V-cycle as the
+    preconditioner (its pseudo-transient solve diverges, see the findings),
+    BF16 against FP64 blocks: consecutive steps of the mesh at 1/16 of its
+    elements (16 x 64) and at full size (64 x 256).  One JSON line per
+    (mesh, blocks): seconds, Newton steps, V-cycles and status of each step."""
+    import torch
+    from paper_1908_03972_gb300 import build, pmgfr, workloads as W
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    build.build()
+    pmgfr.load()
+    MA, MU = 0.001, 0.01
+    T = W.freestream_T(MA, speed=1.0)
+    stream = torch.cuda.current_stream()
+    for (nr, nt, nsteps) in ((16, 64, 3), (64, 256, 2)):
+        nodes, nbr = W.cylinder_omesh(nr, nt, 0.5, 50.0, Ng=2)
+        for prec, name in ((pmgfr.PMG_PREC_BF16R, "bf16"), (pmgfr.PMG_PREC_FP64, "fp64")):
+            s = pmgfr.Solver(nodes, nbr, [4, 2, 1], [5, 10, 20], stream=stream.cuda_stream, block_prec=prec,
+                             Ma_inf=MA, mu=MU, cutoff=1, kappa=1.0, q_inf=(T, 1.0, 0.0, T), p_gauge=T,
+                             res_scale=W.freestream_scales(MA, speed=1.0), tol=1e-8, dtau_max=10.0)
+            steps = []
+            try:
+                pmgfr.pmg_set_stage_solver(s.h, pmgfr.PMG_STAGE_NK, precond=pmgfr.PMG_NK_PC_VCYCLE, krylov_dim=50,
+                                           max_krylov=200, dtau_pc=0.1, max_newton=60, state_scale=(T, 1.0, 1.0, T))
+                s.set_state(W.freestream_noise_state(s.coords(), MA))
+                for k in range(nsteps):
+                    pmgfr.pmg_nk_stats_read(s.h, reset=True)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    status, st = pmgfr.pmg_esdirk_step(s.h, 0.05, raise_on_error=False)
+                    torch.cuda.synchronize()
+                    sec = time.perf_counter() - t0
+                    ks = pmgfr.pmg_nk_stats_read(s.h, reset=True)
+                    steps.append({"seconds": sec, "status": "converged" if status == 0 else pmgfr.pmg_last_error(),
+                                  "newton": list(st.pseudo_iters[:3]), "drops": list(st.res_drop[:3]),
+                                  "vcycles": ks["vcycles"], "residuals": ks["residuals"]})
+                    if status:
+                        break
+            finally:
+                s.close()
+            print(json.dumps({"study": "cylinder", "mesh": f"{nr}x{nt}", "elements": nr * nt, "blocks": name,
+                              "stage_solver": "Newton-Krylov, FGMRES(50), one V-cycle preconditioner, dtau_pc 0.1",
+                              "steps": steps}), flush=True)
+    return 0
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -584,7 +703,14 @@ def main():
                     help="profiling helper: run N V-cycles of the first stage and exit (no bench line)")
     ap.add_argument("--ncu-blocks", default="fp32", choices=["fp32", "bf16"],
                     help="block precision of the --ncu-window run")
+    ap.add_argument("--study", default="", choices=["", "hierarchy", "cylinder"],
+                    help="hierarchy: the P-hierarchy study on the reduced cylinder; cylinder: Newton-Krylov steps of "
+                         "the cylinder workload (JSON lines, no bench line)")
     args = ap.parse_args()
+    if args.study == "hierarchy":
+        return run_hierarchy_study(args)
+    if args.study == "cylinder":
+        return run_cylinder_study(args)
     world, rank, local = dist_setup()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
