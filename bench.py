@@ -357,12 +357,21 @@ def run_ours(args, wl, world, rank, local):
         qc = np.stack([rho, rho * q0[1], rho * q0[2], rho * (q0[3] / 0.4 + 0.5 * (q0[1] ** 2 + q0[2] ** 2))])
         s.set_stage((qc + wl["dt"] * A * R) / odt, odt)
         s.set_state(q0)
-        # one smoother rebuild, then plain V-cycles (a timed step has 6 rebuilds in 1930 V-cycles)
-        norms = [pmgfr.pmg_vcycle(s.h, 0.01 if k == 0 else 1.0, k == 0) for k in range(args.ncu_window)]
-        torch.cuda.synchronize(device)
-        if rank == 0:
-            print(json.dumps({"ncu_window_vcycles": args.ncu_window, "blocks": args.ncu_blocks,
-                              "first_norm": norms[0], "last_norm": norms[-1]}))
+        if args.ncu_solver == "nk":
+            # one Newton-Krylov solve of the same stage system
+            pmgfr.pmg_set_stage_solver(s.h, pmgfr.PMG_STAGE_NK, **NK_OPTS)
+            it, drop = pmgfr.pmg_stage_solve(s.h)
+            torch.cuda.synchronize(device)
+            if rank == 0:
+                print(json.dumps({"ncu_window": "Newton-Krylov stage", "newton": it, "drop": drop,
+                                  **pmgfr.pmg_nk_stats_read(s.h)}))
+        else:
+            # one smoother rebuild, then plain V-cycles (a timed step has 6 rebuilds in 1930 V-cycles)
+            norms = [pmgfr.pmg_vcycle(s.h, 0.01 if k == 0 else 1.0, k == 0) for k in range(args.ncu_window)]
+            torch.cuda.synchronize(device)
+            if rank == 0:
+                print(json.dumps({"ncu_window_vcycles": args.ncu_window, "blocks": args.ncu_blocks,
+                                  "first_norm": norms[0], "last_norm": norms[-1]}))
         if s is not solver:
             s.close()
         solver.close()
@@ -703,6 +712,8 @@ def main():
                     help="profiling helper: run N V-cycles of the first stage and exit (no bench line)")
     ap.add_argument("--ncu-blocks", default="fp32", choices=["fp32", "bf16"],
                     help="block precision of the --ncu-window run")
+    ap.add_argument("--ncu-solver", default="ptc", choices=["ptc", "nk"],
+                    help="nk: the --ncu-window run is one Newton-Krylov solve of the stage instead of N V-cycles")
     ap.add_argument("--study", default="", choices=["", "hierarchy", "cylinder"],
                     help="hierarchy: the P-hierarchy study on the reduced cylinder; cylinder: Newton-Krylov steps of "
                          "the cylinder workload (JSON lines, no bench line)")
