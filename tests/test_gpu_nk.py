@@ -155,3 +155,49 @@ def test_stage_solver_options_are_validated():
             pmgfr.pmg_set_stage_solver(gpu.h, 5)
     finally:
         gpu.close()
+
+
+@pytest.mark.parametrize("gauge", [False, True])
+def test_one_newton_step_on_hexahedra_matches_oracle(gauge):
+    """The same fixed-count Newton step on the cubed-sphere shell (2 x 2 x 6
+    elements per panel, Q2 hexahedra, slip wall, Ma = 0.001, P{2-1-0}) from
+    the free stream with noise in v: five variables, the hexahedral residual
+    and V-cycle as the preconditioner (measured differences 2e-9 with one
+    Krylov step, 2e-7 with two)."""
+    from paper_1908_03972_gb300 import pmgfr
+    ma = 0.001
+    T = W.freestream_T(ma, speed=1.0)
+    nodes, nbr = W.cubed_sphere_shell(2, 6, 0.5, 20.0, Ng=2)
+    kw = dict(Ma_inf=ma, cutoff=1, kappa=1.0)
+    orc = O.Oracle3(nodes, nbr, 2, [2, 1, 0], [5, 10, 20], q_inf=(T, 1.0, 0.0, 0.0, T),
+                    res_scale=W.freestream_scales3(ma, speed=1.0), **kw)
+    gpu = pmgfr.Solver(nodes, nbr, [2, 1, 0], [5, 10, 20], block_prec=0, dim=3, q_inf3=(T, 1.0, 0.0, 0.0, T),
+                       res_scale3=W.freestream_scales3(ma, speed=1.0), p_gauge=T if gauge else 0.0, **kw)
+    try:
+        E, N, _ = orc.coords().shape
+        q = W.uniform_state3(E, N, T, 1.0, 0.0, 0.0, T)
+        q[2] += 1e-3 * np.random.default_rng(7).standard_normal((E, N))
+        A, _, _ = O.esdirk3()
+        odt = A[1, 1] * 0.1
+        rho = q[0] / q[4]
+        qc = np.stack([rho, rho * q[1], rho * q[2], rho * q[3],
+                       rho * (q[4] / 0.4 + 0.5 * (q[1] ** 2 + q[2] ** 2 + q[3] ** 2))])
+        src = qc / odt + orc.residual(q)
+        orc.set_stage(src, odt)
+        gpu.set_stage(src, odt)
+        sc = (T, 1.0, 1.0, 1.0, T)
+        k = 2
+        pmgfr.pmg_set_stage_solver(gpu.h, pmgfr.PMG_STAGE_NK, max_newton=1, krylov_dim=k, max_krylov=k, eta=1e-30,
+                                   dtau_pc=1.0, delta0=1e-4, state_scale=sc, max_backtrack=0)
+        gpu.set_state(q)
+        with pytest.raises(pmgfr.PmgError):
+            pmgfr.pmg_stage_solve(gpu.h)
+        dg = gpu.get_state() - q
+        out = nk.nk_stage_solve(orc, q, src, odt, 1.0 / np.array(W.freestream_scales3(ma, speed=1.0)), np.array(sc),
+                                precond="vcycle", dtau_pc=1.0, max_newton=1, m=k, max_krylov=k, eta=1e-30,
+                                max_backtrack=0, delta0=1e-4)
+        do = out["q"] - q
+        for v in range(5):
+            assert np.abs(dg[v] - do[v]).max() <= 1e-6 * np.abs(do[v]).max(), v
+    finally:
+        gpu.close()
