@@ -338,8 +338,9 @@ pmg_status pmg_esdirk_step(pmg_ctx* ctx, double dt, pmg_step_stats* stats);
  *   stage): solve A delta = F(q), A = -dF/dq, to the relative tolerance eta
  *   by restarted FGMRES(krylov_dim) with right preconditioning, in the space
  *   where each equation is divided by its res_scale (the stage norm); then
- *   q += lam delta, lam halved (at most max_backtrack times, the last trial
- *   kept) until ||F|| falls by the factor (1 - 1e-4 lam).  The stage ends
+ *   q += lam delta, lam starting at min(1, max_update / (the largest relative
+ *   change of p or T)) and halved (at most max_backtrack times, the last
+ *   trial kept) until ||F|| falls by the factor (1 - 1e-4 lam).  The stage ends
  *   when ||F|| <= tol ||F^0|| (PMG_OK), after max_newton steps (PMG_ENOTCONV)
  *   or on a non-finite norm (PMG_ENONFINITE).
  *   A z = -(F(q + h z) - F(q)) / h, h = delta0 / rms(z_v / state_scale_v),
@@ -369,6 +370,10 @@ typedef struct {
                               takes the RMS of the variable over the stage's first
                               iterate (plus |p_gauge| for the pressure) */
   int max_backtrack;       /* step halvings of the line search (< 0: 6) */
+  double max_update;       /* the line search starts from lam = min(1, max_update / r), r
+                              the largest relative change |dp|/p, |dT|/T of any point
+                              under the full correction (<= 0: 0.2): keeps p and T
+                              positive far from the solution */
   double pc_eps;           /* V-cycle preconditioner: eps = pc_eps ||F(q)|| (<= 0: 0.1;
                               with 1 the V-cycle sees the whole Newton defect and
                               can leave its linear range) */

@@ -17,8 +17,10 @@ preconditioner as future work.  This module writes that variant out:
   (F as the oracle's stage_F; the element-Jacobi smoother of eq.
   smoothing_element_jacobi updates q += D^-1 F, so D approximates
   A = -dF/dq): solve A delta = F(q) inexactly, then q <- q + lam delta with
-  lam halved until ||F||_W falls by the factor (1 - 1e-4 lam) (at most
-  max_backtrack halvings; the last trial is taken regardless).
+  lam starting at min(1, max_update / r), r the largest relative change
+  |dp|/p, |dT|/T of any point under the full step, and halved until ||F||_W
+  falls by the factor (1 - 1e-4 lam) (at most max_backtrack halvings; the
+  last trial is taken regardless).
 - ||.||_W: each equation divided by its residual scale (the stage norm of the
   pseudo-transient solver).
 - Krylov: restarted FGMRES(m), right-preconditioned (Saad, SIAM J. Sci.
@@ -94,7 +96,7 @@ def fgmres(apply_A, apply_M, b, m, max_it, rtol):
 
 def nk_stage_solve(orc, q, src, odt, W, s, *, tol=1e-8, max_newton=30, m=20, max_krylov=40, eta=1e-2,
                    precond="vcycle", dtau_pc=10.0, pc_refresh=1, delta0=1e-7, max_backtrack=6, norm0=None,
-                   pc_eps=0.1):
+                   pc_eps=0.1, max_update=0.2):
     """Newton-Krylov solve of the stage system with source src and omega dt =
     odt on the oracle `orc`, from q.  W: 1 / residual scale per equation; s:
     state scale per variable.  Stops when ||F||_W <= tol * ||F(q_start)||_W
@@ -156,7 +158,9 @@ def nk_stage_solve(orc, q, src, odt, W, s, *, tol=1e-8, max_newton=30, m=20, max
         stats["krylov"] += its
         stats["newton"] += 1
         delta = delta.reshape(shape)
-        lam = 1.0
+        # the largest relative change of p (absolute) and T under the full step
+        rel = max(float(np.max(np.abs(delta[0]) / np.abs(q[0]))), float(np.max(np.abs(delta[-1]) / np.abs(q[-1]))))
+        lam = max_update / rel if rel > max_update else 1.0
         for t in range(max_backtrack + 1):
             qn = q + lam * delta
             Fn = orc.stage_F(qn)

@@ -944,6 +944,7 @@ static pmg_nk_options nk_defaults(const Ctx& c, const pmg_nk_options* o) {
   if (!(r.delta0 > 0.0)) r.delta0 = 1e-7;
   if (r.max_backtrack < 0) r.max_backtrack = 6;
   if (!(r.pc_eps > 0.0)) r.pc_eps = 0.1;
+  if (!(r.max_update > 0.0)) r.max_update = 0.2;
   return r;
 }
 
@@ -1203,8 +1204,12 @@ static pmg_status nk_stage_solve(Ctx& c, int* iters, double* drop, int* n_refres
     }
     st = w.krylov(w.o.pc_eps * nrm, refresh && w.o.precond == PMG_NK_PC_VCYCLE);
     if (st) return st;
-    // backtracking on ||F||
-    double lam = 1.0, nn = 0.0;
+    // backtracking on ||F||, from a step that changes p and T by at most max_update
+    launch_rel_change(c.nk_q, c.nk_x, w.plane, c.nv - 1, c.ph.p_ref, c.nk_part, c.nk_dots, c.stream);
+    PMG_CK_LAUNCH();
+    st = w.fetch(1);
+    if (st) return st;
+    double lam = c.h_nk[0] > w.o.max_update ? w.o.max_update / c.h_nk[0] : 1.0, nn = 0.0;
     for (int t = 0; t <= w.o.max_backtrack; ++t) {
       w.combine(L.q, c.nk_q, 1.0, nullptr, 0.0, w.one, c.nk_x, lam, w.one);
       system_residual(c, 0, true);
@@ -1729,7 +1734,7 @@ pmg_status pmg_set_stage_solver(pmg_ctx* h, int solver, const pmg_nk_options* op
   if (o.precond != PMG_NK_PC_BLOCK && o.precond != PMG_NK_PC_VCYCLE)
     return fail(PMG_EINVAL, "unknown Newton-Krylov preconditioner");
   if (!(o.eta < 1.0) || !std::isfinite(o.dtau_pc) || !std::isfinite(o.delta0) || !(o.delta0 < 1.0) ||
-      !std::isfinite(o.pc_eps))
+      !std::isfinite(o.pc_eps) || !std::isfinite(o.max_update))
     return fail(PMG_EINVAL, "Newton-Krylov options out of range (eta < 1, delta0 < 1, finite dtau_pc)");
   for (int v = 0; v < 5; ++v)
     if (!std::isfinite(o.state_scale[v])) return fail(PMG_EINVAL, "state_scale must be finite");

@@ -99,4 +99,52 @@ void launch_plane_combine(double* out, const double* x0, double a0, const double
   plane_combine_kernel<<<blocks, kKrylovThreads, 0, s>>>(out, x0, a0, x1, a1, s0, x2, a2, s2, plane, n);
 }
 
+// Largest relative change |dx| / |x (+ p_ref for the pressure)| over the
+// pressure plane (v = 0) and the temperature plane (v = tslot); a non-finite
+// ratio counts as 1e300.  One partial maximum per block, then one block.
+__device__ __forceinline__ double block_max(double m, double* sm) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = 0.0;
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  }
+  return m;
+}
+
+__global__ void __launch_bounds__(kKrylovThreads) rel_change_partial_kernel(const double* __restrict__ x,
+                                                                           const double* __restrict__ dx,
+                                                                           size_t plane, int tslot, double p_ref,
+                                                                           double* __restrict__ part) {
+  __shared__ double sm[kKrylovThreads / 32];
+  double m = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < 2 * plane; i += (size_t)gridDim.x * blockDim.x) {
+    const bool pres = i < plane;
+    const size_t j = pres ? i : (size_t)tslot * plane + (i - plane);
+    const double r = fabs(dx[j]) / fabs(pres ? x[j] + p_ref : x[j]);
+    m = r <= 1e300 ? fmax(m, r) : 1e300;
+  }
+  m = block_max(m, sm);
+  if (threadIdx.x == 0) part[blockIdx.x] = m;
+}
+
+__global__ void __launch_bounds__(kKrylovThreads) max_partials_kernel(const double* __restrict__ part, int nb,
+                                                                     double* __restrict__ out) {
+  __shared__ double sm[kKrylovThreads / 32];
+  double m = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) m = fmax(m, part[i]);
+  m = block_max(m, sm);
+  if (threadIdx.x == 0) out[0] = m;
+}
+
+void launch_rel_change(const double* x, const double* dx, size_t plane, int tslot, double p_ref, double* part,
+                       double* out, cudaStream_t s) {
+  rel_change_partial_kernel<<<kDotBlocks, kKrylovThreads, 0, s>>>(x, dx, plane, tslot, p_ref, part);
+  max_partials_kernel<<<1, kKrylovThreads, 0, s>>>(part, kDotBlocks, out);
+}
+
 }  // namespace pmg

@@ -109,6 +109,7 @@ class pmg_nk_options(ctypes.Structure):
         ("delta0", ctypes.c_double),
         ("state_scale", ctypes.c_double * 5),
         ("max_backtrack", ctypes.c_int),
+        ("max_update", ctypes.c_double),
         ("pc_eps", ctypes.c_double),
     ]
 
@@ -366,7 +367,7 @@ def pmg_stage_history(h):
 
 def pmg_set_stage_solver(h, solver, *, max_newton=0, krylov_dim=0, max_krylov=0, eta=0.0,
                          precond=PMG_NK_PC_VCYCLE, dtau_pc=0.0, pc_refresh=0, delta0=0.0, state_scale=(0.0,) * 5,
-                         max_backtrack=-1, pc_eps=0.0):
+                         max_backtrack=-1, max_update=0.0, pc_eps=0.0):
     """PMG_STAGE_PTC, or PMG_STAGE_NK with its options (0 / negative: the defaults)."""
     o = pmg_nk_options()
     o.max_newton, o.krylov_dim, o.max_krylov, o.eta = max_newton, krylov_dim, max_krylov, eta
@@ -374,6 +375,7 @@ def pmg_set_stage_solver(h, solver, *, max_newton=0, krylov_dim=0, max_krylov=0,
     for v in range(5):
         o.state_scale[v] = state_scale[v] if v < len(state_scale) else 0.0
     o.max_backtrack = max_backtrack
+    o.max_update = max_update
     o.pc_eps = pc_eps
     _check(load().pmg_set_stage_solver(h, int(solver), ctypes.byref(o)))
 
