@@ -2,19 +2,24 @@
  * pmgfr.h -- C interface of the GB300 implicit P-multigrid flux
  * reconstruction library (libpmgfr.so).
  *
- * The library solves the 2D Euler equations with Weiss-Smith/Turkel local
- * preconditioning, discretised by FR/CPR (Gauss-Legendre solution points,
- * DG/Radau correction functions) and advanced by ESDIRK2, 3 or 4 with dual time
- * stepping.  Each implicit stage is solved by pseudo-transient continuation
- * whose pseudo-iteration is one FAS V-cycle over polynomial levels with an
- * element-Jacobi smoother (Wang & Yu, arXiv 1908.03972, Sections 2-3).
+ * The library solves the compressible Euler and Navier-Stokes equations (2D
+ * quadrilaterals; inviscid hexahedra with pmg_config.dim = 3) with
+ * Weiss-Smith/Turkel local preconditioning, discretised by FR/CPR
+ * (Gauss-Legendre solution points, DG/Radau correction functions) and advanced
+ * by ESDIRK2, 3 or 4 with dual time stepping.  Each implicit stage is solved by
+ * pseudo-transient continuation whose pseudo-iteration is one FAS V-cycle over
+ * polynomial levels with an element-Jacobi smoother (Wang & Yu, arXiv
+ * 1908.03972, Sections 2-3), or, chosen with pmg_set_stage_solver, by
+ * Newton-Krylov with that V-cycle as the preconditioner.
  *
  * Conventions shared by every call
- *  - Working variables are primitive q_p = (p, u, v, T) with R = 1.
+ *  - Working variables are primitive q_p = (p, u, v, T) with R = 1
+ *    ((p, u, v, w, T) on hexahedra).
  *  - A state array of level l is FP64, variable-major ("SoA"):
  *      q[(v * E + e) * N + pt],  v in 0..3, N = (P_l + 1)^2,
  *    and solution point (i, j) of an element has pt = j * (P_l + 1) + i with
- *    i along the first reference direction xi.
+ *    i along the first reference direction xi (hexahedra: v in 0..4,
+ *    N = (P_l + 1)^3, pt = (k * (P_l + 1) + j) * (P_l + 1) + i).
  *  - Pointers flagged by on_device = 1 are caller-owned device buffers on the
  *    context's device; on_device = 0 means caller-owned host memory.  The
  *    library copies what it needs and never keeps caller pointers.
