@@ -651,7 +651,7 @@ def run_cylinder_study(args):
     I{5-10-20}, ESDIRK3 dt = 0.05, from the free stream with 1e-3 noise in v,
     gauge storage) with Newton-Krylov stages and one V-cycle as the
     preconditioner (its pseudo-transient solve diverges, see the findings),
-    BF16 against FP64 blocks: consecutive steps of the mesh at 1/16 of its
+    BF16, FP32 and FP64 blocks: consecutive steps of the mesh at 1/16 of its
     elements (16 x 64) and at full size (64 x 256).  One JSON line per
     (mesh, blocks): seconds, Newton steps, V-cycles and status of each step."""
     import torch
@@ -665,7 +665,8 @@ def run_cylinder_study(args):
     stream = torch.cuda.current_stream()
     for (nr, nt, nsteps) in ((16, 64, 3), (64, 256, 2)):
         nodes, nbr = W.cylinder_omesh(nr, nt, 0.5, 50.0, Ng=2)
-        for prec, name in ((pmgfr.PMG_PREC_BF16R, "bf16"), (pmgfr.PMG_PREC_FP64, "fp64")):
+        for prec, name in ((pmgfr.PMG_PREC_BF16R, "bf16"), (pmgfr.PMG_PREC_FP32, "fp32"),
+                           (pmgfr.PMG_PREC_FP64, "fp64")):
             s = pmgfr.Solver(nodes, nbr, [4, 2, 1], [5, 10, 20], stream=stream.cuda_stream, block_prec=prec,
                              Ma_inf=MA, mu=MU, cutoff=1, kappa=1.0, q_inf=(T, 1.0, 0.0, T), p_gauge=T,
                              res_scale=W.freestream_scales(MA, speed=1.0), tol=1e-8, dtau_max=10.0)
