@@ -1176,6 +1176,15 @@ static pmg_status nk_stage_solve(Ctx& c, int* iters, double* drop, int* n_refres
   st = w.set_state_scales(L.q);
   if (st) return st;
   const double n0 = nrm;
+  // on an error after this point: the stage source and the last accepted
+  // iterate go back where the caller expects them
+  auto recover = [&](pmg_status err) {
+    cudaMemcpyAsync(c.src, c.nk_src, w.n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream);
+    cudaMemcpyAsync(L.q, c.nk_q, w.n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream);
+    cudaStreamSynchronize(c.stream);
+    c.F0_valid = false;
+    return err;
+  };
   for (int k = 0;; ++k) {
     c.hist_norm.push_back(nrm);
     c.hist_dtau.push_back(0.0);
@@ -1196,26 +1205,26 @@ static pmg_status nk_stage_solve(Ctx& c, int* iters, double* drop, int* n_refres
       if (n_refresh) ++*n_refresh;
       if (w.o.precond == PMG_NK_PC_BLOCK) {   // blocks at the iterate (lev[0].q holds it here)
         st = set_dtau(c, w.o.dtau_pc);
-        if (st) return st;
+        if (st) return recover(st);
         refresh_level(c, 0);
         st = check_singular(c);
-        if (st) return st;
+        if (st) return recover(st);
       }
     }
     st = w.krylov(w.o.pc_eps * nrm, refresh && w.o.precond == PMG_NK_PC_VCYCLE);
-    if (st) return st;
+    if (st) return recover(st);
     // backtracking on ||F||, from a step that changes p and T by at most max_update
     launch_rel_change(c.nk_q, c.nk_x, w.plane, c.nv - 1, c.ph.p_ref, c.nk_part, c.nk_dots, c.stream);
     PMG_CK_LAUNCH();
     st = w.fetch(1);
-    if (st) return st;
+    if (st) return recover(st);
     double lam = c.h_nk[0] > w.o.max_update ? w.o.max_update / c.h_nk[0] : 1.0, nn = 0.0;
     for (int t = 0; t <= w.o.max_backtrack; ++t) {
       w.combine(L.q, c.nk_q, 1.0, nullptr, 0.0, w.one, c.nk_x, lam, w.one);
       system_residual(c, 0, true);
       PMG_CK_LAUNCH();
       st = read_norm(c, &nn);
-      if (st) return st;
+      if (st) return recover(st);
       ++c.nk_count[3];
       if (std::isfinite(nn) && nn <= (1.0 - 1e-4 * lam) * nrm) break;
       if (t < w.o.max_backtrack) lam *= 0.5;

@@ -160,3 +160,23 @@ def test_copy_wait_that_gives_up_gives_etimeout_and_same_result(prec, flux):
     finally:
         ref.close()
         test.close()
+
+
+def test_newton_krylov_failure_restores_stage_source_and_iterate():
+    """A Newton-Krylov stage whose preconditioner V-cycles report PMG_ETIMEOUT
+    (every bulk-copy wait gives up at once): the call fails with that status,
+    and the stage source it rewrites for the preconditioner and the finest
+    state are those of before the call, so the stage residual is unchanged."""
+    from paper_1908_03972_gb300 import pmgfr
+    s, q = _solver(copy_wait_s=-1.0)
+    try:
+        F0 = s.stage_F(q)
+        pmgfr.pmg_set_stage_solver(s.h, pmgfr.PMG_STAGE_NK, state_scale=(TINF, 1.0, 1.0, TINF))
+        s.set_state(q)
+        with pytest.raises(pmgfr.PmgError) as ei:
+            pmgfr.pmg_stage_solve(s.h)
+        assert ei.value.status == pmgfr.PMG_ETIMEOUT
+        assert np.array_equal(s.get_state(), q)
+        assert np.array_equal(s.stage_F(q), F0)
+    finally:
+        s.close()
