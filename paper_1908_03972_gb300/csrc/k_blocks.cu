@@ -272,6 +272,11 @@ static size_t factor_smem(int n, int wbytes) {
 
 void launch_factor(const Ctx& c, LevelDev& L, int level, int prec, int* flag, cudaStream_t s) {
   const int n = L.n, base = level * c.E;   // the flag holds 1 + level E + element of the highest bad block
+  const int C = factor_cluster_size(n, prec);
+  if (C > 1) {   // too large for one CTA: a cluster of C (k_factor_cluster.cu)
+    launch_factor_cluster(c, L, level, prec, C, flag, s);
+    return;
+  }
   if (prec == PMG_PREC_FP64)
     factor_kernel<double><<<c.E, 256, factor_smem(n, 8), s>>>(n, L.Dfull, (double*)L.Dinv, L.rs, L.cs, flag, base);
   else if (prec == PMG_PREC_BF16R)
@@ -281,13 +286,12 @@ void launch_factor(const Ctx& c, LevelDev& L, int level, int prec, int* flag, cu
     factor_kernel<float><<<c.E, 256, factor_smem(n, 4), s>>>(n, L.Dfull, (float*)L.Dinv, L.rs, L.cs, flag, base);
 }
 
-// Largest block the shared-memory factorisation holds in the precision prec
-// (227 KB of shared memory per CTA): n = 168 in FP64, 238 in FP32 and BF16
-// (their elimination runs in FP32).
+// Largest block the shared-memory factorisation holds in the precision prec:
+// one CTA (227 KB) up to n = 168 in FP64 and 238 in FP32 and BF16 (their
+// elimination runs in FP32), a cluster of up to 8 CTAs beyond.
 int factor_max_n(int prec) {
-  const int wb = prec == PMG_PREC_FP64 ? 8 : 4;
   int n = 4;
-  while (factor_smem(n + 1, wb) <= (size_t)227 * 1024) ++n;
+  while (factor_cluster_size(n + 1, prec) > 0) ++n;
   return n;
 }
 
@@ -296,9 +300,14 @@ int factor_max_n(int prec) {
 // factor_max_n are left out; the calls that would factor them fail first.
 cudaError_t prepare_kernels(const Ctx& c) {
   int nmax = 4;
-  const int lim = factor_max_n(c.cfg.block_prec);
-  for (int l = 0; l < c.cfg.n_levels; ++l)
-    if (c.lev[l].n <= lim) nmax = std::max(nmax, c.lev[l].n);
+  for (int l = 0; l < c.cfg.n_levels; ++l) {
+    const int C = factor_cluster_size(c.lev[l].n, c.cfg.block_prec);
+    if (C == 1) nmax = std::max(nmax, c.lev[l].n);
+    if (C > 1) {
+      cudaError_t e = prepare_factor_cluster(c.lev[l].n, c.cfg.block_prec, C);
+      if (e != cudaSuccess) return e;
+    }
+  }
   cudaError_t e = cudaFuncSetAttribute(factor_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)factor_smem(nmax, 8));
   if (e != cudaSuccess) return e;

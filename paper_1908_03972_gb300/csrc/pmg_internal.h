@@ -343,5 +343,11 @@ int residual_threads_per_block(int P);
 int residual_blocks_for(int P, int E);
 cudaError_t prepare_kernels(const Ctx& c);
 int factor_max_n(int prec);
+// Blocks larger than one CTA's shared memory (k_factor_cluster.cu): CTAs per
+// block (1: the one-CTA kernel; 2, 4, 8: a cluster; 0: too large).
+int factor_cluster_size(int n, int prec);
+size_t factor_cluster_smem(int n, int C, int tbytes);
+void launch_factor_cluster(const Ctx& c, LevelDev& L, int level, int prec, int C, int* flag, cudaStream_t s);
+cudaError_t prepare_factor_cluster(int n, int prec, int C);
 
 }  // namespace pmg
