@@ -292,7 +292,9 @@ pmg_status pmg_set_blocks(pmg_ctx* ctx, int level, const double* D, int on_devic
 
 /* Factor the assembled blocks of a level (or all, level = -1) in the
  * configured precision: power-of-two row/column equilibration, then
- * Gauss-Jordan elimination with partial pivoting to the explicit inverse.
+ * Gauss-Jordan elimination with partial pivoting to the explicit inverse,
+ * one CTA per block, or a thread-block cluster of 2, 4 or 8 CTAs for blocks
+ * one CTA's shared memory cannot hold (same arithmetic, same result).
  * Returns PMG_ESINGULAR, naming the element and level of the highest such
  * block (level-major order), if a pivot is not finite or not
  * above n eps of the working precision (the equilibrated rows have unit size

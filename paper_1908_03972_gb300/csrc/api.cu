@@ -506,8 +506,8 @@ static pmg_status check_level(const Ctx& c, int level) {
   return PMG_OK;
 }
 
-// Levels whose blocks the shared-memory factorisation cannot hold (hexahedra
-// at P = 3: n = 320) have a residual but no smoother.
+// Levels whose blocks not even a cluster of 8 CTAs can hold in shared memory
+// (n above about 470 in FP64) have a residual but no smoother.
 static pmg_status check_factorable(const Ctx& c, int level) {
   const int lim = factor_max_n(c.cfg.block_prec);
   for (int l = 0; l < c.cfg.n_levels; ++l) {
