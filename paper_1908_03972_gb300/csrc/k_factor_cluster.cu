@@ -38,6 +38,10 @@ template <> struct EpsC<double> { static constexpr double value = 2.220446049250
 
 }  // namespace
 
+// One CTA per SM (its shared memory fills it): 1024 threads keep enough warps
+// in flight for the elimination's shared-memory round trips.
+constexpr int kClusterThreads = 1024;
+
 // Shared memory of one CTA: doubles (row maxima, row scales, own column
 // scales), then the acc-type arrays (own columns, column k, published column
 // k), then ints (interchanges, column order, its inverse).
@@ -47,7 +51,7 @@ size_t factor_cluster_smem(int n, int C, int tbytes) {
 }
 
 template <class W, int C>
-__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256)
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kClusterThreads)
     factor_cluster_kernel(int n, const double* __restrict__ Din, W* __restrict__ Dinv, double* __restrict__ rs,
                           double* __restrict__ cs, int* __restrict__ flag, int flag_base) {
   using T = typename Blk<W>::acc;
@@ -184,9 +188,9 @@ template <class W>
 void launch_cluster_w(int C, int n, int E, const double* D, W* Dinv, double* rs, double* cs, int* flag, int base,
                       cudaStream_t s) {
   const size_t bytes = factor_cluster_smem(n, C, (int)sizeof(typename Blk<W>::acc));
-  if (C == 2) factor_cluster_kernel<W, 2><<<E * 2, 256, bytes, s>>>(n, D, Dinv, rs, cs, flag, base);
-  else if (C == 4) factor_cluster_kernel<W, 4><<<E * 4, 256, bytes, s>>>(n, D, Dinv, rs, cs, flag, base);
-  else factor_cluster_kernel<W, 8><<<E * 8, 256, bytes, s>>>(n, D, Dinv, rs, cs, flag, base);
+  if (C == 2) factor_cluster_kernel<W, 2><<<E * 2, kClusterThreads, bytes, s>>>(n, D, Dinv, rs, cs, flag, base);
+  else if (C == 4) factor_cluster_kernel<W, 4><<<E * 4, kClusterThreads, bytes, s>>>(n, D, Dinv, rs, cs, flag, base);
+  else factor_cluster_kernel<W, 8><<<E * 8, kClusterThreads, bytes, s>>>(n, D, Dinv, rs, cs, flag, base);
 }
 
 template <class W>
