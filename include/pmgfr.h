@@ -361,7 +361,7 @@ pmg_status pmg_esdirk_step(pmg_ctx* ctx, double dt, pmg_step_stats* stats);
  *
  * With the Newton-Krylov solver pmg_step_stats.pseudo_iters counts Newton
  * steps and n_vcycles the preconditioner's V-cycles; pmg_stage_history holds
- * ||F|| after every Newton step (dtau entries 0). */
+ * ||F|| after every Newton step (dtau entries 0 unless ptc_dtau > 0). */
 typedef enum { PMG_STAGE_PTC = 0, PMG_STAGE_NK = 1 } pmg_stage_solver;
 typedef enum { PMG_NK_PC_BLOCK = 0, PMG_NK_PC_VCYCLE = 1 } pmg_nk_precond;
 typedef struct {
@@ -384,6 +384,16 @@ typedef struct {
   double pc_eps;           /* V-cycle preconditioner: eps = pc_eps ||F(q)|| (<= 0: 0.1;
                               with 1 the V-cycle sees the whole Newton defect and
                               can leave its linear range) */
+  double ptc_dtau;         /* > 0: pseudo-transient Newton (Kelley & Keyes): every
+                              Newton step solves (Gamma(q)/dtau + A) delta = F, the
+                              linearised backward-Euler step of the pseudo-time
+                              system (eq. preconditioning), with dtau starting here
+                              and following SER with exponent 1.5 and no upper
+                              bound (dtau *= (||F_old|| / ||F_new||)^1.5); the
+                              preconditioner takes min(dtau, dtau_pc), and the step
+                              lam delta takes lam from the max_update limit alone
+                              (no backtracking).  pmg_stage_history's dtau entries
+                              hold each step's dtau.  <= 0 (default): Newton */
 } pmg_nk_options;
 typedef struct {
   long long newton;        /* Newton steps */

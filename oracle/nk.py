@@ -21,6 +21,16 @@ preconditioner as future work.  This module writes that variant out:
   |dp|/p, |dT|/T of any point under the full step, and halved until ||F||_W
   falls by the factor (1 - 1e-4 lam) (at most max_backtrack halvings; the
   last trial is taken regardless).
+- Pseudo-transient Newton (ptc_dtau > 0; Kelley & Keyes, SIAM J. Numer.
+  Anal. 35, 1998): every Newton step is the backward-Euler step of the
+  paper's pseudo-time system Gamma dq/dtau = F (Section 2.4, eq.
+  preconditioning), linearised: (Gamma(q)/dtau + A) delta = F(q), Gamma
+  pointwise at q.  dtau starts at ptc_dtau and follows the SER rule of eq.
+  ser with exponent 1.5 and no upper bound, dtau <- dtau (||F_old|| /
+  ||F_new||)^1.5; the step lam delta takes lam from the max_update limit
+  alone (no backtracking: a step that raises ||F|| shrinks dtau instead).  The
+  preconditioners take dtau_pc' = min(dtau, dtau_pc): the element blocks are
+  then the block diagonal of Gamma/dtau + A itself.
 - ||.||_W: each equation divided by its residual scale (the stage norm of the
   pseudo-transient solver).
 - Krylov: restarted FGMRES(m), right-preconditioned (Saad, SIAM J. Sci.
@@ -49,6 +59,21 @@ import numpy as np
 def wnorm(F, W):
     """sqrt(sum_v sum (F_v / scale_v)^2), W = 1 / scale."""
     return float(np.sqrt(sum(((F[v] * W[v]) ** 2).sum() for v in range(F.shape[0]))))
+
+
+def gamma_field(orc, q):
+    """Gamma of eq. preconditioning at every point of q (nv, E, N), as an
+    (E, N, nv, nv) array, from the oracle's point matrices (absolute pressure)
+    with the oracle's gamma, Mach number and cut-off."""
+    import oracle as O
+    nv, E, N = q.shape
+    pm = O.point_matrices if nv == 4 else O.point_matrices3
+    cf = orc.cfg
+    G = np.empty((E, N, nv, nv))
+    for e in range(E):
+        for i in range(N):
+            G[e, i] = pm(q[:, e, i], gamma=cf.gamma, Ma_inf=cf.Ma_inf, kappa=cf.kappa, cutoff=cf.cutoff)[1]
+    return G
 
 
 def fgmres(apply_A, apply_M, b, m, max_it, rtol):
@@ -96,13 +121,14 @@ def fgmres(apply_A, apply_M, b, m, max_it, rtol):
 
 def nk_stage_solve(orc, q, src, odt, W, s, *, tol=1e-8, max_newton=30, m=20, max_krylov=40, eta=1e-2,
                    precond="vcycle", dtau_pc=10.0, pc_refresh=1, delta0=1e-7, max_backtrack=6, norm0=None,
-                   pc_eps=0.1, max_update=0.2):
+                   pc_eps=0.1, max_update=0.2, ptc_dtau=0.0):
     """Newton-Krylov solve of the stage system with source src and omega dt =
     odt on the oracle `orc`, from q.  W: 1 / residual scale per equation; s:
     state scale per variable.  Stops when ||F||_W <= tol * ||F(q_start)||_W
     (or tol * norm0 if given).  Returns dict(q, newton, krylov, vcycles,
-    residuals, norms, status) with status 0 converged, 1 not converged within
-    max_newton, 2 non-finite."""
+    residuals, norms, dtaus, step, status): dtaus the pseudo-time step of each
+    Newton step (ptc_dtau > 0), step the last accepted lam delta, status 0
+    converged, 1 not converged within max_newton, 2 non-finite."""
     W = np.asarray(W, dtype=float)
     s = np.asarray(s, dtype=float)
     shape = q.shape
@@ -116,15 +142,21 @@ def nk_stage_solve(orc, q, src, odt, W, s, *, tol=1e-8, max_newton=30, m=20, max
     nrm = wnorm(F, W)
     n0 = nrm if norm0 is None else norm0
     norms = [nrm]
-    stats = dict(newton=0, krylov=0, vcycles=0)
+    stats = dict(newton=0, krylov=0, vcycles=0, step=None)
     D = None
+    ptc = ptc_dtau > 0.0
+    dtau = ptc_dtau
+    dtaus = []
     for k in range(max_newton):
         if nrm <= tol * n0 or n0 == 0.0:
-            return dict(q=q, residuals=n_res, norms=norms, status=0, **stats)
+            return dict(q=q, residuals=n_res, norms=norms, status=0, dtaus=dtaus, **stats)
         eps = pc_eps * nrm
         refresh = [k % pc_refresh == 0]
+        dpc = min(dtau, dtau_pc) if ptc else dtau_pc
         if precond == "block" and refresh[0]:
-            D = orc.blocks(q, dtau_pc)
+            D = orc.blocks(q, dpc)
+        G = gamma_field(orc, q) if ptc else None
+        dtaus.append(dtau)
 
         def apply_A(z, q=q, F=F):
             nonlocal n_res
@@ -135,7 +167,10 @@ def nk_stage_solve(orc, q, src, odt, W, s, *, tol=1e-8, max_newton=30, m=20, max
             h = delta0 / rms
             Fh = orc.stage_F(q + h * zz)
             n_res += 1
-            return (-(Fh - F) / h * Wb).reshape(-1)
+            Az = -(Fh - F) / h
+            if ptc:
+                Az = Az + np.einsum("enij,jen->ien", G, zz) / dtau
+            return (Az * Wb).reshape(-1)
 
         def apply_M(v, q=q, F=F):
             r = v.reshape(shape) / Wb
@@ -147,7 +182,7 @@ def nk_stage_solve(orc, q, src, odt, W, s, *, tol=1e-8, max_newton=30, m=20, max
                     z[:, e, :] = x.reshape(nv, N)
                 return z.reshape(-1)
             orc.set_stage(src - F + eps * r, odt)
-            qp = orc.vcycle(q, dtau_pc, refresh=refresh[0])
+            qp = orc.vcycle(q, dpc, refresh=refresh[0])
             refresh[0] = False
             orc.set_stage(src, odt)
             stats["vcycles"] += 1
@@ -161,7 +196,7 @@ def nk_stage_solve(orc, q, src, odt, W, s, *, tol=1e-8, max_newton=30, m=20, max
         # the largest relative change of p (absolute) and T under the full step
         rel = max(float(np.max(np.abs(delta[0]) / np.abs(q[0]))), float(np.max(np.abs(delta[-1]) / np.abs(q[-1]))))
         lam = max_update / rel if rel > max_update else 1.0
-        for t in range(max_backtrack + 1):
+        for t in range(0 if ptc else max_backtrack + 1):
             qn = q + lam * delta
             Fn = orc.stage_F(qn)
             n_res += 1
@@ -170,9 +205,17 @@ def nk_stage_solve(orc, q, src, odt, W, s, *, tol=1e-8, max_newton=30, m=20, max
                 break
             if t < max_backtrack:
                 lam *= 0.5
+        if ptc:
+            qn = q + lam * delta
+            Fn = orc.stage_F(qn)
+            n_res += 1
+            nn = wnorm(Fn, W)
         if not np.isfinite(nn):
-            return dict(q=qn, residuals=n_res, norms=norms + [nn], status=2, **stats)
+            return dict(q=qn, residuals=n_res, norms=norms + [nn], status=2, dtaus=dtaus, **stats)
+        if ptc:
+            dtau = dtau * (nrm / nn) ** 1.5
+        stats["step"] = lam * delta
         q, F, nrm = qn, Fn, nn
         norms.append(nrm)
     status = 0 if nrm <= tol * n0 else 1
-    return dict(q=q, residuals=n_res, norms=norms, status=status, **stats)
+    return dict(q=q, residuals=n_res, norms=norms, status=status, dtaus=dtaus, **stats)

@@ -945,6 +945,7 @@ static pmg_nk_options nk_defaults(const Ctx& c, const pmg_nk_options* o) {
   if (r.max_backtrack < 0) r.max_backtrack = 6;
   if (!(r.pc_eps > 0.0)) r.pc_eps = 0.1;
   if (!(r.max_update > 0.0)) r.max_update = 0.2;
+  if (!(r.ptc_dtau > 0.0)) r.ptc_dtau = 0.0;
   return r;
 }
 
@@ -972,11 +973,14 @@ struct NkWork {
   size_t n, plane;
   Scale5 one, W, Winv, sinv;
   int m;
+  double ptc_inv = 0.0;   // 1 / dtau of pseudo-transient Newton, 0 for Newton
+  double dpc;             // the preconditioner's dtau
 
   NkWork(Ctx& cc, const pmg_nk_options& oo) : c(cc), L(cc.lev[0]), o(oo) {
     n = L.tot;
     plane = (size_t)c.E * L.N;
     m = o.krylov_dim;
+    dpc = o.dtau_pc;
     for (int v = 0; v < 5; ++v) {
       one.s[v] = 1.0;
       W.s[v] = v < c.nv ? c.ph.nw[v] : 1.0;
@@ -1018,7 +1022,8 @@ struct NkWork {
     }
     return PMG_OK;
   }
-  // w = W A z = -W (F(q + h z) - F(q)) / h at q = nk_q (F(q) in nk_F)
+  // w = W A z = -W (F(q + h z) - F(q)) / h at q = nk_q (F(q) in nk_F),
+  // + W Gamma(q) z / dtau in pseudo-transient Newton
   pmg_status apply_A(const double* z, double* w) {
     combine(c.nk_t, z, 1.0, nullptr, 0.0, sinv, nullptr, 0.0, one);
     double ss;
@@ -1035,6 +1040,7 @@ struct NkWork {
     Scale5 Wh;
     for (int v = 0; v < 5; ++v) Wh.s[v] = -W.s[v] / h;
     combine(w, L.F, 1.0, c.nk_F, -1.0, Wh, nullptr, 0.0, one);
+    if (ptc_inv > 0.0) launch_gamma_apply(c.nv, plane, c.nk_q, z, w, ptc_inv, W, c.ph, c.stream);
     ++c.nk_count[3];
     PMG_CK_LAUNCH();
     return PMG_OK;
@@ -1053,7 +1059,7 @@ struct NkWork {
     system_residual(c, 0, false);   // the V-cycle starts from lev[0].F = F(q) - S
     pmg_status st;
     if (*refresh) {
-      st = set_dtau(c, o.dtau_pc);
+      st = set_dtau(c, dpc);
       if (st) return st;
     }
     st = launch_vcycle(c, *refresh);
@@ -1176,6 +1182,9 @@ static pmg_status nk_stage_solve(Ctx& c, int* iters, double* drop, int* n_refres
   st = w.set_state_scales(L.q);
   if (st) return st;
   const double n0 = nrm;
+  // pseudo-transient Newton: dtau from ptc_dtau, SER (exponent 1.5, no bound)
+  const bool ptc = w.o.ptc_dtau > 0.0;
+  double dtau = w.o.ptc_dtau;
   // on an error after this point: the stage source and the last accepted
   // iterate go back where the caller expects them
   auto recover = [&](pmg_status err) {
@@ -1187,7 +1196,7 @@ static pmg_status nk_stage_solve(Ctx& c, int* iters, double* drop, int* n_refres
   };
   for (int k = 0;; ++k) {
     c.hist_norm.push_back(nrm);
-    c.hist_dtau.push_back(0.0);
+    c.hist_dtau.push_back(ptc ? dtau : 0.0);
     if (nrm <= c.cfg.tol * n0 || n0 == 0.0) {
       finish(k, nrm, n0);
       return PMG_OK;
@@ -1201,10 +1210,14 @@ static pmg_status nk_stage_solve(Ctx& c, int* iters, double* drop, int* n_refres
       return fail(PMG_ENOTCONV, "stage not converged within max_newton Newton steps");
     }
     const bool refresh = k % w.o.pc_refresh == 0;
+    if (ptc) {
+      w.ptc_inv = 1.0 / dtau;
+      w.dpc = std::min(dtau, w.o.dtau_pc);
+    }
     if (refresh) {
       if (n_refresh) ++*n_refresh;
       if (w.o.precond == PMG_NK_PC_BLOCK) {   // blocks at the iterate (lev[0].q holds it here)
-        st = set_dtau(c, w.o.dtau_pc);
+        st = set_dtau(c, w.dpc);
         if (st) return recover(st);
         refresh_level(c, 0);
         st = check_singular(c);
@@ -1213,13 +1226,15 @@ static pmg_status nk_stage_solve(Ctx& c, int* iters, double* drop, int* n_refres
     }
     st = w.krylov(w.o.pc_eps * nrm, refresh && w.o.precond == PMG_NK_PC_VCYCLE);
     if (st) return recover(st);
-    // backtracking on ||F||, from a step that changes p and T by at most max_update
+    // backtracking on ||F||, from a step that changes p and T by at most
+    // max_update (pseudo-transient Newton takes that step as it is)
     launch_rel_change(c.nk_q, c.nk_x, w.plane, c.nv - 1, c.ph.p_ref, c.nk_part, c.nk_dots, c.stream);
     PMG_CK_LAUNCH();
     st = w.fetch(1);
     if (st) return recover(st);
     double lam = c.h_nk[0] > w.o.max_update ? w.o.max_update / c.h_nk[0] : 1.0, nn = 0.0;
-    for (int t = 0; t <= w.o.max_backtrack; ++t) {
+    const int n_back = ptc ? 0 : w.o.max_backtrack;
+    for (int t = 0; t <= n_back; ++t) {
       w.combine(L.q, c.nk_q, 1.0, nullptr, 0.0, w.one, c.nk_x, lam, w.one);
       system_residual(c, 0, true);
       PMG_CK_LAUNCH();
@@ -1227,8 +1242,9 @@ static pmg_status nk_stage_solve(Ctx& c, int* iters, double* drop, int* n_refres
       if (st) return recover(st);
       ++c.nk_count[3];
       if (std::isfinite(nn) && nn <= (1.0 - 1e-4 * lam) * nrm) break;
-      if (t < w.o.max_backtrack) lam *= 0.5;
+      if (t < n_back) lam *= 0.5;
     }
+    if (ptc && nn > 0.0 && std::isfinite(nn)) dtau *= std::pow(nrm / nn, 1.5);
     w.copy(c.nk_q, L.q);
     w.copy(c.nk_F, L.F);
     ++c.nk_count[0];
@@ -1743,8 +1759,9 @@ pmg_status pmg_set_stage_solver(pmg_ctx* h, int solver, const pmg_nk_options* op
   if (o.precond != PMG_NK_PC_BLOCK && o.precond != PMG_NK_PC_VCYCLE)
     return fail(PMG_EINVAL, "unknown Newton-Krylov preconditioner");
   if (!(o.eta < 1.0) || !std::isfinite(o.dtau_pc) || !std::isfinite(o.delta0) || !(o.delta0 < 1.0) ||
-      !std::isfinite(o.pc_eps) || !std::isfinite(o.max_update))
-    return fail(PMG_EINVAL, "Newton-Krylov options out of range (eta < 1, delta0 < 1, finite dtau_pc)");
+      !std::isfinite(o.pc_eps) || !std::isfinite(o.max_update) || !std::isfinite(o.ptc_dtau))
+    return fail(PMG_EINVAL,
+                "Newton-Krylov options out of range (eta < 1, delta0 < 1, finite dtau_pc and ptc_dtau)");
   for (int v = 0; v < 5; ++v)
     if (!std::isfinite(o.state_scale[v])) return fail(PMG_EINVAL, "state_scale must be finite");
   c.stage_solver = solver;

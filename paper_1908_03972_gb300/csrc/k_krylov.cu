@@ -4,6 +4,7 @@
 // combinations whose terms carry a scale per state variable (the vectors are
 // SoA planes of E N values per variable).  All of it is HBM-bound streaming
 // over the finest level's vectors.
+#include "physics3.cuh"
 #include "pmg_internal.h"
 
 namespace pmg {
@@ -145,6 +146,41 @@ void launch_rel_change(const double* x, const double* dx, size_t plane, int tslo
                        double* out, cudaStream_t s) {
   rel_change_partial_kernel<<<kDotBlocks, kKrylovThreads, 0, s>>>(x, dx, plane, tslot, p_ref, part);
   max_partials_kernel<<<1, kKrylovThreads, 0, s>>>(part, kDotBlocks, out);
+}
+
+// out += a w_v (Gamma(q) z)_v at every point: the pseudo-time matrix of eq.
+// preconditioning at the stored state q (pressure p - p_ref), applied to z.
+__global__ void __launch_bounds__(kKrylovThreads) gamma_apply_kernel(int nv, size_t plane, const double* __restrict__ q,
+                                                                    const double* __restrict__ z, double* out,
+                                                                    double a, Scale5 w, Phys ph) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
+    if (nv == 4) {
+      const double qv[4] = {q[i] + ph.p_ref, q[plane + i], q[2 * plane + i], q[3 * plane + i]};
+      double G[16], M[16];
+      gamma_and_M(qv, ph, G, M);
+      for (int v = 0; v < 4; ++v) {
+        double t = 0.0;
+        for (int k = 0; k < 4; ++k) t = fma(G[v * 4 + k], z[k * plane + i], t);
+        out[v * plane + i] += a * w.s[v] * t;
+      }
+    } else {
+      const double qv[5] = {q[i] + ph.p_ref, q[plane + i], q[2 * plane + i], q[3 * plane + i], q[4 * plane + i]};
+      double G[25], M[25];
+      gamma_and_M3(qv, ph, G, M);
+      for (int v = 0; v < 5; ++v) {
+        double t = 0.0;
+        for (int k = 0; k < 5; ++k) t = fma(G[v * 5 + k], z[k * plane + i], t);
+        out[v * plane + i] += a * w.s[v] * t;
+      }
+    }
+  }
+}
+
+void launch_gamma_apply(int nv, size_t plane, const double* q, const double* z, double* out, double a,
+                        const Scale5& w, const Phys& ph, cudaStream_t s) {
+  const size_t want = (plane + kKrylovThreads - 1) / kKrylovThreads;
+  const unsigned blocks = (unsigned)(want < (size_t)4 * kDotBlocks ? want : (size_t)4 * kDotBlocks);
+  gamma_apply_kernel<<<blocks, kKrylovThreads, 0, s>>>(nv, plane, q, z, out, a, w, ph);
 }
 
 }  // namespace pmg

@@ -331,6 +331,9 @@ void launch_combination(double* y, const double* X, size_t ld, int k, const doub
 // out = (a0 x0 + a1 x1) s0[v] + a2 x2 s2[v], v = i / plane (null inputs count as 0)
 void launch_plane_combine(double* out, const double* x0, double a0, const double* x1, double a1, const Scale5& s0,
                           const double* x2, double a2, const Scale5& s2, size_t plane, size_t n, cudaStream_t s);
+// out += a w_v (Gamma(q) z)_v at every point (q stored with p - p_ref)
+void launch_gamma_apply(int nv, size_t plane, const double* q, const double* z, double* out, double a,
+                        const Scale5& w, const Phys& ph, cudaStream_t s);
 // max over the p and T planes of |dx| / |x (+ p_ref for p)| into out[0]
 void launch_rel_change(const double* x, const double* dx, size_t plane, int tslot, double p_ref, double* part,
                        double* out, cudaStream_t s);

@@ -111,6 +111,7 @@ class pmg_nk_options(ctypes.Structure):
         ("max_backtrack", ctypes.c_int),
         ("max_update", ctypes.c_double),
         ("pc_eps", ctypes.c_double),
+        ("ptc_dtau", ctypes.c_double),
     ]
 
 
@@ -367,7 +368,7 @@ def pmg_stage_history(h):
 
 def pmg_set_stage_solver(h, solver, *, max_newton=0, krylov_dim=0, max_krylov=0, eta=0.0,
                          precond=PMG_NK_PC_VCYCLE, dtau_pc=0.0, pc_refresh=0, delta0=0.0, state_scale=(0.0,) * 5,
-                         max_backtrack=-1, max_update=0.0, pc_eps=0.0):
+                         max_backtrack=-1, max_update=0.0, pc_eps=0.0, ptc_dtau=0.0):
     """PMG_STAGE_PTC, or PMG_STAGE_NK with its options (0 / negative: the defaults)."""
     o = pmg_nk_options()
     o.max_newton, o.krylov_dim, o.max_krylov, o.eta = max_newton, krylov_dim, max_krylov, eta
@@ -377,6 +378,7 @@ def pmg_set_stage_solver(h, solver, *, max_newton=0, krylov_dim=0, max_krylov=0,
     o.max_backtrack = max_backtrack
     o.max_update = max_update
     o.pc_eps = pc_eps
+    o.ptc_dtau = ptc_dtau
     _check(load().pmg_set_stage_solver(h, int(solver), ctypes.byref(o)))
 
 

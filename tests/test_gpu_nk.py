@@ -115,6 +115,62 @@ def test_stage_converges_to_the_oracle_solution(precond, prec):
         gpu.close()
 
 
+@pytest.mark.parametrize("precond", ["block", "vcycle"])
+def test_one_pseudo_transient_newton_step_matches_oracle(precond):
+    """One pseudo-transient Newton step (dtau = 0.05, four FGMRES iterations,
+    no early stop): the product carries Gamma(q) z / dtau, the preconditioner
+    takes min(dtau, dtau_pc); the corrections agree to the bound of the plain
+    Newton step."""
+    from paper_1908_03972_gb300 import pmgfr
+    orc, gpu, q, src, odt = _pair(prec=0)
+    k = 4
+    try:
+        pc = pmgfr.PMG_NK_PC_BLOCK if precond == "block" else pmgfr.PMG_NK_PC_VCYCLE
+        pmgfr.pmg_set_stage_solver(gpu.h, pmgfr.PMG_STAGE_NK, max_newton=1, krylov_dim=k, max_krylov=k, eta=1e-30,
+                                   precond=pc, dtau_pc=10.0, delta0=1e-4, state_scale=SC, ptc_dtau=0.05)
+        gpu.set_state(q)
+        with pytest.raises(pmgfr.PmgError) as ei:
+            pmgfr.pmg_stage_solve(gpu.h)
+        assert ei.value.status == pmgfr.PMG_ENOTCONV
+        dg = gpu.get_state() - q
+        out = nk.nk_stage_solve(orc, q, src, odt, WT, SC, precond=precond, dtau_pc=10.0, max_newton=1, m=k,
+                                max_krylov=k, eta=1e-30, delta0=1e-4, ptc_dtau=0.05)
+        do = out["q"] - q
+        for v in range(4):
+            scale = np.abs(do[v]).max()
+            assert np.abs(dg[v] - do[v]).max() <= 1e-6 * scale, (v, np.abs(dg[v] - do[v]).max(), scale)
+        norms, dtau = pmgfr.pmg_stage_history(gpu.h)
+        assert dtau[0] == 0.05 and dtau[1] == pytest.approx(0.05 * (norms[0] / norms[1]) ** 1.5, rel=1e-12)
+    finally:
+        gpu.close()
+
+
+@pytest.mark.parametrize("precond", ["block", "vcycle"])
+def test_pseudo_transient_newton_stage_converges_to_the_oracle_solution(precond):
+    """From dtau = 0.1 the stage reaches a 1e-8 drop on the oracle's converged
+    state (the bounds of the Newton stage test), with the oracle's dtau
+    sequence to the rounding of the norms it is formed from."""
+    from paper_1908_03972_gb300 import pmgfr
+    orc, gpu, q, src, odt = _pair(prec=0)
+    try:
+        pc = pmgfr.PMG_NK_PC_BLOCK if precond == "block" else pmgfr.PMG_NK_PC_VCYCLE
+        pmgfr.pmg_set_stage_solver(gpu.h, pmgfr.PMG_STAGE_NK, krylov_dim=30, max_krylov=80, precond=pc,
+                                   dtau_pc=10.0, state_scale=SC, ptc_dtau=0.1)
+        qg, it, drop = gpu.stage_solve(q)
+        assert drop <= 1e-8 and it <= 10
+        out = nk.nk_stage_solve(orc, q, src, odt, WT, SC, precond=precond, dtau_pc=10.0, m=30, max_krylov=80,
+                                ptc_dtau=0.1)
+        assert out["status"] == 0 and abs(it - out["newton"]) <= 1
+        assert np.abs(qg[0] - out["q"][0]).max() / 2.0 <= 1e-7
+        assert np.abs(qg[1:3] - out["q"][1:3]).max() <= 1e-7
+        norms, dtau = pmgfr.pmg_stage_history(gpu.h)
+        assert len(norms) == it + 1
+        n = min(3, len(out["dtaus"]))
+        assert np.allclose(dtau[:n], out["dtaus"][:n], rtol=1e-3)
+    finally:
+        gpu.close()
+
+
 def test_esdirk_step_with_newton_krylov_stages_matches_pseudo_transient():
     from paper_1908_03972_gb300 import pmgfr
     nodes, nbr = W.periodic_box(8, 8, Ng=1)
@@ -147,7 +203,8 @@ def test_stage_solver_options_are_validated():
     from paper_1908_03972_gb300 import pmgfr
     orc, gpu, q, src, odt = _pair()
     try:
-        for bad in (dict(krylov_dim=65), dict(precond=7), dict(eta=1.5), dict(delta0=2.0)):
+        for bad in (dict(krylov_dim=65), dict(precond=7), dict(eta=1.5), dict(delta0=2.0),
+                    dict(ptc_dtau=float("inf"))):
             with pytest.raises(pmgfr.PmgError) as ei:
                 pmgfr.pmg_set_stage_solver(gpu.h, pmgfr.PMG_STAGE_NK, **bad)
             assert ei.value.status == pmgfr.PMG_EINVAL
@@ -157,13 +214,15 @@ def test_stage_solver_options_are_validated():
         gpu.close()
 
 
-@pytest.mark.parametrize("gauge", [False, True])
-def test_one_newton_step_on_hexahedra_matches_oracle(gauge):
+@pytest.mark.parametrize("gauge,ptc", [(False, 0.0), (True, 0.0), (True, 0.2)])
+def test_one_newton_step_on_hexahedra_matches_oracle(gauge, ptc):
     """The same fixed-count Newton step on the cubed-sphere shell (2 x 2 x 6
     elements per panel, Q2 hexahedra, slip wall, Ma = 0.001, P{2-1-0}) from
     the free stream with noise in v: five variables, the hexahedral residual
     and V-cycle as the preconditioner (measured differences 2e-9 with one
-    Krylov step, 2e-7 with two)."""
+    Krylov step, 2e-7 with two); with ptc > 0 the pseudo-transient Newton
+    step (Gamma/dtau added to the product, the V-cycle at min(dtau,
+    dtau_pc))."""
     from paper_1908_03972_gb300 import pmgfr
     ma = 0.001
     T = W.freestream_T(ma, speed=1.0)
@@ -188,14 +247,14 @@ def test_one_newton_step_on_hexahedra_matches_oracle(gauge):
         sc = (T, 1.0, 1.0, 1.0, T)
         k = 2
         pmgfr.pmg_set_stage_solver(gpu.h, pmgfr.PMG_STAGE_NK, max_newton=1, krylov_dim=k, max_krylov=k, eta=1e-30,
-                                   dtau_pc=1.0, delta0=1e-4, state_scale=sc, max_backtrack=0)
+                                   dtau_pc=1.0, delta0=1e-4, state_scale=sc, max_backtrack=0, ptc_dtau=ptc)
         gpu.set_state(q)
         with pytest.raises(pmgfr.PmgError):
             pmgfr.pmg_stage_solve(gpu.h)
         dg = gpu.get_state() - q
         out = nk.nk_stage_solve(orc, q, src, odt, 1.0 / np.array(W.freestream_scales3(ma, speed=1.0)), np.array(sc),
                                 precond="vcycle", dtau_pc=1.0, max_newton=1, m=k, max_krylov=k, eta=1e-30,
-                                max_backtrack=0, delta0=1e-4)
+                                max_backtrack=0, delta0=1e-4, ptc_dtau=ptc)
         do = out["q"] - q
         for v in range(5):
             assert np.abs(dg[v] - do[v]).max() <= 1e-6 * np.abs(do[v]).max(), v

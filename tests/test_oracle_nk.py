@@ -136,3 +136,66 @@ def test_newton_krylov_reaches_the_pseudo_transient_solution(c1, precond):
     # both stop at a 1e-8 drop: the states differ by the remaining errors
     assert np.abs(out["q"][1:3] - qp[1:3]).max() <= 1e-7
     assert np.abs(out["q"][0] - qp[0]).max() / 2.0 <= 1e-5
+
+
+# ------------------------------------------------- pseudo-transient Newton
+def test_pseudo_transient_newton_small_dtau_is_the_explicit_pseudo_step(c1):
+    """With dtau small, (Gamma/dtau + A) delta = F gives delta = dtau Gamma^-1 F
+    to first order in dtau (the explicit pseudo-time step of eq.
+    preconditioning): one step with dtau = 1e-8 matches the pointwise solve
+    of the oracle's Gamma to 1e-5, and halving dtau halves the step (the
+    step itself is compared: at this size it vanishes in q's rounding)."""
+    orc, q, src, odt = c1
+    F = orc.stage_F(q)
+    G = nk.gamma_field(orc, q)
+    ref = np.einsum("enij,jen->ien", np.linalg.inv(G), F)
+    steps = []
+    for dtau in (1e-8, 0.5e-8):
+        out = nk.nk_stage_solve(orc, q, src, odt, WT, SC, precond="block", dtau_pc=10.0, max_newton=1, m=30,
+                                max_krylov=60, eta=1e-12, ptc_dtau=dtau, tol=0.0)
+        d = out["step"]
+        steps.append(d)
+        scale = np.abs(dtau * ref).max(axis=(1, 2))[:, None, None]
+        assert (np.abs(d - dtau * ref) / scale).max() <= 1e-5
+    s0 = np.abs(steps[0]).max(axis=(1, 2))
+    s1 = np.abs(steps[1]).max(axis=(1, 2))
+    assert np.allclose(s1 / s0, 0.5, rtol=1e-5)
+
+
+def test_pseudo_transient_newton_gamma_sign_and_scale(c1):
+    """With an exact linear solve, delta satisfies Gamma delta / dtau + A delta
+    = F: the Newton step of the pure system at the same state, A delta_N = F,
+    differs from it by the pseudo-time term, so Gamma (delta - ...) checks the
+    sign and the 1/dtau: F - A delta equals Gamma delta / dtau to the linear
+    tolerance, with A delta from a difference of residuals."""
+    orc, q, src, odt = c1
+    dtau = 0.05
+    out = nk.nk_stage_solve(orc, q, src, odt, WT, SC, precond="block", dtau_pc=10.0, max_newton=1, m=60,
+                            max_krylov=120, eta=1e-11, ptc_dtau=dtau, tol=0.0, max_update=1e9)
+    d = out["step"]
+    F = orc.stage_F(q)
+    h = 1e-7 / np.sqrt(np.mean((d / SC[:, None, None]) ** 2))
+    Ad = -(orc.stage_F(q + h * d) - F) / h
+    G = nk.gamma_field(orc, q)
+    Gd = np.einsum("enij,jen->ien", G, d) / dtau
+    scale = np.abs(F).max(axis=(1, 2))[:, None, None]
+    assert (np.abs(F - Ad - Gd) / scale).max() <= 1e-4
+    assert (np.abs(Gd) / scale).max() >= 1e-2        # the pseudo-time term is not negligible here
+
+
+def test_pseudo_transient_newton_reaches_the_stage_solution(c1):
+    """From dtau = 0.1 the SER-grown dtau turns the iteration into Newton: it
+    stops at the stage solution of the plain Newton solver, with dtau growing
+    and the last steps converging faster than 10x each."""
+    orc, q, src, odt = c1
+    out = nk.nk_stage_solve(orc, q, src, odt, WT, SC, precond="block", dtau_pc=10.0, max_newton=30, m=30,
+                            max_krylov=80, ptc_dtau=0.1)
+    assert out["status"] == 0
+    norms, dt = out["norms"], out["dtaus"]
+    assert norms[-1] <= 1e-8 * norms[0]
+    assert dt[-1] > 100.0 * dt[0]
+    assert norms[-1] <= 0.1 * norms[-2]
+    ref = nk.nk_stage_solve(orc, q, src, odt, WT, SC, precond="block", dtau_pc=10.0, max_newton=20, m=30,
+                            max_krylov=80)
+    assert np.abs(out["q"][1:3] - ref["q"][1:3]).max() <= 1e-7
+    assert np.abs(out["q"][0] - ref["q"][0]).max() / 2.0 <= 1e-5
