@@ -1493,21 +1493,17 @@ pmg_status pmg_residual(pmg_ctx* h, int level, const double* q, double* R, int o
 // Scratch of pmg_residual_static: one file-scope device array shared by every
 // call on a device (the gauge-shifted copy of the input state followed by the
 // common face fluxes).  Host code never touches it by name as an address: the
-// device address is looked up once per device with cudaGetSymbolAddress.
+// device address is looked up on every call with cudaGetSymbolAddress (which
+// allocates nothing), so a context torn down and created again in the same
+// process never sees a stale address.
 static constexpr size_t kStaticScratchDoubles = (size_t)1 << 21;   // 16 MiB
 static __device__ __align__(256) double g_static_scratch[kStaticScratchDoubles];
-static double* g_static_scratch_addr[64] = {};
 
-static cudaError_t static_scratch_address(int device, double** out) {
-  if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
-  if (!g_static_scratch_addr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_static_scratch_addr[device] = (double*)p;
-  }
-  *out = g_static_scratch_addr[device];
-  return cudaSuccess;
+static cudaError_t static_scratch_address(double** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  *out = (double*)p;
+  return e;
 }
 
 extern "C" {
@@ -1529,7 +1525,7 @@ pmg_status pmg_residual_static(pmg_ctx* h, int level, const double* q, double* R
   PMG_CK(cudaGetDevice(&cur));
   if (cur != c.device) return fail(PMG_EINVAL, "pmg_residual_static: make the context's device current first");
   double* scratch = nullptr;
-  PMG_CK(static_scratch_address(c.device, &scratch));
+  PMG_CK(static_scratch_address(&scratch));
   double* qs = scratch;
   L.Fcom = scratch + n_state;
   if (visc) {   // broken gradients and face jumps of the viscous terms
