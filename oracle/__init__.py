@@ -342,6 +342,8 @@ class OrcConfig3(ctypes.Structure):
         ("res_scale", ctypes.c_double * 5),
         ("q_inf", ctypes.c_double * 5),
         ("refresh_always", ctypes.c_int),
+        ("mu", ctypes.c_double),
+        ("Pr", ctypes.c_double),
     ]
 
 
@@ -411,7 +413,7 @@ class Oracle3:
 
     def __init__(self, nodes, nbr, Ng, P_levels, n_smooth, *, gamma=1.4, Ma_inf=0.005, kappa=1.0, cutoff=0,
                  dtau_init=0.01, dtau_max=10.0, tol=1e-8, refresh_every=10, max_pseudo=2000,
-                 res_scale=(1.0,) * 5, q_inf=(0.0,) * 5, esdirk_order=3, refresh_always=0):
+                 res_scale=(1.0,) * 5, q_inf=(0.0,) * 5, esdirk_order=3, refresh_always=0, mu=0.0, Pr=0.72):
         cfg = OrcConfig3()
         cfg.n_levels = len(P_levels)
         for l, P in enumerate(P_levels):
@@ -425,6 +427,7 @@ class Oracle3:
             cfg.res_scale[v] = res_scale[v]
             cfg.q_inf[v] = q_inf[v]
         cfg.refresh_always = refresh_always
+        cfg.mu, cfg.Pr = mu, Pr
         self.cfg = cfg
         self.nodes = _f64(nodes)
         self.nbr = np.ascontiguousarray(nbr, dtype=np.int32)
@@ -432,6 +435,9 @@ class Oracle3:
         self.Ng = Ng
         self.P = list(P_levels)
         self.h = _lib3().orc3_create(ctypes.byref(cfg), self.E, Ng, _p(self.nodes), self.nbr.ctypes.data_as(_i))
+        if not self.h:
+            raise ValueError("invalid neighbour table (or a slip wall with mu > 0, "
+                             "or a no-slip wall without the eps cut-off)")
 
     def __del__(self):
         try:

@@ -1687,16 +1687,45 @@ static void roe_flux3(const S qm[5], const S qp[5], const double Sv[3], const Ph
 }
 
 // Boundary ghost states in 3D (reading, as in 2D): slip wall (p, u - 2 u_n n, T),
-// far field the free stream.  n is the unit outward normal.
+// no-slip adiabatic wall (p, -u, T), far field the free stream.  n is the
+// unit outward normal.
 template <class S>
 static void ghost_state3(int bc, const S qm[5], const double n[3], const double qinf[5], S qg[5]) {
   if (bc == 4) {
     for (int v = 0; v < 5; ++v) qg[v] = qinf[v];
     return;
   }
-  S un = qm[1] * n[0] + qm[2] * n[1] + qm[3] * n[2];
   qg[0] = qm[0]; qg[4] = qm[4];
+  if (bc == 3) {
+    for (int c = 0; c < 3; ++c) qg[1 + c] = -qm[1 + c];
+    return;
+  }
+  S un = qm[1] * n[0] + qm[2] * n[1] + qm[3] * n[2];
   for (int c = 0; c < 3; ++c) qg[1 + c] = qm[1 + c] - 2.0 * un * n[c];
+}
+
+// Viscous fluxes in 3D (Section 2.1) from the state and the gradients
+// d[c*5 + v] = d q_v / d x_c (q = (p, u, v, w, T)): stress tau_ij =
+// mu (du_i/dx_j + du_j/dx_i - 2/3 div u delta_ij), heat conduction
+// (mu Cp / Pr) dT/dx_j; fv[c*5 + v] is the flux of variable v in direction c:
+// (0, tau_1c, tau_2c, tau_3c, u_i tau_ic + (mu Cp / Pr) dT/dx_c).
+template <class S>
+static void viscous_flux3(const S q[5], const S d[15], const Phys& ph, S fv[15]) {
+  const double Cp = ph.gamma / (ph.gamma - 1.0), k = ph.mu * Cp / ph.Pr;
+  S g[3][3];   // g[i][c] = d u_i / d x_c
+  for (int i = 0; i < 3; ++i)
+    for (int c = 0; c < 3; ++c) g[i][c] = d[c * 5 + 1 + i];
+  const S dv = g[0][0] + g[1][1] + g[2][2];
+  for (int c = 0; c < 3; ++c) {
+    S tau[3];
+    for (int i = 0; i < 3; ++i) {
+      tau[i] = ph.mu * (g[i][c] + g[c][i]);
+      if (i == c) tau[i] -= ph.mu * (2.0 / 3.0) * dv;
+    }
+    fv[c * 5 + 0] = 0.0;
+    for (int i = 0; i < 3; ++i) fv[c * 5 + 1 + i] = tau[i];
+    fv[c * 5 + 4] = q[1] * tau[0] + q[2] * tau[1] + q[3] * tau[2] + k * d[c * 5 + 4];
+  }
 }
 
 // ---- geometry of a hexahedron
@@ -1726,6 +1755,7 @@ struct LevelGeom3 {
   std::vector<double> J;     // (e, pt)
   std::vector<double> xyz;   // (e, pt, 3)
   std::vector<double> fS;    // (e, face, fp, 3): outward area-scaled normal
+  std::vector<double> fJ;    // (e, face, fp): |J| of the map at the face point
 };
 
 // Reference coordinates of face point (a, b) of face f.
@@ -1795,6 +1825,7 @@ struct OrcConfig3 {
   double res_scale[5];
   double q_inf[5];
   int refresh_always;
+  double mu, Pr;   // constant dynamic viscosity (0: Euler) and Prandtl number
 };
 
 struct Level3 {
@@ -1829,6 +1860,7 @@ static void build_level_geom3(Oracle3* o, int P, LevelGeom3* g) {
   g->J.assign((size_t)E * g->N, 0.0);
   g->xyz.assign((size_t)E * g->N * 3, 0.0);
   g->fS.assign((size_t)E * 6 * g->NF * 3, 0.0);
+  g->fJ.assign((size_t)E * 6 * g->NF, 0.0);
   for (int e = 0; e < E; ++e) {
     const double* xn = &o->nodes[(size_t)e * nn * 3];
     // W^n_k = X_l dX_m/dxi_k at the Gauss-Lobatto points, (n, m, l) cyclic
@@ -1861,12 +1893,17 @@ static void build_level_geom3(Oracle3* o, int P, LevelGeom3* g) {
     for (int f = 0; f < 6; ++f)
       for (int bb = 0; bb < n1; ++bb)
         for (int a = 0; a < n1; ++a) {
-          double r[3], Ja[3][3];
+          double r[3], Ja[3][3], X[3], dX[3][3];
           face_ref(g->b, f, a, bb, r);
           curl_metrics(gl, W, r, Ja);
           const double sg = (f & 1) ? 1.0 : -1.0;
           double* s = &g->fS[(((size_t)e * 6 + f) * g->NF + bb * n1 + a) * 3];
           for (int n = 0; n < 3; ++n) s[n] = sg * Ja[f / 2][n];
+          map3(Ng, xn, r, X, dX);
+          g->fJ[((size_t)e * 6 + f) * g->NF + bb * n1 + a] =
+              dX[0][0] * (dX[1][1] * dX[2][2] - dX[1][2] * dX[2][1]) -
+              dX[0][1] * (dX[1][0] * dX[2][2] - dX[1][2] * dX[2][0]) +
+              dX[0][2] * (dX[1][0] * dX[2][1] - dX[1][1] * dX[2][0]);
         }
   }
 }
@@ -1882,24 +1919,59 @@ static void trace_state3(const Basis1D& b, const S* qe, int N, int f, int a, int
   }
 }
 
-// Frozen neighbour traces at every element face point (5 values each).
+// Broken (uncorrected) gradient of one hexahedron's state at its solution
+// points: reference derivatives by the Lagrange derivative matrix, then the
+// chain rule grad q = (1/|J|) sum_i (J a^i) dq/dxi_i with the element's metric
+// terms.  g[(c*5 + v)*N + pt], c = x, y, z.
+template <class S>
+static void broken_gradient3(const Level3& L, int e, const S* qe, S* g) {
+  const Basis1D& b = L.g.b;
+  const int n1 = L.g.n1, N = L.g.N;
+  for (int v = 0; v < 5; ++v)
+    for (int kk = 0; kk < n1; ++kk)
+      for (int j = 0; j < n1; ++j)
+        for (int i = 0; i < n1; ++i) {
+          const int pt = (kk * n1 + j) * n1 + i;
+          S dr[3] = {0.0, 0.0, 0.0};
+          for (int m = 0; m < n1; ++m) {
+            dr[0] += b.D[i * n1 + m] * qe[v * N + (kk * n1 + j) * n1 + m];
+            dr[1] += b.D[j * n1 + m] * qe[v * N + (kk * n1 + m) * n1 + i];
+            dr[2] += b.D[kk * n1 + m] * qe[v * N + (m * n1 + j) * n1 + i];
+          }
+          const double* ja = &L.g.Ja[((size_t)e * N + pt) * 9];
+          const double J = L.g.J[(size_t)e * N + pt];
+          for (int c = 0; c < 3; ++c)
+            g[(c * 5 + v) * N + pt] = (ja[0 * 3 + c] * dr[0] + ja[1 * 3 + c] * dr[1] + ja[2 * 3 + c] * dr[2]) / J;
+        }
+}
+
+// Frozen neighbour data at every element face point, NT3 values each: the
+// neighbour's state trace (5), with mu > 0 its broken-gradient trace (15,
+// x, y, z per variable) and its |J| at that face point.
+static const int NT3 = 21;
+
 static void neighbour_traces3(const Oracle3* o, const Level3& L, const double* q, std::vector<double>& tr) {
   const int E = o->E, N = L.g.N, n1 = L.g.n1, NF = L.g.NF, P = L.g.P;
-  tr.assign((size_t)E * 6 * NF * 5, 0.0);
-  std::vector<double> qe(5 * N);
+  const bool visc = o->ph.mu > 0.0;
+  tr.assign((size_t)E * 6 * NF * NT3, 0.0);
+  std::vector<double> qe(5 * N), g(15 * N);
   for (int e = 0; e < E; ++e)
     for (int f = 0; f < 6; ++f) {
       const int en = o->nbr[(e * 6 + f) * 3], fn = o->nbr[(e * 6 + f) * 3 + 1], or_ = o->nbr[(e * 6 + f) * 3 + 2];
       if (en < 0) continue;
       for (int v = 0; v < 5; ++v)
         for (int p = 0; p < N; ++p) qe[v * N + p] = q[((size_t)v * E + en) * N + p];
+      if (visc) broken_gradient3<double>(L, en, qe.data(), g.data());
       for (int bb = 0; bb < n1; ++bb)
         for (int a = 0; a < n1; ++a) {
           int a2, b2;
           face_map3(or_, P, a, bb, &a2, &b2);
-          double t[5];
+          double* t = &tr[(((size_t)e * 6 + f) * NF + bb * n1 + a) * NT3];
           trace_state3<double>(L.g.b, qe.data(), N, fn, a2, b2, t);
-          for (int v = 0; v < 5; ++v) tr[(((size_t)e * 6 + f) * NF + bb * n1 + a) * 5 + v] = t[v];
+          if (visc) {
+            for (int c = 0; c < 3; ++c) trace_state3<double>(L.g.b, g.data() + c * 5 * N, N, fn, a2, b2, t + 5 + 5 * c);
+            t[20] = L.g.fJ[((size_t)en * 6 + fn) * NF + b2 * n1 + a2];
+          }
         }
     }
 }
@@ -1909,19 +1981,91 @@ static void neighbour_traces3(const Oracle3* o, const Level3& L, const double* q
 // derivative along each reference direction, and the DG correction of the
 // jumps between the common normal flux (Roe, through the outward J a^d of the
 // face point) and the extrapolated flux polynomial.  Neighbours frozen.
+//
+// With mu > 0 the flux is f_inv - f_vis, with the two-dimensional scheme
+// carried over direction by direction: at a solution point the viscous flux
+// takes the corrected gradient (reference derivatives plus the DG correction
+// of q_com - q^- on the two faces of each reference line, eq. com_q, then the
+// chain rule); at a face point it takes q_com and the common gradient of eq.
+// com_grad_q, the mean of both sides' broken gradients plus their BR2
+// liftings eta_f g'(1) (q_com - q^(+-)) S^(+-) / |J|^(+-) (S the outward
+// area-scaled normal, |J| the map's at the face point).  Boundary faces: the
+// ghost side mirrors the own gradient and |J|; walls carry no viscous energy
+// flux.
 template <class S>
 static void element_residual3(const Oracle3* o, const Level3& L, int e, const S* qe, const double* ntr, S* Re) {
   const Basis1D& b = L.g.b;
   const int P = L.g.P, n1 = L.g.n1, N = L.g.N, NF = L.g.NF;
   const Phys& ph = o->ph;
+  const bool visc = ph.mu > 0.0;
+  const double eta_f = 4.0, gface = 0.5 * n1 * n1;
+  // own and other-side traces and the common state at every face point
+  std::vector<S> qm_all(6 * NF * 5), qp_all(6 * NF * 5), qc_all(6 * NF * 5);
+  for (int f = 0; f < 6; ++f) {
+    const int en = o->nbr[(e * 6 + f) * 3], bc = o->nbr[(e * 6 + f) * 3 + 1];
+    for (int fp = 0; fp < NF; ++fp) {
+      const int a = fp % n1, bb = fp / n1;
+      S* qm = &qm_all[(f * NF + fp) * 5];
+      S* qp = &qp_all[(f * NF + fp) * 5];
+      trace_state3(b, qe, N, f, a, bb, qm);
+      const double* Sv = &L.g.fS[(((size_t)e * 6 + f) * NF + fp) * 3];
+      if (en < 0) {
+        double dS = std::sqrt(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
+        double nu[3] = {Sv[0] / dS, Sv[1] / dS, Sv[2] / dS};
+        ghost_state3(bc, qm, nu, o->cfg.q_inf, qp);
+      } else {
+        const double* t = &ntr[(((size_t)e * 6 + f) * NF + fp) * NT3];
+        for (int v = 0; v < 5; ++v) qp[v] = t[v];
+      }
+      for (int v = 0; v < 5; ++v) qc_all[(f * NF + fp) * 5 + v] = 0.5 * (qm[v] + qp[v]);
+    }
+  }
+  // corrected gradients at the solution points
+  std::vector<S> gb, gc;
+  if (visc) {
+    gb.resize(15 * N);
+    gc.resize(15 * N);
+    broken_gradient3<S>(L, e, qe, gb.data());
+    for (int v = 0; v < 5; ++v)
+      for (int kk = 0; kk < n1; ++kk)
+        for (int j = 0; j < n1; ++j)
+          for (int i = 0; i < n1; ++i) {
+            const int pt = (kk * n1 + j) * n1 + i, idx[3] = {i, j, kk};
+            S dr[3] = {0.0, 0.0, 0.0};
+            for (int m = 0; m < n1; ++m) {
+              dr[0] += b.D[i * n1 + m] * qe[v * N + (kk * n1 + j) * n1 + m];
+              dr[1] += b.D[j * n1 + m] * qe[v * N + (kk * n1 + m) * n1 + i];
+              dr[2] += b.D[kk * n1 + m] * qe[v * N + (m * n1 + j) * n1 + i];
+            }
+            for (int d = 0; d < 3; ++d) {
+              // face point of the line through pt on the faces 2d and 2d + 1
+              const int a = d == 0 ? j : i, bb = d == 2 ? j : kk, fp = bb * n1 + a;
+              const int fL = 2 * d, fR = 2 * d + 1;
+              dr[d] += b.gL[idx[d]] * (qc_all[(fL * NF + fp) * 5 + v] - qm_all[(fL * NF + fp) * 5 + v]) +
+                       b.gR[idx[d]] * (qc_all[(fR * NF + fp) * 5 + v] - qm_all[(fR * NF + fp) * 5 + v]);
+            }
+            const double* ja = &L.g.Ja[((size_t)e * N + pt) * 9];
+            const double J = L.g.J[(size_t)e * N + pt];
+            for (int c = 0; c < 3; ++c)
+              gc[(c * 5 + v) * N + pt] = (ja[0 * 3 + c] * dr[0] + ja[1 * 3 + c] * dr[1] + ja[2 * 3 + c] * dr[2]) / J;
+          }
+  }
   std::vector<S> Ft(3 * 5 * N);   // [i][v][pt]
   for (int pt = 0; pt < N; ++pt) {
     S q[5];
     for (int v = 0; v < 5; ++v) q[v] = qe[v * N + pt];
+    S fv[15];
+    if (visc) {
+      S d[15];
+      for (int c = 0; c < 15; ++c) d[c] = gc[c * N + pt];
+      viscous_flux3(q, d, ph, fv);
+    }
     for (int i = 0; i < 3; ++i) {
       const double* ja = &L.g.Ja[((size_t)e * N + pt) * 9 + i * 3];
       S f[5];
       euler_flux3(q, ja, ph, f);
+      if (visc)
+        for (int v = 0; v < 5; ++v) f[v] -= ja[0] * fv[v] + ja[1] * fv[5 + v] + ja[2] * fv[10 + v];
       for (int v = 0; v < 5; ++v) Ft[(i * 5 + v) * N + pt] = f[v];
     }
   }
@@ -1940,6 +2084,7 @@ static void element_residual3(const Oracle3* o, const Level3& L, int e, const S*
         }
   for (int f = 0; f < 6; ++f) {
     const int en = o->nbr[(e * 6 + f) * 3], bc = o->nbr[(e * 6 + f) * 3 + 1];
+    const bool bnd = en < 0;
     const int d = f / 2;
     const double sg = (f & 1) ? 1.0 : -1.0;
     const std::vector<double>& l = (f & 1) ? b.lp : b.lm;
@@ -1947,18 +2092,28 @@ static void element_residual3(const Oracle3* o, const Level3& L, int e, const S*
     for (int bb = 0; bb < n1; ++bb)
       for (int a = 0; a < n1; ++a) {
         const int fp = bb * n1 + a;
-        S qm[5], qp[5], fo[5];
-        trace_state3(b, qe, N, f, a, bb, qm);
+        S fo[5];
+        const S* qm = &qm_all[(f * NF + fp) * 5];
+        const S* qp = &qp_all[(f * NF + fp) * 5];
         const double* Sv = &L.g.fS[(((size_t)e * 6 + f) * NF + fp) * 3];
-        if (en < 0) {
-          double dS = std::sqrt(Sv[0] * Sv[0] + Sv[1] * Sv[1] + Sv[2] * Sv[2]);
-          double nu[3] = {Sv[0] / dS, Sv[1] / dS, Sv[2] / dS};
-          ghost_state3(bc, qm, nu, o->cfg.q_inf, qp);
-        } else {
-          const double* t = &ntr[(((size_t)e * 6 + f) * NF + fp) * 5];
-          for (int v = 0; v < 5; ++v) qp[v] = t[v];
-        }
         roe_flux3(qm, qp, Sv, ph, fo);
+        if (visc) {
+          const double* t = &ntr[(((size_t)e * 6 + f) * NF + fp) * NT3];
+          const double Jm = L.g.fJ[((size_t)e * 6 + f) * NF + fp], Jp = bnd ? Jm : t[20];
+          S gm[15], gpv[15], dcom[15], qcm[5], fv[15];
+          for (int c = 0; c < 3; ++c) trace_state3(b, gb.data() + c * 5 * N, N, f, a, bb, gm + 5 * c);
+          for (int c = 0; c < 15; ++c) gpv[c] = bnd ? gm[c] : S(t[5 + c]);
+          for (int v = 0; v < 5; ++v) {
+            const S qcv = qc_all[(f * NF + fp) * 5 + v];
+            qcm[v] = qcv;
+            const S rm = eta_f * gface * (qcv - qm[v]) / Jm;   // times S_out
+            const S rp = eta_f * gface * (qcv - qp[v]) / Jp;   // times -S_out
+            for (int c = 0; c < 3; ++c) dcom[c * 5 + v] = 0.5 * (gm[c * 5 + v] + gpv[c * 5 + v] + (rm - rp) * Sv[c]);
+          }
+          viscous_flux3(qcm, dcom, ph, fv);
+          const int nv = (bnd && bc != 4) ? 4 : 5;   // walls: no viscous energy flux
+          for (int v = 0; v < nv; ++v) fo[v] -= fv[v] * Sv[0] + fv[5 + v] * Sv[1] + fv[10 + v] * Sv[2];
+        }
         for (int v = 0; v < 5; ++v) {
           S loc = 0.0;
           for (int m = 0; m < n1; ++m) loc += l[m] * Ft[(d * 5 + v) * N + line_pt3(P, f, a, bb, m)];
@@ -2186,10 +2341,19 @@ void* orc3_create(const OrcConfig3* cfg, int E, int Ng, const double* nodes, con
   Oracle3* o = new Oracle3();
   o->cfg = *cfg;
   o->ph.gamma = cfg->gamma; o->ph.Ma_inf = cfg->Ma_inf; o->ph.kappa = cfg->kappa; o->ph.cutoff = cfg->cutoff;
+  o->ph.mu = cfg->mu; o->ph.Pr = cfg->Pr > 0.0 ? cfg->Pr : 0.72;
   o->E = E; o->Ng = Ng;
   const int nn = (Ng + 1) * (Ng + 1) * (Ng + 1);
   o->nodes.assign(nodes, nodes + (size_t)E * nn * 3);
   o->nbr.assign(nbr, nbr + (size_t)E * 18);
+  for (int i = 0; i < E * 6; ++i) {
+    const int en = nbr[i * 3], fn = nbr[i * 3 + 1], orient = nbr[i * 3 + 2];
+    // as in 2D: slip walls for inviscid runs only, no-slip walls need the cut-off
+    const bool ok = en >= 0 ? (en < E && fn >= 0 && fn < 6 && orient >= 0 && orient < 8)
+                            : (en == -1 && fn >= 2 && fn <= 4 && !(fn == 2 && cfg->mu > 0) &&
+                               !(fn == 3 && !(cfg->cutoff && cfg->kappa * cfg->Ma_inf > 0)));
+    if (!ok) { delete o; return nullptr; }
+  }
   o->lev.resize(cfg->n_levels);
   for (int l = 0; l < cfg->n_levels; ++l) {
     build_level_geom3(o, cfg->P[l], &o->lev[l].g);
