@@ -177,10 +177,12 @@ typedef struct {
                      same rules; dtau may differ in the last bits (device
                      pow). */
   int dim;        /* 2 (or 0): quadrilaterals, q_p = (p, u, v, T);
-                     3: hexahedra, q_p = (p, u, v, w, T), inviscid (mu = 0),
+                     3: hexahedra, q_p = (p, u, v, w, T), Euler (mu = 0) or
+                     Navier-Stokes (mu > 0, the same BR2 viscous terms),
                      binary64 residual throughout (flux_prec is not used),
-                     0 <= P <= 3, slip-wall and far-field boundary faces,
-                     dtau set directly (cfl_mode = 0) */
+                     0 <= P <= 3, slip-wall (mu = 0), no-slip-wall (eps
+                     cut-off) and far-field boundary faces, dtau set
+                     directly (cfl_mode = 0) */
   double res_scale3[5]; /* dim = 3: reference scale of each of the five
                      equations in ||F|| (res_scale is not used) */
   double q_inf3[5];     /* dim = 3: free stream (p absolute, u, v, w, T) of
@@ -471,7 +473,8 @@ pmg_status pmg_autotune(pmg_ctx* ctx, int reps, const char* cache_path, pmg_tune
  * no cudaMalloc, cudaFree or other allocating call, on the device or the
  * host.  Its scratch is a copy of q and the common face fluxes, 4 E N +
  * 16 E (P+1) doubles, plus with mu > 0 the broken gradients and face jumps of
- * the viscous terms, 6 E N + 12 E (P+1) more.  It lives in one static device
+ * the viscous terms, 6 E N + 12 E (P+1) more (hexahedra: 5 E N + 30 E NF,
+ * and 12 E N + 24 E NF, NF = (P+1)^2).  It lives in one static device
  * array of 2^21 doubles (16 MiB) that every GPU loading this library holds
  * until the process exits; a level that needs more returns PMG_EINVAL with
  * the sizes in the message.

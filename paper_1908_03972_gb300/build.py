@@ -20,7 +20,7 @@ BUILD_DIR = os.path.join(HERE, "_build", platform.machine())
 ARCH_STAMP = os.path.join(OUT_DIR, ".arch")
 
 CUDA_SOURCES = ["k_residual.cu", "k_volume_dw.cu", "k_blocks.cu", "k_misc.cu", "k_fused.cu", "k_viscous.cu", "k_loop.cu", "k_krylov.cu", "k_factor_cluster.cu",
-                "k3_residual.cu", "k3_blocks.cu", "k3_misc.cu", "k_tile.cu", "api.cu"]
+                "k3_residual.cu", "k3_blocks.cu", "k3_misc.cu", "k3_viscous.cu", "k_tile.cu", "api.cu"]
 CXX_SOURCES = ["host_tables.cpp", "host_tables3.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -183,7 +183,6 @@ pmg_status pmg_create(const pmg_config* cfg, void* stream, pmg_ctx** out) {
   if (cfg->refresh_every < 1) return fail(PMG_EINVAL, "refresh_every must be >= 1");
   if (cfg->dim != 0 && cfg->dim != 2 && cfg->dim != 3) return fail(PMG_EINVAL, "dim must be 2 or 3 (0 means 2)");
   if (cfg->dim == 3) {
-    if (cfg->mu != 0.0) return fail(PMG_EINVAL, "hexahedral runs are inviscid (mu = 0)");
     if (cfg->cfl_mode) return fail(PMG_EINVAL, "hexahedral runs set dtau directly (cfl_mode = 0)");
     for (int l = 0; l < cfg->n_levels; ++l)
       if (cfg->P[l] > 3) return fail(PMG_EINVAL, "hexahedral levels take P <= 3");
@@ -342,7 +341,6 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
     if (m->nbr[i * 3] != -1) continue;
     const int bc = m->nbr[i * 3 + 1];
     if (bc == PMG_BC_SLIP_WALL && c.ph.mu > 0.0) return fail(PMG_EINVAL, "slip walls are for mu = 0 only");
-    if (bc == PMG_BC_NOSLIP_WALL && c.dim == 3) return fail(PMG_EINVAL, "hexahedral meshes take no no-slip walls");
     if (bc == PMG_BC_NOSLIP_WALL && !(c.ph.eps_min > 0.0))
       return fail(PMG_EINVAL, "a no-slip wall needs the eps cut-off (cutoff = 1, kappa Ma_inf > 0)");
     if (bc == PMG_BC_FARFIELD && !(c.ph.qinf[0] > 0.0 && c.ph.qinf[T_slot] > 0.0))
@@ -449,8 +447,9 @@ pmg_status pmg_upload_mesh(pmg_ctx* h, const pmg_mesh* m) {
       }
     }
     if (c.ph.mu > 0.0) {
-      if (dalloc(&L.Gb, (size_t)6 * c.E * L.N) || dalloc(&L.Qj, (size_t)3 * c.E * 4 * L.n1) ||
-          dalloc(&L.fJinv, geo[l].fJinv.size()))
+      const size_t ng = c.dim == 3 ? (size_t)12 * c.E * L.N : (size_t)6 * c.E * L.N;
+      const size_t nj = c.dim == 3 ? (size_t)4 * c.E * 6 * L.NF : (size_t)3 * c.E * 4 * L.n1;
+      if (dalloc(&L.Gb, ng) || dalloc(&L.Qj, nj) || dalloc(&L.fJinv, geo[l].fJinv.size()))
         return fail(PMG_ENOMEM, "device allocation failed for level data");
       PMG_CK(cudaMemcpy(L.fJinv, geo[l].fJinv.data(), geo[l].fJinv.size() * 8, cudaMemcpyHostToDevice));
     }
@@ -1516,7 +1515,9 @@ pmg_status pmg_residual_static(pmg_ctx* h, int level, const double* q, double* R
   LevelDev L = c.lev[level];   // shallow copy: only the scratch slots are redirected
   const bool visc = c.ph.mu > 0.0;
   const size_t n_state = L.tot, n_face = (size_t)c.nv * c.E * c.nfc * L.NF;
-  const size_t n_visc = visc ? (size_t)6 * c.E * L.N + (size_t)3 * c.E * 4 * L.n1 : 0;
+  const size_t n_grad = (size_t)(c.dim == 3 ? 12 : 6) * c.E * L.N;
+  const size_t n_jump = c.dim == 3 ? (size_t)4 * c.E * 6 * L.NF : (size_t)3 * c.E * 4 * L.n1;
+  const size_t n_visc = visc ? n_grad + n_jump : 0;
   if (n_state + n_face + n_visc > kStaticScratchDoubles)
     return fail(PMG_EINVAL, "pmg_residual_static: level needs " + std::to_string(n_state + n_face + n_visc) +
                                 " scratch doubles, the static scratch holds " +
@@ -1530,7 +1531,7 @@ pmg_status pmg_residual_static(pmg_ctx* h, int level, const double* q, double* R
   L.Fcom = scratch + n_state;
   if (visc) {   // broken gradients and face jumps of the viscous terms
     L.Gb = scratch + n_state + n_face;
-    L.Qj = L.Gb + (size_t)6 * c.E * L.N;
+    L.Qj = L.Gb + n_grad;
   }
   PMG_CK(cudaMemcpyAsync(qs, q, n_state * 8, cudaMemcpyDeviceToDevice, c.stream));
   launch_shift_pressure(n_state / c.nv, -c.ph.p_ref, qs, c.stream);

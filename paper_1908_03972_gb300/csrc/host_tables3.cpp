@@ -119,8 +119,8 @@ void build_faces3(MeshHost& m) {
     for (int f = 0; f < 6; ++f) {
       const int* nb = &m.nbr[(size_t)(e * 6 + f) * 3];
       if (nb[0] < 0) {
-        if (nb[1] != PMG_BC_SLIP_WALL && nb[1] != PMG_BC_FARFIELD)
-          throw std::runtime_error("hexahedral meshes take slip-wall (2) and far-field (4) boundary faces");
+        if (nb[1] != PMG_BC_SLIP_WALL && nb[1] != PMG_BC_NOSLIP_WALL && nb[1] != PMG_BC_FARFIELD)
+          throw std::runtime_error("hexahedral boundary faces are slip walls (2), no-slip walls (3) or far field (4)");
         m.faces.push_back({e, f, -1, nb[1], 0});
         continue;
       }
@@ -142,6 +142,7 @@ void build_level_geometry3(const MeshHost& m, const Ref1D& r, LevelGeomHost& g) 
   g.met.assign(10 * plane, 0.0);
   g.xy.assign(plane * 3, 0.0);
   g.face.assign((size_t)E * 6 * NF * 4, 0.0);
+  g.fJinv.assign((size_t)E * 6 * NF, 0.0);
   std::vector<double> W((size_t)ng * ng * ng * 9);
   for (int e = 0; e < E; ++e) {
     const double* xn = &m.nodes[(size_t)e * nn * 3];
@@ -193,6 +194,14 @@ void build_level_geometry3(const MeshHost& m, const Ref1D& r, LevelGeomHost& g) 
           o[1] = S[1] / dS;
           o[2] = S[2] / dS;
           o[3] = dS;
+          // 1/|J| of the map at the face point (the BR2 lifting's scale)
+          double X[3], dX[3][3];
+          hex_map(Ng, xn, rr, X, dX);
+          const double J = dX[0][0] * (dX[1][1] * dX[2][2] - dX[1][2] * dX[2][1]) -
+                           dX[0][1] * (dX[1][0] * dX[2][2] - dX[1][2] * dX[2][0]) +
+                           dX[0][2] * (dX[1][0] * dX[2][1] - dX[1][1] * dX[2][0]);
+          if (!(J > 0.0)) throw std::runtime_error("hexahedron with non-positive Jacobian on a face");
+          g.fJinv[((size_t)e * 6 + f) * NF + b * n1 + a] = 1.0 / J;
         }
     }
   }

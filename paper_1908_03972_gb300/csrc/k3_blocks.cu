@@ -154,6 +154,7 @@ void launch_assemble3(const Ctx& c, const LevelDev& L, const double* q, const do
     default: PMG_A3(3); break;
   }
 #undef PMG_A3
+  if (c.ph.mu > 0.0) launch_assemble_visc3(c, L, q, s);
 }
 
 template <class W, int P>
@@ -226,6 +227,7 @@ cudaError_t prepare_kernels3(const Ctx& c) {
     }
     if (e != cudaSuccess) return e;
   }
+  if (c.ph.mu > 0.0) return prepare_assemble_visc3();
   return cudaSuccess;
 }
 

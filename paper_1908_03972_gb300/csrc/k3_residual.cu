@@ -60,11 +60,21 @@ __device__ __forceinline__ void line_trace3(const double* __restrict__ q, size_t
   }
 }
 
-template <int P>
+// With VISC (mu > 0) the face launch also forms the viscous common flux of
+// eq. com_grad_q at q_com: the mean of both sides' broken-gradient traces
+// (Gb, extrapolated along each side's normal line; a boundary mirrors the
+// element) plus the BR2 lifting pen (1/|J|^- + 1/|J|^+)/4 dS n (q^+ - q^-);
+// walls carry no viscous energy flux.  It writes q_com - q_own of
+// (u, v, w, T) for both elements (Qj), the jumps the volume launch's
+// corrected gradient takes.
+template <int P, bool VISC>
 __global__ void __launch_bounds__(64) face_flux3_kernel(const int* __restrict__ faces, int n_faces, int E,
                                                         const double* __restrict__ q,
                                                         const double* __restrict__ face,
-                                                        double* __restrict__ Fcom, OpTab op, Phys ph) {
+                                                        double* __restrict__ Fcom, OpTab op, Phys ph,
+                                                        const double* __restrict__ Gb,
+                                                        const double* __restrict__ fJinv,
+                                                        double* __restrict__ Qj) {
   constexpr int n1 = P + 1, N = n1 * n1 * n1, NF = n1 * n1;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= n_faces * NF) return;
@@ -95,6 +105,11 @@ __global__ void __launch_bounds__(64) face_flux3_kernel(const int* __restrict__ 
     sp[2] = ph.qinf[2];
     sp[3] = ph.qinf[3];
     sp[4] = ph.qinf[4] - ref[4];
+  } else if (fR == PMG_BC_NOSLIP_WALL) {   // same p and T, velocity reversed
+    sp[0] = sm[0];
+    sp[4] = sm[4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) sp[1 + c] = -sm[1 + c];
   } else {   // slip wall: same p and T, normal velocity reflected
     const double un = sm[1] * nrm[0] + sm[2] * nrm[1] + sm[3] * nrm[2];
     sp[0] = sm[0];
@@ -116,6 +131,51 @@ __global__ void __launch_bounds__(64) face_flux3_kernel(const int* __restrict__ 
   roe3_flux_jump(qm, qp, dq, pgm, pgp, nrm, dS, ph, out);
   const size_t fplane = (size_t)E * 6 * NF;
   const size_t iL = ((size_t)eL * 6 + fL) * NF + fp;
+  if (VISC) {
+    double gm[12], gp[12];
+    const double* bL = Gb + (size_t)eL * N;
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+      double t = 0.0;
+#pragma unroll
+      for (int m = 0; m < n1; ++m)
+        t = fma((fL & 1) ? lp[m] : lm[m], __ldg(bL + c * plane + line_pt3<P>(fL, a, b, m)), t);
+      gm[c] = t;
+      gp[c] = t;
+    }
+    double iJp = __ldg(fJinv + iL);
+    const double iJm = iJp;
+    if (!bnd) {
+      const int a2 = fp2 % n1, b2 = fp2 / n1;
+      const double* bR = Gb + (size_t)eR * N;
+#pragma unroll
+      for (int c = 0; c < 12; ++c) {
+        double t = 0.0;
+#pragma unroll
+        for (int m = 0; m < n1; ++m)
+          t = fma((fR & 1) ? lp[m] : lm[m], __ldg(bR + c * plane + line_pt3<P>(fR, a2, b2, m)), t);
+        gp[c] = t;
+      }
+      iJp = __ldg(fJinv + ((size_t)eR * 6 + fR) * NF + fp2);
+    }
+    const double wl = 0.25 * op.pen * (iJm + iJp) * dS;
+    double gc[12], fv[12];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) gc[c * 4 + k] = fma(wl * nrm[c], dq[k + 1], 0.5 * (gm[c * 4 + k] + gp[c * 4 + k]));
+    const double uc[3] = {0.5 * (qm[1] + qp[1]), 0.5 * (qm[2] + qp[2]), 0.5 * (qm[3] + qp[3])};
+    viscous_flux3(uc, gc, ph, fv);
+    const int nr = (bnd && fR != PMG_BC_FARFIELD) ? 3 : 4;   // walls: no viscous energy flux
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (r < nr) out[r + 1] -= (fv[r] * nrm[0] + fv[4 + r] * nrm[1] + fv[8 + r] * nrm[2]) * dS;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      Qj[k * fplane + iL] = 0.5 * dq[k + 1];
+      if (!bnd) Qj[k * fplane + ((size_t)eR * 6 + fR) * NF + fp2] = -0.5 * dq[k + 1];
+    }
+  }
 #pragma unroll
   for (int v = 0; v < 5; ++v) Fcom[v * fplane + iL] = out[v];
   if (!bnd) {
@@ -125,9 +185,15 @@ __global__ void __launch_bounds__(64) face_flux3_kernel(const int* __restrict__ 
   }
 }
 
-template <int P, class W, bool APPLY>
+// With VISC the contravariant fluxes take f_inv - f_vis: the viscous flux at
+// each solution point from the corrected gradient, the reference derivatives
+// of (u, v, w, T) plus the DG correction of the face jumps Qj on the two faces
+// of each line through the point (eq. com_q), then the chain rule with the
+// metric terms.
+template <int P, class W, bool APPLY, bool VISC>
 __global__ void __launch_bounds__(64) volume3_kernel(int E, const double* q, const double* __restrict__ met,
-                                                     const double* __restrict__ Fcom, OpTab op, Phys ph,
+                                                     const double* __restrict__ Fcom, const double* __restrict__ Qj,
+                                                     OpTab op, Phys ph,
                                                      double* __restrict__ out, int mode, double inv_odt,
                                                      const double* __restrict__ src, const double* __restrict__ S,
                                                      double* __restrict__ Sout, const double* __restrict__ Pd,
@@ -141,6 +207,7 @@ __global__ void __launch_bounds__(64) volume3_kernel(int E, const double* q, con
   __shared__ Acc sr[APPLY ? EPB : 1][APPLY ? n : 1];
   __shared__ double sD[n1][n1], sgL[n1], sgR[n1], slm[n1], slp[n1];
   __shared__ double sred[2];
+  __shared__ double sV[VISC ? EPB : 1][4][VISC ? N : 1];   // u, v, w, T of the element
   const int le = threadIdx.x / N, pt = threadIdx.x - le * N;
   const int e = blockIdx.x * EPB + le;
   const bool active = (le < EPB) && (e < E);
@@ -159,14 +226,53 @@ __global__ void __launch_bounds__(64) volume3_kernel(int E, const double* q, con
 #pragma unroll
     for (int v = 0; v < 5; ++v) qq[v] = q[v * plane + gi];
     invJ = __ldg(met + 9 * plane + gi);
+    if (VISC)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) sV[VISC ? le : 0][k][VISC ? pt : 0] = qq[k + 1];
+  }
+  if (VISC) __syncthreads();
+  if (active) {
     double qa[5] = {qq[0] + ph.p_ref, qq[1], qq[2], qq[3], qq[4]};
     rho_pt = qa[0] * s_rcp(qa[4]);
+    double ja[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ja[i][c] = __ldg(met + (3 * i + c) * plane + gi);
+    double fv[12];
+    if (VISC) {
+      const int i = pt % n1, j = (pt / n1) % n1, k = pt / (n1 * n1);
+      const int idx[3] = {i, j, k}, fpd[3] = {k * n1 + j, k * n1 + i, j * n1 + i};
+      double g[12];
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const double* V = sV[VISC ? le : 0][w];
+        double dr[3] = {0.0, 0.0, 0.0};
+        const double r0 = V[(k * n1 + j) * n1], r1 = V[k * n1 * n1 + i], r2 = V[j * n1 + i];
+#pragma unroll
+        for (int m = 0; m < n1; ++m) {
+          dr[0] = fma(sD[i][m], V[(k * n1 + j) * n1 + m] - r0, dr[0]);
+          dr[1] = fma(sD[j][m], V[(k * n1 + m) * n1 + i] - r1, dr[1]);
+          dr[2] = fma(sD[k][m], V[(m * n1 + j) * n1 + i] - r2, dr[2]);
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          dr[d] = fma(sgL[idx[d]], __ldg(Qj + w * fplane + ((size_t)e * 6 + 2 * d) * NF + fpd[d]), dr[d]);
+          dr[d] = fma(sgR[idx[d]], __ldg(Qj + w * fplane + ((size_t)e * 6 + 2 * d + 1) * NF + fpd[d]), dr[d]);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) g[c * 4 + w] = invJ * (ja[0][c] * dr[0] + ja[1][c] * dr[1] + ja[2][c] * dr[2]);
+      }
+      const double uvw[3] = {qq[1], qq[2], qq[3]};
+      viscous_flux3(uvw, g, ph, fv);
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      const double ja[3] = {__ldg(met + (3 * i) * plane + gi), __ldg(met + (3 * i + 1) * plane + gi),
-                            __ldg(met + (3 * i + 2) * plane + gi)};
       double f[5];
-      flux3_n(qa, qq[0], ja, ph, f);
+      flux3_n(qa, qq[0], ja[i], ph, f);
+      if (VISC)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) f[r + 1] -= ja[i][0] * fv[r] + ja[i][1] * fv[4 + r] + ja[i][2] * fv[8 + r];
 #pragma unroll
       for (int v = 0; v < 5; ++v) sF[le][i][v][pt] = f[v];
     }
@@ -292,10 +398,65 @@ int residual_blocks_for3(int P, int E) {
   return (E + epb - 1) / epb;
 }
 
+// Broken gradient of (u, v, w, T) at every solution point of hexahedra:
+// Gb[(c*4 + k) * E N + e N + pt], c = x, y, z, by the Lagrange derivative
+// along the three lines through the point (of the differences to each line's
+// first value: the derivative matrix annihilates constants, which keeps
+// T ~ 1/Ma^2 out of the rounding) and the chain rule with J a^i / |J|.
+template <int P>
+__global__ void __launch_bounds__(128) grad3_kernel(int E, const double* __restrict__ q,
+                                                    const double* __restrict__ met, OpTab op,
+                                                    double* __restrict__ Gb) {
+  constexpr int n1 = P + 1, N = n1 * n1 * n1;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= E * N) return;
+  const int e = tid / N, pt = tid - e * N, i = pt % n1, j = (pt / n1) % n1, k = pt / (n1 * n1);
+  const size_t plane = (size_t)E * N;
+  double ja[3][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ja[d][c] = __ldg(met + (3 * d + c) * plane + tid);
+  const double iJ = __ldg(met + 9 * plane + tid);
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    const double* V = q + (w + 1) * plane + (size_t)e * N;
+    const double r0 = __ldg(V + (k * n1 + j) * n1), r1 = __ldg(V + k * n1 * n1 + i), r2 = __ldg(V + j * n1 + i);
+    double dr[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int m = 0; m < n1; ++m) {
+      dr[0] = fma(op.D[i][m], __ldg(V + (k * n1 + j) * n1 + m) - r0, dr[0]);
+      dr[1] = fma(op.D[j][m], __ldg(V + (k * n1 + m) * n1 + i) - r1, dr[1]);
+      dr[2] = fma(op.D[k][m], __ldg(V + (m * n1 + j) * n1 + i) - r2, dr[2]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Gb[(c * 4 + w) * plane + tid] = iJ * (ja[0][c] * dr[0] + ja[1][c] * dr[1] + ja[2][c] * dr[2]);
+  }
+}
+
+void launch_grad3(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s) {
+  const int total = c.E * L.N, threads = 128, blocks = (total + threads - 1) / threads;
+#define PMG_G3(PP) grad3_kernel<PP><<<blocks, threads, 0, s>>>(c.E, q, L.met, L.op, L.Gb)
+  switch (L.P) {
+    case 0: PMG_G3(0); break;
+    case 1: PMG_G3(1); break;
+    case 2: PMG_G3(2); break;
+    default: PMG_G3(3); break;
+  }
+#undef PMG_G3
+}
+
 void launch_face_flux3(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s) {
   const int total = c.n_faces * L.NF, threads = 64, blocks = (total + threads - 1) / threads;
-#define PMG_F3(PP) \
-  face_flux3_kernel<PP><<<blocks, threads, 0, s>>>(c.d_faces, c.n_faces, c.E, q, L.face, L.Fcom, L.op, c.ph)
+  const bool visc = c.ph.mu > 0.0;
+  if (visc) launch_grad3(c, L, q, s);
+#define PMG_F3(PP)                                                                                                \
+  if (visc)                                                                                                       \
+    face_flux3_kernel<PP, true><<<blocks, threads, 0, s>>>(c.d_faces, c.n_faces, c.E, q, L.face, L.Fcom, L.op,   \
+                                                           c.ph, L.Gb, L.fJinv, L.Qj);                           \
+  else                                                                                                            \
+    face_flux3_kernel<PP, false><<<blocks, threads, 0, s>>>(c.d_faces, c.n_faces, c.E, q, L.face, L.Fcom, L.op,  \
+                                                            c.ph, nullptr, nullptr, nullptr)
   switch (L.P) {
     case 0: PMG_F3(0); break;
     case 1: PMG_F3(1); break;
@@ -309,10 +470,16 @@ void launch_volume3(const Ctx& c, const LevelDev& L, const double* q, double* ou
                     const double* src, const double* S, double* Sout, const double* Pd, double* partial,
                     cudaStream_t s, const double* qn) {
   const int blocks = residual_blocks_for3(L.P, c.E);
-#define PMG_V3(PP)                                                                                          \
-  volume3_kernel<PP, double, false><<<blocks, threads3<PP>(), 0, s>>>(c.E, q, L.met, L.Fcom, L.op, c.ph, out, \
-                                                                       (int)mode, inv_odt, src, S, Sout, Pd, qn, \
-                                                                       partial, nullptr, nullptr, nullptr, nullptr)
+  const bool visc = c.ph.mu > 0.0;
+#define PMG_V3(PP)                                                                                               \
+  if (visc)                                                                                                      \
+    volume3_kernel<PP, double, false, true><<<blocks, threads3<PP>(), 0, s>>>(                                  \
+        c.E, q, L.met, L.Fcom, L.Qj, L.op, c.ph, out, (int)mode, inv_odt, src, S, Sout, Pd, qn, partial, nullptr, \
+        nullptr, nullptr, nullptr);                                                                              \
+  else                                                                                                           \
+    volume3_kernel<PP, double, false, false><<<blocks, threads3<PP>(), 0, s>>>(                                 \
+        c.E, q, L.met, L.Fcom, nullptr, L.op, c.ph, out, (int)mode, inv_odt, src, S, Sout, Pd, qn, partial,      \
+        nullptr, nullptr, nullptr, nullptr)
   switch (L.P) {
     case 0: PMG_V3(0); break;
     case 1: PMG_V3(1); break;
@@ -327,10 +494,16 @@ static void volume_apply3_dispatch(const Ctx& c, const LevelDev& L, double* q, d
                                    const double* S, const double* qn, cudaStream_t s) {
   const int blocks = residual_blocks_for3(L.P, c.E);
   const W* Dinv = (const W*)L.Dinv;
-#define PMG_VA3(PP)                                                                                              \
-  volume3_kernel<PP, W, true><<<blocks, threads3<PP>(), 0, s>>>(c.E, q, L.met, L.Fcom, L.op, c.ph, nullptr,       \
-                                                                 (int)RES_SYSTEM, inv_odt, src, S, nullptr, nullptr, \
-                                                                 qn, nullptr, q, Dinv, L.rs, L.cs)
+  const bool visc = c.ph.mu > 0.0;
+#define PMG_VA3(PP)                                                                                             \
+  if (visc)                                                                                                     \
+    volume3_kernel<PP, W, true, true><<<blocks, threads3<PP>(), 0, s>>>(                                       \
+        c.E, q, L.met, L.Fcom, L.Qj, L.op, c.ph, nullptr, (int)RES_SYSTEM, inv_odt, src, S, nullptr, nullptr, qn, \
+        nullptr, q, Dinv, L.rs, L.cs);                                                                          \
+  else                                                                                                          \
+    volume3_kernel<PP, W, true, false><<<blocks, threads3<PP>(), 0, s>>>(                                      \
+        c.E, q, L.met, L.Fcom, nullptr, L.op, c.ph, nullptr, (int)RES_SYSTEM, inv_odt, src, S, nullptr, nullptr, \
+        qn, nullptr, q, Dinv, L.rs, L.cs)
   switch (L.P) {
     case 0: PMG_VA3(0); break;
     case 1: PMG_VA3(1); break;

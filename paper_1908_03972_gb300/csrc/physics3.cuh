@@ -140,11 +140,36 @@ __host__ __device__ inline void ghost_state3(int bc, const S qm[5], const double
     for (int v = 0; v < 5; ++v) qg[v] = S(ph.qinf[v]);
     return;
   }
-  const S un = qm[1] * n[0] + qm[2] * n[1] + qm[3] * n[2];
   qg[0] = qm[0];
   qg[4] = qm[4];
+  if (bc == 3) {   // no-slip adiabatic wall: velocity reversed
+#pragma unroll
+    for (int c = 0; c < 3; ++c) qg[1 + c] = -qm[1 + c];
+    return;
+  }
+  const S un = qm[1] * n[0] + qm[2] * n[1] + qm[3] * n[2];
 #pragma unroll
   for (int c = 0; c < 3; ++c) qg[1 + c] = qm[1 + c] - 2.0 * un * n[c];
+}
+
+// Viscous fluxes in 3D (Section 2.1) from the velocity (u0, u1, u2) and the
+// gradients g[c*4 + k] = d(u, v, w, T)_k / dx_c: the stress tau_ij =
+// mu (du_i/dx_j + du_j/dx_i) - (2/3) mu div(u) delta_ij and the heat flux
+// kT dT/dx_c.  fv[c*4 + r] is the flux in direction c of row r + 1 (x-, y-,
+// z-momentum, energy: u_i tau_ic + kT dT/dx_c); the mass row is zero.
+template <class S>
+__host__ __device__ inline void viscous_flux3(const S uvw[3], const S g[12], const Phys& ph, S fv[12]) {
+  const S div3 = (g[0] + g[5] + g[10]) * (2.0 / 3.0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    S tau[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) tau[i] = ph.mu * (g[c * 4 + i] + g[i * 4 + c]);
+    tau[c] = tau[c] - ph.mu * div3;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) fv[c * 4 + i] = tau[i];
+    fv[c * 4 + 3] = uvw[0] * tau[0] + uvw[1] * tau[1] + uvw[2] * tau[2] + ph.kT * g[c * 4 + 3];
+  }
 }
 
 }  // namespace pmg

@@ -71,7 +71,7 @@ struct LevelGeomHost {
   std::vector<double> met;   // 5 planes of E*N: a, b, c, d, 1/|J|
   std::vector<double> xy;    // (E, N, 2)
   std::vector<double> face;  // (E, 4, n1, 3): unit outward normal, area factor
-  std::vector<double> fJinv; // (E, 4, n1): 1/|J| at the face points
+  std::vector<double> fJinv; // (E, 4, n1) or (E, 6, NF): 1/|J| at the face points
 };
 
 Ref1D make_ref1d(int P);
@@ -121,10 +121,12 @@ struct LevelDev {
   double* met = nullptr;       // 5 * E * N (2D), 10 * E * N (3D)
   double* face = nullptr;      // E * 4 * n1 * 3 (2D), E * 6 * NF * 4 (3D)
   double* Fcom = nullptr;      // nv * E * faces * NF common fluxes, outward
-  // viscous terms (mu > 0 only)
-  double* Gb = nullptr;        // 6 * E * N broken gradients of (u, v, T): x planes, then y
-  double* Qj = nullptr;        // 3 * E * 4 * n1: q_com - q_own of (u, v, T) at each element face point
-  double* fJinv = nullptr;     // E * 4 * n1: 1/|J| at the face points
+  // viscous terms (mu > 0 only); hexahedra in brackets
+  double* Gb = nullptr;        // 6 [12] * E * N broken gradients of (u, v, T) [(u, v, w, T)]:
+                               // x planes, then y [, then z]
+  double* Qj = nullptr;        // 3 * E * 4 * n1 [4 * E * 6 * NF]: q_com - q_own of the same
+                               // variables at each element face point
+  double* fJinv = nullptr;     // E * 4 * n1 [E * 6 * NF]: 1/|J| at the face points
   double* Dfull = nullptr;     // E * n * n assembled FP64 blocks (row-major)
   void* Dinv = nullptr;        // E * n * n factored inverse (column-major), FP32 or FP64
   double* rs = nullptr;        // E * n row scales
@@ -308,6 +310,11 @@ void launch_volume_apply3(const Ctx& c, const LevelDev& L, double* q, double inv
 int residual_blocks_for3(int P, int E);
 void launch_assemble3(const Ctx& c, const LevelDev& L, const double* q, const double* d_dtau, double inv_odt,
                       cudaStream_t s);
+// viscous terms on hexahedra: broken gradients (Gb, 12 planes) and the
+// viscous part of the element blocks (k3_viscous.cu)
+void launch_grad3(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s);
+void launch_assemble_visc3(const Ctx& c, const LevelDev& L, const double* q, cudaStream_t s);
+cudaError_t prepare_assemble_visc3();
 void launch_apply3(const Ctx& c, const LevelDev& L, int prec, const double* r, double* x, int accumulate,
                    cudaStream_t s);
 cudaError_t prepare_kernels3(const Ctx& c);
