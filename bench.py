@@ -34,6 +34,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -695,6 +696,92 @@ def run_cylinder_study(args):
                               "steps": steps}), flush=True)
     return 0
 
+def run_ellipse_study(args):
+    """The extruded-ellipse workload (chord 1, thickness 0.1, incidence 8
+    degrees, O-mesh 48 radial x 64 around x 20 spanwise hexahedra over a span
+    of 0.2, periodic in z, far field at 20 chords; P{3-2-1-0}, I{5-10-20-40},
+    Re = 60000, Ma = 0.1 and 0.01, no-slip wall, gauge storage), FP32 and
+    FP64 blocks: the time of a residual, of the smoother's rebuild (assembly
+    and factorisation of every level's blocks) and of a V-cycle, and the
+    first ESDIRK3 step (dt = 0.001) from the free stream with 1e-3 noise in v
+    by Newton-Krylov stages with one V-cycle as the preconditioner (dtau_pc
+    1e-3, blocks rebuilt every second Newton step; at dt = 0.01 the
+    preconditioner's V-cycle returns non-finite directions in the first
+    stage).  One JSON line per (Ma, blocks); the step with FP32 blocks only."""
+    import torch
+    from paper_1908_03972_gb300 import build, pmgfr, workloads as W
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    build.build()
+    pmgfr.load()
+    nr, nt, nz = (48, 64, 20) if not args.study_small else (12, 16, 5)
+    nodes, nbr = W.extruded_ellipse(nr, nt, nz, span=0.2, Ng=2)
+    alpha = math.radians(8.0)
+    stream = torch.cuda.current_stream()
+    for MA in (0.1, 0.01):
+        T = W.freestream_T(MA, speed=1.0)
+        qinf = (T, math.cos(alpha), math.sin(alpha), 0.0, T)
+        for prec, name in ((pmgfr.PMG_PREC_FP32, "fp32"), (pmgfr.PMG_PREC_FP64, "fp64")):
+            rec = {"study": "ellipse", "mesh": f"{nr}x{nt}x{nz}", "elements": nr * nt * nz, "Ma": MA,
+                   "Re": 60000, "blocks": name, "levels": "P{3-2-1-0}, I{5-10-20-40}"}
+            s = pmgfr.Solver(nodes, nbr, [3, 2, 1, 0], [5, 10, 20, 40], stream=stream.cuda_stream, block_prec=prec,
+                             dim=3, Ma_inf=MA, mu=1.0 / 60000.0, cutoff=1, kappa=1.0, q_inf3=qinf, p_gauge=T,
+                             res_scale3=W.freestream_scales3(MA, speed=1.0), tol=1e-8, dtau_max=1.0)
+            try:
+                xyz = s.coords()
+                E, N = xyz.shape[0], xyz.shape[1]
+                q = W.uniform_state3(E, N, T, qinf[1], qinf[2], 0.0, T)
+                q[2] += 1e-3 * np.random.default_rng(7).standard_normal((E, N))
+                s.set_state(q)
+
+                def timed(fn, reps):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    for _ in range(reps):
+                        fn()
+                    torch.cuda.synchronize()
+                    return (time.perf_counter() - t0) / reps
+
+                dev = torch.device("cuda", torch.cuda.current_device())
+                q_dev = torch.from_numpy(np.ascontiguousarray(q)).to(dev)
+                r_dev = torch.empty_like(q_dev)
+                rec["residual_s"] = timed(lambda: pmgfr.pmg_residual(s.h, 0, q_dev, r_dev), 3)
+                del q_dev, r_dev
+                # a stage system of the size of an implicit stage with omega dt = 0.005
+                rho = q[0] / q[4]
+                qc = np.stack([rho, rho * q[1], rho * q[2], rho * q[3],
+                               rho * (q[4] / 0.4 + 0.5 * (q[1] ** 2 + q[2] ** 2 + q[3] ** 2))])
+                odt = 0.005
+                s.set_stage(qc / odt, odt)
+                rec["vcycle_rebuild_s"] = timed(lambda: pmgfr.pmg_vcycle(s.h, 1e-3, True), 2)
+                rec["vcycle_s"] = timed(lambda: pmgfr.pmg_vcycle(s.h, 1e-3, False), 5)
+                rec["rebuild_s"] = rec["vcycle_rebuild_s"] - rec["vcycle_s"]
+                if name == "fp64":   # FP64 blocks: timings only
+                    raise StopIteration
+                pmgfr.pmg_set_stage_solver(s.h, pmgfr.PMG_STAGE_NK, precond=pmgfr.PMG_NK_PC_VCYCLE, krylov_dim=30,
+                                           max_krylov=40, dtau_pc=1e-3, max_newton=10, pc_refresh=2,
+                                           state_scale=(T, 1.0, 1.0, 1.0, T))
+                s.set_state(q)
+                pmgfr.pmg_nk_stats_read(s.h, reset=True)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                status, st = pmgfr.pmg_esdirk_step(s.h, 0.001, raise_on_error=False)
+                torch.cuda.synchronize()
+                ks = pmgfr.pmg_nk_stats_read(s.h, reset=True)
+                rec["first_step"] = {"dt": 0.001, "seconds": time.perf_counter() - t0,
+                                     "status": "converged" if status == 0 else pmgfr.pmg_last_error(),
+                                     "newton": list(st.pseudo_iters[:3]), "drops": list(st.res_drop[:3]),
+                                     "vcycles": ks["vcycles"]}
+            except StopIteration:
+                pass
+            except Exception as exc:   # report what was measured before the failure
+                rec["error"] = str(exc)
+            finally:
+                s.close()
+            print(json.dumps(rec), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -716,14 +803,18 @@ def main():
                     help="block precision of the --ncu-window run")
     ap.add_argument("--ncu-solver", default="ptc", choices=["ptc", "nk"],
                     help="nk: the --ncu-window run is one Newton-Krylov solve of the stage instead of N V-cycles")
-    ap.add_argument("--study", default="", choices=["", "hierarchy", "cylinder"],
+    ap.add_argument("--study", default="", choices=["", "hierarchy", "cylinder", "ellipse"],
                     help="hierarchy: the P-hierarchy study on the reduced cylinder; cylinder: Newton-Krylov steps of "
-                         "the cylinder workload (JSON lines, no bench line)")
+                         "the cylinder workload; ellipse: the extruded-ellipse workload's residual, rebuild, "
+                         "V-cycle and first stage (JSON lines, no bench line)")
+    ap.add_argument("--study-small", action="store_true", help="the ellipse study on a 12 x 16 x 5 mesh")
     args = ap.parse_args()
     if args.study == "hierarchy":
         return run_hierarchy_study(args)
     if args.study == "cylinder":
         return run_cylinder_study(args)
+    if args.study == "ellipse":
+        return run_ellipse_study(args)
     world, rank, local = dist_setup()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":

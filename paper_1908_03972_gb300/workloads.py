@@ -161,6 +161,55 @@ def cylinder_omesh(n_r: int, n_theta: int, r_in: float = 0.5, r_out: float = 50.
     return nodes, nbr
 
 
+def ellipse_omesh(n_r: int, n_theta: int, chord: float = 1.0, thickness: float = 0.1, r_out: float = 20.0,
+                  Ng: int = 2, wall: int = BC_NOSLIP_WALL, outer: int = BC_FARFIELD):
+    """O-mesh around an ellipse of the given chord and thickness centred at
+    the origin, major axis along x, in elliptic coordinates x = c cosh(m)
+    cos(t), y = c sinh(m) sin(t) (c the focal distance): the ellipse is
+    m = m0 with tanh(m0) = thickness / chord, the outer boundary m1 with
+    c cosh(m1) = r_out.  Element e = j*n_r + i spans [m_i, m_i+1] x
+    [t_j, t_j+1] with m equispaced (radii growing geometrically away from the
+    body) and t equispaced (points clustered at the leading and trailing
+    edges); xi along m, eta along t.  Its Lagrange nodes sit at equispaced m
+    and t, so the wall nodes lie exactly on the ellipse.  Faces at m0 carry
+    ``wall``, faces at m1 ``outer``; the angular direction is periodic.
+    """
+    a, b = 0.5 * chord, 0.5 * thickness
+    m0 = math.atanh(b / a)
+    c = a / math.cosh(m0)
+    m1 = math.acosh(r_out / c)
+    mk = m0 + (m1 - m0) * np.arange(n_r + 1) / n_r
+    dth = 2 * math.pi / n_theta
+    t = np.linspace(0.0, 1.0, Ng + 1)
+    E = n_r * n_theta
+    nodes = np.zeros((E, (Ng + 1) ** 2, 2))
+    for j in range(n_theta):
+        for i in range(n_r):
+            e = j * n_r + i
+            A, B = np.meshgrid(t, t, indexing="xy")   # A along xi = m, B along eta = t
+            M = mk[i] + A * (mk[i + 1] - mk[i])
+            TH = (j + B) * dth
+            nodes[e, :, 0] = (c * np.cosh(M) * np.cos(TH)).reshape(-1)
+            nodes[e, :, 1] = (c * np.sinh(M) * np.sin(TH)).reshape(-1)
+    nbr = np.zeros((E, 4, 3), dtype=np.int32)
+    for j in range(n_theta):
+        for i in range(n_r):
+            e = j * n_r + i
+            nbr[e, 0] = (((j - 1) % n_theta) * n_r + i, 2, 0)
+            nbr[e, 1] = (j * n_r + i + 1, 3, 0) if i < n_r - 1 else (-1, outer, 0)
+            nbr[e, 2] = (((j + 1) % n_theta) * n_r + i, 0, 0)
+            nbr[e, 3] = (j * n_r + i - 1, 1, 0) if i > 0 else (-1, wall, 0)
+    return nodes, nbr
+
+
+def extruded_ellipse(n_r: int, n_theta: int, n_z: int, span: float = 0.2, Ng: int = 2, **kw):
+    """The ellipse O-mesh extruded along z over ``span`` with ``n_z`` layers,
+    periodic in z (the extruded-ellipse workload: 48 x 64 x 20 = 61,440
+    hexahedra at full size)."""
+    nodes2, nbr2 = ellipse_omesh(n_r, n_theta, Ng=Ng, **kw)
+    return extrude(nodes2, nbr2, Ng, nz=n_z, z0=0.0, z1=span)
+
+
 def flip_elements(nodes: np.ndarray, nbr: np.ndarray, which, Ng: int):
     """Rotate the local numbering of the listed elements by 180 degrees.
 

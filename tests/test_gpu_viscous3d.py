@@ -244,3 +244,46 @@ def test_viscous_stage_solve3_parity():
         assert np.abs(qg[0] - qo[0]).max() / 2.0 <= 1e-7 and np.abs(qg[1:4] - qo[1:4]).max() <= 1e-7
     finally:
         gpu.close()
+
+
+# ---------------------------------------------------------------- the extruded ellipse
+def _ellipse_state(xyz, T, qinf, seed=7):
+    E, N, _ = xyz.shape
+    q = W.uniform_state3(E, N, T, qinf[1], qinf[2], 0.0, T)
+    q[2] += 1e-3 * np.random.default_rng(seed).standard_normal((E, N))
+    return q
+
+
+def test_extruded_ellipse_reduced_parity():
+    """The extruded-ellipse workload at 6 x 16 x 2 elements (Q2, no-slip wall,
+    far field, periodic span; 8 degrees incidence, Ma = 0.1, gauge storage)
+    from the free stream with noise: the P = 3 residual, and P{2-1-0}
+    V-cycles (the smoother built, then frozen) with FP64 blocks."""
+    import math
+    nodes, nbr = W.extruded_ellipse(6, 16, 2, span=0.2, Ng=2)
+    Ma = 0.1
+    T = W.freestream_T(Ma, speed=1.0)
+    a = math.radians(8.0)
+    qinf = (T, math.cos(a), math.sin(a), 0.0, T)
+    kw = dict(q_inf=qinf, **WALL)
+    orc, gpu = _pair(nodes, nbr, 2, [3], [1], Ma=Ma, p_gauge=T, **kw)
+    try:
+        q = _ellipse_state(orc.coords(), T, qinf)
+        Ro, Rg = orc.residual(q), gpu.residual(q)
+        assert _rel(Rg, Ro, _scale(orc, 0, Ma, speed=1.0)) <= 1e-10
+    finally:
+        gpu.close()
+    orc, gpu = _pair(nodes, nbr, 2, [2, 1, 0], [2, 3, 4], Ma=Ma, p_gauge=T, **kw)
+    try:
+        q = _ellipse_state(orc.coords(), T, qinf)
+        _stage(orc, gpu, q, dt=0.01)
+        qo = orc.vcycle(q, 1e-3, refresh=True)
+        qg, _ = gpu.vcycle(q, 1e-3, refresh=True)
+        dq = np.abs(qo - q).max(axis=(1, 2))
+        assert (np.abs(qg - qo).max(axis=(1, 2)) / dq).max() <= 1e-8
+        qo2 = orc.vcycle(qo, 1e-2, refresh=False)
+        qg2, _ = gpu.vcycle(qo, 1e-2, refresh=False)
+        dq2 = np.abs(qo2 - qo).max(axis=(1, 2))
+        assert (np.abs(qg2 - qo2).max(axis=(1, 2)) / dq2).max() <= 1e-8
+    finally:
+        gpu.close()
