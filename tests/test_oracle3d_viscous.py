@@ -169,3 +169,42 @@ def test_viscous_blocks_match_central_differences():
             Rm = orc.stage_F(q - dq)[:, e].reshape(-1)
             fd = -(Rp - Rm) / (2 * dq[v, e, p])
             assert np.abs(D[e][:, col] - fd).max() <= 1e-6 * np.abs(D[e][:, col]).max(), (e, col)
+
+
+def test_extruded_ellipse_mesh():
+    """The extruded-ellipse mesh: wall nodes on the ellipse (chord 1,
+    thickness 0.1), far-field nodes on the confocal ellipse through x = 20,
+    positive Jacobians at every solution point, symmetric connectivity
+    (periodic in z and around), and a P = 2 free stream kept steady by the
+    oracle's conservative-curl metrics (P >= geometry order)."""
+    nr, nt, nz = 4, 12, 3
+    nodes, nbr = W.extruded_ellipse(nr, nt, nz, span=0.2, Ng=2)
+    assert nodes.shape == (nr * nt * nz, 27, 3)
+    n1 = 3
+    for e in range(nodes.shape[0]):
+        for f in range(6):
+            en, fn, o = nbr[e, f]
+            if en < 0:
+                assert (f, fn) in ((0, 3), (1, 4)), (e, f, fn)
+                pts = nodes[e].reshape(n1, n1, n1, 3)[:, :, 0 if f == 0 else -1, :2].reshape(-1, 2)
+                if f == 0:
+                    assert np.abs((pts[:, 0] / 0.5) ** 2 + (pts[:, 1] / 0.05) ** 2 - 1).max() < 1e-12
+                else:
+                    c = 0.5 / math.cosh(math.atanh(0.1))
+                    m = np.arccosh(np.full(len(pts), 20.0 / c))
+                    assert np.abs((pts[:, 0] / (c * np.cosh(m))) ** 2 + (pts[:, 1] / (c * np.sinh(m))) ** 2 - 1).max() < 1e-12
+            else:
+                assert tuple(nbr[en, fn][:2]) == (e, f)
+    T = W.freestream_T(0.1, speed=1.0)
+    a = math.radians(8.0)
+    qinf = (T, math.cos(a), math.sin(a), 0.0, T)
+    orc = O.Oracle3(nodes, nbr, 2, [2], [1], Ma_inf=0.1, mu=1.0 / 60000.0, cutoff=1, kappa=1.0, q_inf=qinf)
+    _, J, _, xyz = orc.geometry()
+    assert (J > 0).all()
+    assert np.abs(xyz[..., 2]).max() <= 0.2 + 1e-12
+    # a uniform state with zero velocity at rest is steady everywhere (walls included)
+    q = W.uniform_state3(orc.E, xyz.shape[1], T, 0.0, 0.0, 0.0, T)
+    orc2 = O.Oracle3(nodes, nbr, 2, [2], [1], Ma_inf=0.1, mu=1.0 / 60000.0, cutoff=1, kappa=1.0,
+                     q_inf=(T, 0.0, 0.0, 0.0, T))
+    R = orc2.residual(q)
+    assert np.abs(R).max() <= 1e-9 * T
