@@ -714,10 +714,34 @@ def run_ellipse_study(args):
         raise SystemExit("bench.py needs a CUDA GPU")
     build.build()
     pmgfr.load()
-    nr, nt, nz = (48, 64, 20) if not args.study_small else (12, 16, 5)
+    nr, nt, nz = {"full": (48, 64, 20), "half": (24, 32, 10), "small": (12, 16, 5)}[args.study_mesh]
     nodes, nbr = W.extruded_ellipse(nr, nt, nz, span=0.2, Ng=2)
     alpha = math.radians(8.0)
     stream = torch.cuda.current_stream()
+    if args.ncu_window > 0:   # profiling helper: one V-cycle with rebuild, then N without (Ma = 0.1, FP32)
+        MA = 0.1
+        T = W.freestream_T(MA, speed=1.0)
+        qinf = (T, math.cos(alpha), math.sin(alpha), 0.0, T)
+        s = pmgfr.Solver(nodes, nbr, [3, 2, 1, 0], [5, 10, 20, 40], stream=stream.cuda_stream,
+                         block_prec=pmgfr.PMG_PREC_FP32, dim=3, Ma_inf=MA, mu=1.0 / 60000.0, cutoff=1, kappa=1.0,
+                         q_inf3=qinf, p_gauge=T, res_scale3=W.freestream_scales3(MA, speed=1.0))
+        try:
+            xyz = s.coords()
+            q = W.uniform_state3(xyz.shape[0], xyz.shape[1], T, qinf[1], qinf[2], 0.0, T)
+            q[2] += 1e-3 * np.random.default_rng(7).standard_normal(q.shape[1:])
+            rho = q[0] / q[4]
+            qc = np.stack([rho, rho * q[1], rho * q[2], rho * q[3],
+                           rho * (q[4] / 0.4 + 0.5 * (q[1] ** 2 + q[2] ** 2 + q[3] ** 2))])
+            s.set_stage(qc / 0.005, 0.005)
+            s.set_state(q)
+            norms = [pmgfr.pmg_vcycle(s.h, 1e-3, True)]
+            norms += [pmgfr.pmg_vcycle(s.h, 1e-3, False) for _ in range(args.ncu_window)]
+            torch.cuda.synchronize()
+            print(json.dumps({"ncu_window_vcycles": args.ncu_window + 1, "workload": "extruded ellipse",
+                              "first_norm": norms[0], "last_norm": norms[-1]}))
+        finally:
+            s.close()
+        return 0
     for MA in (0.1, 0.01):
         T = W.freestream_T(MA, speed=1.0)
         qinf = (T, math.cos(alpha), math.sin(alpha), 0.0, T)
@@ -807,7 +831,8 @@ def main():
                     help="hierarchy: the P-hierarchy study on the reduced cylinder; cylinder: Newton-Krylov steps of "
                          "the cylinder workload; ellipse: the extruded-ellipse workload's residual, rebuild, "
                          "V-cycle and first stage (JSON lines, no bench line)")
-    ap.add_argument("--study-small", action="store_true", help="the ellipse study on a 12 x 16 x 5 mesh")
+    ap.add_argument("--study-mesh", default="full", choices=["full", "half", "small"],
+                    help="the ellipse study's mesh: 48 x 64 x 20, 24 x 32 x 10 or 12 x 16 x 5 elements")
     args = ap.parse_args()
     if args.study == "hierarchy":
         return run_hierarchy_study(args)
