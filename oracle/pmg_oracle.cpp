@@ -5,8 +5,9 @@
 // (constant mu, Section 2.1) Navier-Stokes equations with Weiss-Smith/Turkel
 // local preconditioning.  Viscous terms follow Section 2.3: q_com of eq.
 // com_q, common gradient of eq. com_grad_q with BR2 liftings.  The paper does
-// not state the BR2 penalty; eta_f = 4 (faces per element) is the reading
-// taken, and its value is parity unpinned (every pin holds for any eta_f > 0).
+// not state the BR2 penalty; eta_f = 4 (the faces of a quadrilateral) is the
+// reading taken, for hexahedra too, and its value is parity unpinned (every
+// pin holds for any eta_f > 0).
 // Boundary faces (slip wall, no-slip adiabatic wall, far field) use ghost
 // states through the same common fluxes; the paper states none (reading).  It exists only to
 // check the CUDA library: tests, the smoke check and the CPU-baseline leg of
