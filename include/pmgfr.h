@@ -3,7 +3,7 @@
  * reconstruction library (libpmgfr.so).
  *
  * The library solves the compressible Euler and Navier-Stokes equations (2D
- * quadrilaterals; inviscid hexahedra with pmg_config.dim = 3) with
+ * quadrilaterals; hexahedra with pmg_config.dim = 3) with
  * Weiss-Smith/Turkel local preconditioning, discretised by FR/CPR
  * (Gauss-Legendre solution points, DG/Radau correction functions) and advanced
  * by ESDIRK2, 3 or 4 with dual time stepping.  Each implicit stage is solved by
