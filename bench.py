@@ -745,7 +745,8 @@ def run_ellipse_study(args):
     for MA in (0.1, 0.01):
         T = W.freestream_T(MA, speed=1.0)
         qinf = (T, math.cos(alpha), math.sin(alpha), 0.0, T)
-        for prec, name in ((pmgfr.PMG_PREC_FP32, "fp32"), (pmgfr.PMG_PREC_FP64, "fp64")):
+        precs = ((pmgfr.PMG_PREC_FP32, "fp32"), (pmgfr.PMG_PREC_FP64, "fp64"))
+        for prec, name in precs[:1] if args.study_fp32_only else precs:
             rec = {"study": "ellipse", "mesh": f"{nr}x{nt}x{nz}", "elements": nr * nt * nz, "Ma": MA,
                    "Re": 60000, "blocks": name, "levels": "P{3-2-1-0}, I{5-10-20-40}"}
             s = pmgfr.Solver(nodes, nbr, [3, 2, 1, 0], [5, 10, 20, 40], stream=stream.cuda_stream, block_prec=prec,
@@ -783,7 +784,8 @@ def run_ellipse_study(args):
                 if name == "fp64":   # FP64 blocks: timings only
                     raise StopIteration
                 pmgfr.pmg_set_stage_solver(s.h, pmgfr.PMG_STAGE_NK, precond=pmgfr.PMG_NK_PC_VCYCLE, krylov_dim=30,
-                                           max_krylov=40, dtau_pc=1e-3, max_newton=10, pc_refresh=2,
+                                           max_krylov=40, dtau_pc=1e-3, max_newton=10,
+                                           pc_refresh=args.nk_pc_refresh,
                                            state_scale=(T, 1.0, 1.0, 1.0, T))
                 s.set_state(q)
                 pmgfr.pmg_nk_stats_read(s.h, reset=True)
@@ -792,7 +794,8 @@ def run_ellipse_study(args):
                 status, st = pmgfr.pmg_esdirk_step(s.h, 0.001, raise_on_error=False)
                 torch.cuda.synchronize()
                 ks = pmgfr.pmg_nk_stats_read(s.h, reset=True)
-                rec["first_step"] = {"dt": 0.001, "seconds": time.perf_counter() - t0,
+                rec["first_step"] = {"dt": 0.001, "pc_refresh": args.nk_pc_refresh,
+                                     "seconds": time.perf_counter() - t0,
                                      "status": "converged" if status == 0 else pmgfr.pmg_last_error(),
                                      "newton": list(st.pseudo_iters[:3]), "drops": list(st.res_drop[:3]),
                                      "vcycles": ks["vcycles"]}
@@ -831,6 +834,9 @@ def main():
                     help="hierarchy: the P-hierarchy study on the reduced cylinder; cylinder: Newton-Krylov steps of "
                          "the cylinder workload; ellipse: the extruded-ellipse workload's residual, rebuild, "
                          "V-cycle and first stage (JSON lines, no bench line)")
+    ap.add_argument("--study-fp32-only", action="store_true", help="the ellipse study without its FP64 legs")
+    ap.add_argument("--nk-pc-refresh", type=int, default=2,
+                    help="the ellipse study's step: rebuild the preconditioner's blocks every N Newton steps")
     ap.add_argument("--study-mesh", default="full", choices=["full", "half", "small"],
                     help="the ellipse study's mesh: 48 x 64 x 20, 24 x 32 x 10 or 12 x 16 x 5 elements")
     args = ap.parse_args()
