@@ -235,12 +235,28 @@ __global__ void __launch_bounds__(256) factor_kernel(int n, const double* __rest
     for (int j = tid; j < n; j += nt) A[k * n + j] = (j == k) ? ipiv : A[k * n + j] * ipiv;
     for (int i = tid; i < n; i += nt) colk[i] = A[i * n + k];
     __syncthreads();
-    for (int t = tid; t < n * n; t += nt) {
-      int i = t / n, j = t - i * n;
-      if (i == k) continue;
-      T f = colk[i];
-      if (j == k) A[t] = -f * A[k * n + k];
-      else A[t] -= f * A[k * n + j];
+    if (sizeof(T) == 4 && n <= nt) {
+      // FP32 elimination (issue-bound): thread (r0, j) updates column j in
+      // rows r0, r0 + rpp, ... with the pivot row's entry in a register and
+      // no index division; the same operation on every entry as below
+      const int rpp = nt / n, j = tid % n, r0 = tid / n;
+      if (r0 < rpp) {
+        const T akj = A[k * n + j];
+        for (int i = r0; i < n; i += rpp) {
+          if (i == k) continue;
+          const T f = colk[i];
+          if (j == k) A[i * n + j] = -f * akj;
+          else A[i * n + j] -= f * akj;
+        }
+      }
+    } else {
+      for (int t = tid; t < n * n; t += nt) {
+        int i = t / n, j = t - i * n;
+        if (i == k) continue;
+        T f = colk[i];
+        if (j == k) A[t] = -f * A[k * n + k];
+        else A[t] -= f * A[k * n + j];
+      }
     }
     __syncthreads();
   }
